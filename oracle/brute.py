@@ -1,0 +1,70 @@
+"""Brute-force per-point evaluator -- TEST INFRASTRUCTURE ONLY.
+
+An independent restatement of the four operators of Listings 1-4 (arXiv 1510.04995, Sect. 2.2)
+as a table of terms.  Each term is (coefficient source, list of neighbour offsets (dx, dy, dz));
+a point's update is the running sum, in table order, of coefficient * (sum of the neighbours in
+list order).  Every level is recomputed point by point over the whole interior in pure Python,
+so it is only meant for tiny grids (8^3, T <= 3), where it must agree bit for bit with the C loop
+nests (same terms, same order, one rounding per operation).
+"""
+from __future__ import annotations
+
+import numpy as np
+
+
+def _axis(r):
+    return [(r, 0, 0), (-r, 0, 0)], [(0, r, 0), (0, -r, 0)], [(0, 0, r), (0, 0, -r)]
+
+
+def term_table(stencil: int):
+    """List of (("c", index) | ("C", grid), offsets).  'c' = constant coefficient, 'C' = grid."""
+    if stencil == 0:
+        x, y, z = _axis(1)
+        return [(("c", 0), [(0, 0, 0)]), (("c", 1), x), (("c", 1), y), (("c", 1), z)]
+    if stencil == 1:
+        return [(("C", 0), [(0, 0, 0)]), (("C", 1), [(1, 0, 0)]), (("C", 2), [(-1, 0, 0)]),
+                (("C", 3), [(0, 1, 0)]), (("C", 4), [(0, -1, 0)]), (("C", 5), [(0, 0, 1)]),
+                (("C", 6), [(0, 0, -1)])]
+    if stencil == 2:
+        tab = [(("c", 0), [(0, 0, 0)])]
+        for r in range(1, 5):
+            x, y, z = _axis(r)
+            tab.append((("c", r), x + y + z))
+        return tab
+    tab = [(("C", 0), [(0, 0, 0)])]
+    g = 1
+    for r in range(1, 5):
+        for pair in _axis(r):
+            tab.append((("C", g), pair))
+            g += 1
+    return tab
+
+
+def sweep(stencil: int, u, u_prev, coeffs, c, T: int, R: int):
+    """Return (level T, level T-1) as new arrays; inputs are padded [nz+2R][ny+2R][nx+2R]."""
+    a = [u.copy(), u_prev.copy()]
+    nz, ny, nx = (s - 2 * R for s in u.shape)
+    second = stencil in (2, 3)
+    tab = term_table(stencil)
+    for t in range(T):
+        V, U = a[t % 2], a[(t + 1) % 2]
+        new = U.copy()
+        for k in range(R, R + nz):
+            for j in range(R, R + ny):
+                for i in range(R, R + nx):
+                    acc = None
+                    for (kind, q), offs in tab:
+                        s = None
+                        for dx, dy, dz in offs:
+                            v = float(V[k + dz, j + dy, i + dx])
+                            s = v if s is None else s + v
+                        w = float(c[q]) if kind == "c" else float(coeffs[q, k, j, i])
+                        term = w * s
+                        acc = term if acc is None else acc + term
+                    if second:
+                        acc = (2.0 * float(V[k, j, i]) - float(U[k, j, i])) + acc
+                    new[k, j, i] = acc
+        a[(t + 1) % 2] = new
+    if T % 2 == 1:
+        a = [a[1], a[0]]
+    return a[0], a[1]
