@@ -1,0 +1,219 @@
+/*
+ * girih.h -- C ABI of the GB300 (sm_103a) temporally blocked stencil sweep library.
+ *
+ * The library advances a 3D grid by T time steps of one of four Jacobi-style stencils
+ * (Malas, Hager, Ltaief, Keyes, "Multi-dimensional intra-tile parallelization for
+ * memory-starved stencil computations", arXiv 1510.04995):
+ *   GIRIH_7PT_CONST  Listing 1: first order in time, radius 1, constants c0, c1.
+ *   GIRIH_7PT_VAR    Listing 2: first order in time, radius 1, 7 coefficient grids.
+ *   GIRIH_25PT_CONST Listing 3 with the per-point factor fixed to 1: second order in time
+ *                    (U = 2V - U + ...), radius 4, constants c0..c4.
+ *   GIRIH_25PT_VAR   Listing 4's 13 axis-symmetric coefficient grids, second order in time.
+ * Two algorithms reach the same result (Sect. 2.1): the naive sweep (one pass over the grid per
+ * time step, Sect. 2.1.1) and the multi-threaded wavefront-diamond sweep (MWD, Sect. 4.2.1):
+ * diamond tiles along y (Sect. 2.1.2), a wavefront along z, several time steps per pass over
+ * memory, one tile shared by a cluster of thread blocks (the paper's thread group, Sect. 4.1).
+ *
+ * Conventions for every function:
+ *  - Return value: GIRIH_OK (0) or one of the GIRIH_E* codes below.  On failure a message is
+ *    available from girih_last_error() (thread-local, valid until the next call on that thread).
+ *  - Device pointers are raw CUDA device addresses owned by the caller; the library never frees
+ *    them.  Streams are cudaStream_t passed as void* (NULL = legacy default stream).
+ *  - Grid layout ("padded layout"): element (i, j, k) with 0 <= i < ldx, 0 <= j < ny+2R,
+ *    0 <= k < nz+2R lives at offset (k*(ny+2R) + j)*ldx + i, x fastest.  The interior is
+ *    i in [R, R+nx), j in [R, R+ny), k in [R, R+nz); the R-wide halo is read, never written
+ *    (the listings' loops start at R and stop R before the end).  ldx >= nx + 2R is the leading
+ *    dimension (Sect. 4.2.3 pads the leading dimension); 0 means dense (nx + 2R).
+ */
+#ifndef GIRIH_H
+#define GIRIH_H
+
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define GIRIH_API __attribute__((visibility("default")))
+#else
+#define GIRIH_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- enums and status codes -------------------------------------------------------------- */
+typedef enum { GIRIH_7PT_CONST = 0, GIRIH_7PT_VAR = 1, GIRIH_25PT_CONST = 2, GIRIH_25PT_VAR = 3 } girih_stencil;
+typedef enum { GIRIH_F64 = 0, GIRIH_F32 = 1 } girih_dtype;
+typedef enum { GIRIH_ALGO_NAIVE = 0, GIRIH_ALGO_MWD = 1 } girih_algo;
+/* Wavefront synchronisation variants of Sect. 4.2.1:
+ *   FED     -- fixed execution to data: each thread block of the cluster always updates the
+ *              same x slab of the tile; one cluster-wide barrier per wavefront step.
+ *   RELAXED -- each time level of the tile only waits for its own predecessor level
+ *              (left-neighbour hand-off), through per-level progress counters.            */
+typedef enum { GIRIH_FED = 0, GIRIH_RELAXED = 1 } girih_variant;
+
+#define GIRIH_OK 0
+#define GIRIH_EINVAL 1   /* bad enum, size, T, pointer, alignment, or config: nothing enqueued */
+#define GIRIH_ENOMEM 2   /* a host or device allocation failed                                 */
+#define GIRIH_ECUDA 3    /* a CUDA call failed (message has the CUDA error string)             */
+#define GIRIH_EKERNEL 4  /* a kernel's own consistency check fired                             */
+#define GIRIH_ETIMEOUT 5 /* a bounded device-side wait ran out                                 */
+#define GIRIH_ENOTIMPL 6 /* the combination is not available                                   */
+
+/* Tunable parameters of the blocked sweep (Sect. 4.2.2 tunes diamond width, wavefront width
+ * and the thread-group shape).  Fields:
+ *   algo     GIRIH_ALGO_NAIVE or GIRIH_ALGO_MWD.
+ *   dw       diamond width D_w along y (a multiple of 2R, >= 2R); MWD only.
+ *   nf       wavefront tile width N_F: z planes each time level advances per step (1..4).
+ *   cluster  thread blocks sharing one tile along x (1, 2, 4, 8 or 16).
+ *   threads  threads per block (multiple of 32, 64..1024).
+ *   variant  girih_variant.                                                              */
+typedef struct girih_config {
+  int32_t algo;
+  int32_t dw;
+  int32_t nf;
+  int32_t cluster;
+  int32_t threads;
+  int32_t variant;
+} girih_config;
+
+/* Per-call parameters.  c[] holds the constant coefficients: 7PT_CONST uses c[0]=c0 (centre),
+ * c[1]=c1 (the six neighbours); 25PT_CONST uses c[0] (centre) and c[r] for the six neighbours at
+ * distance r = 1..4.  Ignored by the variable-coefficient stencils.  If force_cfg is non-zero,
+ * cfg replaces the plan's configuration for this call.                                     */
+typedef struct girih_params {
+  double c[5];
+  int32_t force_cfg;
+  girih_config cfg;
+} girih_params;
+
+typedef struct girih_plan_s* girih_plan_t;
+
+/* ---- plan / run ---------------------------------------------------------------------------- */
+
+/* Create a plan for T steps of `stencil` on an nx*ny*nz interior (halo R implied: 1 for the
+ * 7-point, 4 for the 25-point stencils) in `dtype`, leading dimension ldx (0 = dense).
+ * Queries the current device and picks a default configuration (largest feasible diamond).
+ * Writes *out = NULL on failure.  EINVAL: bad enum, nx/ny/nz < 1, T < 0, ldx < nx + 2R.    */
+GIRIH_API int girih_plan(girih_plan_t* out, int32_t stencil, int64_t nx, int64_t ny, int64_t nz, int64_t ldx,
+               int32_t dtype, int64_t T);
+
+/* Release a plan (NULL is accepted). */
+GIRIH_API int girih_plan_destroy(girih_plan_t plan);
+
+/* Read or replace the plan's configuration.  girih_plan_set_config returns EINVAL (and leaves
+ * the plan unchanged) if the configuration is not feasible on this device for this problem.  */
+GIRIH_API int girih_plan_get_config(girih_plan_t plan, girih_config* cfg);
+GIRIH_API int girih_plan_set_config(girih_plan_t plan, const girih_config* cfg);
+
+/* Feasibility of a configuration for the plan's problem on the current device: GIRIH_OK or
+ * EINVAL.  If smem_bytes is not NULL it receives the shared memory one block needs.            */
+GIRIH_API int girih_config_check(girih_plan_t plan, const girih_config* cfg, int64_t* smem_bytes);
+
+/* Advance the grids by the plan's T steps, asynchronously on `stream`.
+ *   u       device buffer with level 0 (u^0); on return level T.
+ *   u_prev  device buffer: for the second-order stencils level -1 on entry and level T-1 on
+ *           return; for the first-order stencils scratch whose halo must equal u's halo (on
+ *           return it holds level T-1, or is unchanged when T = 0).
+ *   coeffs  NULL for the constant stencils; else 7 (7PT_VAR: C0 centre, C1 x+1, C2 x-1, C3 y+1,
+ *           C4 y-1, C5 z+1, C6 z-1; Listing 2) or 13 (25PT_VAR: C00 centre, then for r = 1..4
+ *           the x, y, z pairs at distance r; Listing 4) grids of the padded layout, back to
+ *           back; their halo cells are never read.
+ *   params  coefficients and optional forced configuration (NULL: 7PT_CONST/25PT_CONST use the
+ *           workload constants c0=0.4,c1=0.1 / c0=-0.9,c_r=0.1/2^r).
+ * Pointers must be 8-byte (F64) or 4-byte (F32) aligned and u != u_prev.  The two buffers'
+ * roles alternate every step (Listing 3's pointer swap); for odd T one in-place exchange kernel
+ * puts level T back into u.  EINVAL leaves the buffers untouched and enqueues nothing.       */
+GIRIH_API int girih_run(girih_plan_t plan, void* u, void* u_prev, const void* coeffs, const girih_params* params,
+              void* stream);
+
+/* Convenience for callers holding HOST arrays (pinned or pageable): copies u, u_prev and coeffs
+ * to device buffers the plan owns (allocated on first use, freed by girih_plan_destroy), runs
+ * girih_run on `stream`, copies u and u_prev back, and synchronises the stream.               */
+GIRIH_API int girih_run_host(girih_plan_t plan, void* u_host, void* u_prev_host, const void* coeffs_host,
+                   const girih_params* params, void* stream);
+
+/* Elements of one padded grid for the plan ((nz+2R)*(ny+2R)*ldx) and the halo width R. */
+GIRIH_API int girih_plan_layout(girih_plan_t plan, int64_t* elems_per_grid, int32_t* radius, int64_t* ldx);
+
+/* Number of kernel launches girih_run enqueues with the given configuration (NULL = plan's). */
+GIRIH_API int girih_plan_launch_count(girih_plan_t plan, const girih_config* cfg, int64_t* launches);
+
+GIRIH_API const char* girih_last_error(void);
+
+/* ---- models of Sect. 3.3 / 3.4 ------------------------------------------------------------- */
+
+/* Cache block size C_S in bytes of one wavefront-diamond tile (Eq. 3; for R = 1 this is the
+ * paper's Eq. 2 up to the paper's own approximation): n_xb = bytes of the tile's leading
+ * dimension, dw = diamond width, nf = wavefront width, r = radius, nd = domain-sized streams.  */
+GIRIH_API double girih_model_cache_block(double n_xb, int32_t dw, int32_t nf, int32_t r, int32_t nd);
+
+/* Code balance B_C in bytes per lattice-site update of the blocked sweep (Eq. 5; Eq. 4 for
+ * R = 1) for elements of `elem_bytes` bytes (8: the paper's 16R factor; 4: 8R).             */
+GIRIH_API double girih_model_code_balance(int32_t dw, int32_t r, int32_t nd, int32_t elem_bytes);
+
+/* ---- auto-tuner (Sect. 4.2.2) ---------------------------------------------------------------- */
+
+/* One timing row of the tuner's database. */
+typedef struct girih_tune_row {
+  girih_config cfg;
+  double glups;      /* giga lattice-site updates per second, at the accepted test length */
+  double seconds;    /* time of that accepted measurement                                  */
+  int64_t steps;     /* time steps of the accepted measurement                             */
+  int64_t smem;      /* shared memory per block                                            */
+} girih_tune_row;
+
+/* Enumerate the candidate configurations (naive sweep plus every MWD diamond width, wavefront
+ * width, cluster size and thread count) for the plan's problem; infeasible ones (shared memory
+ * above the device limit, per the cache-block model of Eq. 3, or an unschedulable cluster) are
+ * dropped.  Writes up to `cap` configurations and returns their number in *count.             */
+GIRIH_API int girih_tune_candidates(girih_plan_t plan, girih_config* out, int32_t cap, int32_t* count);
+
+/* Time one configuration the way Sect. 4.2.2 does: on tuner-owned device arrays, with a test
+ * length that grows in whole diamond rows until two consecutive measurements agree within
+ * `tol` (relative) or max_steps is reached.  Fills *row.                                       */
+GIRIH_API int girih_tune_measure(girih_plan_t plan, const girih_config* cfg, double tol, int64_t max_steps,
+                       girih_tune_row* row);
+
+/* Exhaustive tuning: measure every candidate, append one CSV line per candidate to db_path
+ * (NULL: no file), set the plan's configuration to the fastest and return it in *best.       */
+GIRIH_API int girih_tune_exhaustive(girih_plan_t plan, double tol, int64_t max_steps, const char* db_path,
+                          girih_tune_row* best, int32_t* n_measured);
+
+/* ---- learned tuner: 3-layer MLP (D -> 64 -> 64 -> 1, ReLU), FP32, CUDA kernels --------------- */
+
+/* Features of a configuration for the network (writes GIRIH_MLP_FEATURES floats). */
+#define GIRIH_MLP_FEATURES 16
+#define GIRIH_MLP_HIDDEN 64
+GIRIH_API int girih_mlp_features(int32_t stencil, int32_t dtype, int64_t nx, int64_t ny, int64_t nz,
+                       const girih_config* cfg, float* out);
+
+/* Number of parameters for input width d: 64d + 64 + 64*64 + 64 + 64 + 1, laid out as
+ * [W1 (64 x d row-major), b1, W2 (64 x 64), b2, W3 (1 x 64), b3].                            */
+GIRIH_API int64_t girih_mlp_num_params(int32_t d);
+
+/* Forward pass on device arrays: y[n] = net(X[n x d]).  workspace: device scratch of at least
+ * girih_mlp_workspace_floats(n) floats.                                                        */
+GIRIH_API int64_t girih_mlp_workspace_floats(int32_t n);
+GIRIH_API int girih_mlp_forward(const float* params, const float* X, int32_t n, int32_t d, float* y, float* workspace,
+                      void* stream);
+
+/* Gradient of the mean squared error (1/n) sum (y - t)^2 with respect to the parameters, on
+ * device: grad has girih_mlp_num_params(d) floats; loss (device, 1 float) may be NULL.         */
+GIRIH_API int girih_mlp_backward(const float* params, const float* X, const float* t, int32_t n, int32_t d, float* grad,
+                       float* loss, float* workspace, void* stream);
+
+/* Optimiser steps on device arrays of np floats. step counts from 1 (Adam bias correction).  */
+GIRIH_API int girih_mlp_sgd(float* params, const float* grad, int64_t np, float lr, void* stream);
+GIRIH_API int girih_mlp_adam(float* params, const float* grad, float* m, float* v, int64_t np, int64_t step, float lr,
+                   float beta1, float beta2, float eps, void* stream);
+
+/* Learned tuning: score all candidates of girih_tune_candidates with the network (device
+ * parameters `params`, trained on log GLUP/s), measure the best `k` with girih_tune_measure,
+ * set the plan's configuration to the fastest of those and return it in *best.              */
+GIRIH_API int girih_tune_learned(girih_plan_t plan, const float* params, int32_t k, double tol, int64_t max_steps,
+                       girih_tune_row* best, int32_t* n_measured);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GIRIH_H */

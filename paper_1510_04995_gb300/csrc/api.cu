@@ -1,0 +1,351 @@
+// C ABI of the stencil sweep library: plans, validation, the per-row launch loop of the
+// wavefront-diamond sweep, the naive loop, and the paper's cache-block / code-balance models.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+
+#include "internal.h"
+#include "plan.h"
+
+namespace girih {
+
+thread_local std::string g_err;
+
+void g_err_clear() { g_err.clear(); }
+
+int fail(int code, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  g_err = buf;
+  return code;
+}
+
+int cuda_fail(cudaError_t e, const char* where) {
+  return fail(GIRIH_ECUDA, "%s: %s (%s)", where, cudaGetErrorString(e), cudaGetErrorName(e));
+}
+
+static int64_t floor_div(int64_t a, int64_t b) { return a >= 0 ? a / b : -((-a + b - 1) / b); }
+
+// Diamond rows of the sweep: rows 0..rho_max have at least one step in [0, T).
+int64_t mwd_rows(int64_t T, int dw, int R) {
+  if (T <= 0) return 0;
+  const int64_t Hh = dw / R / 2;
+  int64_t rho = 0;
+  while ((rho + 1 - 1) * Hh + 1 <= T - 1) ++rho;  // next row's first step still below T
+  return rho + 1;
+}
+
+// Diamonds of row rho whose y projection [a*dw - rho*dw/2, +dw) meets [0, ny).
+void mwd_row_span(int64_t rho, int dw, int64_t ny, int64_t* a_min, int64_t* ndiam) {
+  const int64_t h = rho * (dw / 2);
+  const int64_t lo = floor_div(h, dw);
+  const int64_t hi = floor_div(ny + h + dw - 1, dw) - 1;  // ceil((ny + h)/dw) - 1
+  *a_min = lo;
+  *ndiam = std::max<int64_t>(hi - lo + 1, 0);
+}
+
+static int slab_width(int64_t nx, int C) {
+  int64_t w = (nx + C - 1) / C;
+  int64_t p = 32;
+  while (p < w) p *= 2;
+  return (int)p;
+}
+
+int check_config(const Plan* p, const girih_config* c, int64_t* smem_out, int* xw_out) {
+  if (!c) return fail(GIRIH_EINVAL, "config is NULL");
+  if (c->algo == GIRIH_ALGO_NAIVE) {
+    if (smem_out) *smem_out = 0;
+    return GIRIH_OK;
+  }
+  if (c->algo != GIRIH_ALGO_MWD) return fail(GIRIH_EINVAL, "unknown algo %d", c->algo);
+  if (c->variant != GIRIH_FED) return fail(GIRIH_ENOTIMPL, "only the FED wavefront variant is available");
+  const int R = p->R;
+  if (c->dw < 2 * R || c->dw % (2 * R) != 0)
+    return fail(GIRIH_EINVAL, "dw=%d must be a positive multiple of 2R=%d", c->dw, 2 * R);
+  if (c->nf < 1 || c->nf > 4) return fail(GIRIH_EINVAL, "nf=%d outside 1..4", c->nf);
+  if (!(c->cluster == 1 || c->cluster == 2 || c->cluster == 4 || c->cluster == 8 || c->cluster == 16))
+    return fail(GIRIH_EINVAL, "cluster=%d not in {1,2,4,8,16}", c->cluster);
+  if (c->threads < 64 || c->threads > 512 || c->threads % 32 != 0)
+    return fail(GIRIH_EINVAL, "threads=%d must be a multiple of 32 in 64..512", c->threads);
+  const int XW = slab_width(p->nx, c->cluster);
+  if (c->cluster > 1 && (int64_t)XW * (c->cluster - 1) >= p->nx)
+    return fail(GIRIH_EINVAL, "cluster=%d leaves an empty x slab for nx=%lld", c->cluster, (long long)p->nx);
+  if (p->ny > (1 << 28) || p->nx > (1 << 28) || p->nz > (1 << 28))
+    return fail(GIRIH_EINVAL, "grid too large for the blocked kernel");
+  const MwdShape sh = mwd_shape(p->stencil, p->dtype, c->dw, c->nf, XW);
+  if (sh.smem_bytes > p->smem_optin)
+    return fail(GIRIH_EINVAL, "config needs %lld bytes of shared memory per block (device limit %lld)",
+                (long long)sh.smem_bytes, (long long)p->smem_optin);
+  int maxc = 0;
+  cudaError_t e = mwd_prepare(p->stencil, p->dtype, c->cluster, c->threads, sh.smem_bytes, &maxc);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return fail(GIRIH_EINVAL, "cluster of %d blocks with %lld bytes cannot be configured: %s", c->cluster,
+                (long long)sh.smem_bytes, cudaGetErrorString(e));
+  }
+  if (maxc < 1) return fail(GIRIH_EINVAL, "cluster of %d blocks cannot be scheduled", c->cluster);
+  if (smem_out) *smem_out = sh.smem_bytes;
+  if (xw_out) *xw_out = XW;
+  return GIRIH_OK;
+}
+
+// Default configuration: the widest diamond whose tile fits (Sect. 4.2.2 prunes with the
+// cache-block model; here the block's shared memory is the cache), smallest cluster first.
+static girih_config default_config(Plan* p) {
+  girih_config best{GIRIH_ALGO_NAIVE, 0, 1, 1, 256, GIRIH_FED};
+  int best_dw = 0;
+  const int R = p->R;
+  for (int C : {1, 2, 4, 8, 16}) {
+    for (int dw = 2 * R; dw <= 64 * R; dw += 2 * R) {
+      girih_config c{GIRIH_ALGO_MWD, dw, 1, C, 256, GIRIH_FED};
+      int64_t smem = 0;
+      if (check_config(p, &c, &smem, nullptr) != GIRIH_OK) continue;
+      if (dw > best_dw && dw <= (R == 1 ? 16 : 32)) {
+        best_dw = dw;
+        best = c;
+      }
+    }
+  }
+  g_err.clear();
+  return best;
+}
+
+int run_sweep(Plan* p, int64_t T, void* u, void* u_prev, const void* coeffs, const double* c,
+              const girih_config& cfg, cudaStream_t st) {
+  Grid g{p->nx, p->ny, p->nz, p->ldx, p->ny + 2 * p->R, p->gstride};
+  cudaError_t e = cudaSuccess;
+  if (cfg.algo == GIRIH_ALGO_NAIVE) {
+    NaiveArgs a{};
+    a.g = g;
+    a.coef = coeffs;
+    for (int i = 0; i < 5; ++i) a.c[i] = c[i];
+    a.zc = 64;
+    void* buf[2] = {u, u_prev};
+    for (int64_t t = 0; t < T && e == cudaSuccess; ++t) {
+      a.V = buf[t % 2];
+      a.U = buf[(t + 1) % 2];
+      e = launch_naive_step(p->stencil, p->dtype, a, st);
+    }
+  } else {
+    int64_t smem = 0;
+    int XW = 0;
+    const int rc = check_config(p, &cfg, &smem, &XW);
+    if (rc != GIRIH_OK) return rc;
+    const MwdShape sh = mwd_shape(p->stencil, p->dtype, cfg.dw, cfg.nf, XW);
+    MwdArgs a{};
+    a.g = g;
+    a.buf0 = u;
+    a.buf1 = u_prev;
+    a.coef = coeffs;
+    for (int i = 0; i < 5; ++i) a.c[i] = c[i];
+    a.T = (int32_t)T;
+    a.dw = cfg.dw;
+    a.nf = cfg.nf;
+    a.K = p->R + cfg.nf;
+    a.H = cfg.dw / p->R;
+    a.C = cfg.cluster;
+    a.XW = XW;
+    a.NZ = sh.NZ;
+    a.YW = sh.YW;
+    a.XT = sh.XT;
+    const int64_t rows = mwd_rows(T, cfg.dw, p->R);
+    for (int64_t rho = 0; rho < rows && e == cudaSuccess; ++rho) {
+      int64_t a_min = 0, nd = 0;
+      mwd_row_span(rho, cfg.dw, p->ny, &a_min, &nd);
+      if (nd == 0) continue;
+      a.rho = (int32_t)rho;
+      a.a_min = (int32_t)a_min;
+      e = launch_mwd_row(p->stencil, p->dtype, a, (int)nd, cfg.threads, st);
+    }
+  }
+  if (e == cudaSuccess && T % 2 == 1) e = launch_swap(u, u_prev, p->gstride * p->elem, st);
+  if (e != cudaSuccess) return cuda_fail(e, "kernel launch");
+  return GIRIH_OK;
+}
+
+static const double kConst7[5] = {0.4, 0.1, 0, 0, 0};
+static const double kConst25[5] = {-0.9, 0.05, 0.025, 0.0125, 0.00625};
+
+int validate_run(Plan* p, void* u, void* u_prev, const void* coeffs, const girih_params* params,
+                 const double** c, const girih_config** cfg) {
+  if (!p) return fail(GIRIH_EINVAL, "plan is NULL");
+  if (!u || !u_prev) return fail(GIRIH_EINVAL, "u and u_prev must be non-NULL");
+  if (u == u_prev) return fail(GIRIH_EINVAL, "u and u_prev must be distinct buffers");
+  const uintptr_t mis = (reinterpret_cast<uintptr_t>(u) | reinterpret_cast<uintptr_t>(u_prev)) % p->elem;
+  if (mis) return fail(GIRIH_EINVAL, "buffers must be %d-byte aligned", p->elem);
+  const int nc = ncoef_of(p->stencil);
+  if (nc > 0) {
+    if (!coeffs) return fail(GIRIH_EINVAL, "stencil %d needs %d coefficient grids", p->stencil, nc);
+    if (reinterpret_cast<uintptr_t>(coeffs) % p->elem) return fail(GIRIH_EINVAL, "coeffs misaligned");
+  }
+  const int64_t bytes = p->gstride * p->elem;
+  const char* cu = static_cast<const char*>(u);
+  const char* cp = static_cast<const char*>(u_prev);
+  if (cu < cp + bytes && cp < cu + bytes) return fail(GIRIH_EINVAL, "u and u_prev overlap");
+  *c = (params) ? params->c : (p->stencil >= 2 ? kConst25 : kConst7);
+  *cfg = (params && params->force_cfg) ? &params->cfg : &p->cfg;
+  if ((*cfg)->algo == GIRIH_ALGO_MWD) {
+    const int rc = check_config(p, *cfg, nullptr, nullptr);
+    if (rc != GIRIH_OK) return rc;
+  } else if ((*cfg)->algo != GIRIH_ALGO_NAIVE) {
+    return fail(GIRIH_EINVAL, "unknown algo %d", (*cfg)->algo);
+  }
+  return GIRIH_OK;
+}
+
+}  // namespace girih
+
+using namespace girih;
+
+extern "C" {
+
+const char* girih_last_error(void) { return g_err.c_str(); }
+
+int girih_plan(girih_plan_t* out, int32_t stencil, int64_t nx, int64_t ny, int64_t nz, int64_t ldx, int32_t dtype,
+               int64_t T) {
+  if (!out) return fail(GIRIH_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (stencil < 0 || stencil > 3) return fail(GIRIH_EINVAL, "unknown stencil %d", stencil);
+  if (dtype != GIRIH_F64 && dtype != GIRIH_F32) return fail(GIRIH_EINVAL, "unknown dtype %d", dtype);
+  if (nx < 1 || ny < 1 || nz < 1) return fail(GIRIH_EINVAL, "sizes must be >= 1");
+  if (T < 0 || T > (1LL << 30)) return fail(GIRIH_EINVAL, "T=%lld out of range", (long long)T);
+  const int R = radius_of(stencil);
+  if (ldx == 0) ldx = nx + 2 * R;
+  if (ldx < nx + 2 * R) return fail(GIRIH_EINVAL, "ldx=%lld < nx + 2R", (long long)ldx);
+  Plan* p = new (std::nothrow) Plan();
+  if (!p) return fail(GIRIH_ENOMEM, "plan allocation failed");
+  p->stencil = stencil;
+  p->dtype = dtype;
+  p->R = R;
+  p->nx = nx;
+  p->ny = ny;
+  p->nz = nz;
+  p->ldx = ldx;
+  p->T = T;
+  p->elem = dtype == GIRIH_F64 ? 8 : 4;
+  p->gstride = (nz + 2 * R) * (ny + 2 * R) * ldx;
+  cudaError_t e = cudaGetDevice(&p->device);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&p->sm_count, cudaDevAttrMultiProcessorCount, p->device);
+  int optin = 0;
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, p->device);
+  if (e != cudaSuccess) {
+    delete p;
+    cudaGetLastError();
+    return cuda_fail(e, "device query");
+  }
+  p->smem_optin = optin;
+  p->cfg = default_config(p);
+  *out = p;
+  return GIRIH_OK;
+}
+
+int girih_plan_destroy(girih_plan_t plan) {
+  if (!plan) return GIRIH_OK;
+  Plan* p = plan;
+  for (void* d : {p->host_u, p->host_up, p->host_co, p->tune_u, p->tune_up, p->tune_co})
+    if (d) cudaFree(d);
+  delete p;
+  return GIRIH_OK;
+}
+
+int girih_plan_get_config(girih_plan_t plan, girih_config* cfg) {
+  if (!plan || !cfg) return fail(GIRIH_EINVAL, "NULL argument");
+  *cfg = plan->cfg;
+  return GIRIH_OK;
+}
+
+int girih_plan_set_config(girih_plan_t plan, const girih_config* cfg) {
+  if (!plan) return fail(GIRIH_EINVAL, "plan is NULL");
+  const int rc = check_config(plan, cfg, nullptr, nullptr);
+  if (rc != GIRIH_OK) return rc;
+  plan->cfg = *cfg;
+  return GIRIH_OK;
+}
+
+int girih_config_check(girih_plan_t plan, const girih_config* cfg, int64_t* smem_bytes) {
+  if (!plan) return fail(GIRIH_EINVAL, "plan is NULL");
+  return check_config(plan, cfg, smem_bytes, nullptr);
+}
+
+int girih_plan_layout(girih_plan_t plan, int64_t* elems, int32_t* radius, int64_t* ldx) {
+  if (!plan) return fail(GIRIH_EINVAL, "plan is NULL");
+  if (elems) *elems = plan->gstride;
+  if (radius) *radius = plan->R;
+  if (ldx) *ldx = plan->ldx;
+  return GIRIH_OK;
+}
+
+int girih_plan_launch_count(girih_plan_t plan, const girih_config* cfg, int64_t* launches) {
+  if (!plan || !launches) return fail(GIRIH_EINVAL, "NULL argument");
+  const girih_config& c = cfg ? *cfg : plan->cfg;
+  const int64_t T = plan->T;
+  int64_t n = (c.algo == GIRIH_ALGO_NAIVE) ? T : mwd_rows(T, c.dw, plan->R);
+  if (T % 2 == 1) ++n;
+  *launches = n;
+  return GIRIH_OK;
+}
+
+int girih_run(girih_plan_t plan, void* u, void* u_prev, const void* coeffs, const girih_params* params,
+              void* stream) {
+  const double* c = nullptr;
+  const girih_config* cfg = nullptr;
+  int rc = validate_run(plan, u, u_prev, coeffs, params, &c, &cfg);
+  if (rc != GIRIH_OK) return rc;
+  if (plan->T == 0) return GIRIH_OK;
+  return run_sweep(plan, plan->T, u, u_prev, coeffs, c, *cfg, static_cast<cudaStream_t>(stream));
+}
+
+int girih_run_host(girih_plan_t plan, void* u_host, void* u_prev_host, const void* coeffs_host,
+                   const girih_params* params, void* stream) {
+  if (!plan) return fail(GIRIH_EINVAL, "plan is NULL");
+  Plan* p = plan;
+  if (!u_host || !u_prev_host) return fail(GIRIH_EINVAL, "host arrays must be non-NULL");
+  const int nc = ncoef_of(p->stencil);
+  if (nc > 0 && !coeffs_host) return fail(GIRIH_EINVAL, "coefficient grids missing");
+  const size_t bytes = (size_t)(p->gstride * p->elem);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  cudaError_t e = cudaSuccess;
+  if (!p->host_u) e = cudaMalloc(&p->host_u, bytes);
+  if (e == cudaSuccess && !p->host_up) e = cudaMalloc(&p->host_up, bytes);
+  if (e == cudaSuccess && nc > 0 && !p->host_co) e = cudaMalloc(&p->host_co, bytes * nc);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return fail(GIRIH_ENOMEM, "device buffers for host run: %s", cudaGetErrorString(e));
+  }
+  e = cudaMemcpyAsync(p->host_u, u_host, bytes, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(p->host_up, u_prev_host, bytes, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess && nc > 0) e = cudaMemcpyAsync(p->host_co, coeffs_host, bytes * nc, cudaMemcpyHostToDevice, st);
+  if (e != cudaSuccess) return cuda_fail(e, "host to device copy");
+  int rc = girih_run(plan, p->host_u, p->host_up, nc > 0 ? p->host_co : nullptr, params, stream);
+  if (rc != GIRIH_OK) return rc;
+  e = cudaMemcpyAsync(u_host, p->host_u, bytes, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(u_prev_host, p->host_up, bytes, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return cuda_fail(e, "device to host copy");
+  return GIRIH_OK;
+}
+
+// Eq. 3 (general R; Eq. 2 for R = 1 is the same expression up to the paper's approximation):
+// C_S = N_xb * [ N_D * D_w * (D_w/2 - R + N_F) + 2R (D_w + W_w) ],  W_w = D_w - 2R + N_F.
+double girih_model_cache_block(double n_xb, int32_t dw, int32_t nf, int32_t r, int32_t nd) {
+  const double ww = (double)dw - 2.0 * r + nf;
+  return n_xb * ((double)nd * dw * ((double)dw / 2.0 - r + nf) + 2.0 * r * (dw + ww));
+}
+
+// Eq. 5 (Eq. 4 for R = 1): B_C = 2 s R [ (2 D_w - 2R) + (N_D D_w + 2R) ] / D_w^2 bytes/LUP,
+// s = element size (the paper's 16R is 2 s R with s = 8).
+double girih_model_code_balance(int32_t dw, int32_t r, int32_t nd, int32_t elem_bytes) {
+  if (dw <= 0) return 0.0;
+  const double d = dw;
+  return 2.0 * elem_bytes * r * ((2.0 * d - 2.0 * r) + (nd * d + 2.0 * r)) / (d * d);
+}
+
+}  // extern "C"

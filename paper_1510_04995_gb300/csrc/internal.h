@@ -1,0 +1,62 @@
+// Internal interfaces between the C-ABI layer (api.cu, tuner.cu) and the kernel translation
+// units (naive.cu, mwd.cu, mlp.cu).  Not part of the public ABI.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/girih.h"
+
+namespace girih {
+
+// Geometry of one padded grid.
+struct Grid {
+  int64_t nx, ny, nz, ldx;  // interior sizes and leading dimension
+  int64_t sy;               // ny + 2R (rows per plane)
+  int64_t gstride;          // elements per grid: (nz+2R)*sy*ldx
+};
+
+// One naive time step (Sect. 2.1.1): U <- S(V) (and U's own old value for second order).
+struct NaiveArgs {
+  Grid g;
+  const void* V;
+  void* U;
+  const void* coef;
+  double c[5];
+  int32_t zc;  // z planes per block
+};
+cudaError_t launch_naive_step(int stencil, int dtype, const NaiveArgs& a, cudaStream_t st);
+int naive_block_rows(int stencil, int dtype);  // threads per block = 32 * rows
+
+// One row of diamonds of the multi-threaded wavefront-diamond sweep (Sect. 4.2.1).
+struct MwdArgs {
+  Grid g;
+  void* buf0;        // global buffer holding even time levels (the caller's u)
+  void* buf1;        // odd time levels (the caller's u_prev)
+  const void* coef;
+  double c[5];
+  int32_t T;         // total time steps of the sweep
+  int32_t rho;       // diamond row index
+  int32_t dw, nf, K, H;  // diamond width, wavefront width, level skew (R + nf), levels per diamond
+  int32_t a_min;     // index of the first diamond of the row
+  int32_t C, XW;     // blocks per tile (cluster) and x slab width per block
+  int32_t NZ, YW, XT;  // shared ring: planes, rows, columns per buffer
+};
+
+struct MwdShape {
+  int32_t NZ, YW, XT;
+  int64_t smem_bytes;
+};
+MwdShape mwd_shape(int stencil, int dtype, int dw, int nf, int XW);
+// Launch one diamond row: ndiam tiles, each a cluster of a.C blocks of `threads` threads.
+cudaError_t launch_mwd_row(int stencil, int dtype, const MwdArgs& a, int ndiam, int threads, cudaStream_t st);
+// Configure kernel attributes (dynamic shared memory, non-portable clusters); returns the max
+// active clusters the device reports for the configuration (0 = cannot be scheduled).
+cudaError_t mwd_prepare(int stencil, int dtype, int C, int threads, int64_t smem, int* max_clusters);
+
+// In-place exchange of two device arrays (odd T puts level T back into u).
+cudaError_t launch_swap(void* a, void* b, int64_t bytes, cudaStream_t st);
+
+inline int radius_of(int stencil) { return stencil >= 2 ? 4 : 1; }
+inline int ncoef_of(int stencil) { return stencil == 1 ? 7 : (stencil == 3 ? 13 : 0); }
+
+}  // namespace girih

@@ -1,0 +1,32 @@
+// The opaque plan behind girih_plan_t, and helpers shared by api.cu and tuner.cu.
+#pragma once
+#include <cstdarg>
+#include <cstdint>
+
+#include "internal.h"
+
+struct girih_plan_s {
+  int32_t stencil = 0, dtype = 0, R = 1, elem = 8;
+  int64_t nx = 0, ny = 0, nz = 0, ldx = 0, T = 0, gstride = 0;
+  int device = 0, sm_count = 0;
+  int64_t smem_optin = 0;
+  girih_config cfg{};
+  // device buffers owned by the plan: girih_run_host staging and the tuner's own arrays
+  void* host_u = nullptr;
+  void* host_up = nullptr;
+  void* host_co = nullptr;
+  void* tune_u = nullptr;
+  void* tune_up = nullptr;
+  void* tune_co = nullptr;
+};
+
+namespace girih {
+using Plan = girih_plan_s;
+int fail(int code, const char* fmt, ...);
+void g_err_clear();
+int cuda_fail(cudaError_t e, const char* where);
+int check_config(const Plan* p, const girih_config* c, int64_t* smem_out, int* xw_out);
+int run_sweep(Plan* p, int64_t T, void* u, void* u_prev, const void* coeffs, const double* c,
+              const girih_config& cfg, cudaStream_t st);
+int64_t mwd_rows(int64_t T, int dw, int R);
+}  // namespace girih

@@ -1,0 +1,218 @@
+"""Level-tag model of the blocked (wavefront-diamond) kernel's schedule -- test infrastructure.
+
+It replays, on the CPU, the loop structure of the blocked kernel in csrc/mwd.cu for one
+configuration: per diamond row, per tile, per x slab (block of the cluster), per wavefront step,
+the same plane loads, write-backs, compute items and x-halo pushes, with the same index formulas.
+Instead of values, every cell carries the time level it holds.  The model checks:
+  * every global and shared-memory index the kernel would touch is inside its buffer;
+  * every read sees exactly the time level the update needs (halo cells match any level);
+  * no shared cell is both written and read (by different items) within one step, and the cells
+    being loaded are not read in that step (the single barrier per step suffices);
+  * at the end, buffer T%2 holds level T and buffer (T-1)%2 holds level T-1 everywhere.
+Tiles of a row advance in lock step (one legal interleaving of independent tiles).
+"""
+from __future__ import annotations
+
+import numpy as np
+
+HALO = -1000
+
+
+def slab_width(nx, C):
+    w = -(-nx // C)
+    p = 32
+    while p < w:
+        p *= 2
+    return p
+
+
+def shape(R, dw, nf, XW):
+    H = dw // R
+    K = R + nf
+    NZ = 2 * nf + R + max(R, nf) + (H - 2) * K
+    return NZ, dw + 2 * R, XW + 2 * R
+
+
+def rows(T, dw, R):
+    if T <= 0:
+        return 0
+    Hh = dw // R // 2
+    rho = 0
+    while rho * Hh + 1 <= T - 1:
+        rho += 1
+    return rho + 1
+
+
+def row_span(rho, dw, ny):
+    h = rho * (dw // 2)
+    lo = h // dw
+    hi = -(-(ny + h) // dw) - 1
+    return lo, max(hi - lo + 1, 0)
+
+
+def simulate(R, second_order, nx, ny, nz, T, dw, nf, C):
+    XW = slab_width(nx, C)
+    NZ, YW, XT = shape(R, dw, nf, XW)
+    H = dw // R
+    K = R + nf
+    Hh = H // 2
+    G = np.full((2, nz + 2 * R, ny + 2 * R, nx + 2 * R), HALO, dtype=np.int64)
+    G[0, R:-R, R:-R, R:-R] = 0
+    G[1, R:-R, R:-R, R:-R] = -1
+    max_g = max_s = 0
+
+    def gtag(p, z, y, x):
+        nonlocal max_g
+        assert -R <= z < nz + R and -R <= y < ny + R and -R <= x < nx + R, (z, y, x)
+        return G[p, z + R, y + R, x + R]
+
+    for rho in range(rows(T, dw, R)):
+        a_min, nd = row_span(rho, dw, ny)
+        tb = max((rho - 1) * Hh + 1, 0)
+        te = min((rho + 1) * Hh - 1, T - 1)
+        if tb > te or nd == 0:
+            continue
+        nlev = te - tb + 1
+        smax = nlev - 1
+        W = -(-(nz + smax * K) // nf)
+        tiles = []
+        for ti in range(nd):
+            a = a_min + ti
+            b = a - rho
+            P0 = a * dw - rho * (dw // 2)
+            Y0 = P0 - R
+            lev = []
+            for s in range(nlev):
+                t = tb + s
+                lo = max(a * dw - R * t, b * dw + R * t, 0)
+                hi = min((a + 1) * dw - R * t, (b + 1) * dw + R * t, ny)
+                lev.append((lo, max(hi - lo, 0)))
+            mask = []
+            for yy in range(YW):
+                y = Y0 + yy
+                m = 0
+                if 0 <= y < ny and P0 <= y < P0 + dw:
+                    cnt, par = 0, 0
+                    for s in range(nlev):
+                        t = tb + s
+                        if max(a * dw - R * t, b * dw + R * t) <= y < min((a + 1) * dw - R * t, (b + 1) * dw + R * t):
+                            cnt += 1
+                            par = (t + 1) & 1
+                    m = 3 if cnt >= 2 else ((1 << par) if cnt == 1 else 0)
+                mask.append(m)
+            S = np.full((C, 2, NZ, YW, XT), -5000, dtype=np.int64)  # -5000: never loaded
+            tiles.append(dict(a=a, P0=P0, Y0=Y0, lev=lev, mask=mask, S=S))
+
+        def load_plane(tl, rank, z, loaded):
+            nonlocal max_s
+            x0 = rank * XW
+            xw = min(XW, nx - x0)
+            if z < -R or z >= nz + R or xw <= 0:
+                return
+            slot = (z + R) % NZ
+            Y0 = tl["Y0"]
+            ylo, yhi = max(Y0, -R), min(Y0 + YW, ny + R)
+            for p in range(2):
+                for y in range(ylo, yhi):
+                    for xx in range(xw + 2 * R):
+                        assert 0 <= y - Y0 < YW and 0 <= xx < XT
+                        tl["S"][rank, p, slot, y - Y0, xx] = gtag(p, z, y, x0 - R + xx)
+                        loaded.add((rank, p, slot, y - Y0, xx))
+
+        def write_plane(tl, rank, z, wb_reads):
+            x0 = rank * XW
+            xw = min(XW, nx - x0)
+            if z < 0 or z >= nz or xw <= 0:
+                return
+            slot = (z + R) % NZ
+            for yy in range(YW):
+                m = tl["mask"][yy]
+                if not m:
+                    continue
+                y = tl["Y0"] + yy
+                for xl in range(xw):
+                    for p in range(2):
+                        if m >> p & 1:
+                            gtag(p, z, y, x0 + xl)
+                            G[p, z + R, y + R, x0 + xl + R] = tl["S"][rank, p, slot, yy, xl + R]
+                            wb_reads.add((rank, p, slot, yy, xl + R))
+
+        def check_read(tagv, want):
+            assert tagv == want or tagv == HALO, (tagv, want)
+
+        for tl in tiles:
+            for rank in range(C):
+                for z in range(-R, nf + R):
+                    load_plane(tl, rank, z, set())
+        for w in range(W):
+            for tl in tiles:
+                loaded, wb_reads, reads, writes = set(), set(), {}, {}
+                for rank in range(C):
+                    for f in range(nf):
+                        load_plane(tl, rank, (w + 1) * nf + R + f, loaded)
+                    if w > 0:
+                        for f in range(nf):
+                            write_plane(tl, rank, (w - 1) * nf - smax * K + f, wb_reads)
+                pending = []
+                for rank in range(C):
+                    x0 = rank * XW
+                    xw = min(XW, nx - x0)
+                    if xw <= 0:
+                        continue
+                    for s in range(nlev):
+                        zb = w * nf - s * K
+                        if zb + nf <= 0 or zb >= nz:
+                            continue
+                        t = tb + s
+                        pin, pout = t & 1, (t & 1) ^ 1
+                        lo, width = tl["lev"][s]
+                        for row in range(width):
+                            y = lo + row
+                            yy = y - tl["Y0"]
+                            for f in range(nf):
+                                z = zb + f
+                                if z < 0 or z >= nz:
+                                    continue
+                                sl = (z + R) % NZ
+                                for xl in range(xw):
+                                    xx = xl + R
+                                    item = (rank, s, y, z, xl)
+                                    Sx = tl["S"][rank]
+                                    for d in range(-R, R + 1):
+                                        for cell in ((pin, sl, yy, xx + d), (pin, sl, yy + d, xx),
+                                                     (pin, (sl + d) % NZ, yy, xx)):
+                                            assert 0 <= cell[2] < YW and 0 <= cell[3] < XT, cell
+                                            check_read(Sx[cell], t)
+                                            reads.setdefault((rank,) + cell, set()).add(item)
+                                    if second_order:
+                                        check_read(Sx[pout, sl, yy, xx], t - 1)
+                                        reads.setdefault((rank, pout, sl, yy, xx), set()).add(item)
+                                    outs = [(rank, pout, sl, yy, xx)]
+                                    if C > 1 and xl < R and rank > 0:
+                                        outs.append((rank - 1, pout, sl, yy, xx + XW))
+                                    if C > 1 and xl >= XW - R and rank < C - 1:
+                                        outs.append((rank + 1, pout, sl, yy, xx - XW))
+                                    for o in outs:
+                                        assert 0 <= o[4] < XT
+                                        assert o not in writes, ("double write", o)
+                                        writes[o] = item
+                                    pending.append((outs, t + 1))
+                # race checks within the step
+                for cell, it in writes.items():
+                    rs = reads.get(cell, set())
+                    assert rs <= {it}, ("read and written in one step", cell)
+                    assert cell not in loaded and cell not in wb_reads, ("write vs load/write-back", cell)
+                for cell in loaded:
+                    assert cell not in reads, ("load into a slot read this step", cell)
+                for outs, lv in pending:
+                    for o in outs:
+                        tl["S"][o] = lv
+        for tl in tiles:
+            for rank in range(C):
+                for f in range(nf):
+                    write_plane(tl, rank, (W - 1) * nf - smax * K + f, set())
+    inner = (slice(R, -R),) * 3
+    if T > 0:
+        assert np.all(G[T % 2][inner] == T)
+        assert np.all(G[(T - 1) % 2][inner] == T - 1)
+    return True

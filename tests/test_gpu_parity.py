@@ -1,0 +1,168 @@
+"""GPU sweeps against the FP64 oracle (element by element) and blocked against naive (bit for bit).
+
+Sizes are ragged on purpose (not multiples of the 32-wide x slabs, of the diamond width or of
+the z chunk) and span several tiles; T covers 1, H-1, H, H+1 and 2H+3 so that truncated diamond
+rows are exercised.  Tolerances: FP64 max normwise relative error <= 1e-12; FP32 relative L2
+error <= 1e-5 (7-point) and <= 1e-4 (25-point) against the FP64 oracle run on the FP64 inputs.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import paper_1510_04995_gb300 as girih
+from paper_1510_04995_gb300 import inputs
+
+from gpu_util import gpu_sweep, normwise, rel_l2
+
+pytestmark = pytest.mark.gpu
+
+SIZES = {1: (70, 45, 33), 4: (70, 50, 29)}
+FP32_TOL = {0: 1e-5, 1: 1e-5, 2: 1e-4, 3: 1e-4}
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _build():
+    import __graft_entry__
+    __graft_entry__.build()
+
+
+def _ref(stencil, nx, ny, nz, T, seed=3):
+    u, up, co, c = inputs.make_problem(stencil, nx, ny, nz, seed=seed)
+    ru, rup = u.copy(), up.copy()
+    oracle.sweep(stencil, ru, rup, co, c, T, nx, ny, nz, nthreads=8)
+    return u, up, co, c, ru, rup
+
+
+MWD_CFGS = {
+    1: [dict(dw=4, nf=1, cluster=1, threads=128), dict(dw=8, nf=2, cluster=2, threads=256),
+        dict(dw=16, nf=1, cluster=4, threads=512), dict(dw=6, nf=3, cluster=2, threads=64)],
+    4: [dict(dw=8, nf=1, cluster=1, threads=256), dict(dw=16, nf=2, cluster=2, threads=256),
+        dict(dw=24, nf=1, cluster=4, threads=128)],
+}
+
+
+@pytest.mark.parametrize("stencil", [0, 1, 2, 3])
+def test_naive_fp64_vs_oracle(stencil):
+    R = inputs.RADIUS[stencil]
+    nx, ny, nz = SIZES[R]
+    T = 5
+    u, up, co, c, ru, rup = _ref(stencil, nx, ny, nz, T)
+    gu, gup = gpu_sweep(stencil, "f64", u, up, co, c, T, nx, ny, nz, girih.config(girih.NAIVE))
+    assert normwise(gu, ru, R) <= 1e-12
+    assert normwise(gup, rup, R) <= 1e-12
+    # the halo is never written
+    m = np.ones(u.shape, bool)
+    m[R:-R, R:-R, R:-R] = False
+    assert np.array_equal(gu[m], u[m]) and np.array_equal(gup[m], up[m])
+
+
+@pytest.mark.parametrize("stencil", [0, 1, 2, 3])
+@pytest.mark.parametrize("ci", [0, 1, 2, 3])
+def test_mwd_fp64_vs_oracle_and_naive(stencil, ci):
+    R = inputs.RADIUS[stencil]
+    cfgs = MWD_CFGS[R]
+    if ci >= len(cfgs):
+        pytest.skip("no such config for this radius")
+    kw = cfgs[ci]
+    H = kw["dw"] // R
+    nx, ny, nz = SIZES[R]
+    Ts = [1, H - 1, H, H + 1, 2 * H + 3] if ci == 0 else [H + 1]
+    for T in sorted(set(t for t in Ts if t >= 1)):
+        u, up, co, c, ru, rup = _ref(stencil, nx, ny, nz, T)
+        cfg = girih.config(girih.MWD, **kw)
+        bu, bup = gpu_sweep(stencil, "f64", u, up, co, c, T, nx, ny, nz, cfg)
+        assert normwise(bu, ru, R) <= 1e-12, (T, kw)
+        assert normwise(bup, rup, R) <= 1e-12, (T, kw)
+        nu, nup = gpu_sweep(stencil, "f64", u, up, co, c, T, nx, ny, nz, girih.config(girih.NAIVE))
+        assert np.array_equal(bu, nu), (T, kw)
+        assert np.array_equal(bup, nup), (T, kw)
+
+
+@pytest.mark.parametrize("stencil", [0, 1, 2, 3])
+@pytest.mark.parametrize("algo", ["naive", "mwd"])
+def test_fp32_error_vs_fp64_oracle(stencil, algo):
+    R = inputs.RADIUS[stencil]
+    nx, ny, nz = SIZES[R]
+    T = 12
+    u, up, co, c, ru, rup = _ref(stencil, nx, ny, nz, T)
+    cfg = girih.config(girih.NAIVE) if algo == "naive" else girih.config(girih.MWD, **MWD_CFGS[R][1])
+    gu, _ = gpu_sweep(stencil, "f32", u, up, co, c, T, nx, ny, nz, cfg)
+    assert rel_l2(gu, ru, R) <= FP32_TOL[stencil]
+
+
+@pytest.mark.parametrize("stencil", [0, 3])
+def test_fp32_mwd_bitwise_equals_naive(stencil):
+    R = inputs.RADIUS[stencil]
+    nx, ny, nz = SIZES[R]
+    T = 2 * (8 // R) + 3 if R == 1 else 7
+    u, up, co, c = inputs.make_problem(stencil, nx, ny, nz, seed=5)
+    for kw in MWD_CFGS[R]:
+        bu, bup = gpu_sweep(stencil, "f32", u, up, co, c, T, nx, ny, nz, girih.config(girih.MWD, **kw))
+        nu, nup = gpu_sweep(stencil, "f32", u, up, co, c, T, nx, ny, nz, girih.config(girih.NAIVE))
+        assert np.array_equal(bu, nu) and np.array_equal(bup, nup), kw
+
+
+@pytest.mark.parametrize("stencil", [0, 2])
+def test_padded_leading_dimension(stencil):
+    R = inputs.RADIUS[stencil]
+    nx, ny, nz, T = 45, 21, 17, 6
+    ldx = nx + 2 * R + 11
+    u, up, co, c = inputs.make_problem(stencil, nx, ny, nz, seed=9, ldx=ldx)
+    ru, rup = u.copy(), up.copy()
+    oracle.sweep(stencil, ru, rup, co, c, T, nx, ny, nz)
+    for cfg in (girih.config(girih.NAIVE), girih.config(girih.MWD, dw=4 * R, nf=1, cluster=2, threads=128)):
+        gu, _ = gpu_sweep(stencil, "f64", u, up, co, c, T, nx, ny, nz, cfg, ldx=ldx)
+        assert normwise(gu[:, :, :nx + 2 * R], ru[:, :, :nx + 2 * R], R) <= 1e-12
+        assert np.array_equal(gu[:, :, nx + 2 * R:], u[:, :, nx + 2 * R:])  # padding untouched
+
+
+@pytest.mark.parametrize("shape", [(1, 1, 1), (3, 2, 5), (33, 1, 9), (1, 40, 3), (5, 7, 1)])
+def test_degenerate_shapes(shape):
+    nx, ny, nz = shape
+    for stencil in (0, 2):
+        R = inputs.RADIUS[stencil]
+        T = 5
+        u, up, co, c, ru, rup = _ref(stencil, nx, ny, nz, T)
+        for cfg in (girih.config(girih.NAIVE), girih.config(girih.MWD, dw=2 * R, nf=1, cluster=1, threads=64)):
+            gu, gup = gpu_sweep(stencil, "f64", u, up, co, c, T, nx, ny, nz, cfg)
+            assert np.max(np.abs(gu - ru)) <= 1e-12 * max(1.0, np.max(np.abs(ru))), (shape, stencil, cfg)
+
+
+def test_t0_is_noop():
+    u, up, co, c = inputs.make_problem(0, 20, 20, 20)
+    gu, gup = gpu_sweep(0, "f64", u, up, co, c, 0, 20, 20, 20, girih.config(girih.MWD, dw=8, cluster=1))
+    assert np.array_equal(gu, u) and np.array_equal(gup, up)
+
+
+def test_invalid_arguments_leave_buffers_untouched():
+    import torch
+    p = girih.plan(girih.S7V, 16, 16, 16, dtype="f64", T=3)
+    u = torch.ones(p.shape, dtype=torch.float64, device="cuda")
+    up = torch.ones(p.shape, dtype=torch.float64, device="cuda")
+    assert girih.lib().girih_run(p.handle, u.data_ptr(), up.data_ptr(), None, None, None) == 1  # no coefficients
+    assert girih.lib().girih_run(p.handle, u.data_ptr(), u.data_ptr(), None, None, None) == 1  # aliasing
+    assert girih.lib().girih_run(p.handle, u.data_ptr() + 4, up.data_ptr(), u.data_ptr(), None, None) == 1
+    bad = girih.config(girih.MWD, dw=3, nf=1, cluster=1, threads=128)
+    with pytest.raises(girih.GirihError):
+        p.set_config(bad)
+    with pytest.raises(girih.GirihError):
+        girih.run(p, u, up, torch.ones((7,) + p.shape, dtype=torch.float64, device="cuda"), cfg=bad)
+    torch.cuda.synchronize()
+    assert bool((u == 1).all()) and bool((up == 1).all())
+
+
+def test_run_host_matches_device_run():
+    stencil, nx, ny, nz, T = 2, 30, 26, 22, 6
+    u, up, co, c = inputs.make_problem(stencil, nx, ny, nz, seed=4)
+    p = girih.plan(stencil, nx, ny, nz, dtype="f64", T=T)
+    hu, hup = u.copy(), up.copy()
+    girih.run_host(p, hu, hup, None, c=c)
+    gu, gup = gpu_sweep(stencil, "f64", u, up, co, c, T, nx, ny, nz, p.config)
+    assert np.array_equal(hu, gu) and np.array_equal(hup, gup)
+
+
+def test_launch_count():
+    p = girih.plan(0, 64, 64, 64, dtype="f64", T=9)
+    assert p.launch_count(girih.config(girih.NAIVE)) == 10  # 9 steps + one exchange for odd T
+    # dw=8, R=1: rows 0..(T-2)//4+1 -> 3 rows, plus the exchange
+    assert p.launch_count(girih.config(girih.MWD, dw=8)) == 4

@@ -1,0 +1,23 @@
+"""CPU check of the blocked kernel's schedule (bounds, levels read, one-barrier-per-step races)."""
+import pytest
+
+from mwd_schedule_model import simulate
+
+CASES = [
+    # R, second order, nx, ny, nz, T, dw, nf, C
+    (1, False, 37, 19, 7, 9, 4, 1, 1),
+    (1, False, 70, 23, 6, 5, 8, 2, 2),
+    (1, False, 70, 17, 5, 8, 16, 1, 4),
+    (1, False, 40, 13, 6, 7, 6, 3, 2),
+    (1, False, 3, 2, 5, 5, 2, 1, 1),
+    (1, False, 65, 9, 4, 11, 4, 4, 4),
+    (4, True, 70, 29, 12, 5, 8, 1, 1),
+    (4, True, 70, 35, 11, 9, 16, 2, 2),
+    (4, True, 44, 30, 10, 6, 24, 1, 4),
+    (4, True, 5, 7, 3, 5, 8, 1, 1),
+]
+
+
+@pytest.mark.parametrize("case", CASES)
+def test_schedule_model(case):
+    assert simulate(*case)
