@@ -1,0 +1,334 @@
+"""Benchmark of the temporally blocked stencil sweep on GB300.
+
+One "step" is one complete sweep: girih_run advancing the whole grid by T time steps with the
+blocked (wavefront-diamond) kernel.  Default workload: 7-point constant-coefficient stencil,
+FP64, 512^3 interior, T = 64 (the blocked-vs-naive configuration).  Prints ONE JSON line.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME] [--impl reference]
+
+value     GLUP/s of the blocked sweep (giga lattice-site updates per second, all ranks), inputs
+          resident in HBM; each grid (1 GiB per buffer at FP64 512^3) is larger than L2.
+naive     the naive GPU sweep (one pass per time step) on the same workload, same timing.
+e2e       same metric through girih_run_host: pinned host buffers copied in and out every step.
+roofline  the blocked kernel's achieved rate against its bound (FP64: the DP pipe; FP32: HBM).
+cpu_baseline  the FP64 oracle (plain C loops, OpenMP over z) on this host's cores, on a bounded
+          sample of the same grid (fewer time steps).
+--impl reference  times only that oracle, per step on a bounded sample, as the reference arm.
+Multi-GPU (torchrun): every rank runs an independent replica of the workload (the sweep is not
+sharded across GPUs); value = all ranks' updates / max-over-ranks time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOADS = {
+    # name: (stencil, dtype, nx, ny, nz, T)
+    "7pt_const_f64_512": (0, "f64", 512, 512, 512, 64),
+    "7pt_const_f32_512": (0, "f32", 512, 512, 512, 64),
+    "7pt_var_f64_480": (1, "f64", 480, 480, 480, 32),
+    "7pt_var_f32_480": (1, "f32", 480, 480, 480, 32),
+    "25pt_const_f64_384": (2, "f64", 384, 384, 384, 32),
+    "25pt_const_f32_384": (2, "f32", 384, 384, 384, 32),
+    "25pt_var_f64_384": (3, "f64", 384, 384, 384, 32),
+    "25pt_var_f32_384": (3, "f32", 384, 384, 384, 32),
+}
+DEFAULT = "7pt_const_f64_512"
+STENCIL_NAME = {0: "7-point constant", 1: "7-point variable", 2: "25-point constant", 3: "25-point variable"}
+# FP instructions per LUP of the point update (explicitly rounded ops, see csrc/stencil.cuh)
+INSTR_PER_LUP = {0: 7, 1: 7, 2: 28, 3: 28}
+# domain-sized streams N_D of the code-balance model and the spatial minimum bytes per LUP (in elements)
+ND = {0: 2, 1: 9, 2: 2, 3: 15}
+SPATIAL_ELEMS = {0: 2, 1: 9, 2: 3, 3: 16}
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+def _tuned(workload):
+    path = os.path.join(ROOT, "paper_1510_04995_gb300", "tuned_configs.json")
+    try:
+        with open(path) as f:
+            return json.load(f).get(workload)
+    except Exception:
+        return None
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.idx = gpu_index
+        self.p = None
+
+    def __enter__(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(self.idx), f"--query-gpu={self.Q}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.p = None
+        return self
+
+    def __exit__(self, *a):
+        self.out = ""
+        if self.p:
+            self.p.terminate()
+            try:
+                self.out, _ = self.p.communicate(timeout=5)
+            except Exception:
+                self.p.kill()
+
+    def summary(self):
+        rows = []
+        for line in (self.out or "").strip().splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                rows.append((float(f[1]), float(f[2]), f[5:9]))
+            except ValueError:
+                continue
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for _, _, r in rows for i in range(4) if r[i].lower() == "active"})
+        return {"sm_mhz": statistics.median(r[0] for r in rows), "sm_max_mhz": max(r[1] for r in rows),
+                "reasons": reasons, "samples": len(rows)}
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def cpu_baseline(stencil, nx, ny, nz, budget_s=10.0, max_T=64, min_T=1):
+    """Time the FP64 oracle on this host's cores on the workload's grid for a bounded number of steps."""
+    import numpy as np
+
+    import oracle
+    from paper_1510_04995_gb300 import inputs
+    oracle.build()
+    cores = len(os.sched_getaffinity(0))
+    u, up, co, c = inputs.make_problem(stencil, nx, ny, nz)
+    t0 = time.perf_counter()
+    oracle.sweep(stencil, u, up, co, c, 1, nx, ny, nz, nthreads=cores)
+    t1 = time.perf_counter() - t0
+    T = int(max(min_T, min(max_T, budget_s / max(t1, 1e-6))))
+    t0 = time.perf_counter()
+    oracle.sweep(stencil, u, up, co, c, T, nx, ny, nz, nthreads=cores)
+    dt = time.perf_counter() - t0
+    glups = nx * ny * nz * T / dt * 1e-9
+    del u, up, co
+    return {"value": glups, "unit": "GLUP/s", "cores": cores, "kind": "oracle",
+            "sample": f"{nx}x{ny}x{nz} grid, {T} time steps (FP64 oracle, OpenMP over z), {dt:.1f} s"}
+
+
+def run_reference(args, wl):
+    ws, rank, _ = _dist()
+    if rank != 0:
+        return 0
+    stencil, dtype, nx, ny, nz, T = WORKLOADS[wl]
+    import oracle
+    from paper_1510_04995_gb300 import inputs
+    oracle.build()
+    cores = len(os.sched_getaffinity(0))
+    u, up, co, c = inputs.make_problem(stencil, nx, ny, nz)
+    t0 = time.perf_counter()
+    oracle.sweep(stencil, u, up, co, c, 1, nx, ny, nz, nthreads=cores)
+    one = time.perf_counter() - t0
+    # each step is a bounded sample: as many time steps of the grid as fit in ~10 s (>= 1)
+    steps_per = int(max(1, min(T, 10.0 / max(one, 1e-6) / max(1, args.steps + args.warmup) * 3)))
+    for _ in range(args.warmup):
+        oracle.sweep(stencil, u, up, co, c, steps_per, nx, ny, nz, nthreads=cores)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle.sweep(stencil, u, up, co, c, steps_per, nx, ny, nz, nthreads=cores)
+    dt = time.perf_counter() - t0
+    glups = nx * ny * nz * steps_per * args.steps / dt * 1e-9
+    sample = f"{nx}x{ny}x{nz} grid, {steps_per} time steps per bench step (of the workload's {T})"
+    line = {"impl": "reference", "metric": "GLUP/s", "value": glups, "unit": "GLUP/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": wl, "stencil": STENCIL_NAME[stencil], "nx": nx, "ny": ny,
+                                            "nz": nz, "T": T, "bench_dtype": dtype},
+            "cpu_baseline": {"value": glups, "unit": "GLUP/s", "cores": cores, "kind": "oracle", "sample": sample},
+            "e2e": {"value": glups, "unit": "GLUP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="girih")
+    ap.add_argument("--workload", default=DEFAULT, choices=sorted(WORKLOADS))
+    ap.add_argument("--algo", default="tuned", choices=["tuned", "naive", "mwd"])
+    ap.add_argument("--dw", type=int, default=0)
+    ap.add_argument("--nf", type=int, default=1)
+    ap.add_argument("--cluster", type=int, default=0)
+    ap.add_argument("--threads", type=int, default=256)
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-naive", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args, args.workload)
+
+    import torch
+    import torch.distributed as dist
+
+    import paper_1510_04995_gb300 as girih
+    from paper_1510_04995_gb300 import build as gbuild
+    from paper_1510_04995_gb300 import inputs
+
+    ws, rank, local = _dist()
+    if ws > 1:
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local)
+    gbuild.build()
+    stencil, dtype, nx, ny, nz, T = WORKLOADS[args.workload]
+    p = girih.plan(stencil, nx, ny, nz, dtype=dtype, T=T)
+    if args.algo == "naive":
+        cfg = girih.config(girih.NAIVE)
+    elif args.algo == "mwd" and args.dw:
+        cfg = girih.config(girih.MWD, dw=args.dw, nf=args.nf, cluster=args.cluster or 1, threads=args.threads)
+    else:
+        tuned = _tuned(args.workload)
+        cfg = girih.Config(**tuned) if tuned else p.config
+    p.set_config(cfg)
+
+    u, up, co, c = inputs.make_problem(stencil, nx, ny, nz, backend="torch", device=dev)
+    tdt = torch.float64 if dtype == "f64" else torch.float32
+    u, up = u.to(tdt).contiguous(), up.to(tdt).contiguous()
+    co = co.to(tdt).contiguous() if co is not None else None
+    stream = torch.cuda.current_stream(dev)
+
+    def barrier():
+        if ws > 1:
+            dist.barrier()
+        torch.cuda.synchronize(dev)
+
+    def timed(config, steps, warmup):
+        for _ in range(warmup):
+            girih.run(p, u, up, co, c=c, cfg=config, stream=stream)
+        barrier()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        for _ in range(steps):
+            girih.run(p, u, up, co, c=c, cfg=config, stream=stream)
+        ev1.record(stream)
+        barrier()
+        ms = ev0.elapsed_time(ev1)
+        if ws > 1:
+            t = torch.tensor([ms], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ms = float(t.item())
+        return ms
+
+    lups = nx * ny * nz * T
+    with ClockSampler(local) as clk:
+        ms = timed(cfg, args.steps, args.warmup)
+    clocks = clk.summary()
+    value = lups * args.steps * ws / (ms * 1e-3) * 1e-9
+    naive = None
+    if not args.no_naive and cfg.algo != girih.NAIVE:
+        nms = timed(girih.config(girih.NAIVE), max(1, args.steps // 2), 1)
+        naive = lups * max(1, args.steps // 2) * ws / (nms * 1e-3) * 1e-9
+
+    # roofline of the dominant kernel (every launch of the timed region is the blocked kernel,
+    # except the exchange kernel for odd T, which the default workloads do not have)
+    launches = p.launch_count(cfg)
+    peaks, src = _peaks()
+    elem = 8 if dtype == "f64" else 4
+    per_gpu = lups * args.steps / (ms * 1e-3)
+    if dtype == "f64":
+        # FP64 pipe: 152 SMs x 2 DFMA per clock (1.25 TFLOP/s nominal) at the maximum SM clock
+        peak_inst = 152 * 2 * float(peaks.get("sm_max_mhz", 2070.0)) * 1e6
+        achieved = per_gpu * INSTR_PER_LUP[stencil]
+        roof = {"bound": "alu", "achieved": achieved * 1e-12, "peak": peak_inst * 1e-12,
+                "unit": "TFLOP/s", "frac": achieved / peak_inst, "traffic": None,
+                "note": "FP64 instructions/s (one per explicitly rounded op, 7 or 28 per LUP) vs 152 SMs x 2 DFMA/clk "
+                        f"x max SM clock ({src} peaks file clock); HBM is not the bound"}
+    else:
+        bc = (girih.model_code_balance(cfg.dw, inputs.RADIUS[stencil], ND[stencil], elem)
+              if cfg.algo == girih.MWD else SPATIAL_ELEMS[stencil] * elem)
+        achieved = per_gpu * bc
+        roof = {"bound": "hbm", "achieved": achieved * 1e-9, "peak": float(peaks["hbm_gbs"]), "unit": "GB/s",
+                "frac": achieved * 1e-9 / float(peaks["hbm_gbs"]), "traffic": None,
+                "note": f"algorithmic bytes = model code balance {bc:.2f} B/LUP x LUPs ({src} HBM peak)"}
+
+    e2e = None
+    if not args.no_e2e:
+        hu = torch.empty(u.shape, dtype=tdt, pin_memory=True)
+        hup = torch.empty(u.shape, dtype=tdt, pin_memory=True)
+        hco = torch.empty(co.shape, dtype=tdt, pin_memory=True) if co is not None else None
+        hu.copy_(u)
+        hup.copy_(up)
+        if hco is not None:
+            hco.copy_(co)
+        girih.run_host(p, hu, hup, hco, c=c, stream=stream)  # warm-up (allocates the staging buffers)
+        barrier()
+        t0 = time.perf_counter()
+        n_e2e = max(1, min(args.steps, 3))
+        for _ in range(n_e2e):
+            girih.run_host(p, hu, hup, hco, c=c, stream=stream)
+        barrier()
+        et = time.perf_counter() - t0
+        if ws > 1:
+            t = torch.tensor([et], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            et = float(t.item())
+        nbytes = u.numel() * elem
+        e2e = {"value": lups * n_e2e * ws / et * 1e-9, "unit": "GLUP/s",
+               "h2d_bytes_per_step": 2 * nbytes + (co.numel() * elem if co is not None else 0),
+               "d2h_bytes_per_step": 2 * nbytes}
+        del hu, hup, hco
+
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu:
+        del u, up, co
+        torch.cuda.empty_cache()
+        cpu = cpu_baseline(stencil, nx, ny, nz)
+
+    if rank == 0:
+        line = {
+            "metric": "GLUP/s", "value": value, "unit": "GLUP/s", "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": dtype, "data": "synthetic",
+            "config": {"workload": args.workload, "stencil": STENCIL_NAME[stencil], "nx": nx, "ny": ny, "nz": nz,
+                       "T": T, "algo": "mwd" if cfg.algo == girih.MWD else "naive", "kernel_config": cfg.as_dict(),
+                       "l2": "inputs larger than L2 (each grid > 126 MB)", "parallelism": f"replicas x{ws}"},
+            "naive_glups": naive, "speedup_vs_naive": (value / naive) if naive else None,
+            "gpu_launches": launches * args.steps,
+            "roofline": roof, "clocks": clocks, "e2e": e2e, "cpu_baseline": cpu,
+        }
+        print(json.dumps(line))
+    if ws > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

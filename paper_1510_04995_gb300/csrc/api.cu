@@ -52,11 +52,11 @@ void mwd_row_span(int64_t rho, int dw, int64_t ny, int64_t* a_min, int64_t* ndia
   *ndiam = std::max<int64_t>(hi - lo + 1, 0);
 }
 
+// x slab per block: nx split evenly over the cluster, rounded up to a multiple of 16 elements
+// (blocks past the end of the grid stay idle but take part in the cluster barriers).
 static int slab_width(int64_t nx, int C) {
-  int64_t w = (nx + C - 1) / C;
-  int64_t p = 32;
-  while (p < w) p *= 2;
-  return (int)p;
+  const int64_t w = (nx + C - 1) / C;
+  return (int)((w + 15) / 16 * 16);
 }
 
 int check_config(const Plan* p, const girih_config* c, int64_t* smem_out, int* xw_out) {
@@ -76,8 +76,6 @@ int check_config(const Plan* p, const girih_config* c, int64_t* smem_out, int* x
   if (c->threads < 64 || c->threads > 512 || c->threads % 32 != 0)
     return fail(GIRIH_EINVAL, "threads=%d must be a multiple of 32 in 64..512", c->threads);
   const int XW = slab_width(p->nx, c->cluster);
-  if (c->cluster > 1 && (int64_t)XW * (c->cluster - 1) >= p->nx)
-    return fail(GIRIH_EINVAL, "cluster=%d leaves an empty x slab for nx=%lld", c->cluster, (long long)p->nx);
   if (p->ny > (1 << 28) || p->nx > (1 << 28) || p->nz > (1 << 28))
     return fail(GIRIH_EINVAL, "grid too large for the blocked kernel");
   const MwdShape sh = mwd_shape(p->stencil, p->dtype, c->dw, c->nf, XW);

@@ -20,10 +20,7 @@ HALO = -1000
 
 def slab_width(nx, C):
     w = -(-nx // C)
-    p = 32
-    while p < w:
-        p *= 2
-    return p
+    return -(-w // 16) * 16
 
 
 def shape(R, dw, nf, XW):

@@ -35,9 +35,9 @@ def _ref(stencil, nx, ny, nz, T, seed=3):
 
 MWD_CFGS = {
     1: [dict(dw=4, nf=1, cluster=1, threads=128), dict(dw=8, nf=2, cluster=2, threads=256),
-        dict(dw=16, nf=1, cluster=4, threads=512), dict(dw=6, nf=3, cluster=2, threads=64)],
-    4: [dict(dw=8, nf=1, cluster=1, threads=256), dict(dw=16, nf=2, cluster=2, threads=256),
-        dict(dw=24, nf=1, cluster=4, threads=128)],
+        dict(dw=16, nf=1, cluster=8, threads=512), dict(dw=6, nf=3, cluster=2, threads=64)],
+    4: [dict(dw=8, nf=1, cluster=4, threads=256), dict(dw=16, nf=1, cluster=8, threads=256),
+        dict(dw=8, nf=2, cluster=8, threads=128), dict(dw=16, nf=2, cluster=16, threads=64)],
 }
 
 
@@ -110,7 +110,7 @@ def test_padded_leading_dimension(stencil):
     u, up, co, c = inputs.make_problem(stencil, nx, ny, nz, seed=9, ldx=ldx)
     ru, rup = u.copy(), up.copy()
     oracle.sweep(stencil, ru, rup, co, c, T, nx, ny, nz)
-    for cfg in (girih.config(girih.NAIVE), girih.config(girih.MWD, dw=4 * R, nf=1, cluster=2, threads=128)):
+    for cfg in (girih.config(girih.NAIVE), girih.config(girih.MWD, dw=2 * R, nf=1, cluster=2, threads=128)):
         gu, _ = gpu_sweep(stencil, "f64", u, up, co, c, T, nx, ny, nz, cfg, ldx=ldx)
         assert normwise(gu[:, :, :nx + 2 * R], ru[:, :, :nx + 2 * R], R) <= 1e-12
         assert np.array_equal(gu[:, :, nx + 2 * R:], u[:, :, nx + 2 * R:])  # padding untouched

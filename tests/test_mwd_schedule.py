@@ -14,6 +14,8 @@ CASES = [
     (4, True, 70, 29, 12, 5, 8, 1, 1),
     (4, True, 70, 35, 11, 9, 16, 2, 2),
     (4, True, 44, 30, 10, 6, 24, 1, 4),
+    (4, True, 70, 29, 9, 7, 16, 1, 8),
+    (1, False, 70, 12, 5, 6, 4, 1, 16),
     (4, True, 5, 7, 3, 5, 8, 1, 1),
 ]
 
