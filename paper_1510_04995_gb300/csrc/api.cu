@@ -73,9 +73,15 @@ int check_config(const Plan* p, const girih_config* c, int64_t* smem_out, int* x
   if (c->nf < 1 || c->nf > 4) return fail(GIRIH_EINVAL, "nf=%d outside 1..4", c->nf);
   if (!(c->cluster == 1 || c->cluster == 2 || c->cluster == 4 || c->cluster == 8 || c->cluster == 16))
     return fail(GIRIH_EINVAL, "cluster=%d not in {1,2,4,8,16}", c->cluster);
-  if (c->threads < 64 || c->threads > 512 || c->threads % 32 != 0)
-    return fail(GIRIH_EINVAL, "threads=%d must be a multiple of 32 in 64..512", c->threads);
+  if (c->threads < 64 || c->threads > 1024 || c->threads % 32 != 0)
+    return fail(GIRIH_EINVAL, "threads=%d must be a multiple of 32 in 64..1024", c->threads);
   const int XW = slab_width(p->nx, c->cluster);
+  const int G = mwd_pairs_per_thread(R, c->dw, XW, c->threads);
+  if (G == 0)
+    return fail(GIRIH_EINVAL, "dw=%d with a %d-wide slab has %d row pairs, more than 4 per thread of %d", c->dw, XW,
+                mwd_max_pairs(R, c->dw) * XW, c->threads);
+  if (p->dtype == GIRIH_F64 && R == 4 && G > 2)
+    return fail(GIRIH_EINVAL, "25-point FP64 tiles allow at most 2 row pairs per thread (registers)");
   if (p->ny > (1 << 28) || p->nx > (1 << 28) || p->nz > (1 << 28))
     return fail(GIRIH_EINVAL, "grid too large for the blocked kernel");
   const MwdShape sh = mwd_shape(p->stencil, p->dtype, c->dw, c->nf, XW);
@@ -83,7 +89,7 @@ int check_config(const Plan* p, const girih_config* c, int64_t* smem_out, int* x
     return fail(GIRIH_EINVAL, "config needs %lld bytes of shared memory per block (device limit %lld)",
                 (long long)sh.smem_bytes, (long long)p->smem_optin);
   int maxc = 0;
-  cudaError_t e = mwd_prepare(p->stencil, p->dtype, c->cluster, c->threads, sh.smem_bytes, &maxc);
+  cudaError_t e = mwd_prepare(p->stencil, p->dtype, c->cluster, c->threads, G, sh.smem_bytes, &maxc);
   if (e != cudaSuccess) {
     cudaGetLastError();
     return fail(GIRIH_EINVAL, "cluster of %d blocks with %lld bytes cannot be configured: %s", c->cluster,
@@ -103,7 +109,7 @@ static girih_config default_config(Plan* p) {
   const int R = p->R;
   for (int C : {1, 2, 4, 8, 16}) {
     for (int dw = 2 * R; dw <= 64 * R; dw += 2 * R) {
-      girih_config c{GIRIH_ALGO_MWD, dw, 1, C, 256, GIRIH_FED};
+      girih_config c{GIRIH_ALGO_MWD, dw, 1, C, 512, GIRIH_FED};
       int64_t smem = 0;
       if (check_config(p, &c, &smem, nullptr) != GIRIH_OK) continue;
       if (dw > best_dw && dw <= (R == 1 ? 16 : 32)) {
@@ -161,7 +167,8 @@ int run_sweep(Plan* p, int64_t T, void* u, void* u_prev, const void* coeffs, con
       if (nd == 0) continue;
       a.rho = (int32_t)rho;
       a.a_min = (int32_t)a_min;
-      e = launch_mwd_row(p->stencil, p->dtype, a, (int)nd, cfg.threads, st);
+      e = launch_mwd_row(p->stencil, p->dtype, a, (int)nd, cfg.threads,
+                         mwd_pairs_per_thread(p->R, cfg.dw, XW, cfg.threads), st);
     }
   }
   if (e == cudaSuccess && T % 2 == 1) e = launch_swap(u, u_prev, p->gstride * p->elem, st);

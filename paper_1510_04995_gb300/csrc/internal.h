@@ -48,10 +48,15 @@ struct MwdShape {
 };
 MwdShape mwd_shape(int stencil, int dtype, int dw, int nf, int XW);
 // Launch one diamond row: ndiam tiles, each a cluster of a.C blocks of `threads` threads.
-cudaError_t launch_mwd_row(int stencil, int dtype, const MwdArgs& a, int ndiam, int threads, cudaStream_t st);
+// G = row pairs per thread (1, 2 or 4), from mwd_pairs_per_thread.
+cudaError_t launch_mwd_row(int stencil, int dtype, const MwdArgs& a, int ndiam, int threads, int G, cudaStream_t st);
 // Configure kernel attributes (dynamic shared memory, non-portable clusters); returns the max
 // active clusters the device reports for the configuration (0 = cannot be scheduled).
-cudaError_t mwd_prepare(int stencil, int dtype, int C, int threads, int64_t smem, int* max_clusters);
+cudaError_t mwd_prepare(int stencil, int dtype, int C, int threads, int G, int64_t smem, int* max_clusters);
+int mwd_max_pairs(int R, int dw);
+int mwd_pairs_per_thread(int R, int dw, int XW, int threads);
+// Planes are staged this many wavefront steps ahead of use.
+#define MWD_PREFETCH 2
 
 // In-place exchange of two device arrays (odd T puts level T back into u).
 cudaError_t launch_swap(void* a, void* b, int64_t bytes, cudaStream_t st);

@@ -29,24 +29,22 @@
 
 namespace girih {
 
+// Accessor of one row of a row pair: z neighbours and the centre come from the thread's own
+// register window (w[R] = centre), y neighbours from the pair's shared loads (yl), x neighbours
+// and the level t-1 centre from the shared ring.
 template <int S, typename T>
-struct MwdAcc {
-  const T* V;        // level t buffer of the ring
-  const T* U;        // level t-1 buffer of the ring (second order)
+struct PairAcc {
+  const T* w;        // window of this row, planes z-R..z+R
+  const T* yv;       // y neighbours: yv[R + d] = value at row y + d (d != 0)
+  const T* X;        // pointer to the centre in the level-t ring buffer
+  T uc;
   const T* coef;
-  int64_t gs, p;     // coefficient grid stride, padded global index of the point
-  int pe, xt, NZ;    // plane elems, row pitch, ring depth
-  int sl, off;       // ring slot of the point's plane, offset of the point within a plane
-  __device__ __forceinline__ int slot(int d) const {
-    int s = sl + d;
-    s = (s < 0) ? s + NZ : s;
-    return (s >= NZ) ? s - NZ : s;
-  }
-  __device__ __forceinline__ T c() const { return V[sl * pe + off]; }
-  __device__ __forceinline__ T x(int d) const { return V[sl * pe + off + d]; }
-  __device__ __forceinline__ T y(int d) const { return V[sl * pe + off + d * xt]; }
-  __device__ __forceinline__ T z(int d) const { return V[slot(d) * pe + off]; }
-  __device__ __forceinline__ T u() const { return U[sl * pe + off]; }
+  int64_t gs, p;
+  __device__ __forceinline__ T c() const { return w[Traits<S>::R]; }
+  __device__ __forceinline__ T x(int d) const { return X[d]; }
+  __device__ __forceinline__ T y(int d) const { return yv[Traits<S>::R + d]; }
+  __device__ __forceinline__ T z(int d) const { return w[Traits<S>::R + d]; }
+  __device__ __forceinline__ T u() const { return uc; }
   __device__ __forceinline__ T k(int g) const { return __ldg(coef + g * gs + p); }
 };
 
@@ -56,10 +54,20 @@ __device__ __forceinline__ int lev_lo_of(int a, int b, int dw, int R, int t) {
 __device__ __forceinline__ int lev_hi_of(int a, int b, int dw, int R, int t) {
   return min((a + 1) * dw - R * t, (b + 1) * dw + R * t);
 }
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait_group() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
 
-template <int S, typename T>
-__global__ void __launch_bounds__(512) mwd_fed_kernel(const MwdArgs A) {
+// G = row pairs owned per thread.  Each pair (level s, rows y0 and y0+1, column xl) is owned
+// by one thread for the whole launch (fixed execution to data), which keeps the two rows'
+// z windows in registers across wavefront steps: per step and plane, a pair loads 2 new z
+// values, 2R rows of y neighbours shared by both rows, 2R x neighbours per row, and stores 2.
+template <int S, typename T, int G>
+__global__ void __launch_bounds__(1024 / G) mwd_fed_kernel(const MwdArgs A) {
   constexpr int R = Traits<S>::R;
+  constexpr int PD = MWD_PREFETCH;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* sm = reinterpret_cast<T*>(smem_raw);
   const int NZ = A.NZ, YW = A.YW, XT = A.XT, XW = A.XW, C = A.C, nf = A.nf, K = A.K;
@@ -67,7 +75,8 @@ __global__ void __launch_bounds__(512) mwd_fed_kernel(const MwdArgs A) {
   const int be = NZ * pe;
   int* lev_lo = reinterpret_cast<int*>(sm + 2 * be);
   int* lev_w = lev_lo + A.H;
-  int* row_mask = lev_w + A.H;
+  int* lev_pp = lev_w + A.H;  // prefix count of row pairs per level
+  int* row_mask = lev_pp + A.H + 1;
 
   const int nx = (int)A.g.nx, ny = (int)A.g.ny, nz = (int)A.g.nz;
   const int64_t ldx = A.g.ldx, sy = A.g.sy, gplane = sy * ldx;
@@ -86,12 +95,18 @@ __global__ void __launch_bounds__(512) mwd_fed_kernel(const MwdArgs A) {
   const int nlev = te - tb + 1, smax = nlev - 1;
   const int NT = blockDim.x, tid = threadIdx.x;
 
-  for (int s = tid; s < nlev; s += NT) {
-    const int t = tb + s;
-    const int lo = max(lev_lo_of(a, b, dw, R, t), 0);
-    const int hi = min(lev_hi_of(a, b, dw, R, t), ny);
-    lev_lo[s] = lo;
-    lev_w[s] = max(hi - lo, 0);
+  if (tid == 0) {
+    int acc = 0;
+    for (int s = 0; s < nlev; ++s) {
+      const int t = tb + s;
+      const int lo = max(lev_lo_of(a, b, dw, R, t), 0);
+      const int hi = min(lev_hi_of(a, b, dw, R, t), ny);
+      lev_lo[s] = lo;
+      lev_w[s] = max(hi - lo, 0);
+      lev_pp[s] = acc;
+      acc += (max(hi - lo, 0) + 1) / 2;
+    }
+    lev_pp[nlev] = acc;
   }
   for (int yy = tid; yy < YW; yy += NT) {
     const int y = Y0 + yy;
@@ -117,8 +132,6 @@ __global__ void __launch_bounds__(512) mwd_fed_kernel(const MwdArgs A) {
 #pragma unroll
   for (int i = 0; i < 5; ++i) cst[i] = static_cast<T>(A.c[i]);
 
-  // Rows and columns of the padded grid this block stages: y in [Y0, Y0+YW) clipped to the
-  // padded grid, x in [x0-R, x0+xw+R) (slab plus x halo).
   const int ylo = max(Y0, -R), yhi = min(Y0 + YW, ny + R);
   const int nrow = max(yhi - ylo, 0);
   const int ncol = (xw > 0) ? xw + 2 * R : 0;
@@ -128,7 +141,8 @@ __global__ void __launch_bounds__(512) mwd_fed_kernel(const MwdArgs A) {
     const int slot = (z + R) % NZ;
     const int per = nrow * ncol;
     for (int i = tid; i < 2 * per; i += NT) {
-      const int p = i / per, rem = i - p * per;
+      const int p = i >= per;
+      const int rem = i - p * per;
       const int r = rem / ncol, xx = rem - r * ncol;
       const int y = ylo + r;
       const int64_t gi = (int64_t)(z + R) * gplane + (int64_t)(y + R) * ldx + (x0 + xx);
@@ -155,8 +169,28 @@ __global__ void __launch_bounds__(512) mwd_fed_kernel(const MwdArgs A) {
   };
 
   __syncthreads();  // level tables ready
-  for (int z = -R; z < nf + R; ++z) load_plane(z);
-  cp_async_wait_all();
+
+  // this thread's row pairs: level s, first row y0 (second row y0+1 may lie outside the level)
+  int gs_[G], gy_[G], gx_[G];
+  bool gv_[G];
+  const int npairs = lev_pp[nlev];
+#pragma unroll
+  for (int g = 0; g < G; ++g) {
+    const int id = tid + g * NT;
+    const int pr = id / XW, xl = id - pr * XW;
+    gv_[g] = (pr < npairs) && (xl < xw);
+    int s = 0;
+    if (pr < npairs)
+      while (lev_pp[s + 1] <= pr) ++s;
+    gs_[g] = s;
+    gy_[g] = (pr < npairs) ? lev_lo[s] + 2 * (pr - lev_pp[s]) : 0;
+    gx_[g] = xl;
+  }
+  T win[G][2][2 * R + 1];
+
+  for (int z = -R; z < PD * nf + R; ++z) load_plane(z);
+  cp_async_commit();
+  cp_async_wait_group<0>();
   sync_all();
 
   const uint32_t sm_base = smem_addr(sm);
@@ -165,48 +199,89 @@ __global__ void __launch_bounds__(512) mwd_fed_kernel(const MwdArgs A) {
 
   const int W = (nz + smax * K + nf - 1) / nf;
   for (int w = 0; w < W; ++w) {
-    if (xw > 0) {
-      for (int f = 0; f < nf; ++f) load_plane((w + 1) * nf + R + f);
-      if (w > 0)
-        for (int f = 0; f < nf; ++f) write_plane((w - 1) * nf - smax * K + f);
-      // compute: all active levels of this step, items linearised over (level, row, plane, x)
-      int base = 0, it = tid;
-      for (int s = 0; s < nlev; ++s) {
-        const int zb = w * nf - s * K;
-        if (zb + nf <= 0 || zb >= nz) continue;
-        const int n = lev_w[s] * nf * XW;
-        const int t = tb + s;
-        const int pin = t & 1, pout = pin ^ 1;
-        const int ylo_s = lev_lo[s];
-        for (; it < base + n; it += NT) {
-          const int i = it - base;
-          const int xl = i % XW, r2 = i / XW;
-          const int f = r2 % nf, row = r2 / nf;
-          const int z = zb + f;
-          if (xl >= xw || z < 0 || z >= nz) continue;
-          const int y = ylo_s + row;
-          const int sl = (z + R) % NZ;
-          const int off = (y - Y0) * XT + xl + R;
-          const int64_t gp = (int64_t)(z + R) * gplane + (int64_t)(y + R) * ldx + (x0 + xl + R);
-          MwdAcc<S, T> acc{sm + pin * be, sm + pout * be, coef, A.g.gstride, gp, pe, XT, NZ, sl, off};
-          const T res = point_update<S, T>(acc, cst);
-          const int so = pout * be + sl * pe + off;
-          sm[so] = res;
-          if (C > 1) {
-            if (xl < R && rank > 0)  // my left edge is the left neighbour's right halo
-              st_cluster(left_base + (uint32_t)((so + XW) * (int)sizeof(T)), res);
-            if (xl >= XW - R && rank < C - 1)  // my right edge is the right neighbour's left halo
-              st_cluster(right_base + (uint32_t)((so - XW) * (int)sizeof(T)), res);
+    for (int f = 0; f < nf; ++f) load_plane((w + PD) * nf + R + f);
+    cp_async_commit();
+    if (w > 0)
+      for (int f = 0; f < nf; ++f) write_plane((w - 1) * nf - smax * K + f);
+#pragma unroll
+    for (int g = 0; g < G; ++g) {
+      if (!gv_[g]) continue;
+      const int s = gs_[g];
+      const int t = tb + s;
+      const int pin = t & 1, pout = pin ^ 1;
+      const int y0 = gy_[g], xl = gx_[g];
+      const int hi = lev_lo[s] + lev_w[s];
+      const bool row1 = (y0 + 1) < hi;
+      const int yy0 = y0 - Y0;
+      const T* Vb = sm + pin * be;
+      T* Ub = sm + pout * be;
+      for (int f = 0; f < nf; ++f) {
+        const int z = w * nf - s * K + f;
+        if (z < 0 || z >= nz) continue;
+        const int sl = (z + R) % NZ;
+        const int col = yy0 * XT + xl + R;  // offset of row y0 within a plane
+        if (z == 0) {  // first plane of this level: fill the whole window
+#pragma unroll
+          for (int d = -R; d <= R; ++d) {
+            int sd = sl + d;
+            sd = sd < 0 ? sd + NZ : (sd >= NZ ? sd - NZ : sd);
+            win[g][0][R + d] = Vb[sd * pe + col];
+            win[g][1][R + d] = Vb[sd * pe + col + XT];
+          }
+        } else {  // slide the window up by one plane
+          int sd = sl + R;
+          sd = sd >= NZ ? sd - NZ : sd;
+#pragma unroll
+          for (int d = 0; d < 2 * R; ++d) {
+            win[g][0][d] = win[g][0][d + 1];
+            win[g][1][d] = win[g][1][d + 1];
+          }
+          win[g][0][2 * R] = Vb[sd * pe + col];
+          win[g][1][2 * R] = Vb[sd * pe + col + XT];
+        }
+        const T* P = Vb + sl * pe + col;  // centre of row y0 at plane z
+        T yv0[2 * R + 1], yv1[2 * R + 1];  // y neighbours of row y0 and row y0+1
+#pragma unroll
+        for (int d = 1; d <= R; ++d) {
+          yv0[R - d] = P[-d * XT];
+          // row y0+1+R can lie one row past the tile when the second row is not updated
+          yv1[R + d] = (d < R || row1) ? P[(1 + d) * XT] : T(0);
+        }
+#pragma unroll
+        for (int d = 1; d <= R; ++d) {
+          yv0[R + d] = (d == 1) ? win[g][1][R] : yv1[R + d - 1];
+          yv1[R - d] = (d == 1) ? win[g][0][R] : yv0[R - d + 1];
+        }
+        const int64_t gp = (int64_t)(z + R) * gplane + (int64_t)(y0 + R) * ldx + (x0 + xl + R);
+        PairAcc<S, T> acc0{win[g][0], yv0, P, T(0), coef, A.g.gstride, gp};
+        if constexpr (Traits<S>::ORDER2) acc0.uc = Ub[sl * pe + col];
+        const T r0 = point_update<S, T>(acc0, cst);
+        T r1 = T(0);
+        if (row1) {
+          PairAcc<S, T> acc1{win[g][1], yv1, P + XT, T(0), coef, A.g.gstride, gp + ldx};
+          if constexpr (Traits<S>::ORDER2) acc1.uc = Ub[sl * pe + col + XT];
+          r1 = point_update<S, T>(acc1, cst);
+        }
+        const int so = pout * be + sl * pe + col;
+        sm[so] = r0;
+        if (row1) sm[so + XT] = r1;
+        if (C > 1) {
+          if (xl < R && rank > 0) {  // my left edge is the left neighbour's right halo
+            st_cluster(left_base + (uint32_t)((so + XW) * (int)sizeof(T)), r0);
+            if (row1) st_cluster(left_base + (uint32_t)((so + XT + XW) * (int)sizeof(T)), r1);
+          }
+          if (xl >= XW - R && rank < C - 1) {  // my right edge is the right neighbour's left halo
+            st_cluster(right_base + (uint32_t)((so - XW) * (int)sizeof(T)), r0);
+            if (row1) st_cluster(right_base + (uint32_t)((so + XT - XW) * (int)sizeof(T)), r1);
           }
         }
-        base += n;
       }
     }
-    cp_async_wait_all();
+    cp_async_wait_group<PD - 1>();
     sync_all();
   }
-  if (xw > 0)
-    for (int f = 0; f < nf; ++f) write_plane((W - 1) * nf - smax * K + f);
+  cp_async_wait_group<0>();
+  for (int f = 0; f < nf; ++f) write_plane((W - 1) * nf - smax * K + f);
 }
 
 MwdShape mwd_shape(int stencil, int dtype, int dw, int nf, int XW) {
@@ -214,31 +289,65 @@ MwdShape mwd_shape(int stencil, int dtype, int dw, int nf, int XW) {
   const int H = dw / R;
   const int K = R + nf;
   MwdShape s;
-  s.NZ = 2 * nf + R + (R > nf ? R : nf) + (H - 2) * K;
+  s.NZ = (MWD_PREFETCH + 1) * nf + R + (R > nf ? R : nf) + (H - 2) * K;
   s.YW = dw + 2 * R;
   s.XT = XW + 2 * R;
   const int elem = dtype == GIRIH_F64 ? 8 : 4;
-  s.smem_bytes = 2LL * s.NZ * s.YW * s.XT * elem + (2LL * H + s.YW) * 4;
+  s.smem_bytes = 2LL * s.NZ * s.YW * s.XT * elem + (3LL * H + 1 + s.YW) * 4;
   return s;
 }
 
-template <int S, typename T>
-static void* kernel_ptr() {
-  return reinterpret_cast<void*>(&mwd_fed_kernel<S, T>);
+// Row pairs of the widest (unclipped) diamond: levels k = 1..H-1 have 2R*min(k, H-k) rows.
+int mwd_max_pairs(int R, int dw) {
+  const int H = dw / R;
+  int n = 0;
+  for (int k = 1; k < H; ++k) n += R * (k < H - k ? k : H - k);
+  return n;
 }
 
-static void* pick(int stencil, int dtype) {
+// Pairs per thread for a configuration (1, 2 or 4), or 0 if the tile needs more.
+int mwd_pairs_per_thread(int R, int dw, int XW, int threads) {
+  const int64_t ng = (int64_t)mwd_max_pairs(R, dw) * XW;
+  for (int G : {1, 2, 4})
+    if (threads <= 1024 / G && ng <= (int64_t)G * threads) return G;
+  return 0;
+}
+
+template <int S, typename T, int G>
+static void* kernel_ptr_g() {
+  return reinterpret_cast<void*>(&mwd_fed_kernel<S, T, G>);
+}
+template <int S, typename T>
+static void* kernel_ptr(int G) {
+  return G == 1 ? kernel_ptr_g<S, T, 1>() : (G == 2 ? kernel_ptr_g<S, T, 2>() : kernel_ptr_g<S, T, 4>());
+}
+
+static void* pick(int stencil, int dtype, int G) {
   const bool f64 = dtype == GIRIH_F64;
   switch (stencil) {
-    case 0: return f64 ? kernel_ptr<0, double>() : kernel_ptr<0, float>();
-    case 1: return f64 ? kernel_ptr<1, double>() : kernel_ptr<1, float>();
-    case 2: return f64 ? kernel_ptr<2, double>() : kernel_ptr<2, float>();
-    default: return f64 ? kernel_ptr<3, double>() : kernel_ptr<3, float>();
+    case 0: return f64 ? kernel_ptr<0, double>(G) : kernel_ptr<0, float>(G);
+    case 1: return f64 ? kernel_ptr<1, double>(G) : kernel_ptr<1, float>(G);
+    case 2: return f64 ? kernel_ptr<2, double>(G) : kernel_ptr<2, float>(G);
+    default: return f64 ? kernel_ptr<3, double>(G) : kernel_ptr<3, float>(G);
   }
 }
 
-cudaError_t mwd_prepare(int stencil, int dtype, int C, int threads, int64_t smem, int* max_clusters) {
-  const void* k = pick(stencil, dtype);
+static cudaLaunchConfig_t launch_config(int C, int threads, int64_t smem, cudaLaunchAttribute* attr) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)C, 1, 1);
+  cfg.blockDim = dim3((unsigned)threads, 1, 1);
+  cfg.dynamicSmemBytes = (size_t)smem;
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = (unsigned)C;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cfg;
+}
+
+cudaError_t mwd_prepare(int stencil, int dtype, int C, int threads, int G, int64_t smem, int* max_clusters) {
+  const void* k = pick(stencil, dtype, G);
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   if (C > 8) {
@@ -246,17 +355,8 @@ cudaError_t mwd_prepare(int stencil, int dtype, int C, int threads, int64_t smem
     if (e != cudaSuccess) return e;
   }
   if (max_clusters) {
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3(C, 1, 1);
-    cfg.blockDim = dim3(threads, 1, 1);
-    cfg.dynamicSmemBytes = (size_t)smem;
     cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeClusterDimension;
-    attr[0].val.clusterDim.x = C;
-    attr[0].val.clusterDim.y = 1;
-    attr[0].val.clusterDim.z = 1;
-    cfg.attrs = attr;
-    cfg.numAttrs = 1;
+    cudaLaunchConfig_t cfg = launch_config(C, threads, smem, attr);
     int n = 0;
     e = cudaOccupancyMaxActiveClusters(&n, k, &cfg);
     if (e != cudaSuccess) return e;
@@ -265,27 +365,15 @@ cudaError_t mwd_prepare(int stencil, int dtype, int C, int threads, int64_t smem
   return cudaSuccess;
 }
 
-cudaError_t launch_mwd_row(int stencil, int dtype, const MwdArgs& a, int ndiam, int threads, cudaStream_t st) {
+cudaError_t launch_mwd_row(int stencil, int dtype, const MwdArgs& a, int ndiam, int threads, int G, cudaStream_t st) {
   const MwdShape sh = mwd_shape(stencil, dtype, a.dw, a.nf, a.XW);
-  cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3((unsigned)(ndiam * a.C), 1, 1);
-  cfg.blockDim = dim3((unsigned)threads, 1, 1);
-  cfg.dynamicSmemBytes = (size_t)sh.smem_bytes;
-  cfg.stream = st;
   cudaLaunchAttribute attr[1];
-  attr[0].id = cudaLaunchAttributeClusterDimension;
-  attr[0].val.clusterDim.x = (unsigned)a.C;
-  attr[0].val.clusterDim.y = 1;
-  attr[0].val.clusterDim.z = 1;
-  cfg.attrs = attr;
-  cfg.numAttrs = 1;
-  const bool f64 = dtype == GIRIH_F64;
-  switch (stencil) {
-    case 0: return f64 ? cudaLaunchKernelEx(&cfg, mwd_fed_kernel<0, double>, a) : cudaLaunchKernelEx(&cfg, mwd_fed_kernel<0, float>, a);
-    case 1: return f64 ? cudaLaunchKernelEx(&cfg, mwd_fed_kernel<1, double>, a) : cudaLaunchKernelEx(&cfg, mwd_fed_kernel<1, float>, a);
-    case 2: return f64 ? cudaLaunchKernelEx(&cfg, mwd_fed_kernel<2, double>, a) : cudaLaunchKernelEx(&cfg, mwd_fed_kernel<2, float>, a);
-    default: return f64 ? cudaLaunchKernelEx(&cfg, mwd_fed_kernel<3, double>, a) : cudaLaunchKernelEx(&cfg, mwd_fed_kernel<3, float>, a);
-  }
+  cudaLaunchConfig_t cfg = launch_config(a.C, threads, sh.smem_bytes, attr);
+  cfg.gridDim = dim3((unsigned)(ndiam * a.C), 1, 1);
+  cfg.stream = st;
+  const void* k = pick(stencil, dtype, G);
+  void* args[] = {const_cast<MwdArgs*>(&a)};
+  return cudaLaunchKernelExC(&cfg, k, args);
 }
 
 }  // namespace girih

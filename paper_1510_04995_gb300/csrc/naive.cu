@@ -4,7 +4,8 @@
 // every block owns a 32 x ROWS column of x-y cells over a chunk of z planes.  Each thread keeps
 // its column's 2R+1 values along z in registers (rotated as the block walks up in z), the current
 // z plane of the block (plus an R-wide halo) is staged in shared memory for the x and y
-// neighbours, and the next plane's value is prefetched one iteration ahead.  Every input is read
+// neighbours (double-buffered, one barrier per plane), and the column's next planes are
+// prefetched several iterations ahead into a register queue so that enough loads are in flight.  Every input is read
 // from HBM once per step (halo re-reads hit L2), every output written once: 2s bytes per LUP
 // for the 7-point constant stencil, s = element size.
 #include <algorithm>
@@ -16,7 +17,7 @@ namespace girih {
 
 template <int S, typename T, int ROWS>
 struct NaiveAcc {
-  const T (*tile)[32 + 2 * Traits<S>::R];
+  T (*tile)[32 + 2 * Traits<S>::R];
   const T* w;        // register window, w[R] = centre
   const T* coef;
   int64_t gs, p;     // grid stride, padded linear index of the point
@@ -30,11 +31,13 @@ struct NaiveAcc {
   __device__ __forceinline__ T k(int g) const { return __ldg(coef + g * gs + p); }
 };
 
-template <int S, typename T, int ROWS>
+template <int S, typename T, int ROWS, int PD>
 __global__ void __launch_bounds__(32 * ROWS) naive_kernel(const NaiveArgs a) {
   constexpr int R = Traits<S>::R;
   constexpr int TXW = 32 + 2 * R, TYW = ROWS + 2 * R;
-  __shared__ T tile[TYW][TXW];
+  constexpr int NH = 2 * R * (32 + ROWS);                 // halo cells of the tile (star stencil)
+  constexpr int HPT = (NH + 32 * ROWS - 1) / (32 * ROWS);  // halo cells per thread
+  __shared__ T tile[2][TYW][TXW];                           // double-buffered: one barrier per plane
   const T* __restrict__ V = static_cast<const T*>(a.V);
   T* __restrict__ U = static_cast<T*>(a.U);
   const T* __restrict__ coef = static_cast<const T*>(a.coef);
@@ -51,20 +54,17 @@ __global__ void __launch_bounds__(32 * ROWS) naive_kernel(const NaiveArgs a) {
   const int64_t z0 = (int64_t)blockIdx.z * a.zc;
   const int64_t z1 = min(z0 + (int64_t)a.zc, nz);
   const int64_t col = (y + R) * ldx + (x + R);  // offset of this column within a plane
+  const int64_t zlast = z1 - 1 + 2 * R;         // last padded plane this block reads
 
-  T w[2 * R + 1];
+  // this thread's halo cells (fixed for the whole z walk)
+  int hoff[HPT];
+  int64_t hcol[HPT];
 #pragma unroll
-  for (int i = 0; i < 2 * R; ++i) w[i] = inb ? V[(z0 + i) * plane + col] : T(0);
-  w[2 * R] = inb ? V[(z0 + 2 * R) * plane + col] : T(0);
-
-  constexpr int NH = 2 * R * (32 + ROWS);  // halo cells of the tile (star stencil: no corners)
-  for (int64_t z = z0; z < z1; ++z) {
-    // prefetch the column value entering the window at the next plane
-    const T nxt = (inb && z + 1 < z1) ? V[(z + 1 + 2 * R) * plane + col] : T(0);
-    __syncthreads();
-    tile[ty + R][tx + R] = w[R];
-    for (int i = tid; i < NH; i += 32 * ROWS) {
-      int hx, hy;
+  for (int k = 0; k < HPT; ++k) {
+    const int i = tid + k * 32 * ROWS;
+    int hx = 0, hy = 0;
+    bool ok = i < NH;
+    if (ok) {
       if (i < 2 * R * 32) {
         const int r = i / 32;
         hx = R + (i % 32);
@@ -75,18 +75,54 @@ __global__ void __launch_bounds__(32 * ROWS) naive_kernel(const NaiveArgs a) {
         hx = (cc < R) ? cc : 32 + cc;
       }
       const int64_t px = (int64_t)blockIdx.x * 32 + hx, py = (int64_t)blockIdx.y * ROWS + hy;
-      tile[hy][hx] = (px < nx + 2 * R && py < ny + 2 * R) ? V[(z + R) * plane + py * ldx + px] : T(0);
+      ok = px < nx + 2 * R && py < ny + 2 * R;
+      hcol[k] = ok ? py * ldx + px : -1;
+    } else {
+      hcol[k] = -1;
     }
+    hoff[k] = (i < NH) ? hy * TXW + hx : -1;
+  }
+
+  // register window w (padded planes z..z+2R for interior plane z) and a queue of PD planes ahead:
+  // PD outstanding loads per thread keep enough bytes in flight to saturate HBM.
+  T w[2 * R + 1], q[PD], hv[HPT];
+#pragma unroll
+  for (int i = 0; i <= 2 * R; ++i) w[i] = inb ? V[(z0 + i) * plane + col] : T(0);
+#pragma unroll
+  for (int i = 0; i < PD; ++i) {
+    const int64_t pz = z0 + 2 * R + 1 + i;
+    q[i] = (inb && pz <= zlast) ? V[pz * plane + col] : T(0);
+  }
+#pragma unroll
+  for (int k = 0; k < HPT; ++k) hv[k] = (hcol[k] >= 0) ? V[(z0 + R) * plane + hcol[k]] : T(0);
+
+  int buf = 0;
+  for (int64_t z = z0; z < z1; ++z) {
+    T(*tl)[TXW] = tile[buf];
+    tl[ty + R][tx + R] = w[R];
+#pragma unroll
+    for (int k = 0; k < HPT; ++k)
+      if (hoff[k] >= 0) (&tl[0][0])[hoff[k]] = hv[k];
+    // prefetch the next plane's halo cells
+#pragma unroll
+    for (int k = 0; k < HPT; ++k) hv[k] = (hcol[k] >= 0 && z + 1 < z1) ? V[(z + 1 + R) * plane + hcol[k]] : T(0);
     __syncthreads();
     if (active) {
       const int64_t p = (z + R) * plane + col;
-      NaiveAcc<S, T, ROWS> acc{tile, w, coef, a.g.gstride, p, tx, ty, T(0)};
+      NaiveAcc<S, T, ROWS> acc{tl, w, coef, a.g.gstride, p, tx, ty, T(0)};
       if constexpr (Traits<S>::ORDER2) acc.uc = U[p];
       U[p] = point_update<S, T>(acc, cst);
     }
 #pragma unroll
     for (int i = 0; i < 2 * R; ++i) w[i] = w[i + 1];
-    w[2 * R] = nxt;
+    w[2 * R] = q[0];
+#pragma unroll
+    for (int i = 0; i < PD - 1; ++i) q[i] = q[i + 1];
+    {
+      const int64_t pz = z + 2 * R + 1 + PD;
+      q[PD - 1] = (inb && pz <= zlast) ? V[pz * plane + col] : T(0);
+    }
+    buf ^= 1;
   }
 }
 
@@ -99,7 +135,7 @@ static cudaError_t launch_one(const NaiveArgs& a, cudaStream_t st) {
   dim3 block(32, kRows);
   dim3 grid((unsigned)((a.g.nx + 31) / 32), (unsigned)((a.g.ny + kRows - 1) / kRows),
             (unsigned)((a.g.nz + a.zc - 1) / a.zc));
-  naive_kernel<S, T, kRows><<<grid, block, 0, st>>>(a);
+  naive_kernel<S, T, kRows, (sizeof(T) == 8 ? 3 : 4)><<<grid, block, 0, st>>>(a);
   return cudaGetLastError();
 }
 

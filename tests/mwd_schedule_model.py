@@ -23,10 +23,13 @@ def slab_width(nx, C):
     return -(-w // 16) * 16
 
 
+PD = 2  # planes are staged this many steps ahead (cp.async groups, wait_group PD-1)
+
+
 def shape(R, dw, nf, XW):
     H = dw // R
     K = R + nf
-    NZ = 2 * nf + R + max(R, nf) + (H - 2) * K
+    NZ = (PD + 1) * nf + R + max(R, nf) + (H - 2) * K
     return NZ, dw + 2 * R, XW + 2 * R
 
 
@@ -138,15 +141,20 @@ def simulate(R, second_order, nx, ny, nz, T, dw, nf, C):
             assert tagv == want or tagv == HALO, (tagv, want)
 
         for tl in tiles:
+            tl["inflight"] = []  # (issue step, cells) of cp.async groups
+            tl["win"] = {}
             for rank in range(C):
-                for z in range(-R, nf + R):
+                for z in range(-R, PD * nf + R):
                     load_plane(tl, rank, z, set())
         for w in range(W):
             for tl in tiles:
                 loaded, wb_reads, reads, writes = set(), set(), {}, {}
                 for rank in range(C):
                     for f in range(nf):
-                        load_plane(tl, rank, (w + 1) * nf + R + f, loaded)
+                        load_plane(tl, rank, (w + PD) * nf + R + f, loaded)
+                tl["inflight"] = [(ws, c) for ws, c in tl["inflight"] if ws > w - PD] + [(w, loaded)]
+                busy = set().union(*[c for _, c in tl["inflight"]])
+                for rank in range(C):
                     if w > 0:
                         for f in range(nf):
                             write_plane(tl, rank, (w - 1) * nf - smax * K + f, wb_reads)
@@ -163,9 +171,11 @@ def simulate(R, second_order, nx, ny, nz, T, dw, nf, C):
                         t = tb + s
                         pin, pout = t & 1, (t & 1) ^ 1
                         lo, width = tl["lev"][s]
-                        for row in range(width):
-                            y = lo + row
-                            yy = y - tl["Y0"]
+                        hi = lo + width
+                        Sx = tl["S"][rank]
+                        for y0 in range(lo, hi, 2):
+                            row1 = y0 + 1 < hi
+                            yy0 = y0 - tl["Y0"]
                             for f in range(nf):
                                 z = zb + f
                                 if z < 0 or z >= nz:
@@ -173,34 +183,49 @@ def simulate(R, second_order, nx, ny, nz, T, dw, nf, C):
                                 sl = (z + R) % NZ
                                 for xl in range(xw):
                                     xx = xl + R
-                                    item = (rank, s, y, z, xl)
-                                    Sx = tl["S"][rank]
-                                    for d in range(-R, R + 1):
-                                        for cell in ((pin, sl, yy, xx + d), (pin, sl, yy + d, xx),
-                                                     (pin, (sl + d) % NZ, yy, xx)):
-                                            assert 0 <= cell[2] < YW and 0 <= cell[3] < XT, cell
-                                            check_read(Sx[cell], t)
-                                            reads.setdefault((rank,) + cell, set()).add(item)
-                                    if second_order:
-                                        check_read(Sx[pout, sl, yy, xx], t - 1)
-                                        reads.setdefault((rank, pout, sl, yy, xx), set()).add(item)
-                                    outs = [(rank, pout, sl, yy, xx)]
-                                    if C > 1 and xl < R and rank > 0:
-                                        outs.append((rank - 1, pout, sl, yy, xx + XW))
-                                    if C > 1 and xl >= XW - R and rank < C - 1:
-                                        outs.append((rank + 1, pout, sl, yy, xx - XW))
-                                    for o in outs:
-                                        assert 0 <= o[4] < XT
-                                        assert o not in writes, ("double write", o)
-                                        writes[o] = item
-                                    pending.append((outs, t + 1))
+                                    item = (rank, s, y0, z, xl)
+                                    key = (rank, s, y0, xl)
+                                    def rd(cell, want):
+                                        assert 0 <= cell[2] < YW and 0 <= cell[3] < XT, cell
+                                        check_read(Sx[cell], want)
+                                        reads.setdefault((rank,) + cell, set()).add(item)
+                                        return Sx[cell]
+                                    if z == 0:
+                                        tl["win"][key] = [[rd((pin, (sl + d) % NZ, yy0 + r, xx), t)
+                                                           for d in range(-R, R + 1)] for r in (0, 1)]
+                                    else:
+                                        wv = tl["win"][key]
+                                        for r in (0, 1):
+                                            wv[r] = wv[r][1:] + [rd((pin, (sl + R) % NZ, yy0 + r, xx), t)]
+                                    for r in (0, 1):  # centre of each row is its window's middle
+                                        check_read(tl["win"][key][r][R], t)
+                                    for d in range(1, R + 1):
+                                        rd((pin, sl, yy0 - d, xx), t)
+                                        if d < R or row1:
+                                            rd((pin, sl, yy0 + 1 + d, xx), t)
+                                    for r in (0, 1) if row1 else (0,):
+                                        for d in range(-R, R + 1):
+                                            if d:
+                                                rd((pin, sl, yy0 + r, xx + d), t)
+                                        if second_order:
+                                            rd((pout, sl, yy0 + r, xx), t - 1)
+                                        outs = [(rank, pout, sl, yy0 + r, xx)]
+                                        if C > 1 and xl < R and rank > 0:
+                                            outs.append((rank - 1, pout, sl, yy0 + r, xx + XW))
+                                        if C > 1 and xl >= XW - R and rank < C - 1:
+                                            outs.append((rank + 1, pout, sl, yy0 + r, xx - XW))
+                                        for o in outs:
+                                            assert 0 <= o[4] < XT and 0 <= o[3] < YW
+                                            assert o not in writes, ("double write", o)
+                                            writes[o] = item
+                                        pending.append((outs, t + 1))
                 # race checks within the step
                 for cell, it in writes.items():
                     rs = reads.get(cell, set())
                     assert rs <= {it}, ("read and written in one step", cell)
-                    assert cell not in loaded and cell not in wb_reads, ("write vs load/write-back", cell)
-                for cell in loaded:
-                    assert cell not in reads, ("load into a slot read this step", cell)
+                    assert cell not in busy and cell not in wb_reads, ("write vs load/write-back", cell)
+                for cell in busy:
+                    assert cell not in reads and cell not in wb_reads, ("slot read while its load is in flight", cell)
                 for outs, lv in pending:
                     for o in outs:
                         tl["S"][o] = lv

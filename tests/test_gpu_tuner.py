@@ -1,0 +1,66 @@
+"""Auto-tuner on small grids: candidate pruning, measurement, exhaustive arg-max, learned top-k."""
+import ctypes
+import os
+
+import numpy as np
+import pytest
+
+import paper_1510_04995_gb300 as girih
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _build():
+    import __graft_entry__
+    __graft_entry__.build()
+
+
+def _cands(p):
+    n = ctypes.c_int32()
+    girih.check(girih.lib().girih_tune_candidates(p.handle, None, 0, ctypes.byref(n)))
+    arr = (girih.Config * n.value)()
+    girih.check(girih.lib().girih_tune_candidates(p.handle, arr, n.value, ctypes.byref(n)))
+    return list(arr)
+
+
+def test_candidates_are_feasible_and_pruned():
+    p = girih.plan(girih.S25V, 96, 64, 32, dtype="f64", T=8)
+    cs = _cands(p)
+    assert cs[0].algo == girih.NAIVE and len(cs) > 1
+    for c in cs:
+        assert p.feasible(c)
+        if c.algo == girih.MWD:
+            assert p.check_config(c) <= 232448
+    # a configuration whose tile exceeds shared memory is pruned
+    assert not p.feasible(girih.config(girih.MWD, dw=64, nf=2, cluster=1, threads=256))
+
+
+def test_measure_and_exhaustive_argmax(tmp_path):
+    p = girih.plan(girih.S7C, 64, 48, 40, dtype="f32", T=8)
+    row = girih.TuneRow()
+    girih.check(girih.lib().girih_tune_measure(p.handle, ctypes.byref(girih.config(girih.NAIVE)), 0.5, 16,
+                                                ctypes.byref(row)))
+    assert row.glups > 0 and row.steps >= 2
+    db = str(tmp_path / "db.csv")
+    best = girih.TuneRow()
+    nm = ctypes.c_int32()
+    girih.check(girih.lib().girih_tune_exhaustive(p.handle, 0.5, 8, db.encode(), ctypes.byref(best),
+                                                   ctypes.byref(nm)))
+    rows = np.loadtxt(db, delimiter=",", ndmin=2)
+    assert rows.shape[0] == nm.value == len(_cands(p))
+    assert best.glups == pytest.approx(rows[:, 11].max(), rel=1e-5)
+    assert p.config.as_dict() == best.cfg.as_dict()
+
+
+def test_learned_tuner_measures_only_top_k():
+    import torch
+    p = girih.plan(girih.S7C, 64, 48, 40, dtype="f32", T=8)
+    npar = girih.lib().girih_mlp_num_params(girih.MLP_FEATURES)
+    params = torch.zeros(npar, device="cuda")
+    params[-1] = 1.0  # constant network: ties broken by candidate order
+    best = girih.TuneRow()
+    nm = ctypes.c_int32()
+    girih.check(girih.lib().girih_tune_learned(p.handle, ctypes.c_void_p(params.data_ptr()), 3, 0.5, 8,
+                                                ctypes.byref(best), ctypes.byref(nm)))
+    assert nm.value == 3 and best.glups > 0
