@@ -191,6 +191,7 @@ def main():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-naive", action="store_true")
+    ap.add_argument("--grid", default="", help="override nx,ny,nz (profiling a smaller case of the same kernel)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args, args.workload)
@@ -209,6 +210,8 @@ def main():
     dev = torch.device("cuda", local)
     gbuild.build()
     stencil, dtype, nx, ny, nz, T = WORKLOADS[args.workload]
+    if args.grid:
+        nx, ny, nz = (int(v) for v in args.grid.split(","))
     p = girih.plan(stencil, nx, ny, nz, dtype=dtype, T=T)
     if args.algo == "naive":
         cfg = girih.config(girih.NAIVE)

@@ -34,10 +34,10 @@ def _ref(stencil, nx, ny, nz, T, seed=3):
 
 
 MWD_CFGS = {
-    1: [dict(dw=4, nf=1, cluster=1, threads=128), dict(dw=8, nf=2, cluster=2, threads=256),
-        dict(dw=16, nf=1, cluster=8, threads=512), dict(dw=6, nf=3, cluster=2, threads=64)],
+    1: [dict(dw=4, nf=1, cluster=1, threads=256), dict(dw=8, nf=2, cluster=2, threads=256),
+        dict(dw=16, nf=1, cluster=8, threads=1024), dict(dw=6, nf=3, cluster=2, threads=512)],
     4: [dict(dw=8, nf=1, cluster=4, threads=256), dict(dw=16, nf=1, cluster=8, threads=256),
-        dict(dw=8, nf=2, cluster=8, threads=128), dict(dw=16, nf=2, cluster=16, threads=64)],
+        dict(dw=8, nf=2, cluster=8, threads=128), dict(dw=16, nf=1, cluster=16, threads=128)],
 }
 
 
@@ -123,7 +123,7 @@ def test_degenerate_shapes(shape):
         R = inputs.RADIUS[stencil]
         T = 5
         u, up, co, c, ru, rup = _ref(stencil, nx, ny, nz, T)
-        for cfg in (girih.config(girih.NAIVE), girih.config(girih.MWD, dw=2 * R, nf=1, cluster=1, threads=64)):
+        for cfg in (girih.config(girih.NAIVE), girih.config(girih.MWD, dw=2 * R, nf=1, cluster=1, threads=256)):
             gu, gup = gpu_sweep(stencil, "f64", u, up, co, c, T, nx, ny, nz, cfg)
             assert np.max(np.abs(gu - ru)) <= 1e-12 * max(1.0, np.max(np.abs(ru))), (shape, stencil, cfg)
 
