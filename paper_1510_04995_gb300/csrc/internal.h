@@ -58,6 +58,7 @@ int mwd_pairs_per_thread(int R, int dw, int XW, int threads);
 // Planes are staged this many wavefront steps ahead of use.
 #define MWD_PREFETCH 2
 
+
 // In-place exchange of two device arrays (odd T puts level T back into u).
 cudaError_t launch_swap(void* a, void* b, int64_t bytes, cudaStream_t st);
 

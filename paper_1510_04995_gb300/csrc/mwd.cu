@@ -60,10 +60,23 @@ __device__ __forceinline__ void cp_async_wait_group() {
   asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
 }
 
+__device__ __forceinline__ void cluster_arrive_release() {
+  asm volatile("barrier.cluster.arrive.release.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void cluster_wait_acquire() {
+  asm volatile("barrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
 // G = row pairs owned per thread.  Each pair (level s, rows y0 and y0+1, column xl) is owned
 // by one thread for the whole launch (fixed execution to data), which keeps the two rows'
 // z windows in registers across wavefront steps: per step and plane, a pair loads 2 new z
 // values, 2R rows of y neighbours shared by both rows, 2R x neighbours per row, and stores 2.
+// Step w: compute; wait for this thread's staged planes of step w+1; cluster arrive (release:
+// publishes the step's shared and DSMEM writes); write back the planes the top level finished
+// in step w-1 and stage the planes of step w+PD (both overlap the barrier, and the write-back
+// stores are not held by the release); cluster wait (acquire).  The write-back and staging may
+// run while other threads already compute step w+1: the ring depth keeps those planes apart.
+// A single block (C = 1) uses one __syncthreads in place of the arrive.
 template <int S, typename T, int G>
 __global__ void __launch_bounds__(1024 / G) mwd_fed_kernel(const MwdArgs A) {
   constexpr int R = Traits<S>::R;
@@ -79,7 +92,8 @@ __global__ void __launch_bounds__(1024 / G) mwd_fed_kernel(const MwdArgs A) {
   int* row_mask = lev_pp + A.H + 1;
 
   const int nx = (int)A.g.nx, ny = (int)A.g.ny, nz = (int)A.g.nz;
-  const int64_t ldx = A.g.ldx, sy = A.g.sy, gplane = sy * ldx;
+  const int ldx = (int)A.g.ldx;
+  const int64_t gplane = A.g.sy * A.g.ldx;
   const int rank = (C > 1) ? (int)cluster_ctarank() : 0;
   const int tile = blockIdx.x / C;
   const int dw = A.dw, rho = A.rho;
@@ -124,55 +138,57 @@ __global__ void __launch_bounds__(1024 / G) mwd_fed_kernel(const MwdArgs A) {
     }
     row_mask[yy] = m;
   }
+  __syncthreads();  // level tables ready
 
-  const T* gbuf[2] = {static_cast<const T*>(A.buf0), static_cast<const T*>(A.buf1)};
-  T* gout[2] = {static_cast<T*>(A.buf0), static_cast<T*>(A.buf1)};
+  const T* gb0 = static_cast<const T*>(A.buf0);
+  const T* gb1 = static_cast<const T*>(A.buf1);
+  T* go0 = static_cast<T*>(A.buf0);
+  T* go1 = static_cast<T*>(A.buf1);
   const T* coef = static_cast<const T*>(A.coef);
   T cst[5];
 #pragma unroll
   for (int i = 0; i < 5; ++i) cst[i] = static_cast<T>(A.c[i]);
 
+  // Plane staging and write-back go row by row: warp k takes rows k, k + NT/32, ..., its lanes
+  // walk the row's columns (coalesced, no per-element index arithmetic beyond an add).
+  // Staged: rows y in [Y0, Y0+YW) clipped to the padded grid, columns x in [x0-R, x0+xw+R).
   const int ylo = max(Y0, -R), yhi = min(Y0 + YW, ny + R);
   const int nrow = max(yhi - ylo, 0);
   const int ncol = (xw > 0) ? xw + 2 * R : 0;
-
+  const int lane = tid & 31, warp = tid >> 5, nwarps = NT >> 5;
   auto load_plane = [&](int z) {
     if (z < -R || z >= nz + R || ncol == 0) return;
     const int slot = (z + R) % NZ;
-    const int per = nrow * ncol;
-    for (int i = tid; i < 2 * per; i += NT) {
-      const int p = i >= per;
-      const int rem = i - p * per;
-      const int r = rem / ncol, xx = rem - r * ncol;
-      const int y = ylo + r;
-      const int64_t gi = (int64_t)(z + R) * gplane + (int64_t)(y + R) * ldx + (x0 + xx);
-      cp_async(sm + p * be + slot * pe + (y - Y0) * XT + xx, gbuf[p] + gi);
+    const int64_t gz = (int64_t)(z + R) * gplane;
+    for (int rr = warp; rr < 2 * nrow; rr += nwarps) {
+      const int p = rr >= nrow;
+      const int y = ylo + rr - p * nrow;
+      const T* src = (p ? gb1 : gb0) + gz + (int64_t)(y + R) * ldx + x0;
+      T* dst = sm + p * be + slot * pe + (y - Y0) * XT;
+      for (int xx = lane; xx < ncol; xx += 32) cp_async(dst + xx, src + xx);
     }
   };
+  // Written back: rows of the projection the tile updated (row mask: which buffers), own columns.
   auto write_plane = [&](int z) {
     if (z < 0 || z >= nz || xw <= 0) return;
-    const int slot = (z + R) % NZ;
-    const int per = YW * xw;
-    for (int i = tid; i < per; i += NT) {
-      const int yy = i / xw, xl = i - yy * xw;
+    const int so = ((z + R) % NZ) * pe;
+    const int64_t gz = (int64_t)(z + R) * gplane;
+    for (int yy = warp; yy < YW; yy += nwarps) {
       const int m = row_mask[yy];
       if (m == 0) continue;
-      const int64_t gi = (int64_t)(z + R) * gplane + (int64_t)(Y0 + yy + R) * ldx + (x0 + xl + R);
-      const int so = slot * pe + yy * XT + xl + R;
-      if (m & 1) gout[0][gi] = sm[so];
-      if (m & 2) gout[1][gi] = sm[be + so];
+      const int64_t go = gz + (int64_t)(Y0 + yy + R) * ldx + (x0 + R);
+      const T* src = sm + so + yy * XT + R;
+      for (int xl = lane; xl < xw; xl += 32) {
+        if (m & 1) go0[go + xl] = src[xl];
+        if (m & 2) go1[go + xl] = src[be + xl];
+      }
     }
   };
-  auto sync_all = [&]() {
-    if (C > 1) cluster_barrier();
-    else __syncthreads();
-  };
-
-  __syncthreads();  // level tables ready
 
   // this thread's row pairs: level s, first row y0 (second row y0+1 may lie outside the level)
-  int gs_[G], gy_[G], gx_[G];
-  bool gv_[G];
+  int gs_[G], gcol_[G], gx_[G];
+  bool gv_[G], grow1_[G];
+  int64_t gg_[G];
   const int npairs = lev_pp[nlev];
 #pragma unroll
   for (int g = 0; g < G; ++g) {
@@ -182,16 +198,21 @@ __global__ void __launch_bounds__(1024 / G) mwd_fed_kernel(const MwdArgs A) {
     int s = 0;
     if (pr < npairs)
       while (lev_pp[s + 1] <= pr) ++s;
+    const int y0 = (pr < npairs) ? lev_lo[s] + 2 * (pr - lev_pp[s]) : 0;
     gs_[g] = s;
-    gy_[g] = (pr < npairs) ? lev_lo[s] + 2 * (pr - lev_pp[s]) : 0;
     gx_[g] = xl;
+    grow1_[g] = (pr < npairs) && (y0 + 1 < lev_lo[s] + lev_w[s]);
+    gcol_[g] = (y0 - Y0) * XT + xl + R;
+    gg_[g] = (int64_t)(y0 + R) * ldx + (x0 + xl + R);
   }
   T win[G][2][2 * R + 1];
 
-  for (int z = -R; z < PD * nf + R; ++z) load_plane(z);
+  if (xw > 0)
+    for (int z = -R; z < PD * nf + R; ++z) load_plane(z);
   cp_async_commit();
   cp_async_wait_group<0>();
-  sync_all();
+  if (C > 1) cluster_barrier();
+  else __syncthreads();
 
   const uint32_t sm_base = smem_addr(sm);
   const uint32_t left_base = (C > 1 && rank > 0) ? map_to_rank(sm_base, rank - 1) : 0u;
@@ -199,27 +220,23 @@ __global__ void __launch_bounds__(1024 / G) mwd_fed_kernel(const MwdArgs A) {
 
   const int W = (nz + smax * K + nf - 1) / nf;
   for (int w = 0; w < W; ++w) {
-    for (int f = 0; f < nf; ++f) load_plane((w + PD) * nf + R + f);
-    cp_async_commit();
-    if (w > 0)
-      for (int f = 0; f < nf; ++f) write_plane((w - 1) * nf - smax * K + f);
 #pragma unroll
     for (int g = 0; g < G; ++g) {
       if (!gv_[g]) continue;
       const int s = gs_[g];
+      const int zb = w * nf - s * K;
+      if (zb + nf <= 0 || zb >= nz) continue;
       const int t = tb + s;
-      const int pin = t & 1, pout = pin ^ 1;
-      const int y0 = gy_[g], xl = gx_[g];
-      const int hi = lev_lo[s] + lev_w[s];
-      const bool row1 = (y0 + 1) < hi;
-      const int yy0 = y0 - Y0;
+      const int pin = t & 1;
       const T* Vb = sm + pin * be;
-      T* Ub = sm + pout * be;
-      for (int f = 0; f < nf; ++f) {
-        const int z = w * nf - s * K + f;
+      T* Ub = sm + (pin ^ 1) * be;
+      const int col = gcol_[g], xl = gx_[g];
+      const bool row1 = grow1_[g];
+      int sl = (zb + R) % NZ;
+      sl = sl < 0 ? sl + NZ : sl;
+      for (int f = 0; f < nf; ++f, sl = (sl + 1 == NZ) ? 0 : sl + 1) {
+        const int z = zb + f;
         if (z < 0 || z >= nz) continue;
-        const int sl = (z + R) % NZ;
-        const int col = yy0 * XT + xl + R;  // offset of row y0 within a plane
         if (z == 0) {  // first plane of this level: fill the whole window
 #pragma unroll
           for (int d = -R; d <= R; ++d) {
@@ -252,20 +269,21 @@ __global__ void __launch_bounds__(1024 / G) mwd_fed_kernel(const MwdArgs A) {
           yv0[R + d] = (d == 1) ? win[g][1][R] : yv1[R + d - 1];
           yv1[R - d] = (d == 1) ? win[g][0][R] : yv0[R - d + 1];
         }
-        const int64_t gp = (int64_t)(z + R) * gplane + (int64_t)(y0 + R) * ldx + (x0 + xl + R);
+        const int64_t gp = (int64_t)(z + R) * gplane + gg_[g];
+        const int uo = sl * pe + col;
         PairAcc<S, T> acc0{win[g][0], yv0, P, T(0), coef, A.g.gstride, gp};
-        if constexpr (Traits<S>::ORDER2) acc0.uc = Ub[sl * pe + col];
+        if constexpr (Traits<S>::ORDER2) acc0.uc = Ub[uo];
         const T r0 = point_update<S, T>(acc0, cst);
+        Ub[uo] = r0;
         T r1 = T(0);
         if (row1) {
           PairAcc<S, T> acc1{win[g][1], yv1, P + XT, T(0), coef, A.g.gstride, gp + ldx};
-          if constexpr (Traits<S>::ORDER2) acc1.uc = Ub[sl * pe + col + XT];
+          if constexpr (Traits<S>::ORDER2) acc1.uc = Ub[uo + XT];
           r1 = point_update<S, T>(acc1, cst);
+          Ub[uo + XT] = r1;
         }
-        const int so = pout * be + sl * pe + col;
-        sm[so] = r0;
-        if (row1) sm[so + XT] = r1;
         if (C > 1) {
+          const int so = (pin ^ 1) * be + uo;
           if (xl < R && rank > 0) {  // my left edge is the left neighbour's right halo
             st_cluster(left_base + (uint32_t)((so + XW) * (int)sizeof(T)), r0);
             if (row1) st_cluster(left_base + (uint32_t)((so + XT + XW) * (int)sizeof(T)), r1);
@@ -278,10 +296,19 @@ __global__ void __launch_bounds__(1024 / G) mwd_fed_kernel(const MwdArgs A) {
       }
     }
     cp_async_wait_group<PD - 1>();
-    sync_all();
+    if (C > 1) cluster_arrive_release();
+    else __syncthreads();  // a single block needs no second barrier: see the loop comment
+    if (xw > 0) {
+      if (w > 0)
+        for (int f = 0; f < nf; ++f) write_plane((w - 1) * nf - smax * K + f);
+      for (int f = 0; f < nf; ++f) load_plane((w + PD) * nf + R + f);
+    }
+    cp_async_commit();
+    if (C > 1) cluster_wait_acquire();
   }
   cp_async_wait_group<0>();
-  for (int f = 0; f < nf; ++f) write_plane((W - 1) * nf - smax * K + f);
+  if (xw > 0)
+    for (int f = 0; f < nf; ++f) write_plane((W - 1) * nf - smax * K + f);
 }
 
 MwdShape mwd_shape(int stencil, int dtype, int dw, int nf, int XW) {

@@ -141,6 +141,7 @@ def simulate(R, second_order, nx, ny, nz, T, dw, nf, C):
             assert tagv == want or tagv == HALO, (tagv, want)
 
         for tl in tiles:
+            tl["prev_wb"] = set()  # write-back reads of the previous step (may overlap this step)
             tl["inflight"] = []  # (issue step, cells) of cp.async groups
             tl["win"] = {}
             for rank in range(C):
@@ -224,6 +225,8 @@ def simulate(R, second_order, nx, ny, nz, T, dw, nf, C):
                     rs = reads.get(cell, set())
                     assert rs <= {it}, ("read and written in one step", cell)
                     assert cell not in busy and cell not in wb_reads, ("write vs load/write-back", cell)
+                    assert cell not in tl["prev_wb"], ("write vs the previous step's write-back", cell)
+                tl["prev_wb"] = wb_reads
                 for cell in busy:
                     assert cell not in reads and cell not in wb_reads, ("slot read while its load is in flight", cell)
                 for outs, lv in pending:

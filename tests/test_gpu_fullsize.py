@@ -1,0 +1,78 @@
+"""Full-size checks in the benchmark's launch configuration.
+
+* Blocked == naive bit for bit on every benchmark workload (full grids, full T).
+* Sampled outputs against the FP64 oracle: the value of a point after T steps depends only on
+  initial values within distance R*T along each axis, so the oracle run on the (2RT+1)^3 block
+  around a sample (clipped by the real halo at the domain faces) reproduces that point exactly;
+  the block's own artificial boundary cannot reach the centre within T steps.
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+import paper_1510_04995_gb300 as girih
+from paper_1510_04995_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _build():
+    import __graft_entry__
+    __graft_entry__.build()
+
+
+def _bench_cfg(workload, p):
+    import bench
+    tuned = bench._tuned(workload)
+    return girih.Config(**tuned) if tuned else p.config
+
+
+def _run_pair(workload):
+    import torch
+    import bench
+    stencil, dtype, nx, ny, nz, T = bench.WORKLOADS[workload]
+    p = girih.plan(stencil, nx, ny, nz, dtype=dtype, T=T)
+    cfg = _bench_cfg(workload, p)
+    u, up, co, c = inputs.make_problem(stencil, nx, ny, nz, backend="torch", device="cuda")
+    tdt = torch.float64 if dtype == "f64" else torch.float32
+    u, up = u.to(tdt).contiguous(), up.to(tdt).contiguous()
+    co = co.to(tdt).contiguous() if co is not None else None
+    bu, bup = u.clone(), up.clone()
+    girih.run(p, bu, bup, co, c=c, cfg=cfg)
+    girih.run(p, u, up, co, c=c, cfg=girih.config(girih.NAIVE))
+    torch.cuda.synchronize()
+    return p, cfg, (bu, bup), (u, up), (stencil, dtype, nx, ny, nz, T)
+
+
+@pytest.mark.parametrize("workload", ["7pt_const_f64_512", "7pt_const_f32_512", "7pt_var_f32_480",
+                                      "25pt_const_f32_384", "25pt_var_f32_384", "25pt_const_f64_384"])
+def test_blocked_equals_naive_full_size(workload):
+    import torch
+    p, cfg, (bu, bup), (nu, nup), _ = _run_pair(workload)
+    assert torch.equal(bu, nu) and torch.equal(bup, nup), (workload, cfg)
+
+
+def test_sampled_points_against_oracle_cones():
+    import torch
+    workload = "7pt_const_f64_512"
+    p, cfg, (bu, _), _, (stencil, dtype, nx, ny, nz, T) = _run_pair(workload)
+    R = inputs.RADIUS[stencil]
+    h = R * T
+    u0, _, co, c = inputs.make_problem(stencil, nx, ny, nz)
+    scale = float(bu.abs().max())
+    samples = [(0, 0, 0), (nx - 1, ny // 2, nz - 1), (nx // 2, ny // 2, nz // 2), (nx // 3, ny - 1, 5)]
+    for (i, j, k) in samples:
+        lo = [max(q - h, 0) for q in (i, j, k)]
+        hi = [min(q + h + 1, n) for q, n in zip((i, j, k), (nx, ny, nz))]
+        sub = np.ascontiguousarray(u0[lo[2]:hi[2] + 2 * R, lo[1]:hi[1] + 2 * R, lo[0]:hi[0] + 2 * R])
+        sup = sub.copy()
+        oracle.sweep(stencil, sub, sup, None, c, T, hi[0] - lo[0], hi[1] - lo[1], hi[2] - lo[2], nthreads=16)
+        ref = sub[k - lo[2] + R, j - lo[1] + R, i - lo[0] + R]
+        got = float(bu[k + R, j + R, i + R])
+        assert abs(got - ref) <= 1e-12 * scale, ((i, j, k), got, ref)
