@@ -160,6 +160,7 @@ typedef struct girih_tune_row {
   double seconds;    /* time of that accepted measurement                                  */
   int64_t steps;     /* time steps of the accepted measurement                             */
   int64_t smem;      /* shared memory per block                                            */
+  double tune_seconds; /* host wall time spent measuring this candidate (all test lengths) */
 } girih_tune_row;
 
 /* Enumerate the candidate configurations (naive sweep plus every MWD diamond width, wavefront
@@ -175,7 +176,9 @@ GIRIH_API int girih_tune_measure(girih_plan_t plan, const girih_config* cfg, dou
                        girih_tune_row* row);
 
 /* Exhaustive tuning: measure every candidate, append one CSV line per candidate to db_path
- * (NULL: no file), set the plan's configuration to the fastest and return it in *best.       */
+ * (NULL: no file), set the plan's configuration to the fastest and return it in *best.  CSV
+ * columns: stencil, dtype, nx, ny, nz, algo, dw, nf, cluster, threads, variant, glups, seconds,
+ * steps, smem, tune_seconds.                                                                   */
 GIRIH_API int girih_tune_exhaustive(girih_plan_t plan, double tol, int64_t max_steps, const char* db_path,
                           girih_tune_row* best, int32_t* n_measured);
 

@@ -52,7 +52,7 @@ class Params(ctypes.Structure):
 
 class TuneRow(ctypes.Structure):
     _fields_ = [("cfg", Config), ("glups", ctypes.c_double), ("seconds", ctypes.c_double),
-                ("steps", ctypes.c_int64), ("smem", ctypes.c_int64)]
+                ("steps", ctypes.c_int64), ("smem", ctypes.c_int64), ("tune_seconds", ctypes.c_double)]
 
 
 def config(algo=MWD, dw=8, nf=1, cluster=1, threads=256, variant=FED) -> Config:

@@ -13,6 +13,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <chrono>
 #include <cmath>
 #include <cstdio>
 #include <vector>
@@ -69,6 +70,7 @@ static const double kC7[5] = {0.4, 0.1, 0, 0, 0};
 static const double kC25[5] = {-0.9, 0.05, 0.025, 0.0125, 0.00625};
 
 int measure(Plan* p, const girih_config& cfg, double tol, int64_t max_steps, girih_tune_row* row) {
+  const auto wall0 = std::chrono::steady_clock::now();
   int rc = check_config(p, &cfg, &row->smem, nullptr);
   if (rc != GIRIH_OK) return rc;
   rc = ensure_tune_arrays(p);
@@ -112,6 +114,7 @@ int measure(Plan* p, const girih_config& cfg, double tol, int64_t max_steps, gir
   row->glups = glups;
   row->seconds = secs;
   row->steps = used;
+  row->tune_seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - wall0).count();
   return GIRIH_OK;
 }
 
@@ -153,9 +156,9 @@ int girih_tune_measure(girih_plan_t plan, const girih_config* cfg, double tol, i
 }
 
 static void append_csv(FILE* f, const Plan* p, const girih_tune_row& r) {
-  fprintf(f, "%d,%d,%lld,%lld,%lld,%d,%d,%d,%d,%d,%d,%.6f,%.6e,%lld,%lld\n", p->stencil, p->dtype,
+  fprintf(f, "%d,%d,%lld,%lld,%lld,%d,%d,%d,%d,%d,%d,%.6f,%.6e,%lld,%lld,%.6e\n", p->stencil, p->dtype,
           (long long)p->nx, (long long)p->ny, (long long)p->nz, r.cfg.algo, r.cfg.dw, r.cfg.nf, r.cfg.cluster,
-          r.cfg.threads, r.cfg.variant, r.glups, r.seconds, (long long)r.steps, (long long)r.smem);
+          r.cfg.threads, r.cfg.variant, r.glups, r.seconds, (long long)r.steps, (long long)r.smem, r.tune_seconds);
 }
 
 int girih_tune_exhaustive(girih_plan_t plan, double tol, int64_t max_steps, const char* db_path,

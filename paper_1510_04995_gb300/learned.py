@@ -1,0 +1,181 @@
+"""Learned tuner: the network of ``csrc/mlp.cu`` trained on the exhaustive tuner's own timings.
+
+The paper's auto-tuner (Sect. 4.2.2) measures every thread-group shape and hill-climbs the
+diamond and wavefront widths.  Here the exhaustive tuner (``girih_tune_exhaustive``) records one
+row per feasible candidate into a CSV timing database.  This module:
+
+* ``collect``  runs the exhaustive tuner over a list of problems and appends to the database,
+  recording the wall time each problem's exhaustive tuning took;
+* ``train``    fits the 3-layer network (16 -> 64 -> 64 -> 1, ReLU) with the library's CUDA
+  forward/backward/Adam kernels to the per-problem centred log throughput of each candidate
+  (only the ranking within a problem matters, so the problem's mean is removed);
+* ``evaluate`` scores held-out problems: the network ranks all candidates, the best measured of
+  its top k is compared with the exhaustive best (regret) and the k measurements' cost with the
+  exhaustive tuning cost;
+* ``tune``     the live learned tuner on one plan (``girih_tune_learned``: score, measure top k).
+
+Everything numeric runs in the library (features, network, measurement); numpy only reshapes.
+"""
+from __future__ import annotations
+
+import ctypes
+import csv
+import math
+import os
+import time
+
+import numpy as np
+
+from . import (F32, F64, MLP_FEATURES, Config, TuneRow, check, config, lib, plan)
+
+# The 12 non-cubic grids of the learned-tuner sweep (nx, ny, nz), and the held-out ones (#3, #7, #10).
+GRIDS = [(128, 256, 512), (256, 128, 512), (192, 384, 512), (256, 512, 512), (384, 256, 512),
+         (320, 640, 512), (512, 384, 512), (448, 768, 512), (640, 512, 512), (576, 704, 512),
+         (768, 512, 512), (768, 768, 512)]
+HELD_OUT = (2, 6, 9)
+FIELDS = ["stencil", "dtype", "nx", "ny", "nz", "algo", "dw", "nf", "cluster", "threads", "variant", "glups",
+          "seconds", "steps", "smem", "tune_seconds"]
+
+
+def _dt(d):
+    return {"f64": F64, "f32": F32, F64: F64, F32: F32}[d]
+
+
+def collect(db_path: str, problems, T: int = 16, tol: float = 0.05, max_steps: int = 32, times_path: str | None = None,
+            log=print):
+    """Exhaustively tune every (stencil, dtype, nx, ny, nz) problem; rows go to db_path."""
+    for (stencil, dtype, nx, ny, nz) in problems:
+        p = plan(stencil, nx, ny, nz, dtype=dtype, T=T)
+        best = TuneRow()
+        nm = ctypes.c_int32()
+        t0 = time.perf_counter()
+        check(lib().girih_tune_exhaustive(p.handle, tol, max_steps, db_path.encode(), ctypes.byref(best),
+                                          ctypes.byref(nm)))
+        dt = time.perf_counter() - t0
+        if times_path:
+            with open(times_path, "a") as f:
+                f.write(f"{stencil},{_dt(dtype)},{nx},{ny},{nz},{nm.value},{dt:.4f},{best.glups:.4f}\n")
+        if log:
+            log(f"tuned s={stencil} {dtype} {nx}x{ny}x{nz}: {nm.value} candidates in {dt:.1f} s, best "
+                f"{best.glups:.1f} GLUP/s {best.cfg}")
+        p.close()
+
+
+def load_db(path: str):
+    rows = []
+    with open(path) as f:
+        for r in csv.reader(f):
+            if not r or r[0].startswith("#"):
+                continue
+            vals = [float(v) for v in r]
+            rows.append(dict(zip(FIELDS, vals)))
+    return rows
+
+
+def problem_key(r):
+    return (int(r["stencil"]), int(r["dtype"]), int(r["nx"]), int(r["ny"]), int(r["nz"]))
+
+
+def row_config(r) -> Config:
+    return Config(int(r["algo"]), int(r["dw"]), int(r["nf"]), int(r["cluster"]), int(r["threads"]),
+                  int(r["variant"]))
+
+
+def features(rows) -> np.ndarray:
+    X = np.zeros((len(rows), MLP_FEATURES), dtype=np.float32)
+    for i, r in enumerate(rows):
+        cfg = row_config(r)
+        check(lib().girih_mlp_features(int(r["stencil"]), int(r["dtype"]), int(r["nx"]), int(r["ny"]), int(r["nz"]),
+                                       ctypes.byref(cfg), X[i].ctypes.data_as(ctypes.c_void_p)))
+    return X
+
+
+def targets(rows) -> np.ndarray:
+    """Per-problem centred log throughput."""
+    y = np.array([math.log(max(r["glups"], 1e-6)) for r in rows])
+    keys = [problem_key(r) for r in rows]
+    for k in set(keys):
+        idx = [i for i, kk in enumerate(keys) if kk == k]
+        y[idx] -= y[idx].mean()
+    return y.astype(np.float32)
+
+
+def init_params(seed: int = 0) -> np.ndarray:
+    """He-uniform initial weights, zero biases (host-side random draw, passed to the kernels)."""
+    rng = np.random.default_rng(seed)
+    d, h = MLP_FEATURES, 64
+    W1 = rng.uniform(-1, 1, (h, d)) * math.sqrt(6.0 / d)
+    W2 = rng.uniform(-1, 1, (h, h)) * math.sqrt(6.0 / h)
+    W3 = rng.uniform(-1, 1, (1, h)) * math.sqrt(6.0 / h)
+    return np.concatenate([W1.ravel(), np.zeros(h), W2.ravel(), np.zeros(h), W3.ravel(), np.zeros(1)]).astype(
+        np.float32)
+
+
+def train(X: np.ndarray, y: np.ndarray, epochs: int = 2000, lr: float = 3e-3, seed: int = 0, log=None):
+    """Full-batch Adam on the GPU with the library's kernels; returns (params, loss history)."""
+    import torch
+    L = lib()
+    n, d = X.shape
+    npar = L.girih_mlp_num_params(d)
+    dev = "cuda"
+    P = torch.from_numpy(init_params(seed)).to(dev)
+    dX = torch.from_numpy(np.ascontiguousarray(X, dtype=np.float32)).to(dev)
+    dy = torch.from_numpy(np.ascontiguousarray(y, dtype=np.float32)).to(dev)
+    g = torch.zeros(npar, device=dev)
+    m = torch.zeros(npar, device=dev)
+    v = torch.zeros(npar, device=dev)
+    loss = torch.zeros(1, device=dev)
+    ws = torch.zeros(L.girih_mlp_workspace_floats(n), device=dev)
+    ptr = lambda t: ctypes.c_void_p(t.data_ptr())
+    hist = []
+    for step in range(1, epochs + 1):
+        check(L.girih_mlp_backward(ptr(P), ptr(dX), ptr(dy), n, d, ptr(g), ptr(loss), ptr(ws), None))
+        check(L.girih_mlp_adam(ptr(P), ptr(g), ptr(m), ptr(v), npar, step, ctypes.c_float(lr), ctypes.c_float(0.9),
+                               ctypes.c_float(0.999), ctypes.c_float(1e-8), None))
+        if step % 100 == 0 or step == epochs:
+            hist.append((step, float(loss.item())))
+            if log:
+                log(f"epoch {step}: loss {hist[-1][1]:.5f}")
+    torch.cuda.synchronize()
+    return P.cpu().numpy(), hist
+
+
+def predict(params: np.ndarray, X: np.ndarray) -> np.ndarray:
+    import torch
+    L = lib()
+    n, d = X.shape
+    P = torch.from_numpy(np.ascontiguousarray(params, dtype=np.float32)).cuda()
+    dX = torch.from_numpy(np.ascontiguousarray(X, dtype=np.float32)).cuda()
+    y = torch.zeros(n, device="cuda")
+    ws = torch.zeros(L.girih_mlp_workspace_floats(n), device="cuda")
+    ptr = lambda t: ctypes.c_void_p(t.data_ptr())
+    check(L.girih_mlp_forward(ptr(P), ptr(dX), n, d, ptr(y), ptr(ws), None))
+    torch.cuda.synchronize()
+    return y.cpu().numpy()
+
+
+def evaluate(rows, scores: np.ndarray, k: int):
+    """Per problem: exhaustive best, best of the network's top k, and the measurement-cost ratio."""
+    out = []
+    keys = [problem_key(r) for r in rows]
+    for key in sorted(set(keys)):
+        idx = [i for i, kk in enumerate(keys) if kk == key]
+        g = np.array([rows[i]["glups"] for i in idx])
+        cost = np.array([rows[i]["tune_seconds"] for i in idx])
+        top = np.argsort(-scores[idx], kind="stable")[:k]
+        out.append({"problem": key, "candidates": len(idx), "exhaustive_best": float(g.max()),
+                    "learned_best": float(g[top].max()), "ratio": float(g[top].max() / g.max()),
+                    "cost_fraction": float(cost[top].sum() / cost.sum())})
+    return out
+
+
+def tune(p, params: np.ndarray, k: int = 5, tol: float = 0.05, max_steps: int = 32):
+    """Live learned tuning of a plan: returns (TuneRow, measured count, seconds)."""
+    import torch
+    P = torch.from_numpy(np.ascontiguousarray(params, dtype=np.float32)).cuda()
+    best = TuneRow()
+    nm = ctypes.c_int32()
+    t0 = time.perf_counter()
+    check(lib().girih_tune_learned(p.handle, ctypes.c_void_p(P.data_ptr()), k, tol, max_steps, ctypes.byref(best),
+                                   ctypes.byref(nm)))
+    return best, nm.value, time.perf_counter() - t0
