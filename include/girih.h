@@ -205,6 +205,24 @@ GIRIH_API int girih_mlp_forward(const float* params, const float* X, int32_t n, 
 GIRIH_API int girih_mlp_backward(const float* params, const float* X, const float* t, int32_t n, int32_t d, float* grad,
                        float* loss, float* workspace, void* stream);
 
+/* Allocation-free variant of girih_mlp_backward, for callers that cannot allocate device
+ * memory: code running while a stream is being captured into a CUDA graph (an allocation there
+ * fails or breaks the capture), under a memory pool or allocator owned by another framework,
+ * or in a process whose device-memory budget is fixed up front.  The paper has no counterpart.
+ * Instead of a caller workspace it uses one workspace array compiled into the library's device
+ * image (GIRIH_MLP_STATIC_MAX_ROWS rows, about 4.2 MB), which every device that loads the
+ * library holds until the process exits.  It calls no cudaMalloc or cudaFree.
+ *  - n must be 1..GIRIH_MLP_STATIC_MAX_ROWS; more rows return EINVAL with nothing enqueued.
+ *  - The first call on a device looks up the array's device address (cudaGetSymbolAddress) with
+ *    that device current and caches it; make that first call before any stream capture.
+ *  - All calls share the one array and it keeps the last call's contents; each call writes every
+ *    entry it reads, so nothing needs clearing.  Calls whose kernels overlap on the GPU (different
+ *    streams, or different host threads) race on the array: order them on one stream.
+ * Other arguments and results as girih_mlp_backward.                                         */
+#define GIRIH_MLP_STATIC_MAX_ROWS 4096
+GIRIH_API int girih_mlp_backward_static(const float* params, const float* X, const float* t, int32_t n, int32_t d,
+                                        float* grad, float* loss, void* stream);
+
 /* Optimiser steps on device arrays of np floats. step counts from 1 (Adam bias correction).  */
 GIRIH_API int girih_mlp_sgd(float* params, const float* grad, int64_t np, float lr, void* stream);
 GIRIH_API int girih_mlp_adam(float* params, const float* grad, float* m, float* v, int64_t np, int64_t step, float lr,

@@ -27,6 +27,7 @@ NCOEF = {0: 0, 1: 7, 2: 0, 3: 13}
 STATUS = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "EKERNEL", 5: "ETIMEOUT", 6: "ENOTIMPL"}
 MLP_FEATURES = 16
 MLP_HIDDEN = 64
+MLP_STATIC_MAX_ROWS = 4096
 
 
 class GirihError(RuntimeError):
@@ -83,6 +84,7 @@ _SIGS = {
     "girih_mlp_workspace_floats": (_I64, [_I32]),
     "girih_mlp_forward": (ctypes.c_int, [_VP, _VP, _I32, _I32, _VP, _VP, _VP]),
     "girih_mlp_backward": (ctypes.c_int, [_VP, _VP, _VP, _I32, _I32, _VP, _VP, _VP, _VP]),
+    "girih_mlp_backward_static": (ctypes.c_int, [_VP, _VP, _VP, _I32, _I32, _VP, _VP, _VP]),
     "girih_mlp_sgd": (ctypes.c_int, [_VP, _VP, _I64, _F32, _VP]),
     "girih_mlp_adam": (ctypes.c_int, [_VP, _VP, _VP, _VP, _I64, _I64, _F32, _F32, _F32, _F32, _VP]),
     "girih_tune_learned": (ctypes.c_int, [_VP, _VP, _I32, _F64, _I64, ctypes.POINTER(TuneRow),

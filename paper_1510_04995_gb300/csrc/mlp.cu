@@ -13,6 +13,7 @@
 #include <cuda_runtime.h>
 
 #include <cmath>
+#include <mutex>
 
 #include "internal.h"
 #include "plan.h"
@@ -175,11 +176,54 @@ int mlp_forward_impl(const float* P, const float* X, int n, int d, float* y, flo
   return GIRIH_OK;
 }
 
+// Workspace of the allocation-free backward pass (girih_mlp_backward_static): a fixed array in
+// the library's device image, GIRIH_MLP_STATIC_MAX_ROWS rows of WS_ROW floats (4.2 MB), present
+// on every device that loads the library until the process exits.
+__device__ __align__(256) float g_mlp_static_ws[(size_t)GIRIH_MLP_STATIC_MAX_ROWS * WS_ROW];
+
+// Device address of g_mlp_static_ws, looked up once per device (with that device current).
+static float* static_ws_address(int* rc) {
+  static std::mutex mu;
+  static float* addr[256] = {};
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess || dev < 0 || dev >= 256) {
+    *rc = cuda_fail(e == cudaSuccess ? cudaErrorInvalidDevice : e, "current device");
+    return nullptr;
+  }
+  std::lock_guard<std::mutex> lk(mu);
+  if (!addr[dev]) {
+    void* p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_mlp_static_ws);
+    if (e != cudaSuccess) {
+      *rc = cuda_fail(e, "cudaGetSymbolAddress of the static workspace");
+      return nullptr;
+    }
+    addr[dev] = static_cast<float*>(p);
+  }
+  *rc = GIRIH_OK;
+  return addr[dev];
+}
+
 }  // namespace girih
 
 using namespace girih;
 
 extern "C" {
+
+int girih_mlp_backward_static(const float* params, const float* X, const float* t, int32_t n, int32_t d,
+                              float* grad, float* loss, void* stream) {
+  if (!t || !grad) return fail(GIRIH_EINVAL, "targets and gradient are required");
+  if (n < 1 || n > GIRIH_MLP_STATIC_MAX_ROWS)
+    return fail(GIRIH_EINVAL, "n=%d rows: the allocation-free backward pass takes 1..%d rows", n,
+                GIRIH_MLP_STATIC_MAX_ROWS);
+  int rc = GIRIH_OK;
+  float* ws = static_ws_address(&rc);
+  if (!ws) return rc;
+  // every workspace entry the gradient sums read is written by this call first (no clearing needed)
+  return mlp_forward_impl(params, X, n, d, nullptr, ws, const_cast<float*>(t), grad, loss,
+                          static_cast<cudaStream_t>(stream));
+}
 
 int64_t girih_mlp_num_params(int32_t d) { return (int64_t)HID * d + HID + HID * HID + HID + HID + 1; }
 
