@@ -38,8 +38,8 @@ struct PairAcc {
   const T* yv;       // y neighbours: yv[R + d] = value at row y + d (d != 0)
   const T* X;        // pointer to the centre in the level-t ring buffer
   T uc;
-  const T* coef;
-  int64_t gs, p;
+  const T* coef;     // coefficient grid 0 at this pair's first row and current plane
+  int64_t gs, p;     // grid stride, offset of this row from coef
   __device__ __forceinline__ T c() const { return w[Traits<S>::R]; }
   __device__ __forceinline__ T x(int d) const { return X[d]; }
   __device__ __forceinline__ T y(int d) const { return yv[Traits<S>::R + d]; }
@@ -53,11 +53,6 @@ __device__ __forceinline__ int lev_lo_of(int a, int b, int dw, int R, int t) {
 }
 __device__ __forceinline__ int lev_hi_of(int a, int b, int dw, int R, int t) {
   return min((a + 1) * dw - R * t, (b + 1) * dw + R * t);
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-template <int N>
-__device__ __forceinline__ void cp_async_wait_group() {
-  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
 }
 
 __device__ __forceinline__ void cluster_arrive_release() {
@@ -77,9 +72,11 @@ __device__ __forceinline__ void cluster_wait_acquire() {
 // stores are not held by the release); cluster wait (acquire).  The write-back and staging may
 // run while other threads already compute step w+1: the ring depth keeps those planes apart.
 // A single block (C = 1) uses one __syncthreads in place of the arrive.
+// All per-pair and per-plane positions advance incrementally: no division in the step loop.
 template <int S, typename T, int G>
 __global__ void __launch_bounds__(1024 / G) mwd_fed_kernel(const MwdArgs A) {
   constexpr int R = Traits<S>::R;
+  constexpr int NC = Traits<S>::NCOEF;
   constexpr int PD = MWD_PREFETCH;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* sm = reinterpret_cast<T*>(smem_raw);
@@ -92,7 +89,7 @@ __global__ void __launch_bounds__(1024 / G) mwd_fed_kernel(const MwdArgs A) {
   int* row_mask = lev_pp + A.H + 1;
 
   const int nx = (int)A.g.nx, ny = (int)A.g.ny, nz = (int)A.g.nz;
-  const int ldx = (int)A.g.ldx;
+  const int64_t ldx = A.g.ldx;
   const int64_t gplane = A.g.sy * A.g.ldx;
   const int rank = (C > 1) ? (int)cluster_ctarank() : 0;
   const int tile = blockIdx.x / C;
@@ -108,6 +105,7 @@ __global__ void __launch_bounds__(1024 / G) mwd_fed_kernel(const MwdArgs A) {
   if (tb > te) return;  // the whole cluster sees the same (tb, te): no barrier is skipped unevenly
   const int nlev = te - tb + 1, smax = nlev - 1;
   const int NT = blockDim.x, tid = threadIdx.x;
+  const int lane = tid & 31, warp = tid >> 5, nwarps = NT >> 5;
 
   if (tid == 0) {
     int acc = 0;
@@ -140,75 +138,65 @@ __global__ void __launch_bounds__(1024 / G) mwd_fed_kernel(const MwdArgs A) {
   }
   __syncthreads();  // level tables ready
 
-  const T* gb0 = static_cast<const T*>(A.buf0);
-  const T* gb1 = static_cast<const T*>(A.buf1);
+  const T* __restrict__ gb0 = static_cast<const T*>(A.buf0);
+  const T* __restrict__ gb1 = static_cast<const T*>(A.buf1);
   T* go0 = static_cast<T*>(A.buf0);
   T* go1 = static_cast<T*>(A.buf1);
-  const T* coef = static_cast<const T*>(A.coef);
   T cst[5];
 #pragma unroll
   for (int i = 0; i < 5; ++i) cst[i] = static_cast<T>(A.c[i]);
 
-  // Plane staging and write-back go row by row: warp k takes rows k, k + NT/32, ..., its lanes
-  // walk the row's columns (coalesced, no per-element index arithmetic beyond an add).
-  // Staged: rows y in [Y0, Y0+YW) clipped to the padded grid, columns x in [x0-R, x0+xw+R).
-  const int ylo = max(Y0, -R), yhi = min(Y0 + YW, ny + R);
-  const int nrow = max(yhi - ylo, 0);
-  const int ncol = (xw > 0) ? xw + 2 * R : 0;
-  const int lane = tid & 31, warp = tid >> 5, nwarps = NT >> 5;
-  auto load_plane = [&](int z) {
-    if (z < -R || z >= nz + R || ncol == 0) return;
-    const int slot = (z + R) % NZ;
-    const int64_t gz = (int64_t)(z + R) * gplane;
-    for (int rr = warp; rr < 2 * nrow; rr += nwarps) {
-      const int p = rr >= nrow;
-      const int y = ylo + rr - p * nrow;
-      const T* src = (p ? gb1 : gb0) + gz + (int64_t)(y + R) * ldx + x0;
-      T* dst = sm + p * be + slot * pe + (y - Y0) * XT;
-      for (int xx = lane; xx < ncol; xx += 32) cp_async(dst + xx, src + xx);
-    }
-  };
-  // Written back: rows of the projection the tile updated (row mask: which buffers), own columns.
-  auto write_plane = [&](int z) {
-    if (z < 0 || z >= nz || xw <= 0) return;
-    const int so = ((z + R) % NZ) * pe;
-    const int64_t gz = (int64_t)(z + R) * gplane;
-    for (int yy = warp; yy < YW; yy += nwarps) {
-      const int m = row_mask[yy];
-      if (m == 0) continue;
-      const int64_t go = gz + (int64_t)(Y0 + yy + R) * ldx + (x0 + R);
-      const T* src = sm + so + yy * XT + R;
-      for (int xl = lane; xl < xw; xl += 32) {
-        if (m & 1) go0[go + xl] = src[xl];
-        if (m & 2) go1[go + xl] = src[be + xl];
-      }
-    }
-  };
-
-  // this thread's row pairs: level s, first row y0 (second row y0+1 may lie outside the level)
-  int gs_[G], gcol_[G], gx_[G];
-  bool gv_[G], grow1_[G];
-  int64_t gg_[G];
+  // ---- this thread's row pairs --------------------------------------------------------------
+  // per pair: level s, ring offsets of row y0 in the level-t and level-t+1 buffers, current
+  // plane z and its ring slot (both advance by nf per step), coefficient pointer, push flags
+  int gzb_[G], gsl_[G], gvo_[G], guo_[G], gflags_[G];
+  const T* gk_[G];
   const int npairs = lev_pp[nlev];
 #pragma unroll
   for (int g = 0; g < G; ++g) {
     const int id = tid + g * NT;
     const int pr = id / XW, xl = id - pr * XW;
-    gv_[g] = (pr < npairs) && (xl < xw);
+    const bool valid = (pr < npairs) && (xl < xw);
     int s = 0;
     if (pr < npairs)
       while (lev_pp[s + 1] <= pr) ++s;
     const int y0 = (pr < npairs) ? lev_lo[s] + 2 * (pr - lev_pp[s]) : 0;
-    gs_[g] = s;
-    gx_[g] = xl;
-    grow1_[g] = (pr < npairs) && (y0 + 1 < lev_lo[s] + lev_w[s]);
-    gcol_[g] = (y0 - Y0) * XT + xl + R;
-    gg_[g] = (int64_t)(y0 + R) * ldx + (x0 + xl + R);
+    const int t = tb + s;
+    const int col = (y0 - Y0) * XT + xl + R;
+    gvo_[g] = (t & 1) * be + col;
+    guo_[g] = ((t & 1) ^ 1) * be + col;
+    gzb_[g] = -s * K;
+    int sl = (-s * K + R) % NZ;
+    gsl_[g] = sl < 0 ? sl + NZ : sl;
+    const bool row1 = (pr < npairs) && (y0 + 1 < lev_lo[s] + lev_w[s]);
+    gflags_[g] = (valid ? 1 : 0) | (row1 ? 2 : 0) | ((C > 1 && xl < R && rank > 0) ? 4 : 0) |
+                 ((C > 1 && xl >= XW - R && rank < C - 1) ? 8 : 0);
+    gk_[g] = NC ? static_cast<const T*>(A.coef) + (int64_t)(-s * K + R) * gplane + (int64_t)(y0 + R) * ldx +
+                      (x0 + xl + R)
+                : nullptr;
   }
   T win[G][2][2 * R + 1];
 
-  if (xw > 0)
-    for (int z = -R; z < PD * nf + R; ++z) load_plane(z);
+  // ---- plane staging (cp.async) and write-back, row by row: warp k takes rows k, k+nwarps, ...
+  const int ylo = max(Y0, -R), yhi = min(Y0 + YW, ny + R);
+  const int nrow = max(yhi - ylo, 0);
+  const int ncol = (xw > 0) ? xw + 2 * R : 0;
+  // next plane to stage and its ring slot; next plane to write back and its ring slot
+  int lz = -R, lsl = 0;
+  int wz = -smax * K, wsl = ((R - smax * K) % NZ + NZ) % NZ;
+
+  if (xw > 0) {
+    for (; lz < PD * nf + R; ++lz, lsl = (lsl + 1 == NZ) ? 0 : lsl + 1) {
+      const int64_t gz = (int64_t)(lz + R) * gplane;
+      for (int rr = warp; rr < 2 * nrow; rr += nwarps) {
+        const int p = rr >= nrow;
+        const int y = ylo + rr - p * nrow;
+        const T* src = (p ? gb1 : gb0) + gz + (int64_t)(y + R) * ldx + x0;
+        T* dst = sm + p * be + lsl * pe + (y - Y0) * XT;
+        for (int xx = lane; xx < ncol; xx += 32) cp_async(dst + xx, src + xx);
+      }
+    }
+  }
   cp_async_commit();
   cp_async_wait_group<0>();
   if (C > 1) cluster_barrier();
@@ -222,93 +210,130 @@ __global__ void __launch_bounds__(1024 / G) mwd_fed_kernel(const MwdArgs A) {
   for (int w = 0; w < W; ++w) {
 #pragma unroll
     for (int g = 0; g < G; ++g) {
-      if (!gv_[g]) continue;
-      const int s = gs_[g];
-      const int zb = w * nf - s * K;
-      if (zb + nf <= 0 || zb >= nz) continue;
-      const int t = tb + s;
-      const int pin = t & 1;
-      const T* Vb = sm + pin * be;
-      T* Ub = sm + (pin ^ 1) * be;
-      const int col = gcol_[g], xl = gx_[g];
-      const bool row1 = grow1_[g];
-      int sl = (zb + R) % NZ;
-      sl = sl < 0 ? sl + NZ : sl;
-      for (int f = 0; f < nf; ++f, sl = (sl + 1 == NZ) ? 0 : sl + 1) {
-        const int z = zb + f;
-        if (z < 0 || z >= nz) continue;
-        if (z == 0) {  // first plane of this level: fill the whole window
+      const int fl = gflags_[g];
+      int z = gzb_[g], sl = gsl_[g];
+      const T* kp = gk_[g];
+      if ((fl & 1) && z + nf > 0 && z < nz) {
+        for (int f = 0; f < nf; ++f) {
+          if (z >= 0 && z < nz) {
+            const T* Vb = sm + gvo_[g];
+            if (z == 0) {  // first plane of this level: fill the whole window
 #pragma unroll
-          for (int d = -R; d <= R; ++d) {
-            int sd = sl + d;
-            sd = sd < 0 ? sd + NZ : (sd >= NZ ? sd - NZ : sd);
-            win[g][0][R + d] = Vb[sd * pe + col];
-            win[g][1][R + d] = Vb[sd * pe + col + XT];
-          }
-        } else {  // slide the window up by one plane
-          int sd = sl + R;
-          sd = sd >= NZ ? sd - NZ : sd;
+              for (int d = -R; d <= R; ++d) {
+                int sd = sl + d;
+                sd = sd < 0 ? sd + NZ : (sd >= NZ ? sd - NZ : sd);
+                win[g][0][R + d] = Vb[sd * pe];
+                win[g][1][R + d] = Vb[sd * pe + XT];
+              }
+            } else {  // slide the window up by one plane
+              const int sd = (sl + R >= NZ) ? sl + R - NZ : sl + R;
 #pragma unroll
-          for (int d = 0; d < 2 * R; ++d) {
-            win[g][0][d] = win[g][0][d + 1];
-            win[g][1][d] = win[g][1][d + 1];
-          }
-          win[g][0][2 * R] = Vb[sd * pe + col];
-          win[g][1][2 * R] = Vb[sd * pe + col + XT];
-        }
-        const T* P = Vb + sl * pe + col;  // centre of row y0 at plane z
-        T yv0[2 * R + 1], yv1[2 * R + 1];  // y neighbours of row y0 and row y0+1
+              for (int d = 0; d < 2 * R; ++d) {
+                win[g][0][d] = win[g][0][d + 1];
+                win[g][1][d] = win[g][1][d + 1];
+              }
+              win[g][0][2 * R] = Vb[sd * pe];
+              win[g][1][2 * R] = Vb[sd * pe + XT];
+            }
+            const bool row1 = fl & 2;
+            const T* P = Vb + sl * pe;  // centre of row y0 at plane z
+            T yv0[2 * R + 1], yv1[2 * R + 1];  // y neighbours of row y0 and row y0+1
 #pragma unroll
-        for (int d = 1; d <= R; ++d) {
-          yv0[R - d] = P[-d * XT];
-          // row y0+1+R can lie one row past the tile when the second row is not updated
-          yv1[R + d] = (d < R || row1) ? P[(1 + d) * XT] : T(0);
-        }
+            for (int d = 1; d <= R; ++d) {
+              yv0[R - d] = P[-d * XT];
+              // row y0+1+R can lie one row past the tile when the second row is not updated
+              yv1[R + d] = (d < R || row1) ? P[(1 + d) * XT] : T(0);
+            }
 #pragma unroll
-        for (int d = 1; d <= R; ++d) {
-          yv0[R + d] = (d == 1) ? win[g][1][R] : yv1[R + d - 1];
-          yv1[R - d] = (d == 1) ? win[g][0][R] : yv0[R - d + 1];
-        }
-        const int64_t gp = (int64_t)(z + R) * gplane + gg_[g];
-        const int uo = sl * pe + col;
-        PairAcc<S, T> acc0{win[g][0], yv0, P, T(0), coef, A.g.gstride, gp};
-        if constexpr (Traits<S>::ORDER2) acc0.uc = Ub[uo];
-        const T r0 = point_update<S, T>(acc0, cst);
-        Ub[uo] = r0;
-        T r1 = T(0);
-        if (row1) {
-          PairAcc<S, T> acc1{win[g][1], yv1, P + XT, T(0), coef, A.g.gstride, gp + ldx};
-          if constexpr (Traits<S>::ORDER2) acc1.uc = Ub[uo + XT];
-          r1 = point_update<S, T>(acc1, cst);
-          Ub[uo + XT] = r1;
-        }
-        if (C > 1) {
-          const int so = (pin ^ 1) * be + uo;
-          if (xl < R && rank > 0) {  // my left edge is the left neighbour's right halo
-            st_cluster(left_base + (uint32_t)((so + XW) * (int)sizeof(T)), r0);
-            if (row1) st_cluster(left_base + (uint32_t)((so + XT + XW) * (int)sizeof(T)), r1);
+            for (int d = 1; d <= R; ++d) {
+              yv0[R + d] = (d == 1) ? win[g][1][R] : yv1[R + d - 1];
+              yv1[R - d] = (d == 1) ? win[g][0][R] : yv0[R - d + 1];
+            }
+            T* Ub = sm + guo_[g] + sl * pe;
+            PairAcc<S, T> acc0{win[g][0], yv0, P, T(0), kp, A.g.gstride, 0};
+            if constexpr (Traits<S>::ORDER2) acc0.uc = Ub[0];
+            const T r0 = point_update<S, T>(acc0, cst);
+            Ub[0] = r0;
+            T r1 = T(0);
+            if (row1) {
+              PairAcc<S, T> acc1{win[g][1], yv1, P + XT, T(0), kp, A.g.gstride, ldx};
+              if constexpr (Traits<S>::ORDER2) acc1.uc = Ub[XT];
+              r1 = point_update<S, T>(acc1, cst);
+              Ub[XT] = r1;
+            }
+            if (fl & 12) {
+              const uint32_t so = (uint32_t)(guo_[g] + sl * pe) * (uint32_t)sizeof(T);
+              if (fl & 4) {  // my left edge is the left neighbour's right halo
+                st_cluster(left_base + so + (uint32_t)(XW * (int)sizeof(T)), r0);
+                if (row1) st_cluster(left_base + so + (uint32_t)((XT + XW) * (int)sizeof(T)), r1);
+              }
+              if (fl & 8) {  // my right edge is the right neighbour's left halo
+                st_cluster(right_base + so - (uint32_t)(XW * (int)sizeof(T)), r0);
+                if (row1) st_cluster(right_base + so + (uint32_t)((XT - XW) * (int)sizeof(T)), r1);
+              }
+            }
           }
-          if (xl >= XW - R && rank < C - 1) {  // my right edge is the right neighbour's left halo
-            st_cluster(right_base + (uint32_t)((so - XW) * (int)sizeof(T)), r0);
-            if (row1) st_cluster(right_base + (uint32_t)((so + XT - XW) * (int)sizeof(T)), r1);
-          }
+          ++z;
+          sl = (sl + 1 == NZ) ? 0 : sl + 1;
+          if constexpr (NC > 0) kp += gplane;
         }
       }
+      gzb_[g] += nf;
+      gsl_[g] = (gsl_[g] + nf >= NZ) ? gsl_[g] + nf - NZ : gsl_[g] + nf;
+      if constexpr (NC > 0) gk_[g] += nf * gplane;
     }
     cp_async_wait_group<PD - 1>();
     if (C > 1) cluster_arrive_release();
     else __syncthreads();  // a single block needs no second barrier: see the loop comment
     if (xw > 0) {
-      if (w > 0)
-        for (int f = 0; f < nf; ++f) write_plane((w - 1) * nf - smax * K + f);
-      for (int f = 0; f < nf; ++f) load_plane((w + PD) * nf + R + f);
+      if (w > 0) {  // planes the top level finished in step w-1
+        for (int f = 0; f < nf; ++f, ++wz, wsl = (wsl + 1 == NZ) ? 0 : wsl + 1) {
+          if (wz < 0 || wz >= nz) continue;
+          const int64_t gz = (int64_t)(wz + R) * gplane;
+          for (int yy = warp; yy < YW; yy += nwarps) {
+            const int m = row_mask[yy];
+            if (m == 0) continue;
+            const int64_t go = gz + (int64_t)(Y0 + yy + R) * ldx + (x0 + R);
+            const T* src = sm + wsl * pe + yy * XT + R;
+            for (int xl = lane; xl < xw; xl += 32) {
+              if (m & 1) go0[go + xl] = src[xl];
+              if (m & 2) go1[go + xl] = src[be + xl];
+            }
+          }
+        }
+      }
+      for (int f = 0; f < nf; ++f, ++lz, lsl = (lsl + 1 == NZ) ? 0 : lsl + 1) {  // planes of step w+PD
+        if (lz >= nz + R) continue;
+        const int64_t gz = (int64_t)(lz + R) * gplane;
+        for (int rr = warp; rr < 2 * nrow; rr += nwarps) {
+          const int p = rr >= nrow;
+          const int y = ylo + rr - p * nrow;
+          const T* src = (p ? gb1 : gb0) + gz + (int64_t)(y + R) * ldx + x0;
+          T* dst = sm + p * be + lsl * pe + (y - Y0) * XT;
+          for (int xx = lane; xx < ncol; xx += 32) cp_async(dst + xx, src + xx);
+        }
+      }
     }
     cp_async_commit();
     if (C > 1) cluster_wait_acquire();
   }
   cp_async_wait_group<0>();
-  if (xw > 0)
-    for (int f = 0; f < nf; ++f) write_plane((W - 1) * nf - smax * K + f);
+  if (xw > 0) {  // planes the top level finished in the last step
+    for (int f = 0; f < nf; ++f, ++wz, wsl = (wsl + 1 == NZ) ? 0 : wsl + 1) {
+      if (wz < 0 || wz >= nz) continue;
+      const int64_t gz = (int64_t)(wz + R) * gplane;
+      for (int yy = warp; yy < YW; yy += nwarps) {
+        const int m = row_mask[yy];
+        if (m == 0) continue;
+        const int64_t go = gz + (int64_t)(Y0 + yy + R) * ldx + (x0 + R);
+        const T* src = sm + wsl * pe + yy * XT + R;
+        for (int xl = lane; xl < xw; xl += 32) {
+          if (m & 1) go0[go + xl] = src[xl];
+          if (m & 2) go1[go + xl] = src[be + xl];
+        }
+      }
+    }
+  }
 }
 
 MwdShape mwd_shape(int stencil, int dtype, int dw, int nf, int XW) {

@@ -2,12 +2,10 @@
 //
 // On the GPU this is the "optimal spatial blocking" reference of Sect. 5 (diamond width 0):
 // every block owns a 32 x 16 tile of x-y columns over a chunk of z planes, each thread two
-// columns (rows ty and ty+8).  Each thread keeps its columns' 2R+1 values along z in registers
-// (rotated as the block walks up in z), the current z plane of the block (plus an R-wide halo)
-// is staged in shared memory for the x and y neighbours (double-buffered, one barrier per plane),
-// the columns' next planes are prefetched several iterations ahead into a register queue and the
-// halo cells two planes ahead, so that enough loads are in flight to saturate HBM.  Offsets within
-// a plane are 32-bit (a plane of the padded grid holds fewer than 2^31 elements).  Every input is read
+// columns (rows ty and ty+8).  The tile's planes (with their R-wide halo) are staged into a
+// shared-memory ring by cp.async several planes ahead of use; each thread keeps its columns'
+// 2R+1 values along z in registers (rotated as the block walks up in z).  Every input is read
+// from HBM once per step (halo re-reads hit L2), every output written once.  Every input is read
 // from HBM once per step (halo re-reads hit L2), every output written once: 2s bytes per LUP
 // for the 7-point constant stencil, s = element size.
 #include <algorithm>
@@ -19,31 +17,35 @@ namespace girih {
 
 template <int S, typename T>
 struct NaiveAcc {
-  const T* tc;       // centre of this thread's row in the shared tile
-  int tw;            // tile row pitch
+  const T* tc;       // centre of this thread's cell in the shared plane tile
   const T* w;        // register window, w[R] = centre
-  const T* coef;
-  int64_t gs;        // grid stride
-  int64_t p;         // padded linear index of the point
+  const T* kv;       // coefficient values of this point (variable stencils)
   T uc;              // level t-1 centre (second order)
+  static constexpr int TW = 32 + 2 * Traits<S>::R;
   __device__ __forceinline__ T c() const { return w[Traits<S>::R]; }
   __device__ __forceinline__ T x(int d) const { return tc[d]; }
-  __device__ __forceinline__ T y(int d) const { return tc[d * tw]; }
+  __device__ __forceinline__ T y(int d) const { return tc[d * TW]; }
   __device__ __forceinline__ T z(int d) const { return w[Traits<S>::R + d]; }
   __device__ __forceinline__ T u() const { return uc; }
-  __device__ __forceinline__ T k(int g) const { return __ldg(coef + g * gs + p); }
+  __device__ __forceinline__ T k(int g) const { return kv[g]; }
 };
 
-// Block = 32 x TY threads covering a 32 x (2*TY) tile of (x, y) columns over a chunk of z
-// planes; each thread owns rows ty and ty + TY (two independent updates per plane).
+// Block = 32 x TY threads over a 32 x 2TY tile of (x, y) columns and a chunk of z planes; each
+// thread owns rows ty and ty + TY.  The tile's planes (with the R-wide halo) stream through a
+// ring of NP shared-memory slots filled by cp.async PD planes ahead of use (one commit group per
+// plane), so that many loads are in flight without holding registers.  The z window of each
+// owned column stays in registers; its new value and the x/y neighbours come from the ring.
+// One barrier per plane.
 template <int S, typename T, int TY, int PD>
 __global__ void __launch_bounds__(32 * TY) naive_kernel(const NaiveArgs a) {
   constexpr int R = Traits<S>::R;
+  constexpr int NC = Traits<S>::NCOEF;
   constexpr int ROWS = 2 * TY;
-  constexpr int TXW = 32 + 2 * R, TYW = ROWS + 2 * R;
-  constexpr int NH = 2 * R * (32 + ROWS);                 // halo cells of the tile (star stencil)
-  constexpr int HPT = (NH + 32 * TY - 1) / (32 * TY);     // halo cells per thread
-  __shared__ T tile[2][TYW * TXW];                        // double-buffered: one barrier per plane
+  constexpr int TXW = 32 + 2 * R, TYW = ROWS + 2 * R, TP = TXW * TYW;
+  constexpr int NP = R + PD + 2;  // ring slots: planes z-1 .. z+R+PD are live at once
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* ring = reinterpret_cast<T*>(smem_raw);       // [NP][TYW][TXW]
+  T* uring = ring + NP * TP;                       // second order: [NP][ROWS][32] level t-1 centres
   const T* __restrict__ V = static_cast<const T*>(a.V);
   T* __restrict__ U = static_cast<T*>(a.U);
   const T* __restrict__ coef = static_cast<const T*>(a.coef);
@@ -53,103 +55,95 @@ __global__ void __launch_bounds__(32 * TY) naive_kernel(const NaiveArgs a) {
 
   const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * 32 + tx;
   const int nx = (int)a.g.nx, ny = (int)a.g.ny, nz = (int)a.g.nz;
-  const int64_t plane = a.g.sy * a.g.ldx;
   const int ldx = (int)a.g.ldx;
-  const int x = blockIdx.x * 32 + tx;
+  const int64_t plane = a.g.sy * a.g.ldx;
+  const int bx = blockIdx.x * 32, by = blockIdx.y * ROWS;  // padded coords of the tile's corner
   const int z0 = blockIdx.z * a.zc;
-  const int z1 = min(z0 + a.zc, nz);
-  // the block starts at padded plane z0; all offsets below are relative to that plane
-  const T* Vz = V + (int64_t)z0 * plane;
-  T* Uz = U + (int64_t)(z0 + R) * plane;
+  const int nzb = min(a.zc, nz - z0);
+  // tile rows/cols that exist in the padded grid
+  const int trows = min(TYW, ny + 2 * R - by), tcols = min(TXW, nx + 2 * R - bx);
+  const T* Vb = V + (int64_t)z0 * plane + (int64_t)by * ldx + bx;  // padded plane z0, tile corner
+  T* Ub = U + (int64_t)(z0 + R) * plane + (int64_t)(by + R) * ldx + (bx + R);
 
-  int yr[2];
-  bool inb[2], act[2];
-  int colo[2];  // offset of the column within a plane
-#pragma unroll
-  for (int r = 0; r < 2; ++r) {
-    yr[r] = blockIdx.y * ROWS + ty + r * TY;
-    inb[r] = (x < nx + R) && (yr[r] < ny + R);
-    act[r] = (x < nx) && (yr[r] < ny);
-    colo[r] = (yr[r] + R) * ldx + (x + R);
-  }
-
-  // this thread's halo cells (fixed for the whole z walk): tile offset and plane offset
-  int hoff[HPT], hcol[HPT];
-#pragma unroll
-  for (int k = 0; k < HPT; ++k) {
-    const int i = tid + k * 32 * TY;
-    hoff[k] = -1;
-    hcol[k] = -1;
-    if (i < NH) {
-      int hx, hy;
-      if (i < 2 * R * 32) {
-        const int r = i / 32;
-        hx = R + (i % 32);
-        hy = (r < R) ? r : ROWS + r;
-      } else {
-        const int j = i - 2 * R * 32, cc = j / ROWS;
-        hy = R + j % ROWS;
-        hx = (cc < R) ? cc : 32 + cc;
+  // stage padded plane z0 + q (q = 0 .. nzb + 2R - 1) into ring slot q % NP
+  auto stage = [&](int q) {
+    if (q < nzb + 2 * R) {
+      T* dst = ring + (q % NP) * TP;
+      const T* src = Vb + (int64_t)q * plane;
+      for (int r = ty; r < trows; r += TY)
+        for (int c = tx; c < tcols; c += 32) cp_async(dst + r * TXW + c, src + r * ldx + c);
+      if constexpr (Traits<S>::ORDER2) {
+        // level t-1 centres of interior plane z0 + q - R (used when that plane is updated)
+        const int zi = q - R;
+        if (zi >= 0 && zi < nzb) {
+          T* ud = uring + (q % NP) * (ROWS * 32);
+          const T* us = Ub + (int64_t)zi * plane;
+          for (int r = ty; r < ROWS && by + r < ny; r += TY)
+            if (bx + tx < nx) cp_async(ud + r * 32 + tx, us + r * ldx + tx);
+        }
       }
-      const int px = blockIdx.x * 32 + hx, py = blockIdx.y * ROWS + hy;
-      hoff[k] = hy * TXW + hx;
-      if (px < nx + 2 * R && py < ny + 2 * R) hcol[k] = py * ldx + px;
     }
-  }
+    cp_async_commit();
+  };
 
-  // register windows (padded planes z..z+2R for interior plane z) and a queue of PD planes ahead
-  T w[2][2 * R + 1], q[2][PD], hv[2][HPT];
-  const int zlast = z1 - 1 + 2 * R - z0;  // last plane (relative) this block reads
+  // planes z0 .. z0+2R fill the windows; planes up to z0 + 2R + PD are staged ahead
+  for (int q = 0; q <= 2 * R + PD; ++q) stage(q);
+  cp_async_wait_all();
+  __syncthreads();
+
+  bool act[2];
+  int cofs[2];
+  T w[2][2 * R + 1];
 #pragma unroll
   for (int r = 0; r < 2; ++r) {
+    const int row = ty + r * TY;
+    act[r] = (bx + tx < nx) && (by + row < ny);
+    cofs[r] = (row + R) * TXW + tx + R;
 #pragma unroll
-    for (int i = 0; i <= 2 * R; ++i) w[r][i] = inb[r] ? Vz[i * plane + colo[r]] : T(0);
-#pragma unroll
-    for (int i = 0; i < PD; ++i)
-      q[r][i] = (inb[r] && 2 * R + 1 + i <= zlast) ? Vz[(2 * R + 1 + i) * plane + colo[r]] : T(0);
+    for (int i = 0; i <= 2 * R; ++i) w[r][i] = ring[i * TP + cofs[r]];
   }
+  // coefficients of the first plane, then one plane ahead
+  T kv[2][NC > 0 ? NC : 1], kn[2][NC > 0 ? NC : 1];
+  const int64_t gs = a.g.gstride;
+  const T* cb = coef ? coef + (int64_t)(z0 + R) * plane + (int64_t)(by + R) * ldx + (bx + R) : nullptr;
+  if constexpr (NC > 0) {
 #pragma unroll
-  for (int k = 0; k < HPT; ++k) {
-    hv[0][k] = (hcol[k] >= 0) ? Vz[R * plane + hcol[k]] : T(0);
-    hv[1][k] = (hcol[k] >= 0 && z0 + 1 < z1) ? Vz[(R + 1) * plane + hcol[k]] : T(0);
+    for (int r = 0; r < 2; ++r)
+#pragma unroll
+      for (int g = 0; g < NC; ++g) kn[r][g] = act[r] ? __ldg(cb + g * gs + (ty + r * TY) * ldx + tx) : T(0);
   }
 
-  int buf = 0;
-  for (int zr = 0; zr < z1 - z0; ++zr) {
-    T* tl = tile[buf];
+  for (int zr = 0; zr < nzb; ++zr) {
+    if constexpr (NC > 0) {
 #pragma unroll
-    for (int r = 0; r < 2; ++r) tl[(ty + r * TY + R) * TXW + tx + R] = w[r][R];
+      for (int r = 0; r < 2; ++r)
 #pragma unroll
-    for (int k = 0; k < HPT; ++k)
-      if (hoff[k] >= 0) tl[hoff[k]] = hv[0][k];
-    // halo cells two planes ahead
-#pragma unroll
-    for (int k = 0; k < HPT; ++k) {
-      hv[0][k] = hv[1][k];
-      hv[1][k] = (hcol[k] >= 0 && z0 + zr + 2 < z1) ? Vz[(zr + 2 + R) * plane + hcol[k]] : T(0);
+        for (int g = 0; g < NC; ++g) {
+          kv[r][g] = kn[r][g];
+          kn[r][g] = (act[r] && zr + 1 < nzb) ? __ldg(cb + g * gs + (int64_t)(zr + 1) * plane + (ty + r * TY) * ldx + tx)
+                                              : T(0);
+        }
     }
-    __syncthreads();
+    const T* tl = ring + ((zr + R) % NP) * TP;  // padded plane z0 + zr + R = interior plane z0 + zr
 #pragma unroll
     for (int r = 0; r < 2; ++r) {
       if (act[r]) {
-        const int64_t off = (int64_t)zr * plane + colo[r];
-        NaiveAcc<S, T> acc{tl + (ty + r * TY + R) * TXW + tx + R, TXW, w[r], coef, a.g.gstride,
-                           (int64_t)(z0 + zr + R) * plane + colo[r], T(0)};
-        if constexpr (Traits<S>::ORDER2) acc.uc = Uz[off];
-        Uz[off] = point_update<S, T>(acc, cst);
+        NaiveAcc<S, T> acc{tl + cofs[r], w[r], kv[r], T(0)};
+        if constexpr (Traits<S>::ORDER2) acc.uc = uring[((zr + R) % NP) * (ROWS * 32) + (ty + r * TY) * 32 + tx];
+        Ub[(int64_t)zr * plane + (ty + r * TY) * ldx + tx] = point_update<S, T>(acc, cst);
       }
     }
+    // advance: stage the plane PD ahead, wait for the next window value, one barrier
+    stage(zr + 2 * R + PD + 1);
+    cp_async_wait_group<PD>();
+    __syncthreads();
+    const T* nw = ring + ((zr + 2 * R + 1) % NP) * TP;
 #pragma unroll
     for (int r = 0; r < 2; ++r) {
 #pragma unroll
       for (int i = 0; i < 2 * R; ++i) w[r][i] = w[r][i + 1];
-      w[r][2 * R] = q[r][0];
-#pragma unroll
-      for (int i = 0; i < PD - 1; ++i) q[r][i] = q[r][i + 1];
-      const int pz = zr + 2 * R + 1 + PD;
-      q[r][PD - 1] = (inb[r] && pz <= zlast) ? Vz[pz * plane + colo[r]] : T(0);
+      w[r][2 * R] = nw[cofs[r]];
     }
-    buf ^= 1;
   }
 }
 
@@ -157,13 +151,28 @@ constexpr int kTY = 8;
 
 int naive_block_rows(int, int) { return 2 * kTY; }
 
+template <int S>
+constexpr int naive_pd() { return Traits<S>::R == 1 ? 4 : 2; }
+
+template <int S, typename T>
+static size_t naive_smem() {
+  constexpr int R = Traits<S>::R, PD = naive_pd<S>();
+  constexpr int NP = R + PD + 2, TP = (32 + 2 * R) * (2 * kTY + 2 * R);
+  return sizeof(T) * ((size_t)NP * TP + (Traits<S>::ORDER2 ? (size_t)NP * 2 * kTY * 32 : 0));
+}
+
 template <int S, typename T>
 static cudaError_t launch_one(const NaiveArgs& a, cudaStream_t st) {
   dim3 block(32, kTY);
   dim3 grid((unsigned)((a.g.nx + 31) / 32), (unsigned)((a.g.ny + 2 * kTY - 1) / (2 * kTY)),
             (unsigned)((a.g.nz + a.zc - 1) / a.zc));
-  constexpr int PD = (Traits<S>::R == 4 && sizeof(T) == 8) ? 2 : 3;
-  naive_kernel<S, T, kTY, PD><<<grid, block, 0, st>>>(a);
+  const size_t sm = naive_smem<S, T>();
+  auto k = naive_kernel<S, T, kTY, naive_pd<S>()>;
+  if (sm > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+  }
+  k<<<grid, block, sm, st>>>(a);
   return cudaGetLastError();
 }
 
