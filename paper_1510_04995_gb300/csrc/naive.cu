@@ -42,7 +42,9 @@ __global__ void __launch_bounds__(32 * TY) naive_kernel(const NaiveArgs a) {
   constexpr int NC = Traits<S>::NCOEF;
   constexpr int ROWS = 2 * TY;
   constexpr int TXW = 32 + 2 * R, TYW = ROWS + 2 * R, TP = TXW * TYW;
-  constexpr int NP = R + PD + 2;  // ring slots: planes z-1 .. z+R+PD are live at once
+  // ring slots: the first window needs planes 0..2R plus PD staged ahead (2R+PD+1 at once); in
+  // the steady state planes z+R .. z+2R+PD+1 are live (R+PD+2), which is never more
+  constexpr int NP = 2 * R + PD + 1;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* ring = reinterpret_cast<T*>(smem_raw);       // [NP][TYW][TXW]
   T* uring = ring + NP * TP;                       // second order: [NP][ROWS][32] level t-1 centres
@@ -157,7 +159,7 @@ constexpr int naive_pd() { return Traits<S>::R == 1 ? 4 : 2; }
 template <int S, typename T>
 static size_t naive_smem() {
   constexpr int R = Traits<S>::R, PD = naive_pd<S>();
-  constexpr int NP = R + PD + 2, TP = (32 + 2 * R) * (2 * kTY + 2 * R);
+  constexpr int NP = 2 * R + PD + 1, TP = (32 + 2 * R) * (2 * kTY + 2 * R);
   return sizeof(T) * ((size_t)NP * TP + (Traits<S>::ORDER2 ? (size_t)NP * 2 * kTY * 32 : 0));
 }
 
