@@ -130,7 +130,10 @@ int run_sweep(Plan* p, int64_t T, void* u, void* u_prev, const void* coeffs, con
     NaiveArgs a{};
     a.g = g;
     a.coef = coeffs;
-    for (int i = 0; i < 5; ++i) a.c[i] = c[i];
+    for (int i = 0; i < 5; ++i) {
+      a.c[i] = c[i];
+      a.cf[i] = (float)c[i];
+    }
     a.zc = 64;
     void* buf[2] = {u, u_prev};
     for (int64_t t = 0; t < T && e == cudaSuccess; ++t) {
@@ -149,7 +152,10 @@ int run_sweep(Plan* p, int64_t T, void* u, void* u_prev, const void* coeffs, con
     a.buf0 = u;
     a.buf1 = u_prev;
     a.coef = coeffs;
-    for (int i = 0; i < 5; ++i) a.c[i] = c[i];
+    for (int i = 0; i < 5; ++i) {
+      a.c[i] = c[i];
+      a.cf[i] = (float)c[i];
+    }
     a.T = (int32_t)T;
     a.dw = cfg.dw;
     a.nf = cfg.nf;

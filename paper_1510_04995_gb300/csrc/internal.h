@@ -22,6 +22,7 @@ struct NaiveArgs {
   void* U;
   const void* coef;
   double c[5];
+  float cf[5];  // the same constants rounded to FP32 (FP32 kernels read these: no conversion on device)
   int32_t zc;  // z planes per block
 };
 cudaError_t launch_naive_step(int stencil, int dtype, const NaiveArgs& a, cudaStream_t st);
@@ -34,6 +35,7 @@ struct MwdArgs {
   void* buf1;        // odd time levels (the caller's u_prev)
   const void* coef;
   double c[5];
+  float cf[5];       // the same constants rounded to FP32
   int32_t T;         // total time steps of the sweep
   int32_t rho;       // diamond row index
   int32_t dw, nf, K, H;  // diamond width, wavefront width, level skew (R + nf), levels per diamond

@@ -144,7 +144,8 @@ __global__ void __launch_bounds__(1024 / G) mwd_fed_kernel(const MwdArgs A) {
   T* go1 = static_cast<T*>(A.buf1);
   T cst[5];
 #pragma unroll
-  for (int i = 0; i < 5; ++i) cst[i] = static_cast<T>(A.c[i]);
+  for (int i = 0; i < 5; ++i) cst[i] = sizeof(T) == 8 ? static_cast<T>(A.c[i]) : static_cast<T>(A.cf[i]);
+  const int64_t gstride = A.g.gstride;
 
   // ---- this thread's row pairs --------------------------------------------------------------
   // per pair: level s, ring offsets of row y0 in the level-t and level-t+1 buffers, current
@@ -250,13 +251,13 @@ __global__ void __launch_bounds__(1024 / G) mwd_fed_kernel(const MwdArgs A) {
               yv1[R - d] = (d == 1) ? win[g][0][R] : yv0[R - d + 1];
             }
             T* Ub = sm + guo_[g] + sl * pe;
-            PairAcc<S, T> acc0{win[g][0], yv0, P, T(0), kp, A.g.gstride, 0};
+            PairAcc<S, T> acc0{win[g][0], yv0, P, T(0), kp, gstride, 0};
             if constexpr (Traits<S>::ORDER2) acc0.uc = Ub[0];
             const T r0 = point_update<S, T>(acc0, cst);
             Ub[0] = r0;
             T r1 = T(0);
             if (row1) {
-              PairAcc<S, T> acc1{win[g][1], yv1, P + XT, T(0), kp, A.g.gstride, ldx};
+              PairAcc<S, T> acc1{win[g][1], yv1, P + XT, T(0), kp, gstride, ldx};
               if constexpr (Traits<S>::ORDER2) acc1.uc = Ub[XT];
               r1 = point_update<S, T>(acc1, cst);
               Ub[XT] = r1;

@@ -53,7 +53,7 @@ __global__ void __launch_bounds__(32 * TY) naive_kernel(const NaiveArgs a) {
   const T* __restrict__ coef = static_cast<const T*>(a.coef);
   T cst[5];
 #pragma unroll
-  for (int i = 0; i < 5; ++i) cst[i] = static_cast<T>(a.c[i]);
+  for (int i = 0; i < 5; ++i) cst[i] = sizeof(T) == 8 ? static_cast<T>(a.c[i]) : static_cast<T>(a.cf[i]);
 
   const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * 32 + tx;
   const int nx = (int)a.g.nx, ny = (int)a.g.ny, nz = (int)a.g.nz;
@@ -67,21 +67,46 @@ __global__ void __launch_bounds__(32 * TY) naive_kernel(const NaiveArgs a) {
   const T* Vb = V + (int64_t)z0 * plane + (int64_t)by * ldx + bx;  // padded plane z0, tile corner
   T* Ub = U + (int64_t)(z0 + R) * plane + (int64_t)(by + R) * ldx + (bx + R);
 
+  // This thread's cells of one staged plane (fixed for the whole z walk): shared offset within a
+  // ring slot and offset within a global plane relative to the tile corner, -1 = none.
+  constexpr int CPT = (TP + 32 * TY - 1) / (32 * TY);
+  int so[CPT], go[CPT];
+#pragma unroll
+  for (int k = 0; k < CPT; ++k) {
+    const int i = tid + k * 32 * TY;
+    const int r = i / TXW, c = i - r * TXW;
+    const bool ok = i < TP && r < trows && c < tcols;
+    so[k] = ok ? i : -1;
+    go[k] = ok ? r * ldx + c : 0;
+  }
+  constexpr int UPT = (ROWS * 32 + 32 * TY - 1) / (32 * TY);  // level t-1 centres per thread
+  int uso[UPT], ugo[UPT];
+#pragma unroll
+  for (int k = 0; k < UPT; ++k) {
+    const int i = tid + k * 32 * TY;
+    const int r = i / 32, c = i - r * 32;
+    const bool ok = Traits<S>::ORDER2 && i < ROWS * 32 && by + r < ny && bx + c < nx;
+    uso[k] = ok ? i : -1;
+    ugo[k] = ok ? r * ldx + c : 0;
+  }
+
   // stage padded plane z0 + q (q = 0 .. nzb + 2R - 1) into ring slot q % NP
   auto stage = [&](int q) {
     if (q < nzb + 2 * R) {
       T* dst = ring + (q % NP) * TP;
       const T* src = Vb + (int64_t)q * plane;
-      for (int r = ty; r < trows; r += TY)
-        for (int c = tx; c < tcols; c += 32) cp_async(dst + r * TXW + c, src + r * ldx + c);
+#pragma unroll
+      for (int k = 0; k < CPT; ++k)
+        if (so[k] >= 0) cp_async(dst + so[k], src + go[k]);
       if constexpr (Traits<S>::ORDER2) {
         // level t-1 centres of interior plane z0 + q - R (used when that plane is updated)
         const int zi = q - R;
         if (zi >= 0 && zi < nzb) {
           T* ud = uring + (q % NP) * (ROWS * 32);
           const T* us = Ub + (int64_t)zi * plane;
-          for (int r = ty; r < ROWS && by + r < ny; r += TY)
-            if (bx + tx < nx) cp_async(ud + r * 32 + tx, us + r * ldx + tx);
+#pragma unroll
+          for (int k = 0; k < UPT; ++k)
+            if (uso[k] >= 0) cp_async(ud + uso[k], us + ugo[k]);
         }
       }
     }

@@ -179,3 +179,84 @@ def tune(p, params: np.ndarray, k: int = 5, tol: float = 0.05, max_steps: int = 
     check(lib().girih_tune_learned(p.handle, ctypes.c_void_p(P.data_ptr()), k, tol, max_steps, ctypes.byref(best),
                                    ctypes.byref(nm)))
     return best, nm.value, time.perf_counter() - t0
+
+
+def experiment(out_dir: str, stencils=(0, 1, 2, 3), dtypes=("f64", "f32"), grids=None, T: int = 16,
+               tol: float = 0.05, max_steps: int = 32, k: int = 5, epochs: int = 3000, live: bool = True,
+               log=print):
+    """The learned-tuner experiment: exhaustive timings on all grids, network trained on the
+    non-held-out grids, regret and tuning-time fraction on the held-out grids (offline from the
+    database, and live with girih_tune_learned)."""
+    import json
+    grids = grids or GRIDS
+    os.makedirs(out_dir, exist_ok=True)
+    db = os.path.join(out_dir, "tune_db.csv")
+    times = os.path.join(out_dir, "tune_times.csv")
+    problems = [(s, d, *g) for s in stencils for d in dtypes for g in grids]
+    done = set()
+    if os.path.exists(db):
+        done = {problem_key(r) for r in load_db(db)}
+    todo = [p for p in problems if (p[0], _dt(p[1]), p[2], p[3], p[4]) not in done]
+    collect(db, todo, T=T, tol=tol, max_steps=max_steps, times_path=times, log=log)
+    rows = load_db(db)
+    held = {tuple(grids[i]) for i in HELD_OUT if i < len(grids)}
+    train_rows = [r for r in rows if (int(r["nx"]), int(r["ny"]), int(r["nz"])) not in held]
+    test_rows = [r for r in rows if (int(r["nx"]), int(r["ny"]), int(r["nz"])) in held]
+    Xtr, ytr = features(train_rows), targets(train_rows)
+    t0 = time.perf_counter()
+    params, hist = train(Xtr, ytr, epochs=epochs, log=None)
+    train_s = time.perf_counter() - t0
+    np.save(os.path.join(out_dir, "mlp_params.npy"), params)
+    res = evaluate(test_rows, predict(params, features(test_rows)), k) if test_rows else []
+    # the method without the network: the plan's model-based default configuration
+    base = []
+    for key in sorted({problem_key(r) for r in test_rows}):
+        s, d, nx, ny, nz = key
+        p = plan(s, nx, ny, nz, dtype=d, T=T)
+        dflt = p.config.as_dict()
+        rs = [r for r in test_rows if problem_key(r) == key]
+        best = max(r["glups"] for r in rs)
+        match = [r["glups"] for r in rs if row_config(r).as_dict() == dflt]
+        base.append({"problem": key, "default_ratio": (match[0] / best) if match else None})
+        p.close()
+    live_res = []
+    if live:
+        for key in sorted({problem_key(r) for r in test_rows}):
+            s, d, nx, ny, nz = key
+            rs = [r for r in test_rows if problem_key(r) == key]
+            p = plan(s, nx, ny, nz, dtype=d, T=T)
+            row, nm, secs = tune(p, params, k=k, tol=tol, max_steps=max_steps)
+            exh_secs = sum(r["tune_seconds"] for r in rs)
+            live_res.append({"problem": key, "learned_glups": row.glups, "measured": nm, "seconds": secs,
+                             "exhaustive_best": max(r["glups"] for r in rs), "exhaustive_seconds": exh_secs})
+            p.close()
+    report = {"train_problems": len({problem_key(r) for r in train_rows}), "train_rows": len(train_rows),
+              "train_seconds": train_s, "loss_history": hist, "k": k, "offline": res, "default": base,
+              "live": live_res}
+    with open(os.path.join(out_dir, "report.json"), "w") as f:
+        json.dump(report, f, indent=1)
+    return report
+
+
+if __name__ == "__main__":
+    import argparse
+    import json
+    ap = argparse.ArgumentParser(description="learned-tuner experiment (exhaustive DB, train, evaluate)")
+    ap.add_argument("out_dir")
+    ap.add_argument("--stencils", default="0,1,2,3")
+    ap.add_argument("--dtypes", default="f64,f32")
+    ap.add_argument("--grids", default="", help="indices into GRIDS, e.g. 0,1,2 (default all 12)")
+    ap.add_argument("--T", type=int, default=16)
+    ap.add_argument("--tol", type=float, default=0.05)
+    ap.add_argument("--max-steps", type=int, default=32)
+    ap.add_argument("--k", type=int, default=5)
+    ap.add_argument("--epochs", type=int, default=3000)
+    ap.add_argument("--no-live", action="store_true")
+    a = ap.parse_args()
+    from . import build as _b
+    _b.build()
+    gl = [GRIDS[int(i)] for i in a.grids.split(",")] if a.grids else None
+    rep = experiment(a.out_dir, tuple(int(s) for s in a.stencils.split(",")), tuple(a.dtypes.split(",")), gl, a.T,
+                     a.tol, a.max_steps, a.k, a.epochs, not a.no_live)
+    print(json.dumps({k: rep[k] for k in ("train_problems", "train_rows", "train_seconds", "offline", "default",
+                                          "live")}, indent=1))
