@@ -212,7 +212,12 @@ def main():
     stencil, dtype, nx, ny, nz, T = WORKLOADS[args.workload]
     if args.grid:
         nx, ny, nz = (int(v) for v in args.grid.split(","))
-    p = girih.plan(stencil, nx, ny, nz, dtype=dtype, T=T)
+    # leading dimension padded to a 16-byte multiple (Sect. 4.2.3 pads the leading dimension): rows
+    # start on 16-byte boundaries, which lets the blocked kernel move whole rows with bulk copies
+    R = inputs.RADIUS[stencil]
+    a16 = 16 // (8 if dtype == "f64" else 4)
+    ldx = -(-(nx + 2 * R) // a16) * a16
+    p = girih.plan(stencil, nx, ny, nz, dtype=dtype, T=T, ldx=ldx)
     if args.algo == "naive":
         cfg = girih.config(girih.NAIVE)
     elif args.algo == "mwd" and args.dw:
@@ -222,7 +227,7 @@ def main():
         cfg = girih.Config(**tuned) if tuned else p.config
     p.set_config(cfg)
 
-    u, up, co, c = inputs.make_problem(stencil, nx, ny, nz, backend="torch", device=dev)
+    u, up, co, c = inputs.make_problem(stencil, nx, ny, nz, backend="torch", device=dev, ldx=ldx)
     tdt = torch.float64 if dtype == "f64" else torch.float32
     u, up = u.to(tdt).contiguous(), up.to(tdt).contiguous()
     co = co.to(tdt).contiguous() if co is not None else None
@@ -321,7 +326,8 @@ def main():
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": dtype, "data": "synthetic",
             "config": {"workload": args.workload, "stencil": STENCIL_NAME[stencil], "nx": nx, "ny": ny, "nz": nz,
-                       "T": T, "algo": "mwd" if cfg.algo == girih.MWD else "naive", "kernel_config": cfg.as_dict(),
+                       "T": T, "ldx": ldx, "algo": "mwd" if cfg.algo == girih.MWD else "naive",
+                       "kernel_config": cfg.as_dict(),
                        "l2": "inputs larger than L2 (each grid > 126 MB)", "parallelism": f"replicas x{ws}"},
             "naive_glups": naive, "speedup_vs_naive": (value / naive) if naive else None,
             "gpu_launches": launches * args.steps,

@@ -120,7 +120,9 @@ GIRIH_API int girih_config_check(girih_plan_t plan, const girih_config* cfg, int
  *           back; their halo cells are never read.
  *   params  coefficients and optional forced configuration (NULL: 7PT_CONST/25PT_CONST use the
  *           workload constants c0=0.4,c1=0.1 / c0=-0.9,c_r=0.1/2^r).
- * Pointers must be 8-byte (F64) or 4-byte (F32) aligned and u != u_prev.  The two buffers'
+ * Pointers must be 8-byte (F64) or 4-byte (F32) aligned and u != u_prev.  When ldx*elem is a
+ * multiple of 16 bytes and the buffers are 16-byte aligned, the blocked kernel moves rows with the
+ * bulk-copy engine; otherwise it stages elements (same results).  The two buffers'
  * roles alternate every step (Listing 3's pointer swap); for odd T one in-place exchange kernel
  * puts level T back into u.  EINVAL leaves the buffers untouched and enqueues nothing.       */
 GIRIH_API int girih_run(girih_plan_t plan, void* u, void* u_prev, const void* coeffs, const girih_params* params,
@@ -131,6 +133,11 @@ GIRIH_API int girih_run(girih_plan_t plan, void* u, void* u_prev, const void* co
  * girih_run on `stream`, copies u and u_prev back, and synchronises the stream.               */
 GIRIH_API int girih_run_host(girih_plan_t plan, void* u_host, void* u_prev_host, const void* coeffs_host,
                    const girih_params* params, void* stream);
+
+/* Synchronise `stream` and report device-side failures of the plan's previous runs: GIRIH_OK,
+ * GIRIH_ETIMEOUT (a bounded wait of the blocked kernel ran out; the results are not valid) or
+ * GIRIH_EKERNEL.  Clears the plan's error word.  girih_run_host calls it itself.            */
+GIRIH_API int girih_status(girih_plan_t plan, void* stream);
 
 /* Elements of one padded grid for the plan ((nz+2R)*(ny+2R)*ldx) and the halo width R. */
 GIRIH_API int girih_plan_layout(girih_plan_t plan, int64_t* elems_per_grid, int32_t* radius, int64_t* ldx);

@@ -70,6 +70,7 @@ _SIGS = {
     "girih_config_check": (ctypes.c_int, [_VP, ctypes.POINTER(Config), ctypes.POINTER(_I64)]),
     "girih_run": (ctypes.c_int, [_VP, _VP, _VP, _VP, ctypes.POINTER(Params), _VP]),
     "girih_run_host": (ctypes.c_int, [_VP, _VP, _VP, _VP, ctypes.POINTER(Params), _VP]),
+    "girih_status": (ctypes.c_int, [_VP, _VP]),
     "girih_plan_layout": (ctypes.c_int, [_VP, ctypes.POINTER(_I64), ctypes.POINTER(_I32), ctypes.POINTER(_I64)]),
     "girih_plan_launch_count": (ctypes.c_int, [_VP, ctypes.POINTER(Config), ctypes.POINTER(_I64)]),
     "girih_last_error": (ctypes.c_char_p, []),
@@ -223,6 +224,11 @@ def run(p: Plan, u, u_prev, coeffs=None, c=None, cfg: Config | None = None, stre
     check(lib().girih_run(p.handle, ctypes.c_void_p(u.data_ptr()), ctypes.c_void_p(u_prev.data_ptr()),
                           ctypes.c_void_p(coeffs.data_ptr()) if coeffs is not None else None,
                           ctypes.byref(prm), _stream_handle(stream)))
+
+
+def status(p: Plan, stream=None):
+    """Synchronise and raise GirihError if a device-side wait of a previous run ran out."""
+    check(lib().girih_status(p.handle, _stream_handle(stream)))
 
 
 def run_host(p: Plan, u, u_prev, coeffs=None, c=None, cfg: Config | None = None, stream=None):

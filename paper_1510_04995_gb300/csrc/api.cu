@@ -59,7 +59,7 @@ static int slab_width(int64_t nx, int C) {
   return (int)((w + 15) / 16 * 16);
 }
 
-int check_config(const Plan* p, const girih_config* c, int64_t* smem_out, int* xw_out) {
+int check_config(const Plan* p, const girih_config* c, int64_t* smem_out, int* xw_out, int* g_out) {
   if (!c) return fail(GIRIH_EINVAL, "config is NULL");
   if (c->algo == GIRIH_ALGO_NAIVE) {
     if (smem_out) *smem_out = 0;
@@ -76,10 +76,12 @@ int check_config(const Plan* p, const girih_config* c, int64_t* smem_out, int* x
   if (c->threads < 64 || c->threads > 1024 || c->threads % 32 != 0)
     return fail(GIRIH_EINVAL, "threads=%d must be a multiple of 32 in 64..1024", c->threads);
   const int XW = slab_width(p->nx, c->cluster);
-  const int G = mwd_pairs_per_thread(R, c->dw, XW, c->threads);
+  // with a 16-byte aligned layout one warp of the block moves data and the others compute
+  const int cthreads = p->bulk_layout ? c->threads - 32 : c->threads;
+  const int G = mwd_pairs_per_thread(R, c->dw, XW, c->threads, cthreads);
   if (G == 0)
-    return fail(GIRIH_EINVAL, "dw=%d with a %d-wide slab has %d row pairs, more than 4 per thread of %d", c->dw, XW,
-                mwd_max_pairs(R, c->dw) * XW, c->threads);
+    return fail(GIRIH_EINVAL, "dw=%d with a %d-wide slab has %d row pairs, more than 4 per computing thread of %d",
+                c->dw, XW, mwd_max_pairs(R, c->dw) * XW, cthreads);
   if (p->dtype == GIRIH_F64 && R == 4 && G > 2)
     return fail(GIRIH_EINVAL, "25-point FP64 tiles allow at most 2 row pairs per thread (registers)");
   if (p->ny > (1 << 28) || p->nx > (1 << 28) || p->nz > (1 << 28))
@@ -89,7 +91,7 @@ int check_config(const Plan* p, const girih_config* c, int64_t* smem_out, int* x
     return fail(GIRIH_EINVAL, "config needs %lld bytes of shared memory per block (device limit %lld)",
                 (long long)sh.smem_bytes, (long long)p->smem_optin);
   int maxc = 0;
-  cudaError_t e = mwd_prepare(p->stencil, p->dtype, c->cluster, c->threads, G, sh.smem_bytes, &maxc);
+  cudaError_t e = mwd_prepare(p->stencil, p->dtype, c->cluster, c->threads, G, p->bulk_layout, sh.smem_bytes, &maxc);
   if (e != cudaSuccess) {
     cudaGetLastError();
     return fail(GIRIH_EINVAL, "cluster of %d blocks with %lld bytes cannot be configured: %s", c->cluster,
@@ -98,6 +100,7 @@ int check_config(const Plan* p, const girih_config* c, int64_t* smem_out, int* x
   if (maxc < 1) return fail(GIRIH_EINVAL, "cluster of %d blocks cannot be scheduled", c->cluster);
   if (smem_out) *smem_out = sh.smem_bytes;
   if (xw_out) *xw_out = XW;
+  if (g_out) *g_out = G;
   return GIRIH_OK;
 }
 
@@ -111,7 +114,7 @@ static girih_config default_config(Plan* p) {
     for (int dw = 2 * R; dw <= 64 * R; dw += 2 * R) {
       girih_config c{GIRIH_ALGO_MWD, dw, 1, C, 512, GIRIH_FED};
       int64_t smem = 0;
-      if (check_config(p, &c, &smem, nullptr) != GIRIH_OK) continue;
+      if (check_config(p, &c, &smem, nullptr, nullptr) != GIRIH_OK) continue;
       if (dw > best_dw && dw <= (R == 1 ? 16 : 32)) {
         best_dw = dw;
         best = c;
@@ -143,9 +146,12 @@ int run_sweep(Plan* p, int64_t T, void* u, void* u_prev, const void* coeffs, con
     }
   } else {
     int64_t smem = 0;
-    int XW = 0;
-    const int rc = check_config(p, &cfg, &smem, &XW);
+    int XW = 0, G = 0;
+    const int rc = check_config(p, &cfg, &smem, &XW, &G);
     if (rc != GIRIH_OK) return rc;
+    // bulk copies need 16-byte aligned rows: the layout (checked at plan time) and the buffers
+    const bool bulk = p->bulk_layout && ((reinterpret_cast<uintptr_t>(u) | reinterpret_cast<uintptr_t>(u_prev)) & 15) == 0;
+    e = mwd_prepare(p->stencil, p->dtype, cfg.cluster, cfg.threads, G, bulk, smem, nullptr);
     const MwdShape sh = mwd_shape(p->stencil, p->dtype, cfg.dw, cfg.nf, XW);
     MwdArgs a{};
     a.g = g;
@@ -166,15 +172,15 @@ int run_sweep(Plan* p, int64_t T, void* u, void* u_prev, const void* coeffs, con
     a.NZ = sh.NZ;
     a.YW = sh.YW;
     a.XT = sh.XT;
+    a.err = p->err;
     const int64_t rows = mwd_rows(T, cfg.dw, p->R);
-    for (int64_t rho = 0; rho < rows && e == cudaSuccess; ++rho) {
+    for (int64_t rho = 0; rho < rows && e == cudaSuccess; ++rho) {  // one launch per diamond row
       int64_t a_min = 0, nd = 0;
       mwd_row_span(rho, cfg.dw, p->ny, &a_min, &nd);
       if (nd == 0) continue;
       a.rho = (int32_t)rho;
       a.a_min = (int32_t)a_min;
-      e = launch_mwd_row(p->stencil, p->dtype, a, (int)nd, cfg.threads,
-                         mwd_pairs_per_thread(p->R, cfg.dw, XW, cfg.threads), st);
+      e = launch_mwd_row(p->stencil, p->dtype, a, (int)nd, cfg.threads, G, bulk, st);
     }
   }
   if (e == cudaSuccess && T % 2 == 1) e = launch_swap(u, u_prev, p->gstride * p->elem, st);
@@ -204,7 +210,7 @@ int validate_run(Plan* p, void* u, void* u_prev, const void* coeffs, const girih
   *c = (params) ? params->c : (p->stencil >= 2 ? kConst25 : kConst7);
   *cfg = (params && params->force_cfg) ? &params->cfg : &p->cfg;
   if ((*cfg)->algo == GIRIH_ALGO_MWD) {
-    const int rc = check_config(p, *cfg, nullptr, nullptr);
+    const int rc = check_config(p, *cfg, nullptr, nullptr, nullptr);
     if (rc != GIRIH_OK) return rc;
   } else if ((*cfg)->algo != GIRIH_ALGO_NAIVE) {
     return fail(GIRIH_EINVAL, "unknown algo %d", (*cfg)->algo);
@@ -253,6 +259,14 @@ int girih_plan(girih_plan_t* out, int32_t stencil, int64_t nx, int64_t ny, int64
     return cuda_fail(e, "device query");
   }
   p->smem_optin = optin;
+  p->bulk_layout = (ldx * p->elem) % 16 == 0;
+  e = cudaMalloc(&p->err, sizeof(int));
+  if (e == cudaSuccess) e = cudaMemset(p->err, 0, sizeof(int));
+  if (e != cudaSuccess) {
+    delete p;
+    cudaGetLastError();
+    return fail(GIRIH_ENOMEM, "plan error word: %s", cudaGetErrorString(e));
+  }
   p->cfg = default_config(p);
   *out = p;
   return GIRIH_OK;
@@ -261,7 +275,7 @@ int girih_plan(girih_plan_t* out, int32_t stencil, int64_t nx, int64_t ny, int64
 int girih_plan_destroy(girih_plan_t plan) {
   if (!plan) return GIRIH_OK;
   Plan* p = plan;
-  for (void* d : {p->host_u, p->host_up, p->host_co, p->tune_u, p->tune_up, p->tune_co})
+  for (void* d : {p->host_u, p->host_up, p->host_co, p->tune_u, p->tune_up, p->tune_co, (void*)p->err})
     if (d) cudaFree(d);
   delete p;
   return GIRIH_OK;
@@ -275,7 +289,7 @@ int girih_plan_get_config(girih_plan_t plan, girih_config* cfg) {
 
 int girih_plan_set_config(girih_plan_t plan, const girih_config* cfg) {
   if (!plan) return fail(GIRIH_EINVAL, "plan is NULL");
-  const int rc = check_config(plan, cfg, nullptr, nullptr);
+  const int rc = check_config(plan, cfg, nullptr, nullptr, nullptr);
   if (rc != GIRIH_OK) return rc;
   plan->cfg = *cfg;
   return GIRIH_OK;
@@ -283,7 +297,7 @@ int girih_plan_set_config(girih_plan_t plan, const girih_config* cfg) {
 
 int girih_config_check(girih_plan_t plan, const girih_config* cfg, int64_t* smem_bytes) {
   if (!plan) return fail(GIRIH_EINVAL, "plan is NULL");
-  return check_config(plan, cfg, smem_bytes, nullptr);
+  return check_config(plan, cfg, smem_bytes, nullptr, nullptr);
 }
 
 int girih_plan_layout(girih_plan_t plan, int64_t* elems, int32_t* radius, int64_t* ldx) {
@@ -314,6 +328,19 @@ int girih_run(girih_plan_t plan, void* u, void* u_prev, const void* coeffs, cons
   return run_sweep(plan, plan->T, u, u_prev, coeffs, c, *cfg, static_cast<cudaStream_t>(stream));
 }
 
+int girih_status(girih_plan_t plan, void* stream) {
+  if (!plan) return fail(GIRIH_EINVAL, "plan is NULL");
+  cudaError_t e = cudaStreamSynchronize(static_cast<cudaStream_t>(stream));
+  if (e != cudaSuccess) return cuda_fail(e, "stream synchronize");
+  int v = 0;
+  e = cudaMemcpy(&v, plan->err, sizeof(int), cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess && v != 0) e = cudaMemset(plan->err, 0, sizeof(int));
+  if (e != cudaSuccess) return cuda_fail(e, "reading the error word");
+  if (v & GIRIH_ETIMEOUT) return fail(GIRIH_ETIMEOUT, "a bounded device wait ran out (a staged plane never arrived)");
+  if (v) return fail(GIRIH_EKERNEL, "kernel error word %d", v);
+  return GIRIH_OK;
+}
+
 int girih_run_host(girih_plan_t plan, void* u_host, void* u_prev_host, const void* coeffs_host,
                    const girih_params* params, void* stream) {
   if (!plan) return fail(GIRIH_EINVAL, "plan is NULL");
@@ -341,7 +368,7 @@ int girih_run_host(girih_plan_t plan, void* u_host, void* u_prev_host, const voi
   if (e == cudaSuccess) e = cudaMemcpyAsync(u_prev_host, p->host_up, bytes, cudaMemcpyDeviceToHost, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) return cuda_fail(e, "device to host copy");
-  return GIRIH_OK;
+  return girih_status(plan, stream);
 }
 
 // Eq. 3 (general R; Eq. 2 for R = 1 is the same expression up to the paper's approximation):

@@ -42,6 +42,7 @@ struct MwdArgs {
   int32_t a_min;     // index of the first diamond of the row
   int32_t C, XW;     // blocks per tile (cluster) and x slab width per block
   int32_t NZ, YW, XT;  // shared ring: planes, rows, columns per buffer
+  int* err;          // device error word: bounded waits that ran out set GIRIH_ETIMEOUT here
 };
 
 struct MwdShape {
@@ -50,13 +51,15 @@ struct MwdShape {
 };
 MwdShape mwd_shape(int stencil, int dtype, int dw, int nf, int XW);
 // Launch one diamond row: ndiam tiles, each a cluster of a.C blocks of `threads` threads.
-// G = row pairs per thread (1, 2 or 4), from mwd_pairs_per_thread.
-cudaError_t launch_mwd_row(int stencil, int dtype, const MwdArgs& a, int ndiam, int threads, int G, cudaStream_t st);
+// G = row pairs per thread (1, 2 or 4), from mwd_pairs_per_thread; bulk = rows moved by the
+// bulk-copy engine (16-byte aligned layout) instead of per-element cp.async.
+cudaError_t launch_mwd_row(int stencil, int dtype, const MwdArgs& a, int ndiam, int threads, int G, bool bulk,
+                           cudaStream_t st);
 // Configure kernel attributes (dynamic shared memory, non-portable clusters); returns the max
 // active clusters the device reports for the configuration (0 = cannot be scheduled).
-cudaError_t mwd_prepare(int stencil, int dtype, int C, int threads, int G, int64_t smem, int* max_clusters);
+cudaError_t mwd_prepare(int stencil, int dtype, int C, int threads, int G, bool bulk, int64_t smem, int* max_clusters);
 int mwd_max_pairs(int R, int dw);
-int mwd_pairs_per_thread(int R, int dw, int XW, int threads);
+int mwd_pairs_per_thread(int R, int dw, int XW, int threads, int compute_threads);
 // Planes are staged this many wavefront steps ahead of use.
 #define MWD_PREFETCH 2
 

@@ -1,0 +1,453 @@
+// Multi-threaded wavefront-diamond sweep (MWD, arXiv 1510.04995, Sect. 4.2.1), GB300 form.
+//
+// Tiling (Sects. 2.1.2, 3.2).  Updates are points (y, t) of the y-t plane (update t makes level
+// t+1).  Diamond (a, b) holds the updates with  a*Dw <= y + R*t < (a+1)*Dw  and
+// b*Dw <= y - R*t < (b+1)*Dw: a tiling by the two families of lines of slope +-R.  An update
+// depends only on updates of the same diamond or of diamonds (a-1, b), (a, b+1), (a-1, b+1);
+// so the diamonds of one row rho = a - b are independent and rows run in order, one launch per
+// row.  Row rho spans the steps t with (rho-1)*Dw < 2*R*t < (rho+1)*Dw (H-1 levels, H = Dw/R)
+// and its diamonds' y projections [(a+b)*Dw/2, (a+b+2)*Dw/2) partition y.
+//
+// Two buffers, updated in place (Listing 3's pointer swap generalised): level t of a point lives
+// in buffer t%2.  Writing level t+1 overwrites level t-1, whose readers are exactly the updates
+// level t+1 depends on, so any dependency-respecting order is race free; this holds for the
+// global arrays and for the shared-memory copy of a tile alike.
+//
+// Tile = extruded diamond (full z) x x-slab, one thread block per slab, the slabs of one diamond
+// forming a thread-block cluster (the paper's thread group, Sect. 4.1, sharing one tile; the
+// x split is the balanced x decomposition of Listing 5).  Each block keeps a ring of z planes of
+// both buffers in shared memory: [2][NZ][YW = Dw + 2R][XT >= XW + 2R].  The wavefront walks up in
+// z (Sect. 2.1.1): at step w, local level s updates planes [w*nf - s*K, w*nf - s*K + nf) with the
+// level skew K = R + nf, which makes every input of a step come from earlier steps, so one
+// cluster barrier per step is the only synchronisation ("fixed execution to data": each block
+// always updates its own slab).  x-halo columns are kept fresh by pushing boundary results into
+// the neighbour blocks' shared memory (st.shared::cluster, DSMEM) before the barrier.
+//
+// Work per thread: G row pairs (level s, rows y0 and y0+1, column xl), owned for the whole launch,
+// so the two rows' z windows stay in registers across steps (register-rotated z columns): per
+// step and plane a pair loads 2 new z values, 2R rows of y neighbours shared by both rows, 2R x
+// neighbours per row, and stores 2.
+//
+// Data movement, two modes:
+//  BULK  (16-byte aligned rows): warp 0 is a producer that moves whole rows with the bulk-copy
+//        (TMA) engine: cp.async.bulk global->shared completing on one mbarrier per ring slot
+//        (waits are bounded; a timeout sets an error word instead of hanging), and
+//        cp.async.bulk shared->global for the write-back.  The other warps only compute.
+//  plain (any alignment): every thread stages elements with cp.async and writes back with
+//        plain stores.
+// In both modes planes are staged MWD_PREFETCH steps ahead, and a plane is written back once the
+// tile's top level has passed it: only rows of the diamond's projection, only buffers the tile
+// updated in that row.  BULK write-back rows cover padded columns [x0, x0 + XW): the first R are
+// the left neighbour's (its final values, pushed here) and the block's own last R are written by
+// the right neighbour in turn, so every interior column is written exactly once with its final
+// value; the last block of the cluster extends its rows to its slab end.
+#pragma once
+#include "internal.h"
+#include "stencil.cuh"
+
+namespace girih {
+
+// Accessor of one row of a row pair: z neighbours and the centre come from the thread's own
+// register window (w[R] = centre), y neighbours from the pair's shared loads, x neighbours and
+// the level t-1 centre from the shared ring.
+template <int S, typename T>
+struct PairAcc {
+  const T* w;        // window of this row, planes z-R..z+R
+  const T* yv;       // y neighbours: yv[R + d] = value at row y + d (d != 0)
+  const T* X;        // pointer to the centre in the level-t ring buffer
+  T uc;
+  const T* coef;     // coefficient grid 0 at this pair's first row and current plane
+  int64_t gs, p;     // grid stride, offset of this row from coef
+  __device__ __forceinline__ T c() const { return w[Traits<S>::R]; }
+  __device__ __forceinline__ T x(int d) const { return X[d]; }
+  __device__ __forceinline__ T y(int d) const { return yv[Traits<S>::R + d]; }
+  __device__ __forceinline__ T z(int d) const { return w[Traits<S>::R + d]; }
+  __device__ __forceinline__ T u() const { return uc; }
+  __device__ __forceinline__ T k(int g) const { return __ldg(coef + g * gs + p); }
+};
+
+__device__ __forceinline__ int lev_lo_of(int a, int b, int dw, int R, int t) {
+  return max(a * dw - R * t, b * dw + R * t);
+}
+__device__ __forceinline__ int lev_hi_of(int a, int b, int dw, int R, int t) {
+  return min((a + 1) * dw - R * t, (b + 1) * dw + R * t);
+}
+__device__ __forceinline__ void cluster_arrive_release() {
+  asm volatile("barrier.cluster.arrive.release.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void cluster_wait_acquire() {
+  asm volatile("barrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
+// ---- bulk-copy (TMA) and mbarrier helpers ---------------------------------------------------
+__device__ __forceinline__ void mbar_init(uint64_t* m, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(m)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* m, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(m)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* m, uint32_t parity) {
+  uint32_t ok;
+  asm volatile("{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2; selp.u32 %0, 1, 0, p; }"
+               : "=r"(ok)
+               : "r"(smem_addr(m)), "r"(parity)
+               : "memory");
+  return ok != 0;
+}
+__device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t bytes, uint64_t* m) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   smem_addr(dst)),
+               "l"(src), "r"(bytes), "r"(smem_addr(m))
+               : "memory");
+}
+__device__ __forceinline__ void bulk_store(void* dst, const void* src, uint32_t bytes) {
+  asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(dst), "r"(smem_addr(src)),
+               "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait_read() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async;" ::: "memory"); }
+
+// Bound on one mbarrier wait (polls); each poll is a hardware try_wait with its own time slice.
+constexpr long long kMbarPolls = 1ll << 26;
+
+template <int S, typename T, int G, bool BULK>
+__global__ void __launch_bounds__(1024 / G) mwd_fed_kernel(const MwdArgs A) {
+  constexpr int R = Traits<S>::R;
+  constexpr int NC = Traits<S>::NCOEF;
+  constexpr int PD = MWD_PREFETCH;
+  constexpr int A16 = 16 / (int)sizeof(T);  // elements per 16 bytes
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  T* sm = reinterpret_cast<T*>(smem_raw);
+  const int NZ = A.NZ, YW = A.YW, XT = A.XT, XW = A.XW, C = A.C, nf = A.nf, K = A.K;
+  const int pe = YW * XT;
+  const int be = NZ * pe;
+  uint64_t* mbar = reinterpret_cast<uint64_t*>(smem_raw + (((size_t)2 * be * sizeof(T) + 15) / 16) * 16);
+  int* lev_lo = reinterpret_cast<int*>(mbar + NZ);
+  int* lev_w = lev_lo + A.H;
+  int* lev_pp = lev_w + A.H;  // prefix count of row pairs per level
+  int* row_mask = lev_pp + A.H + 1;
+
+  const int nx = (int)A.g.nx, ny = (int)A.g.ny, nz = (int)A.g.nz;
+  const int64_t ldx = A.g.ldx;
+  const int64_t gplane = A.g.sy * A.g.ldx;
+  const int rank = (C > 1) ? (int)cluster_ctarank() : 0;
+  const int tile = blockIdx.x / C;
+  const int dw = A.dw, rho = A.rho;
+  const int a = A.a_min + tile, b = a - rho;
+  const int P0 = a * dw - rho * (dw / 2);  // first y of the diamond's projection
+  const int Y0 = P0 - R;                   // y of shared row 0
+  const int x0 = rank * XW;
+  const int xw = min(XW, nx - x0);         // this block's slab width (<= 0: idle block)
+  const int Hh = A.H / 2;
+  const int tb = max((rho - 1) * Hh + 1, 0);
+  const int te = min((rho + 1) * Hh - 1, A.T - 1);
+  if (tb > te) return;  // the whole cluster sees the same (tb, te): no barrier is skipped unevenly
+  const int nlev = te - tb + 1, smax = nlev - 1;
+  const int NT = blockDim.x, tid = threadIdx.x;
+  const int lane = tid & 31, warp = tid >> 5, nwarps = NT >> 5;
+  const bool producer = BULK && warp == 0;
+  const int ctid = BULK ? tid - 32 : tid;  // index among the computing threads
+  const int CNT = BULK ? NT - 32 : NT;
+
+  if (tid == 0) {
+    int acc = 0;
+    for (int s = 0; s < nlev; ++s) {
+      const int t = tb + s;
+      const int lo = max(lev_lo_of(a, b, dw, R, t), 0);
+      const int hi = min(lev_hi_of(a, b, dw, R, t), ny);
+      lev_lo[s] = lo;
+      lev_w[s] = max(hi - lo, 0);
+      lev_pp[s] = acc;
+      acc += (max(hi - lo, 0) + 1) / 2;
+    }
+    lev_pp[nlev] = acc;
+    if constexpr (BULK) {
+      for (int s = 0; s < NZ; ++s) mbar_init(&mbar[s], 1);
+      asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+  }
+  for (int yy = tid; yy < YW; yy += NT) {
+    const int y = Y0 + yy;
+    int m = 0;
+    if (y >= 0 && y < ny && y >= P0 && y < P0 + dw) {
+      int cnt = 0, par = 0;
+      for (int s = 0; s < nlev; ++s) {
+        const int t = tb + s;
+        if (y >= lev_lo_of(a, b, dw, R, t) && y < lev_hi_of(a, b, dw, R, t)) {
+          ++cnt;
+          par = (t + 1) & 1;
+        }
+      }
+      m = (cnt >= 2) ? 3 : (cnt == 1 ? (1 << par) : 0);
+    }
+    row_mask[yy] = m;
+  }
+  __syncthreads();  // level tables (and mbarriers) ready
+
+  const T* __restrict__ gb0 = static_cast<const T*>(A.buf0);
+  const T* __restrict__ gb1 = static_cast<const T*>(A.buf1);
+  T* go0 = static_cast<T*>(A.buf0);
+  T* go1 = static_cast<T*>(A.buf1);
+  T cst[5];
+#pragma unroll
+  for (int i = 0; i < 5; ++i) cst[i] = sizeof(T) == 8 ? static_cast<T>(A.c[i]) : static_cast<T>(A.cf[i]);
+  const int64_t gstride = A.g.gstride;
+
+  // ---- this thread's row pairs (computing threads only) -------------------------------------
+  // per pair: ring offsets of row y0 in the level-t and level-t+1 buffers, current plane z and
+  // its ring slot (both advance by nf per step), coefficient pointer, flags (valid, second row,
+  // push left, push right)
+  int gzb_[G], gsl_[G], gvo_[G], guo_[G], gflags_[G];
+  const T* gk_[G];
+  const int npairs = lev_pp[nlev];
+#pragma unroll
+  for (int g = 0; g < G; ++g) {
+    const int id = ctid + g * CNT;
+    const int pr = id / XW, xl = id - pr * XW;
+    const bool valid = !producer && (pr < npairs) && (xl < xw);
+    int s = 0;
+    if (valid)
+      while (lev_pp[s + 1] <= pr) ++s;
+    const int y0 = valid ? lev_lo[s] + 2 * (pr - lev_pp[s]) : 0;
+    const int t = tb + s;
+    const int col = (y0 - Y0) * XT + xl + R;
+    gvo_[g] = (t & 1) * be + col;
+    guo_[g] = ((t & 1) ^ 1) * be + col;
+    gzb_[g] = -s * K;
+    const int sl = (-s * K + R) % NZ;
+    gsl_[g] = sl < 0 ? sl + NZ : sl;
+    const bool row1 = valid && (y0 + 1 < lev_lo[s] + lev_w[s]);
+    gflags_[g] = (valid ? 1 : 0) | (row1 ? 2 : 0) | ((C > 1 && xl < R && rank > 0) ? 4 : 0) |
+                 ((C > 1 && xl >= XW - R && rank < C - 1) ? 8 : 0);
+    gk_[g] = NC ? static_cast<const T*>(A.coef) + (int64_t)(-s * K + R) * gplane + (int64_t)(y0 + R) * ldx +
+                      (x0 + xl + R)
+                : nullptr;
+  }
+  T win[G][2][2 * R + 1];
+
+  // ---- staging geometry: rows y in [Y0, Y0+YW) clipped to the padded grid, columns from padded
+  // x0 (interior x0 - R); BULK rows are rounded up to 16 bytes (the host keeps them inside ldx)
+  const int ylo = max(Y0, -R), yhi = min(Y0 + YW, ny + R);
+  const int nrow = max(yhi - ylo, 0);
+  const int ncol = (xw > 0) ? xw + 2 * R : 0;
+  const int lcols = BULK ? (ncol + A16 - 1) / A16 * A16 : ncol;
+  const bool last_rank = x0 + XW >= nx;
+  const int wcols = last_rank ? (xw + R + A16 - 1) / A16 * A16 : XW;  // BULK write-back columns
+  int lz = -R, lsl = 0;                                  // next plane to stage and its slot
+  int wz = -smax * K, wsl = ((R - smax * K) % NZ + NZ) % NZ;  // next plane to write back
+
+  // BULK helpers (producer warp only)
+  auto bulk_stage = [&](int z, int slot) {  // whole warp: rows of both buffers of plane z
+    if (z < -R || z >= nz + R) return;
+    const uint32_t bytes = (uint32_t)(lcols * sizeof(T));
+    if (lane == 0) mbar_expect_tx(&mbar[slot], bytes * 2u * (uint32_t)nrow);
+    __syncwarp();
+    const int64_t gz = (int64_t)(z + R) * gplane;
+    for (int rr = lane; rr < 2 * nrow; rr += 32) {
+      const int p = rr >= nrow;
+      const int y = ylo + rr - p * nrow;
+      bulk_load(sm + p * be + slot * pe + (y - Y0) * XT, (p ? gb1 : gb0) + gz + (int64_t)(y + R) * ldx + x0, bytes,
+                &mbar[slot]);
+    }
+  };
+  auto bulk_wait = [&](int z) {  // lane 0 waits for plane z's staging; error word on timeout
+    if (z < -R || z >= nz + R) return;
+    if (lane == 0) {
+      const int q = z + R;
+      const int slot = q % NZ;
+      const uint32_t parity = (uint32_t)((q / NZ) & 1);
+      long long n = 0;
+      while (!mbar_try_wait(&mbar[slot], parity)) {
+        if (++n >= kMbarPolls) {
+          atomicOr(A.err, GIRIH_ETIMEOUT);
+          break;
+        }
+      }
+    }
+    __syncwarp();
+  };
+  auto bulk_write = [&](int z, int slot) {  // whole warp: masked rows of plane z
+    if (z < 0 || z >= nz) return;
+    fence_proxy_async();
+    const int64_t gz = (int64_t)(z + R) * gplane;
+    const uint32_t bytes = (uint32_t)(wcols * sizeof(T));
+    for (int yy = lane; yy < YW; yy += 32) {
+      const int m = row_mask[yy];
+      if (m == 0) continue;
+      const int64_t go = gz + (int64_t)(Y0 + yy + R) * ldx + x0;
+      const int so = slot * pe + yy * XT;
+      if (m & 1) bulk_store(go0 + go, sm + so, bytes);
+      if (m & 2) bulk_store(go1 + go, sm + be + so, bytes);
+    }
+    bulk_commit();
+  };
+  // plain-mode helpers (all threads)
+  auto plain_stage = [&](int z, int slot) {
+    if (z < -R || z >= nz + R) return;
+    const int64_t gz = (int64_t)(z + R) * gplane;
+    for (int rr = warp; rr < 2 * nrow; rr += nwarps) {
+      const int p = rr >= nrow;
+      const int y = ylo + rr - p * nrow;
+      const T* src = (p ? gb1 : gb0) + gz + (int64_t)(y + R) * ldx + x0;
+      T* dst = sm + p * be + slot * pe + (y - Y0) * XT;
+      for (int xx = lane; xx < ncol; xx += 32) cp_async(dst + xx, src + xx);
+    }
+  };
+  auto plain_write = [&](int z, int slot) {
+    if (z < 0 || z >= nz) return;
+    const int64_t gz = (int64_t)(z + R) * gplane;
+    for (int yy = warp; yy < YW; yy += nwarps) {
+      const int m = row_mask[yy];
+      if (m == 0) continue;
+      const int64_t go = gz + (int64_t)(Y0 + yy + R) * ldx + (x0 + R);
+      const T* src = sm + slot * pe + yy * XT + R;
+      for (int xl = lane; xl < xw; xl += 32) {
+        if (m & 1) go0[go + xl] = src[xl];
+        if (m & 2) go1[go + xl] = src[be + xl];
+      }
+    }
+  };
+
+  // ---- prologue: planes of the first PD steps --------------------------------------------------
+  if (xw > 0) {
+    if constexpr (BULK) {
+      if (producer) {
+        for (; lz < PD * nf + R; ++lz, lsl = (lsl + 1 == NZ) ? 0 : lsl + 1) bulk_stage(lz, lsl);
+        for (int z = -R; z < PD * nf + R; ++z) bulk_wait(z);
+      }
+    } else {
+      for (; lz < PD * nf + R; ++lz, lsl = (lsl + 1 == NZ) ? 0 : lsl + 1) plain_stage(lz, lsl);
+    }
+  }
+  if constexpr (!BULK) {
+    cp_async_commit();
+    cp_async_wait_group<0>();
+  }
+  if (C > 1) cluster_barrier();
+  else __syncthreads();
+
+  const uint32_t sm_base = smem_addr(sm);
+  const uint32_t left_base = (C > 1 && rank > 0) ? map_to_rank(sm_base, rank - 1) : 0u;
+  const uint32_t right_base = (C > 1 && rank < C - 1) ? map_to_rank(sm_base, rank + 1) : 0u;
+
+  const int W = (nz + smax * K + nf - 1) / nf;
+  for (int w = 0; w < W; ++w) {
+    // ---- compute: this thread's pairs at the planes of step w ----
+#pragma unroll
+    for (int g = 0; g < G; ++g) {
+      const int fl = gflags_[g];
+      int z = gzb_[g], sl = gsl_[g];
+      const T* kp = gk_[g];
+      if ((fl & 1) && z + nf > 0 && z < nz) {
+        for (int f = 0; f < nf; ++f) {
+          if (z >= 0 && z < nz) {
+            const T* Vb = sm + gvo_[g];
+            if (z == 0) {  // first plane of this level: fill the whole window
+#pragma unroll
+              for (int d = -R; d <= R; ++d) {
+                int sd = sl + d;
+                sd = sd < 0 ? sd + NZ : (sd >= NZ ? sd - NZ : sd);
+                win[g][0][R + d] = Vb[sd * pe];
+                win[g][1][R + d] = Vb[sd * pe + XT];
+              }
+            } else {  // slide the window up by one plane
+              const int sd = (sl + R >= NZ) ? sl + R - NZ : sl + R;
+#pragma unroll
+              for (int d = 0; d < 2 * R; ++d) {
+                win[g][0][d] = win[g][0][d + 1];
+                win[g][1][d] = win[g][1][d + 1];
+              }
+              win[g][0][2 * R] = Vb[sd * pe];
+              win[g][1][2 * R] = Vb[sd * pe + XT];
+            }
+            const bool row1 = fl & 2;
+            const T* P = Vb + sl * pe;  // centre of row y0 at plane z
+            T yv0[2 * R + 1], yv1[2 * R + 1];  // y neighbours of row y0 and row y0+1
+#pragma unroll
+            for (int d = 1; d <= R; ++d) {
+              yv0[R - d] = P[-d * XT];
+              // row y0+1+R can lie one row past the tile when the second row is not updated
+              yv1[R + d] = (d < R || row1) ? P[(1 + d) * XT] : T(0);
+            }
+#pragma unroll
+            for (int d = 1; d <= R; ++d) {
+              yv0[R + d] = (d == 1) ? win[g][1][R] : yv1[R + d - 1];
+              yv1[R - d] = (d == 1) ? win[g][0][R] : yv0[R - d + 1];
+            }
+            T* Ub = sm + guo_[g] + sl * pe;
+            PairAcc<S, T> acc0{win[g][0], yv0, P, T(0), kp, gstride, 0};
+            if constexpr (Traits<S>::ORDER2) acc0.uc = Ub[0];
+            const T r0 = point_update<S, T>(acc0, cst);
+            Ub[0] = r0;
+            T r1 = T(0);
+            if (row1) {
+              PairAcc<S, T> acc1{win[g][1], yv1, P + XT, T(0), kp, gstride, ldx};
+              if constexpr (Traits<S>::ORDER2) acc1.uc = Ub[XT];
+              r1 = point_update<S, T>(acc1, cst);
+              Ub[XT] = r1;
+            }
+            if (fl & 12) {
+              const uint32_t so = (uint32_t)(guo_[g] + sl * pe) * (uint32_t)sizeof(T);
+              if (fl & 4) {  // my left edge is the left neighbour's right halo
+                st_cluster(left_base + so + (uint32_t)(XW * (int)sizeof(T)), r0);
+                if (row1) st_cluster(left_base + so + (uint32_t)((XT + XW) * (int)sizeof(T)), r1);
+              }
+              if (fl & 8) {  // my right edge is the right neighbour's left halo
+                st_cluster(right_base + so - (uint32_t)(XW * (int)sizeof(T)), r0);
+                if (row1) st_cluster(right_base + so + (uint32_t)((XT - XW) * (int)sizeof(T)), r1);
+              }
+            }
+          }
+          ++z;
+          sl = (sl + 1 == NZ) ? 0 : sl + 1;
+          if constexpr (NC > 0) kp += gplane;
+        }
+      }
+      gzb_[g] += nf;
+      gsl_[g] = (gsl_[g] + nf >= NZ) ? gsl_[g] + nf - NZ : gsl_[g] + nf;
+      if constexpr (NC > 0) gk_[g] += nf * gplane;
+    }
+
+    if constexpr (BULK) {
+      // shared writes of this step become visible to the bulk engine (write-back reads them)
+      if (!producer) fence_proxy_async();
+      if (producer && xw > 0) {
+        if (w > 0)  // planes the top level finished in step w-1
+          for (int f = 0; f < nf; ++f, ++wz, wsl = (wsl + 1 == NZ) ? 0 : wsl + 1) bulk_write(wz, wsl);
+        bulk_wait_read();  // write-backs have read their slots before those slots are restaged
+        __syncwarp();
+        for (int f = 0; f < nf; ++f, ++lz, lsl = (lsl + 1 == NZ) ? 0 : lsl + 1) bulk_stage(lz, lsl);
+        for (int f = 0; f < nf; ++f) bulk_wait((w + 1) * nf + R + f);  // new planes of step w+1
+      }
+      if (C > 1) cluster_barrier();
+      else __syncthreads();
+    } else {
+      cp_async_wait_group<PD - 1>();
+      if (C > 1) cluster_arrive_release();
+      else __syncthreads();  // a single block needs no second barrier
+      if (xw > 0) {
+        if (w > 0)
+          for (int f = 0; f < nf; ++f, ++wz, wsl = (wsl + 1 == NZ) ? 0 : wsl + 1) plain_write(wz, wsl);
+        for (int f = 0; f < nf; ++f, ++lz, lsl = (lsl + 1 == NZ) ? 0 : lsl + 1) plain_stage(lz, lsl);
+      }
+      cp_async_commit();
+      if (C > 1) cluster_wait_acquire();
+    }
+  }
+  // ---- epilogue: planes the top level finished in the last step ----
+  if constexpr (BULK) {
+    if (producer && xw > 0) {
+      for (int f = 0; f < nf; ++f, ++wz, wsl = (wsl + 1 == NZ) ? 0 : wsl + 1) bulk_write(wz, wsl);
+      bulk_wait_all();  // the shared source must outlive the copies
+    }
+  } else {
+    cp_async_wait_group<0>();
+    if (xw > 0)
+      for (int f = 0; f < nf; ++f, ++wz, wsl = (wsl + 1 == NZ) ? 0 : wsl + 1) plain_write(wz, wsl);
+  }
+}
+
+}  // namespace girih

@@ -18,6 +18,8 @@ struct girih_plan_s {
   void* tune_u = nullptr;
   void* tune_up = nullptr;
   void* tune_co = nullptr;
+  int* err = nullptr;  // device error word of the kernels' bounded waits
+  bool bulk_layout = false;  // rows are 16-byte multiples: the blocked kernel may use bulk copies
 };
 
 namespace girih {
@@ -25,7 +27,7 @@ using Plan = girih_plan_s;
 int fail(int code, const char* fmt, ...);
 void g_err_clear();
 int cuda_fail(cudaError_t e, const char* where);
-int check_config(const Plan* p, const girih_config* c, int64_t* smem_out, int* xw_out);
+int check_config(const Plan* p, const girih_config* c, int64_t* smem_out, int* xw_out, int* g_out);
 int run_sweep(Plan* p, int64_t T, void* u, void* u_prev, const void* coeffs, const double* c,
               const girih_config& cfg, cudaStream_t st);
 int64_t mwd_rows(int64_t T, int dw, int R);

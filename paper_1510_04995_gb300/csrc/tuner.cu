@@ -71,7 +71,7 @@ static const double kC25[5] = {-0.9, 0.05, 0.025, 0.0125, 0.00625};
 
 int measure(Plan* p, const girih_config& cfg, double tol, int64_t max_steps, girih_tune_row* row) {
   const auto wall0 = std::chrono::steady_clock::now();
-  int rc = check_config(p, &cfg, &row->smem, nullptr);
+  int rc = check_config(p, &cfg, &row->smem, nullptr, nullptr);
   if (rc != GIRIH_OK) return rc;
   rc = ensure_tune_arrays(p);
   if (rc != GIRIH_OK) return rc;
@@ -96,6 +96,8 @@ int measure(Plan* p, const girih_config& cfg, double tol, int64_t max_steps, gir
     cudaEventRecord(e1, st);
     ce = cudaEventSynchronize(e1);
     if (rc != GIRIH_OK || ce != cudaSuccess) break;
+    rc = girih_status(p, nullptr);
+    if (rc != GIRIH_OK) break;
     float ms = 0.f;
     cudaEventElapsedTime(&ms, e0, e1);
     secs = ms * 1e-3;
@@ -127,7 +129,7 @@ std::vector<girih_config> candidates(Plan* p) {
       for (int C : {1, 2, 4, 8, 16})
         for (int th : {256, 512, 1024}) {
           girih_config c{GIRIH_ALGO_MWD, dw, nf, C, th, GIRIH_FED};
-          if (check_config(p, &c, nullptr, nullptr) == GIRIH_OK) out.push_back(c);
+          if (check_config(p, &c, nullptr, nullptr, nullptr) == GIRIH_OK) out.push_back(c);
         }
   g_err_clear();
   return out;

@@ -17,6 +17,7 @@ def gpu_sweep(stencil, dtype, u, up, co, c, T, nx, ny, nz, cfg, ldx=0):
     du, dup = to_dev(u, dtype), to_dev(up, dtype)
     dco = to_dev(co, dtype) if co is not None else None
     girih.run(p, du, dup, dco, c=c, cfg=cfg)
+    girih.status(p)  # no bounded device wait ran out
     torch.cuda.synchronize()
     return du.double().cpu().numpy(), dup.double().cpu().numpy()
 

@@ -30,7 +30,7 @@ def shape(R, dw, nf, XW):
     H = dw // R
     K = R + nf
     NZ = (PD + 1) * nf + R + max(R, nf) + (H - 2) * K
-    return NZ, dw + 2 * R, XW + 2 * R
+    return NZ, dw + 2 * R, -(-(XW + 2 * R) // 4) * 4
 
 
 def rows(T, dw, R):
@@ -50,7 +50,9 @@ def row_span(rho, dw, ny):
     return lo, max(hi - lo + 1, 0)
 
 
-def simulate(R, second_order, nx, ny, nz, T, dw, nf, C):
+def simulate(R, second_order, nx, ny, nz, T, dw, nf, C, bulk=False, a16=4):
+    """bulk: write-back as the bulk-copy mode does (padded columns [x0, x0 + wcols) of each row,
+    the first R being the left neighbour's final values held in this block's halo copy)."""
     XW = slab_width(nx, C)
     NZ, YW, XT = shape(R, dw, nf, XW)
     H = dw // R
@@ -125,17 +127,28 @@ def simulate(R, second_order, nx, ny, nz, T, dw, nf, C):
             if z < 0 or z >= nz or xw <= 0:
                 return
             slot = (z + R) % NZ
+            if bulk:
+                last = x0 + XW >= nx
+                wcols = -(-(xw + R) // a16) * a16 if last else XW
+                cols = [xx for xx in range(wcols) if x0 - R + xx < nx + R]  # beyond: row padding
+            else:
+                cols = [xl + R for xl in range(xw)]
             for yy in range(YW):
                 m = tl["mask"][yy]
                 if not m:
                     continue
                 y = tl["Y0"] + yy
-                for xl in range(xw):
+                for xx in cols:
+                    x = x0 - R + xx
                     for p in range(2):
                         if m >> p & 1:
-                            gtag(p, z, y, x0 + xl)
-                            G[p, z + R, y + R, x0 + xl + R] = tl["S"][rank, p, slot, yy, xl + R]
-                            wb_reads.add((rank, p, slot, yy, xl + R))
+                            gtag(p, z, y, x)
+                            v = tl["S"][rank, p, slot, yy, xx]
+                            if not (-R <= x < 0 or nx <= x):  # interior: the final level, never stale
+                                G[p, z + R, y + R, x + R] = v
+                            else:
+                                assert v == G[p, z + R, y + R, x + R], ("halo rewritten with a new value", x)
+                            wb_reads.add((rank, p, slot, yy, xx))
 
         def check_read(tagv, want):
             assert tagv == want or tagv == HALO, (tagv, want)

@@ -166,3 +166,28 @@ def test_launch_count():
     assert p.launch_count(girih.config(girih.NAIVE)) == 10  # 9 steps + one exchange for odd T
     # dw=8, R=1: rows 0..(T-2)//4+1 -> 3 rows, plus the exchange
     assert p.launch_count(girih.config(girih.MWD, dw=8)) == 4
+
+
+@pytest.mark.parametrize("stencil,dtype", [(0, "f32"), (1, "f32"), (2, "f32"), (3, "f64"), (0, "f64")])
+def test_bulk_copy_path_equals_element_path(stencil, dtype):
+    """A 16-byte aligned leading dimension selects the bulk-copy (TMA) data movement of the blocked
+    kernel; an unaligned one the per-element path.  Interiors must agree bit for bit, and with
+    the naive sweep."""
+    R = inputs.RADIUS[stencil]
+    nx, ny, nz, T = 67, 41, 23, 9
+    elem = 8 if dtype == "f64" else 4
+    a16 = 16 // elem
+    ld_al = -(-(nx + 2 * R) // a16) * a16 + a16       # aligned, with spare columns
+    ld_un = ld_al + 1                                  # not a multiple of 16 bytes
+    assert (ld_al * elem) % 16 == 0 and (ld_un * elem) % 16 != 0
+    cfg = girih.config(girih.MWD, dw=4 * R, nf=1, cluster=2, threads=256)
+    outs = []
+    for ldx in (ld_al, ld_un):
+        u, up, co, c = inputs.make_problem(stencil, nx, ny, nz, seed=21, ldx=ldx)
+        gu, gup = gpu_sweep(stencil, dtype, u, up, co, c, T, nx, ny, nz, cfg, ldx=ldx)
+        nu, nup = gpu_sweep(stencil, dtype, u, up, co, c, T, nx, ny, nz, girih.config(girih.NAIVE), ldx=ldx)
+        w = nx + 2 * R
+        assert np.array_equal(gu[:, :, :w], nu[:, :, :w]) and np.array_equal(gup[:, :, :w], nup[:, :, :w])
+        assert np.all(gu[:, :, w:] == 0) and np.all(gup[:, :, w:] == 0)  # row padding keeps its (zero) values
+        outs.append(gu[:, :, :w])
+    assert np.array_equal(outs[0], outs[1])

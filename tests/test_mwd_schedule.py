@@ -21,5 +21,6 @@ CASES = [
 
 
 @pytest.mark.parametrize("case", CASES)
-def test_schedule_model(case):
-    assert simulate(*case)
+@pytest.mark.parametrize("bulk", [False, True])
+def test_schedule_model(case, bulk):
+    assert simulate(*case, bulk=bulk)
