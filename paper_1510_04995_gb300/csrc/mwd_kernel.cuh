@@ -110,8 +110,14 @@ __device__ __forceinline__ void bulk_wait_read() { asm volatile("cp.async.bulk.w
 __device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
 __device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async;" ::: "memory"); }
 
-// Bound on one mbarrier wait (polls); each poll is a hardware try_wait with its own time slice.
-constexpr long long kMbarPolls = 1ll << 26;
+__device__ __forceinline__ uint64_t global_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+// Bound on one mbarrier wait, in nanoseconds of the global timer: a staged plane that has not
+// arrived after this long sets GIRIH_ETIMEOUT in the error word and the kernel carries on.
+constexpr uint64_t kMbarWaitNs = 2000000000ull;
 
 template <int S, typename T, int G, bool BULK>
 __global__ void __launch_bounds__(1024 / G) mwd_fed_kernel(const MwdArgs A) {
@@ -259,11 +265,13 @@ __global__ void __launch_bounds__(1024 / G) mwd_fed_kernel(const MwdArgs A) {
       const int q = z + R;
       const int slot = q % NZ;
       const uint32_t parity = (uint32_t)((q / NZ) & 1);
-      long long n = 0;
-      while (!mbar_try_wait(&mbar[slot], parity)) {
-        if (++n >= kMbarPolls) {
-          atomicOr(A.err, GIRIH_ETIMEOUT);
-          break;
+      if (!mbar_try_wait(&mbar[slot], parity)) {
+        const uint64_t t0 = global_ns();
+        while (!mbar_try_wait(&mbar[slot], parity)) {
+          if (global_ns() - t0 > kMbarWaitNs) {
+            atomicOr(A.err, GIRIH_ETIMEOUT);
+            break;
+          }
         }
       }
     }

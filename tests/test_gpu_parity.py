@@ -35,9 +35,9 @@ def _ref(stencil, nx, ny, nz, T, seed=3):
 
 MWD_CFGS = {
     1: [dict(dw=4, nf=1, cluster=1, threads=256), dict(dw=8, nf=2, cluster=2, threads=256),
-        dict(dw=16, nf=1, cluster=8, threads=1024), dict(dw=6, nf=3, cluster=2, threads=512)],
+        dict(dw=12, nf=1, cluster=8, threads=1024), dict(dw=6, nf=3, cluster=2, threads=512)],
     4: [dict(dw=8, nf=1, cluster=4, threads=256), dict(dw=16, nf=1, cluster=8, threads=256),
-        dict(dw=8, nf=2, cluster=8, threads=128), dict(dw=16, nf=1, cluster=16, threads=128)],
+        dict(dw=8, nf=2, cluster=8, threads=128), dict(dw=16, nf=1, cluster=16, threads=256)],
 }
 
 
@@ -180,7 +180,8 @@ def test_bulk_copy_path_equals_element_path(stencil, dtype):
     ld_al = -(-(nx + 2 * R) // a16) * a16 + a16       # aligned, with spare columns
     ld_un = ld_al + 1                                  # not a multiple of 16 bytes
     assert (ld_al * elem) % 16 == 0 and (ld_un * elem) % 16 != 0
-    cfg = girih.config(girih.MWD, dw=4 * R, nf=1, cluster=2, threads=256)
+    dw = 8 if (R == 1 or dtype == "f64") else 16
+    cfg = girih.config(girih.MWD, dw=dw, nf=1, cluster=4, threads=512)  # 4th block of the cluster idle
     outs = []
     for ldx in (ld_al, ld_un):
         u, up, co, c = inputs.make_problem(stencil, nx, ny, nz, seed=21, ldx=ldx)
