@@ -78,15 +78,15 @@ int check_config(const Plan* p, const girih_config* c, int64_t* smem_out, int* x
   const int XW = slab_width(p->nx, c->cluster);
   // with a 16-byte aligned layout one warp of the block moves data and the others compute
   const int cthreads = p->bulk_layout ? c->threads - 32 : c->threads;
-  const int G = mwd_pairs_per_thread(R, c->dw, XW, c->threads, cthreads);
+  const int G = mwd_pairs_per_thread(R, c->dw, XW, c->threads, p->bulk_layout);
   if (G == 0)
-    return fail(GIRIH_EINVAL, "dw=%d with a %d-wide slab has %d row pairs, more than 4 per computing thread of %d",
+    return fail(GIRIH_EINVAL, "dw=%d with a %d-wide slab has %d row pairs: too many for %d computing threads",
                 c->dw, XW, mwd_max_pairs(R, c->dw) * XW, cthreads);
   if (p->dtype == GIRIH_F64 && R == 4 && G > 2)
     return fail(GIRIH_EINVAL, "25-point FP64 tiles allow at most 2 row pairs per thread (registers)");
   if (p->ny > (1 << 28) || p->nx > (1 << 28) || p->nz > (1 << 28))
     return fail(GIRIH_EINVAL, "grid too large for the blocked kernel");
-  const MwdShape sh = mwd_shape(p->stencil, p->dtype, c->dw, c->nf, XW);
+  const MwdShape sh = mwd_shape(p->stencil, p->dtype, c->dw, c->nf, XW, p->bulk_layout);
   if (sh.smem_bytes > p->smem_optin)
     return fail(GIRIH_EINVAL, "config needs %lld bytes of shared memory per block (device limit %lld)",
                 (long long)sh.smem_bytes, (long long)p->smem_optin);
@@ -152,7 +152,7 @@ int run_sweep(Plan* p, int64_t T, void* u, void* u_prev, const void* coeffs, con
     // bulk copies need 16-byte aligned rows: the layout (checked at plan time) and the buffers
     const bool bulk = p->bulk_layout && ((reinterpret_cast<uintptr_t>(u) | reinterpret_cast<uintptr_t>(u_prev)) & 15) == 0;
     e = mwd_prepare(p->stencil, p->dtype, cfg.cluster, cfg.threads, G, bulk, smem, nullptr);
-    const MwdShape sh = mwd_shape(p->stencil, p->dtype, cfg.dw, cfg.nf, XW);
+    const MwdShape sh = mwd_shape(p->stencil, p->dtype, cfg.dw, cfg.nf, XW, p->bulk_layout);
     MwdArgs a{};
     a.g = g;
     a.buf0 = u;
@@ -180,7 +180,7 @@ int run_sweep(Plan* p, int64_t T, void* u, void* u_prev, const void* coeffs, con
       if (nd == 0) continue;
       a.rho = (int32_t)rho;
       a.a_min = (int32_t)a_min;
-      e = launch_mwd_row(p->stencil, p->dtype, a, (int)nd, cfg.threads, G, bulk, st);
+      e = launch_mwd_row(p->stencil, p->dtype, a, (int)nd, cfg.threads, G, bulk, sh.smem_bytes, st);
     }
   }
   if (e == cudaSuccess && T % 2 == 1) e = launch_swap(u, u_prev, p->gstride * p->elem, st);

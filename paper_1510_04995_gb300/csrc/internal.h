@@ -49,19 +49,28 @@ struct MwdShape {
   int32_t NZ, YW, XT;
   int64_t smem_bytes;
 };
-MwdShape mwd_shape(int stencil, int dtype, int dw, int nf, int XW);
+MwdShape mwd_shape(int stencil, int dtype, int dw, int nf, int XW, bool bulk);
 // Launch one diamond row: ndiam tiles, each a cluster of a.C blocks of `threads` threads.
 // G = row pairs per thread (1, 2 or 4), from mwd_pairs_per_thread; bulk = rows moved by the
 // bulk-copy engine (16-byte aligned layout) instead of per-element cp.async.
 cudaError_t launch_mwd_row(int stencil, int dtype, const MwdArgs& a, int ndiam, int threads, int G, bool bulk,
-                           cudaStream_t st);
+                           int64_t smem, cudaStream_t st);
 // Configure kernel attributes (dynamic shared memory, non-portable clusters); returns the max
 // active clusters the device reports for the configuration (0 = cannot be scheduled).
 cudaError_t mwd_prepare(int stencil, int dtype, int C, int threads, int G, bool bulk, int64_t smem, int* max_clusters);
 int mwd_max_pairs(int R, int dw);
-int mwd_pairs_per_thread(int R, int dw, int XW, int threads, int compute_threads);
-// Planes are staged this many wavefront steps ahead of use.
+int mwd_pairs_per_thread(int R, int dw, int XW, int threads, bool bulk);
+// Largest block for G pairs per thread (the kernel's launch bound).
+inline int mwd_max_threads(int G, bool bulk) {
+  const int t = 1024 / G + (bulk ? 32 : 0);
+  return t > 1024 ? 1024 : t;
+}
+// Planes are staged this many wavefront steps ahead of use (element path / bulk-copy path).
 #define MWD_PREFETCH 2
+#define MWD_PREFETCH_BULK 3
+// Extra ring planes per wavefront width in the bulk-copy path: a slot is restaged at least two
+// steps after its plane was written back, so only older write-backs need to have read it.
+#define MWD_BULK_SLACK 2
 
 
 // In-place exchange of two device arrays (odd T puts level T back into u).

@@ -11,14 +11,15 @@ static void* pick(int stencil, int dtype, int G, bool bulk) {
   return stencil < 2 ? mwd_kernel_r1(stencil, dtype, G, bulk) : mwd_kernel_r4(stencil, dtype, G, bulk);
 }
 
-MwdShape mwd_shape(int stencil, int dtype, int dw, int nf, int XW) {
+MwdShape mwd_shape(int stencil, int dtype, int dw, int nf, int XW, bool bulk) {
   const int R = radius_of(stencil);
   const int H = dw / R;
   const int K = R + nf;
   const int elem = dtype == GIRIH_F64 ? 8 : 4;
   const int a16 = 16 / elem;
   MwdShape s;
-  s.NZ = (MWD_PREFETCH + 1) * nf + R + (R > nf ? R : nf) + (H - 2) * K;
+  const int pd = bulk ? MWD_PREFETCH_BULK : MWD_PREFETCH;
+  s.NZ = (pd + 1) * nf + R + (R > nf ? R : nf) + (H - 2) * K + (bulk ? MWD_BULK_SLACK * nf : 0);
   s.YW = dw + 2 * R;
   s.XT = (XW + 2 * R + a16 - 1) / a16 * a16;  // rows start on 16-byte boundaries
   const int64_t ring = 2LL * s.NZ * s.YW * s.XT * elem;
@@ -34,12 +35,13 @@ int mwd_max_pairs(int R, int dw) {
   return n;
 }
 
-// Pairs per thread (1, 2 or 4) for `compute_threads` computing threads in a block of `threads`,
-// or 0 if the tile needs more.
-int mwd_pairs_per_thread(int R, int dw, int XW, int threads, int compute_threads) {
+// Pairs per computing thread (1, 2 or 4) for a block of `threads` (one of them a producer warp
+// in the bulk-copy path), or 0 if the tile needs more.
+int mwd_pairs_per_thread(int R, int dw, int XW, int threads, bool bulk) {
   const int64_t ng = (int64_t)mwd_max_pairs(R, dw) * XW;
+  const int ct = bulk ? threads - 32 : threads;
   for (int G : {1, 2, 4})
-    if (threads <= 1024 / G && ng <= (int64_t)G * compute_threads) return G;
+    if (threads <= mwd_max_threads(G, bulk) && ng <= (int64_t)G * ct) return G;
   return 0;
 }
 
@@ -78,10 +80,9 @@ cudaError_t mwd_prepare(int stencil, int dtype, int C, int threads, int G, bool 
 }
 
 cudaError_t launch_mwd_row(int stencil, int dtype, const MwdArgs& a, int ndiam, int threads, int G, bool bulk,
-                           cudaStream_t st) {
-  const MwdShape sh = mwd_shape(stencil, dtype, a.dw, a.nf, a.XW);
+                           int64_t smem, cudaStream_t st) {
   cudaLaunchAttribute attr[1];
-  cudaLaunchConfig_t cfg = launch_config(a.C, threads, sh.smem_bytes, attr);
+  cudaLaunchConfig_t cfg = launch_config(a.C, threads, smem, attr);
   cfg.gridDim = dim3((unsigned)(ndiam * a.C), 1, 1);
   cfg.stream = st;
   void* args[] = {const_cast<MwdArgs*>(&a)};

@@ -119,11 +119,17 @@ __device__ __forceinline__ uint64_t global_ns() {
 // arrived after this long sets GIRIH_ETIMEOUT in the error word and the kernel carries on.
 constexpr uint64_t kMbarWaitNs = 2000000000ull;
 
+template <int N>
+__device__ __forceinline__ void bulk_wait_read_n() {
+  asm volatile("cp.async.bulk.wait_group.read %0;" ::"n"(N) : "memory");
+}
+
 template <int S, typename T, int G, bool BULK>
-__global__ void __launch_bounds__(1024 / G) mwd_fed_kernel(const MwdArgs A) {
+__global__ void __launch_bounds__((1024 / G + (BULK ? 32 : 0)) > 1024 ? 1024 : (1024 / G + (BULK ? 32 : 0)))
+    mwd_fed_kernel(const MwdArgs A) {
   constexpr int R = Traits<S>::R;
   constexpr int NC = Traits<S>::NCOEF;
-  constexpr int PD = MWD_PREFETCH;
+  constexpr int PD = BULK ? MWD_PREFETCH_BULK : MWD_PREFETCH;
   constexpr int A16 = 16 / (int)sizeof(T);  // elements per 16 bytes
   extern __shared__ __align__(128) unsigned char smem_raw[];
   T* sm = reinterpret_cast<T*>(smem_raw);
@@ -277,20 +283,21 @@ __global__ void __launch_bounds__(1024 / G) mwd_fed_kernel(const MwdArgs A) {
     }
     __syncwarp();
   };
-  auto bulk_write = [&](int z, int slot) {  // whole warp: masked rows of plane z
-    if (z < 0 || z >= nz) return;
-    fence_proxy_async();
-    const int64_t gz = (int64_t)(z + R) * gplane;
-    const uint32_t bytes = (uint32_t)(wcols * sizeof(T));
-    for (int yy = lane; yy < YW; yy += 32) {
-      const int m = row_mask[yy];
-      if (m == 0) continue;
-      const int64_t go = gz + (int64_t)(Y0 + yy + R) * ldx + x0;
-      const int so = slot * pe + yy * XT;
-      if (m & 1) bulk_store(go0 + go, sm + so, bytes);
-      if (m & 2) bulk_store(go1 + go, sm + be + so, bytes);
+  auto bulk_write = [&](int z, int slot) {  // whole warp: masked rows of plane z, one group per call
+    if (z >= 0 && z < nz) {
+      fence_proxy_async();
+      const int64_t gz = (int64_t)(z + R) * gplane;
+      const uint32_t bytes = (uint32_t)(wcols * sizeof(T));
+      for (int yy = lane; yy < YW; yy += 32) {
+        const int m = row_mask[yy];
+        if (m == 0) continue;
+        const int64_t go = gz + (int64_t)(Y0 + yy + R) * ldx + x0;
+        const int so = slot * pe + yy * XT;
+        if (m & 1) bulk_store(go0 + go, sm + so, bytes);
+        if (m & 2) bulk_store(go1 + go, sm + be + so, bytes);
+      }
     }
-    bulk_commit();
+    bulk_commit();  // exactly nf groups per step, so "the last nf groups" are this step's
   };
   // plain-mode helpers (all threads)
   auto plain_stage = [&](int z, int slot) {
@@ -423,11 +430,25 @@ __global__ void __launch_bounds__(1024 / G) mwd_fed_kernel(const MwdArgs A) {
       // shared writes of this step become visible to the bulk engine (write-back reads them)
       if (!producer) fence_proxy_async();
       if (producer && xw > 0) {
-        if (w > 0)  // planes the top level finished in step w-1
-          for (int f = 0; f < nf; ++f, ++wz, wsl = (wsl + 1 == NZ) ? 0 : wsl + 1) bulk_write(wz, wsl);
-        bulk_wait_read();  // write-backs have read their slots before those slots are restaged
+        // Stage the planes of step w+PD first.  Their slots were last written back at least two
+        // steps ago (ring slack): wait until only the previous step's nf write-back groups may
+        // still be reading shared memory.
+        if (nf == 1) bulk_wait_read_n<1>();
+        else if (nf == 2) bulk_wait_read_n<2>();
+        else if (nf == 3) bulk_wait_read_n<3>();
+        else bulk_wait_read_n<4>();
         __syncwarp();
         for (int f = 0; f < nf; ++f, ++lz, lsl = (lsl + 1 == NZ) ? 0 : lsl + 1) bulk_stage(lz, lsl);
+        // then write back the planes the top level finished in step w-1 (nf groups, maybe empty)
+        for (int f = 0; f < nf; ++f) {
+          if (w > 0) {
+            bulk_write(wz, wsl);
+            ++wz;
+            wsl = (wsl + 1 == NZ) ? 0 : wsl + 1;
+          } else {
+            bulk_commit();  // keep nf groups per step
+          }
+        }
         for (int f = 0; f < nf; ++f) bulk_wait((w + 1) * nf + R + f);  // new planes of step w+1
       }
       if (C > 1) cluster_barrier();

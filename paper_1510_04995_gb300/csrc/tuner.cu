@@ -127,7 +127,7 @@ std::vector<girih_config> candidates(Plan* p) {
   for (int dw = 2 * R; dw <= 64 * R; dw += 2 * R)
     for (int nf : {1, 2})
       for (int C : {1, 2, 4, 8, 16})
-        for (int th : {256, 512, 1024}) {
+        for (int th : {256, 288, 512, 544, 1024}) {
           girih_config c{GIRIH_ALGO_MWD, dw, nf, C, th, GIRIH_FED};
           if (check_config(p, &c, nullptr, nullptr, nullptr) == GIRIH_OK) out.push_back(c);
         }

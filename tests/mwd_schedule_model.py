@@ -23,13 +23,16 @@ def slab_width(nx, C):
     return -(-w // 16) * 16
 
 
-PD = 2  # planes are staged this many steps ahead (cp.async groups, wait_group PD-1)
+PD = 2       # element path: planes staged this many steps ahead (cp.async groups, wait_group PD-1)
+PD_BULK = 3  # bulk-copy path
+SLACK = 2    # bulk-copy path: extra ring planes per wavefront width
 
 
-def shape(R, dw, nf, XW):
+def shape(R, dw, nf, XW, bulk=False):
     H = dw // R
     K = R + nf
-    NZ = (PD + 1) * nf + R + max(R, nf) + (H - 2) * K
+    pd = PD_BULK if bulk else PD
+    NZ = (pd + 1) * nf + R + max(R, nf) + (H - 2) * K + (SLACK * nf if bulk else 0)
     return NZ, dw + 2 * R, -(-(XW + 2 * R) // 4) * 4
 
 
@@ -54,7 +57,8 @@ def simulate(R, second_order, nx, ny, nz, T, dw, nf, C, bulk=False, a16=4):
     """bulk: write-back as the bulk-copy mode does (padded columns [x0, x0 + wcols) of each row,
     the first R being the left neighbour's final values held in this block's halo copy)."""
     XW = slab_width(nx, C)
-    NZ, YW, XT = shape(R, dw, nf, XW)
+    NZ, YW, XT = shape(R, dw, nf, XW, bulk)
+    pdm = PD_BULK if bulk else PD
     H = dw // R
     K = R + nf
     Hh = H // 2
@@ -154,19 +158,19 @@ def simulate(R, second_order, nx, ny, nz, T, dw, nf, C, bulk=False, a16=4):
             assert tagv == want or tagv == HALO, (tagv, want)
 
         for tl in tiles:
-            tl["prev_wb"] = set()  # write-back reads of the previous step (may overlap this step)
+            tl["prev_wb"] = [set(), set()]  # write-back reads of the last two steps (still in flight)
             tl["inflight"] = []  # (issue step, cells) of cp.async groups
             tl["win"] = {}
             for rank in range(C):
-                for z in range(-R, PD * nf + R):
+                for z in range(-R, pdm * nf + R):
                     load_plane(tl, rank, z, set())
         for w in range(W):
             for tl in tiles:
                 loaded, wb_reads, reads, writes = set(), set(), {}, {}
                 for rank in range(C):
                     for f in range(nf):
-                        load_plane(tl, rank, (w + PD) * nf + R + f, loaded)
-                tl["inflight"] = [(ws, c) for ws, c in tl["inflight"] if ws > w - PD] + [(w, loaded)]
+                        load_plane(tl, rank, (w + pdm) * nf + R + f, loaded)
+                tl["inflight"] = [(ws, c) for ws, c in tl["inflight"] if ws > w - pdm] + [(w, loaded)]
                 busy = set().union(*[c for _, c in tl["inflight"]])
                 for rank in range(C):
                     if w > 0:
@@ -238,8 +242,12 @@ def simulate(R, second_order, nx, ny, nz, T, dw, nf, C, bulk=False, a16=4):
                     rs = reads.get(cell, set())
                     assert rs <= {it}, ("read and written in one step", cell)
                     assert cell not in busy and cell not in wb_reads, ("write vs load/write-back", cell)
-                    assert cell not in tl["prev_wb"], ("write vs the previous step's write-back", cell)
-                tl["prev_wb"] = wb_reads
+                    for old in tl["prev_wb"][(0 if bulk else 1):]:
+                        assert cell not in old, ("write vs a recent step's write-back", cell)
+                if bulk:
+                    for old in tl["prev_wb"]:
+                        assert not (old & loaded), "slot restaged while a recent write-back may still read it"
+                tl["prev_wb"] = [tl["prev_wb"][1], wb_reads]
                 for cell in busy:
                     assert cell not in reads and cell not in wb_reads, ("slot read while its load is in flight", cell)
                 for outs, lv in pending:
