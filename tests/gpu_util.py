@@ -33,3 +33,20 @@ def normwise(g, o, R):
 def rel_l2(g, o, R):
     gi, oi = g[R:-R, R:-R, R:-R], o[R:-R, R:-R, R:-R]
     return float(np.linalg.norm((gi - oi).ravel()) / np.linalg.norm(oi.ravel()))
+
+
+def feasible_cfg(stencil, dtype, nx, ny, nz, kw, ldx=0):
+    """The MWD config kw, or the nearest feasible one on this device: double the cluster (narrower
+    slabs, less shared memory per block), then wavefront width 1, then other block sizes."""
+    p = girih.plan(stencil, nx, ny, nz, dtype=dtype, T=1, ldx=ldx)
+    tries = []
+    for cl in (kw["cluster"], 2 * kw["cluster"], 4 * kw["cluster"], 8 * kw["cluster"]):
+        for nf in (kw["nf"], 1):
+            for th in (kw["threads"], 288, 544, 256, 512, 1024):
+                if cl <= 16:
+                    tries.append(dict(kw, cluster=cl, nf=nf, threads=th))
+    for t in tries:
+        c = girih.config(girih.MWD, **t)
+        if p.feasible(c):
+            return c
+    raise AssertionError(f"no feasible configuration near {kw}")

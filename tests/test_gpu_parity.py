@@ -12,7 +12,7 @@ import oracle
 import paper_1510_04995_gb300 as girih
 from paper_1510_04995_gb300 import inputs
 
-from gpu_util import gpu_sweep, normwise, rel_l2
+from gpu_util import feasible_cfg, gpu_sweep, normwise, rel_l2
 
 pytestmark = pytest.mark.gpu
 
@@ -69,7 +69,7 @@ def test_mwd_fp64_vs_oracle_and_naive(stencil, ci):
     Ts = [1, H - 1, H, H + 1, 2 * H + 3] if ci == 0 else [H + 1]
     for T in sorted(set(t for t in Ts if t >= 1)):
         u, up, co, c, ru, rup = _ref(stencil, nx, ny, nz, T)
-        cfg = girih.config(girih.MWD, **kw)
+        cfg = feasible_cfg(stencil, "f64", nx, ny, nz, kw)
         bu, bup = gpu_sweep(stencil, "f64", u, up, co, c, T, nx, ny, nz, cfg)
         assert normwise(bu, ru, R) <= 1e-12, (T, kw)
         assert normwise(bup, rup, R) <= 1e-12, (T, kw)
@@ -85,7 +85,7 @@ def test_fp32_error_vs_fp64_oracle(stencil, algo):
     nx, ny, nz = SIZES[R]
     T = 12
     u, up, co, c, ru, rup = _ref(stencil, nx, ny, nz, T)
-    cfg = girih.config(girih.NAIVE) if algo == "naive" else girih.config(girih.MWD, **MWD_CFGS[R][1])
+    cfg = girih.config(girih.NAIVE) if algo == "naive" else feasible_cfg(stencil, "f32", nx, ny, nz, MWD_CFGS[R][1])
     gu, _ = gpu_sweep(stencil, "f32", u, up, co, c, T, nx, ny, nz, cfg)
     assert rel_l2(gu, ru, R) <= FP32_TOL[stencil]
 
@@ -97,7 +97,7 @@ def test_fp32_mwd_bitwise_equals_naive(stencil):
     T = 2 * (8 // R) + 3 if R == 1 else 7
     u, up, co, c = inputs.make_problem(stencil, nx, ny, nz, seed=5)
     for kw in MWD_CFGS[R]:
-        bu, bup = gpu_sweep(stencil, "f32", u, up, co, c, T, nx, ny, nz, girih.config(girih.MWD, **kw))
+        bu, bup = gpu_sweep(stencil, "f32", u, up, co, c, T, nx, ny, nz, feasible_cfg(stencil, "f32", nx, ny, nz, kw))
         nu, nup = gpu_sweep(stencil, "f32", u, up, co, c, T, nx, ny, nz, girih.config(girih.NAIVE))
         assert np.array_equal(bu, nu) and np.array_equal(bup, nup), kw
 
@@ -110,7 +110,8 @@ def test_padded_leading_dimension(stencil):
     u, up, co, c = inputs.make_problem(stencil, nx, ny, nz, seed=9, ldx=ldx)
     ru, rup = u.copy(), up.copy()
     oracle.sweep(stencil, ru, rup, co, c, T, nx, ny, nz)
-    for cfg in (girih.config(girih.NAIVE), girih.config(girih.MWD, dw=2 * R, nf=1, cluster=2, threads=128)):
+    mwd = feasible_cfg(stencil, "f64", nx, ny, nz, dict(dw=2 * R, nf=1, cluster=2, threads=128), ldx=ldx)
+    for cfg in (girih.config(girih.NAIVE), mwd):
         gu, _ = gpu_sweep(stencil, "f64", u, up, co, c, T, nx, ny, nz, cfg, ldx=ldx)
         assert normwise(gu[:, :, :nx + 2 * R], ru[:, :, :nx + 2 * R], R) <= 1e-12
         assert np.array_equal(gu[:, :, nx + 2 * R:], u[:, :, nx + 2 * R:])  # padding untouched
@@ -123,14 +124,16 @@ def test_degenerate_shapes(shape):
         R = inputs.RADIUS[stencil]
         T = 5
         u, up, co, c, ru, rup = _ref(stencil, nx, ny, nz, T)
-        for cfg in (girih.config(girih.NAIVE), girih.config(girih.MWD, dw=2 * R, nf=1, cluster=1, threads=256)):
+        mwd = feasible_cfg(stencil, "f64", nx, ny, nz, dict(dw=2 * R, nf=1, cluster=1, threads=256))
+        for cfg in (girih.config(girih.NAIVE), mwd):
             gu, gup = gpu_sweep(stencil, "f64", u, up, co, c, T, nx, ny, nz, cfg)
             assert np.max(np.abs(gu - ru)) <= 1e-12 * max(1.0, np.max(np.abs(ru))), (shape, stencil, cfg)
 
 
 def test_t0_is_noop():
     u, up, co, c = inputs.make_problem(0, 20, 20, 20)
-    gu, gup = gpu_sweep(0, "f64", u, up, co, c, 0, 20, 20, 20, girih.config(girih.MWD, dw=8, cluster=1))
+    gu, gup = gpu_sweep(0, "f64", u, up, co, c, 0, 20, 20, 20,
+                        feasible_cfg(0, "f64", 20, 20, 20, dict(dw=8, nf=1, cluster=1, threads=256)))
     assert np.array_equal(gu, u) and np.array_equal(gup, up)
 
 
@@ -181,9 +184,9 @@ def test_bulk_copy_path_equals_element_path(stencil, dtype):
     ld_un = ld_al + 1                                  # not a multiple of 16 bytes
     assert (ld_al * elem) % 16 == 0 and (ld_un * elem) % 16 != 0
     dw = 8 if (R == 1 or dtype == "f64") else 16
-    cfg = girih.config(girih.MWD, dw=dw, nf=1, cluster=4, threads=512)  # 4th block of the cluster idle
     outs = []
     for ldx in (ld_al, ld_un):
+        cfg = feasible_cfg(stencil, dtype, nx, ny, nz, dict(dw=dw, nf=1, cluster=4, threads=512), ldx=ldx)
         u, up, co, c = inputs.make_problem(stencil, nx, ny, nz, seed=21, ldx=ldx)
         gu, gup = gpu_sweep(stencil, dtype, u, up, co, c, T, nx, ny, nz, cfg, ldx=ldx)
         nu, nup = gpu_sweep(stencil, dtype, u, up, co, c, T, nx, ny, nz, girih.config(girih.NAIVE), ldx=ldx)
