@@ -46,10 +46,13 @@ typedef enum { GIRIH_F64 = 0, GIRIH_F32 = 1 } girih_dtype;
 typedef enum { GIRIH_ALGO_NAIVE = 0, GIRIH_ALGO_MWD = 1 } girih_algo;
 /* Wavefront synchronisation variants of Sect. 4.2.1:
  *   FED     -- fixed execution to data: each thread block of the cluster always updates the
- *              same x slab of the tile; one cluster-wide barrier per wavefront step.
+ *              same x slab of the tile; one cluster-wide barrier per wavefront step; planes are
+ *              staged element by element (cp.async), any alignment.
+ *   FED_BULK -- FED with whole rows moved by the bulk-copy (TMA) engine from a producer warp;
+ *              needs ldx*elem to be a multiple of 16 bytes and 16-byte aligned buffers.
  *   RELAXED -- each time level of the tile only waits for its own predecessor level
  *              (left-neighbour hand-off), through per-level progress counters.            */
-typedef enum { GIRIH_FED = 0, GIRIH_RELAXED = 1 } girih_variant;
+typedef enum { GIRIH_FED = 0, GIRIH_RELAXED = 1, GIRIH_FED_BULK = 2 } girih_variant;
 
 #define GIRIH_OK 0
 #define GIRIH_EINVAL 1   /* bad enum, size, T, pointer, alignment, or config: nothing enqueued */
@@ -120,9 +123,8 @@ GIRIH_API int girih_config_check(girih_plan_t plan, const girih_config* cfg, int
  *           back; their halo cells are never read.
  *   params  coefficients and optional forced configuration (NULL: 7PT_CONST/25PT_CONST use the
  *           workload constants c0=0.4,c1=0.1 / c0=-0.9,c_r=0.1/2^r).
- * Pointers must be 8-byte (F64) or 4-byte (F32) aligned and u != u_prev.  When ldx*elem is a
- * multiple of 16 bytes and the buffers are 16-byte aligned, the blocked kernel moves rows with the
- * bulk-copy engine; otherwise it stages elements (same results).  The two buffers'
+ * Pointers must be 8-byte (F64) or 4-byte (F32) aligned (16-byte for GIRIH_FED_BULK) and
+ * u != u_prev.  The two buffers'
  * roles alternate every step (Listing 3's pointer swap); for odd T one in-place exchange kernel
  * puts level T back into u.  EINVAL leaves the buffers untouched and enqueues nothing.       */
 GIRIH_API int girih_run(girih_plan_t plan, void* u, void* u_prev, const void* coeffs, const girih_params* params,

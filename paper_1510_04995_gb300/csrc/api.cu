@@ -66,7 +66,11 @@ int check_config(const Plan* p, const girih_config* c, int64_t* smem_out, int* x
     return GIRIH_OK;
   }
   if (c->algo != GIRIH_ALGO_MWD) return fail(GIRIH_EINVAL, "unknown algo %d", c->algo);
-  if (c->variant != GIRIH_FED) return fail(GIRIH_ENOTIMPL, "only the FED wavefront variant is available");
+  if (c->variant == GIRIH_RELAXED) return fail(GIRIH_ENOTIMPL, "the RELAXED wavefront variant is not built");
+  if (c->variant != GIRIH_FED && c->variant != GIRIH_FED_BULK) return fail(GIRIH_EINVAL, "unknown variant %d", c->variant);
+  const bool bulk = c->variant == GIRIH_FED_BULK;
+  if (bulk && !p->bulk_layout)
+    return fail(GIRIH_EINVAL, "FED_BULK needs ldx*elem to be a multiple of 16 bytes (ldx=%lld)", (long long)p->ldx);
   const int R = p->R;
   if (c->dw < 2 * R || c->dw % (2 * R) != 0)
     return fail(GIRIH_EINVAL, "dw=%d must be a positive multiple of 2R=%d", c->dw, 2 * R);
@@ -77,21 +81,22 @@ int check_config(const Plan* p, const girih_config* c, int64_t* smem_out, int* x
     return fail(GIRIH_EINVAL, "threads=%d must be a multiple of 32 in 64..1024", c->threads);
   const int XW = slab_width(p->nx, c->cluster);
   // with a 16-byte aligned layout one warp of the block moves data and the others compute
-  const int cthreads = p->bulk_layout ? c->threads - 32 : c->threads;
-  const int G = mwd_pairs_per_thread(R, c->dw, XW, c->threads, p->bulk_layout);
+  const int cthreads = bulk ? c->threads - 32 : c->threads;
+  const int G = mwd_pairs_per_thread(R, c->dw, XW, c->threads, bulk);
   if (G == 0)
     return fail(GIRIH_EINVAL, "dw=%d with a %d-wide slab has %d row pairs: too many for %d computing threads",
                 c->dw, XW, mwd_max_pairs(R, c->dw) * XW, cthreads);
+  if (R == 4 && G > 4) return fail(GIRIH_EINVAL, "25-point tiles allow at most 4 row pairs per thread (registers)");
   if (p->dtype == GIRIH_F64 && R == 4 && G > 2)
     return fail(GIRIH_EINVAL, "25-point FP64 tiles allow at most 2 row pairs per thread (registers)");
   if (p->ny > (1 << 28) || p->nx > (1 << 28) || p->nz > (1 << 28))
     return fail(GIRIH_EINVAL, "grid too large for the blocked kernel");
-  const MwdShape sh = mwd_shape(p->stencil, p->dtype, c->dw, c->nf, XW, p->bulk_layout);
+  const MwdShape sh = mwd_shape(p->stencil, p->dtype, c->dw, c->nf, XW, bulk);
   if (sh.smem_bytes > p->smem_optin)
     return fail(GIRIH_EINVAL, "config needs %lld bytes of shared memory per block (device limit %lld)",
                 (long long)sh.smem_bytes, (long long)p->smem_optin);
   int maxc = 0;
-  cudaError_t e = mwd_prepare(p->stencil, p->dtype, c->cluster, c->threads, G, p->bulk_layout, sh.smem_bytes, &maxc);
+  cudaError_t e = mwd_prepare(p->stencil, p->dtype, c->cluster, c->threads, G, bulk, sh.smem_bytes, &maxc);
   if (e != cudaSuccess) {
     cudaGetLastError();
     return fail(GIRIH_EINVAL, "cluster of %d blocks with %lld bytes cannot be configured: %s", c->cluster,
@@ -149,10 +154,9 @@ int run_sweep(Plan* p, int64_t T, void* u, void* u_prev, const void* coeffs, con
     int XW = 0, G = 0;
     const int rc = check_config(p, &cfg, &smem, &XW, &G);
     if (rc != GIRIH_OK) return rc;
-    // bulk copies need 16-byte aligned rows: the layout (checked at plan time) and the buffers
-    const bool bulk = p->bulk_layout && ((reinterpret_cast<uintptr_t>(u) | reinterpret_cast<uintptr_t>(u_prev)) & 15) == 0;
+    const bool bulk = cfg.variant == GIRIH_FED_BULK;
     e = mwd_prepare(p->stencil, p->dtype, cfg.cluster, cfg.threads, G, bulk, smem, nullptr);
-    const MwdShape sh = mwd_shape(p->stencil, p->dtype, cfg.dw, cfg.nf, XW, p->bulk_layout);
+    const MwdShape sh = mwd_shape(p->stencil, p->dtype, cfg.dw, cfg.nf, XW, cfg.variant == GIRIH_FED_BULK);
     MwdArgs a{};
     a.g = g;
     a.buf0 = u;
@@ -212,6 +216,9 @@ int validate_run(Plan* p, void* u, void* u_prev, const void* coeffs, const girih
   if ((*cfg)->algo == GIRIH_ALGO_MWD) {
     const int rc = check_config(p, *cfg, nullptr, nullptr, nullptr);
     if (rc != GIRIH_OK) return rc;
+    if ((*cfg)->variant == GIRIH_FED_BULK &&
+        ((reinterpret_cast<uintptr_t>(u) | reinterpret_cast<uintptr_t>(u_prev)) & 15) != 0)
+      return fail(GIRIH_EINVAL, "FED_BULK needs 16-byte aligned buffers");
   } else if ((*cfg)->algo != GIRIH_ALGO_NAIVE) {
     return fail(GIRIH_EINVAL, "unknown algo %d", (*cfg)->algo);
   }

@@ -35,12 +35,12 @@ int mwd_max_pairs(int R, int dw) {
   return n;
 }
 
-// Pairs per computing thread (1, 2 or 4) for a block of `threads` (one of them a producer warp
+// Pairs per computing thread (1, 2, 4 or 8) for a block of `threads` (one of them a producer warp
 // in the bulk-copy path), or 0 if the tile needs more.
 int mwd_pairs_per_thread(int R, int dw, int XW, int threads, bool bulk) {
   const int64_t ng = (int64_t)mwd_max_pairs(R, dw) * XW;
   const int ct = bulk ? threads - 32 : threads;
-  for (int G : {1, 2, 4})
+  for (int G : {1, 2, 4, 8})
     if (threads <= mwd_max_threads(G, bulk) && ng <= (int64_t)G * ct) return G;
   return 0;
 }

@@ -3,10 +3,13 @@
 
 namespace girih {
 
+template <int S, typename T, bool B>
+static void* ptr_g(int G) {  // radius-4 tiles use at most 4 pairs per thread
+  return G == 1 ? (void*)&mwd_fed_kernel<S, T, 1, B> : (G == 2 ? (void*)&mwd_fed_kernel<S, T, 2, B> : (void*)&mwd_fed_kernel<S, T, 4, B>);
+}
 template <int S, typename T>
 static void* ptr_for(int G, bool bulk) {
-  if (bulk) return G == 1 ? (void*)&mwd_fed_kernel<S, T, 1, true> : (G == 2 ? (void*)&mwd_fed_kernel<S, T, 2, true> : (void*)&mwd_fed_kernel<S, T, 4, true>);
-  return G == 1 ? (void*)&mwd_fed_kernel<S, T, 1, false> : (G == 2 ? (void*)&mwd_fed_kernel<S, T, 2, false> : (void*)&mwd_fed_kernel<S, T, 4, false>);
+  return bulk ? ptr_g<S, T, true>(G) : ptr_g<S, T, false>(G);
 }
 
 void* mwd_kernel_r4(int stencil, int dtype, int G, bool bulk) {

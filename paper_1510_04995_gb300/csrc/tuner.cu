@@ -127,10 +127,13 @@ std::vector<girih_config> candidates(Plan* p) {
   for (int dw = 2 * R; dw <= 64 * R; dw += 2 * R)
     for (int nf : {1, 2})
       for (int C : {1, 2, 4, 8, 16})
-        for (int th : {256, 288, 512, 544, 1024}) {
-          girih_config c{GIRIH_ALGO_MWD, dw, nf, C, th, GIRIH_FED};
-          if (check_config(p, &c, nullptr, nullptr, nullptr) == GIRIH_OK) out.push_back(c);
-        }
+        for (int th : {128, 256, 512, 1024})
+          for (int v : {GIRIH_FED, GIRIH_FED_BULK}) {
+            // the bulk-copy variant adds a producer warp to the computing threads
+            girih_config c{GIRIH_ALGO_MWD, dw, nf, C, v == GIRIH_FED_BULK ? th + 32 : th, v};
+            if (c.threads > 1024) continue;
+            if (check_config(p, &c, nullptr, nullptr, nullptr) == GIRIH_OK) out.push_back(c);
+          }
   g_err_clear();
   return out;
 }

@@ -145,6 +145,10 @@ def test_invalid_arguments_leave_buffers_untouched():
     assert girih.lib().girih_run(p.handle, u.data_ptr(), up.data_ptr(), None, None, None) == 1  # no coefficients
     assert girih.lib().girih_run(p.handle, u.data_ptr(), u.data_ptr(), None, None, None) == 1  # aliasing
     assert girih.lib().girih_run(p.handle, u.data_ptr() + 4, up.data_ptr(), u.data_ptr(), None, None) == 1
+    # FED_BULK on a layout whose rows are not 16-byte multiples (18 FP32 elements) is rejected up front
+    p32 = girih.plan(girih.S7C, 16, 16, 16, dtype="f32", T=3)
+    assert not p32.feasible(girih.config(girih.MWD, dw=2, nf=1, cluster=1, threads=288, variant=girih.FED_BULK))
+    assert p32.feasible(girih.config(girih.MWD, dw=2, nf=1, cluster=1, threads=256, variant=girih.FED))
     bad = girih.config(girih.MWD, dw=3, nf=1, cluster=1, threads=128)
     with pytest.raises(girih.GirihError):
         p.set_config(bad)
@@ -173,9 +177,9 @@ def test_launch_count():
 
 @pytest.mark.parametrize("stencil,dtype", [(0, "f32"), (1, "f32"), (2, "f32"), (3, "f64"), (0, "f64")])
 def test_bulk_copy_path_equals_element_path(stencil, dtype):
-    """A 16-byte aligned leading dimension selects the bulk-copy (TMA) data movement of the blocked
-    kernel; an unaligned one the per-element path.  Interiors must agree bit for bit, and with
-    the naive sweep."""
+    """The bulk-copy (TMA) data movement of the blocked kernel (FED_BULK, 16-byte aligned leading
+    dimension) and the per-element path (FED, unaligned leading dimension) agree bit for bit, and
+    with the naive sweep."""
     R = inputs.RADIUS[stencil]
     nx, ny, nz, T = 67, 41, 23, 9
     elem = 8 if dtype == "f64" else 4
@@ -185,8 +189,10 @@ def test_bulk_copy_path_equals_element_path(stencil, dtype):
     assert (ld_al * elem) % 16 == 0 and (ld_un * elem) % 16 != 0
     dw = 8 if (R == 1 or dtype == "f64") else 16
     outs = []
-    for ldx in (ld_al, ld_un):
-        cfg = feasible_cfg(stencil, dtype, nx, ny, nz, dict(dw=dw, nf=1, cluster=4, threads=512), ldx=ldx)
+    for ldx, variant in ((ld_al, girih.FED_BULK), (ld_un, girih.FED)):
+        cfg = feasible_cfg(stencil, dtype, nx, ny, nz, dict(dw=dw, nf=1, cluster=4, threads=544, variant=variant),
+                           ldx=ldx)
+        assert cfg.variant == variant
         u, up, co, c = inputs.make_problem(stencil, nx, ny, nz, seed=21, ldx=ldx)
         gu, gup = gpu_sweep(stencil, dtype, u, up, co, c, T, nx, ny, nz, cfg, ldx=ldx)
         nu, nup = gpu_sweep(stencil, dtype, u, up, co, c, T, nx, ny, nz, girih.config(girih.NAIVE), ldx=ldx)
