@@ -261,9 +261,12 @@ def main():
     clocks = clk.summary()
     value = lups * args.steps * ws / (ms * 1e-3) * 1e-9
     naive = None
-    if not args.no_naive and cfg.algo != girih.NAIVE:
-        nms = timed(girih.config(girih.NAIVE), max(1, args.steps // 2), 1)
-        naive = lups * max(1, args.steps // 2) * ws / (nms * 1e-3) * 1e-9
+    if not args.no_naive:
+        if cfg.algo == girih.NAIVE:
+            naive = value
+        else:
+            nms = timed(girih.config(girih.NAIVE), max(1, args.steps // 2), 1)
+            naive = lups * max(1, args.steps // 2) * ws / (nms * 1e-3) * 1e-9
 
     # roofline of the dominant kernel (every launch of the timed region is the blocked kernel,
     # except the exchange kernel for odd T, which the default workloads do not have)

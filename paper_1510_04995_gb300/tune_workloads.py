@@ -1,0 +1,72 @@
+"""Tune the benchmark workloads with the library's exhaustive tuner and record the winners.
+
+    python -m paper_1510_04995_gb300.tune_workloads [--workloads a,b] [--out tuned_configs.json]
+
+For every workload (stencil, dtype, grid, T) this runs girih_tune_exhaustive (Sect. 4.2.2: all
+feasible candidates, test length grown until two repetitions agree) on tuner-owned arrays of the
+full grid, with the 16-byte aligned leading dimension the benchmark uses, and writes
+{workload: config} to tuned_configs.json next to this file, plus the timing database.
+"""
+from __future__ import annotations
+
+import argparse
+import ctypes
+import json
+import os
+import time
+
+from . import TuneRow, build, check, lib, plan
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+
+WORKLOADS = {
+    "7pt_const_f64_512": (0, "f64", 512, 512, 512, 64),
+    "7pt_const_f32_512": (0, "f32", 512, 512, 512, 64),
+    "7pt_var_f64_480": (1, "f64", 480, 480, 480, 32),
+    "7pt_var_f32_480": (1, "f32", 480, 480, 480, 32),
+    "25pt_const_f64_384": (2, "f64", 384, 384, 384, 32),
+    "25pt_const_f32_384": (2, "f32", 384, 384, 384, 32),
+    "25pt_var_f64_384": (3, "f64", 384, 384, 384, 32),
+    "25pt_var_f32_384": (3, "f32", 384, 384, 384, 32),
+}
+RADIUS = {0: 1, 1: 1, 2: 4, 3: 4}
+
+
+def aligned_ldx(stencil: int, dtype: str, nx: int) -> int:
+    a16 = 16 // (8 if dtype == "f64" else 4)
+    return -(-(nx + 2 * RADIUS[stencil]) // a16) * a16
+
+
+def tune(names, out_path, db_path, tol=0.05, max_steps=64, log=print):
+    build.build()
+    res = {}
+    if os.path.exists(out_path):
+        with open(out_path) as f:
+            res = json.load(f)
+    for name in names:
+        s, d, nx, ny, nz, T = WORKLOADS[name]
+        p = plan(s, nx, ny, nz, dtype=d, T=T, ldx=aligned_ldx(s, d, nx))
+        best = TuneRow()
+        nm = ctypes.c_int32()
+        t0 = time.perf_counter()
+        check(lib().girih_tune_exhaustive(p.handle, tol, max_steps, db_path.encode(), ctypes.byref(best),
+                                          ctypes.byref(nm)))
+        res[name] = best.cfg.as_dict()
+        if log:
+            log(f"{name}: {nm.value} candidates, {time.perf_counter() - t0:.1f} s, best {best.glups:.1f} GLUP/s "
+                f"{best.cfg}")
+        p.close()
+        with open(out_path, "w") as f:
+            json.dump(res, f, indent=1, sort_keys=True)
+    return res
+
+
+if __name__ == "__main__":
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--workloads", default=",".join(WORKLOADS))
+    ap.add_argument("--out", default=os.path.join(HERE, "tuned_configs.json"))
+    ap.add_argument("--db", default=os.path.join(HERE, "tuned_db.csv"))
+    ap.add_argument("--tol", type=float, default=0.05)
+    ap.add_argument("--max-steps", type=int, default=64)
+    a = ap.parse_args()
+    tune(a.workloads.split(","), a.out, a.db, a.tol, a.max_steps)
