@@ -184,12 +184,13 @@ GIRIH_API int girih_tune_candidates(girih_plan_t plan, girih_config* out, int32_
 GIRIH_API int girih_tune_measure(girih_plan_t plan, const girih_config* cfg, double tol, int64_t max_steps,
                        girih_tune_row* row);
 
-/* Exhaustive tuning: measure every candidate, append one CSV line per candidate to db_path
- * (NULL: no file), set the plan's configuration to the fastest and return it in *best.  CSV
- * columns: stencil, dtype, nx, ny, nz, algo, dw, nf, cluster, threads, variant, glups, seconds,
- * steps, smem, tune_seconds.                                                                   */
-GIRIH_API int girih_tune_exhaustive(girih_plan_t plan, double tol, int64_t max_steps, const char* db_path,
-                          girih_tune_row* best, int32_t* n_measured);
+/* Exhaustive tuning: measure every candidate (the given list of n_cands configurations, or all of
+ * girih_tune_candidates when cands is NULL), append one CSV line per candidate to db_path (NULL:
+ * no file), set the plan's configuration to the fastest and return it in *best.  CSV columns:
+ * stencil, dtype, nx, ny, nz, algo, dw, nf, cluster, threads, variant, glups, seconds, steps,
+ * smem, tune_seconds.  Infeasible listed candidates return EINVAL before anything is measured. */
+GIRIH_API int girih_tune_exhaustive(girih_plan_t plan, const girih_config* cands, int32_t n_cands, double tol,
+                                    int64_t max_steps, const char* db_path, girih_tune_row* best, int32_t* n_measured);
 
 /* ---- learned tuner: 3-layer MLP (D -> 64 -> 64 -> 1, ReLU), FP32, CUDA kernels --------------- */
 
@@ -237,11 +238,12 @@ GIRIH_API int girih_mlp_sgd(float* params, const float* grad, int64_t np, float 
 GIRIH_API int girih_mlp_adam(float* params, const float* grad, float* m, float* v, int64_t np, int64_t step, float lr,
                    float beta1, float beta2, float eps, void* stream);
 
-/* Learned tuning: score all candidates of girih_tune_candidates with the network (device
- * parameters `params`, trained on log GLUP/s), measure the best `k` with girih_tune_measure,
- * set the plan's configuration to the fastest of those and return it in *best.              */
-GIRIH_API int girih_tune_learned(girih_plan_t plan, const float* params, int32_t k, double tol, int64_t max_steps,
-                       girih_tune_row* best, int32_t* n_measured);
+/* Learned tuning: score the candidates (the given list, or all of girih_tune_candidates when
+ * cands is NULL) with the network (device parameters `params`, trained on per-problem centred
+ * log GLUP/s), measure the best `k` with girih_tune_measure, set the plan's configuration to the
+ * fastest of those and return it in *best.                                                    */
+GIRIH_API int girih_tune_learned(girih_plan_t plan, const float* params, const girih_config* cands, int32_t n_cands,
+                                 int32_t k, double tol, int64_t max_steps, girih_tune_row* best, int32_t* n_measured);
 
 #ifdef __cplusplus
 }

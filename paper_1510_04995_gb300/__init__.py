@@ -60,6 +60,14 @@ def config(algo=MWD, dw=8, nf=1, cluster=1, threads=256, variant=FED) -> Config:
     return Config(algo, dw, nf, cluster, threads, variant)
 
 
+def config_array(cfgs):
+    """(ctypes array, count) of configurations for the tuner calls; (None, 0) for all candidates."""
+    if cfgs is None:
+        return None, 0
+    arr = (Config * len(cfgs))(*cfgs)
+    return arr, len(cfgs)
+
+
 _lib = None
 _VP, _I32, _I64, _F32, _F64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_float, ctypes.c_double
 _SIGS = {
@@ -78,8 +86,8 @@ _SIGS = {
     "girih_model_code_balance": (_F64, [_I32, _I32, _I32, _I32]),
     "girih_tune_candidates": (ctypes.c_int, [_VP, ctypes.POINTER(Config), _I32, ctypes.POINTER(_I32)]),
     "girih_tune_measure": (ctypes.c_int, [_VP, ctypes.POINTER(Config), _F64, _I64, ctypes.POINTER(TuneRow)]),
-    "girih_tune_exhaustive": (ctypes.c_int, [_VP, _F64, _I64, ctypes.c_char_p, ctypes.POINTER(TuneRow),
-                                             ctypes.POINTER(_I32)]),
+    "girih_tune_exhaustive": (ctypes.c_int, [_VP, ctypes.POINTER(Config), _I32, _F64, _I64, ctypes.c_char_p,
+                                             ctypes.POINTER(TuneRow), ctypes.POINTER(_I32)]),
     "girih_mlp_features": (ctypes.c_int, [_I32, _I32, _I64, _I64, _I64, ctypes.POINTER(Config), _VP]),
     "girih_mlp_num_params": (_I64, [_I32]),
     "girih_mlp_workspace_floats": (_I64, [_I32]),
@@ -88,8 +96,8 @@ _SIGS = {
     "girih_mlp_backward_static": (ctypes.c_int, [_VP, _VP, _VP, _I32, _I32, _VP, _VP, _VP]),
     "girih_mlp_sgd": (ctypes.c_int, [_VP, _VP, _I64, _F32, _VP]),
     "girih_mlp_adam": (ctypes.c_int, [_VP, _VP, _VP, _VP, _I64, _I64, _F32, _F32, _F32, _F32, _VP]),
-    "girih_tune_learned": (ctypes.c_int, [_VP, _VP, _I32, _F64, _I64, ctypes.POINTER(TuneRow),
-                                          ctypes.POINTER(_I32)]),
+    "girih_tune_learned": (ctypes.c_int, [_VP, _VP, ctypes.POINTER(Config), _I32, _I32, _F64, _I64,
+                                          ctypes.POINTER(TuneRow), ctypes.POINTER(_I32)]),
 }
 
 

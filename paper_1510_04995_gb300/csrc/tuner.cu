@@ -166,10 +166,26 @@ static void append_csv(FILE* f, const Plan* p, const girih_tune_row& r) {
           r.cfg.threads, r.cfg.variant, r.glups, r.seconds, (long long)r.steps, (long long)r.smem, r.tune_seconds);
 }
 
-int girih_tune_exhaustive(girih_plan_t plan, double tol, int64_t max_steps, const char* db_path,
-                          girih_tune_row* best, int32_t* n_measured) {
+static int candidate_list(Plan* p, const girih_config* given, int32_t n, std::vector<girih_config>* out) {
+  if (!given) {
+    *out = candidates(p);
+    return GIRIH_OK;
+  }
+  if (n < 1) return fail(GIRIH_EINVAL, "empty candidate list");
+  out->assign(given, given + n);
+  for (const girih_config& c : *out) {
+    const int rc = check_config(p, &c, nullptr, nullptr, nullptr);
+    if (rc != GIRIH_OK) return rc;
+  }
+  return GIRIH_OK;
+}
+
+int girih_tune_exhaustive(girih_plan_t plan, const girih_config* cand_list, int32_t n_cands, double tol,
+                          int64_t max_steps, const char* db_path, girih_tune_row* best, int32_t* n_measured) {
   if (!plan || !best) return fail(GIRIH_EINVAL, "NULL argument");
-  const std::vector<girih_config> cands = candidates(plan);
+  std::vector<girih_config> cands;
+  const int crc = candidate_list(plan, cand_list, n_cands, &cands);
+  if (crc != GIRIH_OK) return crc;
   FILE* f = nullptr;
   if (db_path) {
     f = fopen(db_path, "a");
@@ -223,10 +239,12 @@ int girih_mlp_features(int32_t stencil, int32_t dtype, int64_t nx, int64_t ny, i
   return GIRIH_OK;
 }
 
-int girih_tune_learned(girih_plan_t plan, const float* params, int32_t k, double tol, int64_t max_steps,
-                       girih_tune_row* best, int32_t* n_measured) {
+int girih_tune_learned(girih_plan_t plan, const float* params, const girih_config* cand_list, int32_t n_cands,
+                       int32_t k, double tol, int64_t max_steps, girih_tune_row* best, int32_t* n_measured) {
   if (!plan || !params || !best || k < 1) return fail(GIRIH_EINVAL, "bad arguments");
-  const std::vector<girih_config> cands = candidates(plan);
+  std::vector<girih_config> cands;
+  const int crc = candidate_list(plan, cand_list, n_cands, &cands);
+  if (crc != GIRIH_OK) return crc;
   const int n = (int)cands.size(), d = GIRIH_MLP_FEATURES;
   std::vector<float> X((size_t)n * d), y(n);
   for (int i = 0; i < n; ++i)

@@ -26,7 +26,7 @@ import time
 
 import numpy as np
 
-from . import (F32, F64, MLP_FEATURES, Config, TuneRow, check, config, lib, plan)
+from . import (F32, F64, FED, MLP_FEATURES, MWD, NAIVE, Config, TuneRow, check, config, config_array, lib, plan)
 
 # The 12 non-cubic grids of the learned-tuner sweep (nx, ny, nz), and the held-out ones (#3, #7, #10).
 GRIDS = [(128, 256, 512), (256, 128, 512), (192, 384, 512), (256, 512, 512), (384, 256, 512),
@@ -41,15 +41,31 @@ def _dt(d):
     return {"f64": F64, "f32": F32, F64: F64, F32: F32}[d]
 
 
+def space(p) -> list:
+    """The experiment's search space for a plan: the naive sweep and the feasible blocked sweeps
+    with diamond widths 2R..16R, wavefront widths 1 and 2, clusters 1..16 and 256 or 512 threads."""
+    R = p.R
+    out = [config(NAIVE, 0, 1, 1, 256, FED)]
+    for dw in sorted({2 * R, 4 * R, 6 * R, 8 * R, 12 * R, 16 * R}):
+        for nf in (1, 2):
+            for cl in (1, 2, 4, 8, 16):
+                for th in (256, 512):
+                    c = config(MWD, dw, nf, cl, th, FED)
+                    if p.feasible(c):
+                        out.append(c)
+    return out
+
+
 def collect(db_path: str, problems, T: int = 16, tol: float = 0.05, max_steps: int = 32, times_path: str | None = None,
             log=print):
-    """Exhaustively tune every (stencil, dtype, nx, ny, nz) problem; rows go to db_path."""
+    """Exhaustively tune every (stencil, dtype, nx, ny, nz) problem over space(); rows go to db_path."""
     for (stencil, dtype, nx, ny, nz) in problems:
         p = plan(stencil, nx, ny, nz, dtype=dtype, T=T)
         best = TuneRow()
         nm = ctypes.c_int32()
+        arr, n = config_array(space(p))
         t0 = time.perf_counter()
-        check(lib().girih_tune_exhaustive(p.handle, tol, max_steps, db_path.encode(), ctypes.byref(best),
+        check(lib().girih_tune_exhaustive(p.handle, arr, n, tol, max_steps, db_path.encode(), ctypes.byref(best),
                                           ctypes.byref(nm)))
         dt = time.perf_counter() - t0
         if times_path:
@@ -175,9 +191,10 @@ def tune(p, params: np.ndarray, k: int = 5, tol: float = 0.05, max_steps: int = 
     P = torch.from_numpy(np.ascontiguousarray(params, dtype=np.float32)).cuda()
     best = TuneRow()
     nm = ctypes.c_int32()
+    arr, n = config_array(space(p))
     t0 = time.perf_counter()
-    check(lib().girih_tune_learned(p.handle, ctypes.c_void_p(P.data_ptr()), k, tol, max_steps, ctypes.byref(best),
-                                   ctypes.byref(nm)))
+    check(lib().girih_tune_learned(p.handle, ctypes.c_void_p(P.data_ptr()), arr, n, k, tol, max_steps,
+                                   ctypes.byref(best), ctypes.byref(nm)))
     return best, nm.value, time.perf_counter() - t0
 
 

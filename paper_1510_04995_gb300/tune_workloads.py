@@ -49,7 +49,7 @@ def tune(names, out_path, db_path, tol=0.05, max_steps=64, log=print):
         best = TuneRow()
         nm = ctypes.c_int32()
         t0 = time.perf_counter()
-        check(lib().girih_tune_exhaustive(p.handle, tol, max_steps, db_path.encode(), ctypes.byref(best),
+        check(lib().girih_tune_exhaustive(p.handle, None, 0, tol, max_steps, db_path.encode(), ctypes.byref(best),
                                           ctypes.byref(nm)))
         res[name] = best.cfg.as_dict()
         if log:

@@ -45,7 +45,7 @@ def test_measure_and_exhaustive_argmax(tmp_path):
     db = str(tmp_path / "db.csv")
     best = girih.TuneRow()
     nm = ctypes.c_int32()
-    girih.check(girih.lib().girih_tune_exhaustive(p.handle, 0.5, 8, db.encode(), ctypes.byref(best),
+    girih.check(girih.lib().girih_tune_exhaustive(p.handle, None, 0, 0.5, 8, db.encode(), ctypes.byref(best),
                                                    ctypes.byref(nm)))
     rows = np.loadtxt(db, delimiter=",", ndmin=2)
     assert rows.shape[0] == nm.value == len(_cands(p))
@@ -61,6 +61,20 @@ def test_learned_tuner_measures_only_top_k():
     params[-1] = 1.0  # constant network: ties broken by candidate order
     best = girih.TuneRow()
     nm = ctypes.c_int32()
-    girih.check(girih.lib().girih_tune_learned(p.handle, ctypes.c_void_p(params.data_ptr()), 3, 0.5, 8,
+    girih.check(girih.lib().girih_tune_learned(p.handle, ctypes.c_void_p(params.data_ptr()), None, 0, 3, 0.5, 8,
                                                 ctypes.byref(best), ctypes.byref(nm)))
     assert nm.value == 3 and best.glups > 0
+
+
+def test_explicit_candidate_list(tmp_path):
+    from paper_1510_04995_gb300 import learned
+    p = girih.plan(girih.S25C, 48, 40, 24, dtype="f32", T=8)
+    cands = learned.space(p)
+    assert cands[0].algo == girih.NAIVE and len(cands) > 1
+    arr, n = girih.config_array(cands[:3])
+    best = girih.TuneRow()
+    nm = ctypes.c_int32()
+    girih.check(girih.lib().girih_tune_exhaustive(p.handle, arr, n, 0.5, 8, None, ctypes.byref(best), ctypes.byref(nm)))
+    assert nm.value == 3
+    bad, nb = girih.config_array([girih.config(girih.MWD, dw=3)])
+    assert girih.lib().girih_tune_exhaustive(p.handle, bad, nb, 0.5, 8, None, ctypes.byref(best), ctypes.byref(nm)) == 1
