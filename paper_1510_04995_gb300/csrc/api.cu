@@ -82,10 +82,11 @@ int check_config(const Plan* p, const girih_config* c, int64_t* smem_out, int* x
   const int XW = slab_width(p->nx, c->cluster);
   // with a 16-byte aligned layout one warp of the block moves data and the others compute
   const int cthreads = bulk ? c->threads - 32 : c->threads;
-  const int G = mwd_pairs_per_thread(R, c->dw, XW, c->threads, bulk);
+  const int G = mwd_pairs_per_thread(p->stencil, p->dtype, c->dw, XW, c->threads, bulk);
   if (G == 0)
-    return fail(GIRIH_EINVAL, "dw=%d with a %d-wide slab has %d row pairs: too many for %d computing threads",
-                c->dw, XW, mwd_max_pairs(R, c->dw) * XW, cthreads);
+    return fail(GIRIH_EINVAL, "dw=%d with a %d-wide slab has %d row pairs x %d column groups: too many for %d "
+                "computing threads", c->dw, XW, mwd_max_pairs(R, c->dw), XW / mwd_vx(p->stencil, p->dtype, bulk),
+                cthreads);
   if (R == 4 && G > 4) return fail(GIRIH_EINVAL, "25-point tiles allow at most 4 row pairs per thread (registers)");
   if (p->dtype == GIRIH_F64 && R == 4 && G > 2)
     return fail(GIRIH_EINVAL, "25-point FP64 tiles allow at most 2 row pairs per thread (registers)");

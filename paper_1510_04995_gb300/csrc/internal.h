@@ -59,10 +59,17 @@ cudaError_t launch_mwd_row(int stencil, int dtype, const MwdArgs& a, int ndiam, 
 // active clusters the device reports for the configuration (0 = cannot be scheduled).
 cudaError_t mwd_prepare(int stencil, int dtype, int C, int threads, int G, bool bulk, int64_t smem, int* max_clusters);
 int mwd_max_pairs(int R, int dw);
-int mwd_pairs_per_thread(int R, int dw, int XW, int threads, bool bulk);
-// Largest block for G pairs per thread (the kernel's launch bound).
-inline int mwd_max_threads(int G, bool bulk) {
-  const int t = 1024 / G + (bulk ? 32 : 0);
+int mwd_pairs_per_thread(int stencil, int dtype, int dw, int XW, int threads, bool bulk);
+// Columns per thread of the blocked kernel and its launch-bound divisor (mirror the device side).
+inline int mwd_vx(int stencil, int dtype, bool bulk) {
+  return (bulk || (stencil >= 2 && dtype == GIRIH_F64)) ? 1 : (dtype == GIRIH_F64 ? 2 : 4);
+}
+inline int mwd_lbf(int stencil, int dtype, bool bulk) {
+  return mwd_vx(stencil, dtype, bulk) == 1 ? 1 : (stencil < 2 ? 2 : 4);
+}
+// Largest block for G groups per thread (the kernel's launch bound).
+inline int mwd_max_threads(int G, int lbf, bool bulk) {
+  const int t = 1024 / (G * lbf) + (bulk ? 32 : 0);
   return t > 1024 ? 1024 : t;
 }
 // Planes are staged this many wavefront steps ahead of use (element path / bulk-copy path).

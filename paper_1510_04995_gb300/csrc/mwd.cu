@@ -21,7 +21,9 @@ MwdShape mwd_shape(int stencil, int dtype, int dw, int nf, int XW, bool bulk) {
   const int pd = bulk ? MWD_PREFETCH_BULK : MWD_PREFETCH;
   s.NZ = (pd + 1) * nf + R + (R > nf ? R : nf) + (H - 2) * K + (bulk ? MWD_BULK_SLACK * nf : 0);
   s.YW = dw + 2 * R;
-  s.XT = (XW + 2 * R + a16 - 1) / a16 * a16;  // rows start on 16-byte boundaries
+  // shared row: [halo | slab | halo]; with vector groups the slab starts on a 16-byte boundary
+  const int off = mwd_vx(stencil, dtype, bulk) == 1 ? R : a16;
+  s.XT = (off + XW + R + a16 - 1) / a16 * a16;  // rows start on 16-byte boundaries
   const int64_t ring = 2LL * s.NZ * s.YW * s.XT * elem;
   s.smem_bytes = (ring + 15) / 16 * 16 + 8LL * s.NZ + (3LL * H + 1 + s.YW) * 4;
   return s;
@@ -35,13 +37,18 @@ int mwd_max_pairs(int R, int dw) {
   return n;
 }
 
-// Pairs per computing thread (1, 2, 4 or 8) for a block of `threads` (one of them a producer warp
-// in the bulk-copy path), or 0 if the tile needs more.
-int mwd_pairs_per_thread(int R, int dw, int XW, int threads, bool bulk) {
-  const int64_t ng = (int64_t)mwd_max_pairs(R, dw) * XW;
+// Groups (row pair x VX columns) per computing thread (1, 2, 4 or 8) for a block of `threads`
+// (one warp of them a producer in the bulk-copy path), or 0 if the tile needs more.
+int mwd_pairs_per_thread(int stencil, int dtype, int dw, int XW, int threads, bool bulk) {
+  const int R = radius_of(stencil);
+  const int vx = mwd_vx(stencil, dtype, bulk), lbf = mwd_lbf(stencil, dtype, bulk);
+  const int64_t ng = (int64_t)mwd_max_pairs(R, dw) * (XW / vx);
   const int ct = bulk ? threads - 32 : threads;
-  for (int G : {1, 2, 4, 8})
-    if (threads <= mwd_max_threads(G, bulk) && ng <= (int64_t)G * ct) return G;
+  for (int G : {1, 2, 4, 8}) {
+    if (G == 8 && R == 4) break;  // radius-4 kernels are built for at most 4 groups per thread
+    if (G > 2 && R == 4 && vx > 1) break;  // radius-4 vector groups: registers allow 2 per thread
+    if (threads <= mwd_max_threads(G, lbf, bulk) && ng <= (int64_t)G * ct) return G;
+  }
   return 0;
 }
 

@@ -47,24 +47,73 @@
 
 namespace girih {
 
-// Accessor of one row of a row pair: z neighbours and the centre come from the thread's own
-// register window (w[R] = centre), y neighbours from the pair's shared loads, x neighbours and
-// the level t-1 centre from the shared ring.
-template <int S, typename T>
-struct PairAcc {
-  const T* w;        // window of this row, planes z-R..z+R
-  const T* yv;       // y neighbours: yv[R + d] = value at row y + d (d != 0)
-  const T* X;        // pointer to the centre in the level-t ring buffer
+// Accessor of one point of a row pair handled as VX consecutive columns.  ROW (0: row y0, 1: row
+// y0+1) and I (column within the vector) are compile-time after unrolling, so every access below
+// resolves to a register:
+//   w      this row's z window, w[(R + dz)*VX + i]          (centre plane dz = 0)
+//   other  the other row's window (its centre is this row's y neighbour at distance 1)
+//   ylo    rows y0-R .. y0-1, ylo[j*VX + i] = row y0-R+j    yhi  rows y0+2 .. y0+1+R
+//   xl     this row's x line: R columns left of the vector, the vector, R columns right
+template <int S, typename T, int VX, int ROW, int I>
+struct VecAcc {
+  static constexpr int R = Traits<S>::R;
+  const T* w;
+  const T* other;
+  const T* ylo;
+  const T* yhi;
+  const T* xl;
   T uc;
-  const T* coef;     // coefficient grid 0 at this pair's first row and current plane
-  int64_t gs, p;     // grid stride, offset of this row from coef
-  __device__ __forceinline__ T c() const { return w[Traits<S>::R]; }
-  __device__ __forceinline__ T x(int d) const { return X[d]; }
-  __device__ __forceinline__ T y(int d) const { return yv[Traits<S>::R + d]; }
-  __device__ __forceinline__ T z(int d) const { return w[Traits<S>::R + d]; }
+  const T* coef;     // coefficient grid 0 at this point (variable stencils)
+  int64_t gs;        // grid stride
+  __device__ __forceinline__ T c() const { return w[R * VX + I]; }
+  __device__ __forceinline__ T x(int d) const { return xl[R + I + d]; }
+  __device__ __forceinline__ T z(int d) const { return w[(R + d) * VX + I]; }
+  __device__ __forceinline__ T y(int d) const {
+    if (ROW == 0) return d < 0 ? ylo[(R + d) * VX + I] : (d == 1 ? other[R * VX + I] : yhi[(d - 2) * VX + I]);
+    return d > 0 ? yhi[(d - 1) * VX + I] : (d == -1 ? other[R * VX + I] : ylo[(R + 1 + d) * VX + I]);
+  }
   __device__ __forceinline__ T u() const { return uc; }
-  __device__ __forceinline__ T k(int g) const { return __ldg(coef + g * gs + p); }
+  __device__ __forceinline__ T k(int g) const { return __ldg(coef + g * gs); }
 };
+
+// VX consecutive elements from shared memory (one 16-byte access when VX*sizeof(T) == 16).
+template <typename T, int VX>
+__device__ __forceinline__ void lds_vec(const T* p, T* out) {
+  if constexpr (VX * sizeof(T) == 16) {
+    if constexpr (sizeof(T) == 4) {
+      const float4 v = *reinterpret_cast<const float4*>(p);
+      out[0] = v.x; out[1] = v.y; out[2] = v.z; out[3] = v.w;
+    } else {
+      const double2 v = *reinterpret_cast<const double2*>(p);
+      out[0] = v.x; out[1] = v.y;
+    }
+  } else {
+#pragma unroll
+    for (int i = 0; i < VX; ++i) out[i] = p[i];
+  }
+}
+template <typename T, int VX>
+__device__ __forceinline__ void sts_vec(T* p, const T* v) {
+  if constexpr (VX * sizeof(T) == 16) {
+    if constexpr (sizeof(T) == 4) *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1], v[2], v[3]);
+    else *reinterpret_cast<double2*>(p) = make_double2(v[0], v[1]);
+  } else {
+#pragma unroll
+    for (int i = 0; i < VX; ++i) p[i] = v[i];
+  }
+}
+
+// Columns per thread of the blocked kernel: whole 16-byte vectors on the element path, except
+// the 25-point FP64 tiles (register budget); single columns on the bulk-copy path.
+template <int S, typename T, bool BULK>
+constexpr int mwd_vx() {
+  return (BULK || (Traits<S>::R == 4 && sizeof(T) == 8)) ? 1 : (int)(16 / sizeof(T));
+}
+// Launch-bound divisor for the register growth of vector groups.
+template <int S, typename T, bool BULK>
+constexpr int mwd_lbf() {
+  return mwd_vx<S, T, BULK>() == 1 ? 1 : (Traits<S>::R == 1 ? 2 : 4);
+}
 
 __device__ __forceinline__ int lev_lo_of(int a, int b, int dw, int R, int t) {
   return max(a * dw - R * t, b * dw + R * t);
@@ -124,13 +173,41 @@ __device__ __forceinline__ void bulk_wait_read_n() {
   asm volatile("cp.async.bulk.wait_group.read %0;" ::"n"(N) : "memory");
 }
 
+// The VX point updates of both rows of a group.  Columns I >= nv lie past the slab's end: their
+// results are discarded, and their coefficient reads are redirected to column 0 (in bounds).
+template <int S, typename T, int VX, int I>
+__device__ __forceinline__ void mwd_points_i(const T* w0, const T* w1, const T* ylo, const T* yhi, const T* xl0,
+                                             const T* xl1, const T* u0, const T* u1, const T* kp, int64_t gs,
+                                             int64_t ldx, int nv, bool row1, const T* cst, T* r0, T* r1) {
+  if constexpr (I < VX) {
+    const T* k0 = (Traits<S>::NCOEF > 0 && I < nv) ? kp + I : kp;
+    VecAcc<S, T, VX, 0, I> a0{w0, w1, ylo, yhi, xl0, Traits<S>::ORDER2 ? u0[I] : T(0), k0, gs};
+    r0[I] = point_update<S, T>(a0, cst);
+    if (row1) {
+      VecAcc<S, T, VX, 1, I> a1{w1, w0, ylo, yhi, xl1, Traits<S>::ORDER2 ? u1[I] : T(0), k0 + ldx, gs};
+      r1[I] = point_update<S, T>(a1, cst);
+    }
+    mwd_points_i<S, T, VX, I + 1>(w0, w1, ylo, yhi, xl0, xl1, u0, u1, kp, gs, ldx, nv, row1, cst, r0, r1);
+  }
+}
+template <int S, typename T, int VX>
+__device__ __forceinline__ void mwd_points(const T* w0, const T* w1, const T* ylo, const T* yhi, const T* xl0,
+                                           const T* xl1, const T* u0, const T* u1, const T* kp, int64_t gs,
+                                           int64_t ldx, int nv, bool row1, const T* cst, T* r0, T* r1) {
+  mwd_points_i<S, T, VX, 0>(w0, w1, ylo, yhi, xl0, xl1, u0, u1, kp, gs, ldx, nv, row1, cst, r0, r1);
+}
+
 template <int S, typename T, int G, bool BULK>
-__global__ void __launch_bounds__((1024 / G + (BULK ? 32 : 0)) > 1024 ? 1024 : (1024 / G + (BULK ? 32 : 0)))
+__global__ void __launch_bounds__((1024 / (G * mwd_lbf<S, T, BULK>()) + (BULK ? 32 : 0)) > 1024
+                                      ? 1024
+                                      : (1024 / (G * mwd_lbf<S, T, BULK>()) + (BULK ? 32 : 0)))
     mwd_fed_kernel(const MwdArgs A) {
   constexpr int R = Traits<S>::R;
   constexpr int NC = Traits<S>::NCOEF;
   constexpr int PD = BULK ? MWD_PREFETCH_BULK : MWD_PREFETCH;
   constexpr int A16 = 16 / (int)sizeof(T);  // elements per 16 bytes
+  constexpr int VX = mwd_vx<S, T, BULK>();   // columns per thread
+  constexpr int OFF = VX == 1 ? R : A16;     // shared column of the slab's first column
   extern __shared__ __align__(128) unsigned char smem_raw[];
   T* sm = reinterpret_cast<T*>(smem_raw);
   const int NZ = A.NZ, YW = A.YW, XT = A.XT, XW = A.XW, C = A.C, nf = A.nf, K = A.K;
@@ -208,37 +285,41 @@ __global__ void __launch_bounds__((1024 / G + (BULK ? 32 : 0)) > 1024 ? 1024 : (
   for (int i = 0; i < 5; ++i) cst[i] = sizeof(T) == 8 ? static_cast<T>(A.c[i]) : static_cast<T>(A.cf[i]);
   const int64_t gstride = A.g.gstride;
 
-  // ---- this thread's row pairs (computing threads only) -------------------------------------
-  // per pair: ring offsets of row y0 in the level-t and level-t+1 buffers, current plane z and
-  // its ring slot (both advance by nf per step), coefficient pointer, flags (valid, second row,
-  // push left, push right)
-  int gzb_[G], gsl_[G], gvo_[G], guo_[G], gflags_[G];
+  // ---- this thread's groups (computing threads only): a group is a row pair (level s, rows y0
+  // and y0+1) times VX consecutive columns, owned for the whole launch.  Per group: ring offsets
+  // of (row y0, first column) in the level-t and level-t+1 buffers, current plane z and its ring
+  // slot (both advance by nf per step), coefficient pointer, valid columns of the vector (ragged
+  // slab tail), flags (valid, second row, push left, push right).
+  int gzb_[G], gsl_[G], gvo_[G], guo_[G], gflags_[G], gnv_[G], gx_[G];
   const T* gk_[G];
   const int npairs = lev_pp[nlev];
+  const int nvec = XW / VX;
 #pragma unroll
   for (int g = 0; g < G; ++g) {
     const int id = ctid + g * CNT;
-    const int pr = id / XW, xl = id - pr * XW;
+    const int pr = id / nvec, xl = (id - pr * nvec) * VX;
     const bool valid = !producer && (pr < npairs) && (xl < xw);
     int s = 0;
     if (valid)
       while (lev_pp[s + 1] <= pr) ++s;
     const int y0 = valid ? lev_lo[s] + 2 * (pr - lev_pp[s]) : 0;
     const int t = tb + s;
-    const int col = (y0 - Y0) * XT + xl + R;
+    const int col = (y0 - Y0) * XT + xl + OFF;
     gvo_[g] = (t & 1) * be + col;
     guo_[g] = ((t & 1) ^ 1) * be + col;
     gzb_[g] = -s * K;
     const int sl = (-s * K + R) % NZ;
     gsl_[g] = sl < 0 ? sl + NZ : sl;
+    gnv_[g] = min(VX, xw - xl);
+    gx_[g] = xl;
     const bool row1 = valid && (y0 + 1 < lev_lo[s] + lev_w[s]);
     gflags_[g] = (valid ? 1 : 0) | (row1 ? 2 : 0) | ((C > 1 && xl < R && rank > 0) ? 4 : 0) |
-                 ((C > 1 && xl >= XW - R && rank < C - 1) ? 8 : 0);
+                 ((C > 1 && xl + VX > XW - R && rank < C - 1) ? 8 : 0);
     gk_[g] = NC ? static_cast<const T*>(A.coef) + (int64_t)(-s * K + R) * gplane + (int64_t)(y0 + R) * ldx +
                       (x0 + xl + R)
                 : nullptr;
   }
-  T win[G][2][2 * R + 1];
+  T win[G][2][(2 * R + 1) * VX];
 
   // ---- staging geometry: rows y in [Y0, Y0+YW) clipped to the padded grid, columns from padded
   // x0 (interior x0 - R); BULK rows are rounded up to 16 bytes (the host keeps them inside ldx)
@@ -307,7 +388,7 @@ __global__ void __launch_bounds__((1024 / G + (BULK ? 32 : 0)) > 1024 ? 1024 : (
       const int p = rr >= nrow;
       const int y = ylo + rr - p * nrow;
       const T* src = (p ? gb1 : gb0) + gz + (int64_t)(y + R) * ldx + x0;
-      T* dst = sm + p * be + slot * pe + (y - Y0) * XT;
+      T* dst = sm + p * be + slot * pe + (y - Y0) * XT + (OFF - R);
       for (int xx = lane; xx < ncol; xx += 32) cp_async(dst + xx, src + xx);
     }
   };
@@ -318,7 +399,7 @@ __global__ void __launch_bounds__((1024 / G + (BULK ? 32 : 0)) > 1024 ? 1024 : (
       const int m = row_mask[yy];
       if (m == 0) continue;
       const int64_t go = gz + (int64_t)(Y0 + yy + R) * ldx + (x0 + R);
-      const T* src = sm + slot * pe + yy * XT + R;
+      const T* src = sm + slot * pe + yy * XT + OFF;
       for (int xl = lane; xl < xw; xl += 32) {
         if (m & 1) go0[go + xl] = src[xl];
         if (m & 2) go1[go + xl] = src[be + xl];
@@ -350,7 +431,7 @@ __global__ void __launch_bounds__((1024 / G + (BULK ? 32 : 0)) > 1024 ? 1024 : (
 
   const int W = (nz + smax * K + nf - 1) / nf;
   for (int w = 0; w < W; ++w) {
-    // ---- compute: this thread's pairs at the planes of step w ----
+    // ---- compute: this thread's groups at the planes of step w ----
 #pragma unroll
     for (int g = 0; g < G; ++g) {
       const int fl = gflags_[g];
@@ -365,54 +446,79 @@ __global__ void __launch_bounds__((1024 / G + (BULK ? 32 : 0)) > 1024 ? 1024 : (
               for (int d = -R; d <= R; ++d) {
                 int sd = sl + d;
                 sd = sd < 0 ? sd + NZ : (sd >= NZ ? sd - NZ : sd);
-                win[g][0][R + d] = Vb[sd * pe];
-                win[g][1][R + d] = Vb[sd * pe + XT];
+                lds_vec<T, VX>(Vb + sd * pe, &win[g][0][(R + d) * VX]);
+                lds_vec<T, VX>(Vb + sd * pe + XT, &win[g][1][(R + d) * VX]);
               }
             } else {  // slide the window up by one plane
               const int sd = (sl + R >= NZ) ? sl + R - NZ : sl + R;
 #pragma unroll
-              for (int d = 0; d < 2 * R; ++d) {
-                win[g][0][d] = win[g][0][d + 1];
-                win[g][1][d] = win[g][1][d + 1];
+              for (int d = 0; d < 2 * R * VX; ++d) {
+                win[g][0][d] = win[g][0][d + VX];
+                win[g][1][d] = win[g][1][d + VX];
               }
-              win[g][0][2 * R] = Vb[sd * pe];
-              win[g][1][2 * R] = Vb[sd * pe + XT];
+              lds_vec<T, VX>(Vb + sd * pe, &win[g][0][2 * R * VX]);
+              lds_vec<T, VX>(Vb + sd * pe + XT, &win[g][1][2 * R * VX]);
             }
             const bool row1 = fl & 2;
-            const T* P = Vb + sl * pe;  // centre of row y0 at plane z
-            T yv0[2 * R + 1], yv1[2 * R + 1];  // y neighbours of row y0 and row y0+1
+            const T* P = Vb + sl * pe;  // (row y0, first column) at plane z
+            T ylo[R * VX], yhi[R * VX], xl0[VX + 2 * R], xl1[VX + 2 * R];
 #pragma unroll
-            for (int d = 1; d <= R; ++d) {
-              yv0[R - d] = P[-d * XT];
+            for (int j = 0; j < R; ++j) {
+              lds_vec<T, VX>(P + (j - R) * XT, &ylo[j * VX]);
               // row y0+1+R can lie one row past the tile when the second row is not updated
-              yv1[R + d] = (d < R || row1) ? P[(1 + d) * XT] : T(0);
+              if (j < R - 1 || row1) lds_vec<T, VX>(P + (2 + j) * XT, &yhi[j * VX]);
+              else {
+#pragma unroll
+                for (int i = 0; i < VX; ++i) yhi[j * VX + i] = T(0);
+              }
             }
 #pragma unroll
-            for (int d = 1; d <= R; ++d) {
-              yv0[R + d] = (d == 1) ? win[g][1][R] : yv1[R + d - 1];
-              yv1[R - d] = (d == 1) ? win[g][0][R] : yv0[R - d + 1];
+            for (int d = 1; d <= R; ++d) {  // x lines: R columns each side from the ring
+              xl0[R - d] = P[-d];
+              xl0[R + VX - 1 + d] = P[VX - 1 + d];
+              xl1[R - d] = P[XT - d];
+              xl1[R + VX - 1 + d] = P[XT + VX - 1 + d];
+            }
+#pragma unroll
+            for (int i = 0; i < VX; ++i) {
+              xl0[R + i] = win[g][0][R * VX + i];
+              xl1[R + i] = win[g][1][R * VX + i];
             }
             T* Ub = sm + guo_[g] + sl * pe;
-            PairAcc<S, T> acc0{win[g][0], yv0, P, T(0), kp, gstride, 0};
-            if constexpr (Traits<S>::ORDER2) acc0.uc = Ub[0];
-            const T r0 = point_update<S, T>(acc0, cst);
-            Ub[0] = r0;
-            T r1 = T(0);
-            if (row1) {
-              PairAcc<S, T> acc1{win[g][1], yv1, P + XT, T(0), kp, gstride, ldx};
-              if constexpr (Traits<S>::ORDER2) acc1.uc = Ub[XT];
-              r1 = point_update<S, T>(acc1, cst);
-              Ub[XT] = r1;
+            T r0[VX], r1[VX], u0[VX], u1[VX];
+            if constexpr (Traits<S>::ORDER2) {
+              lds_vec<T, VX>(Ub, u0);
+              if (row1) lds_vec<T, VX>(Ub + XT, u1);
+            }
+            const int nv = gnv_[g];
+            mwd_points<S, T, VX>(win[g][0], win[g][1], ylo, yhi, xl0, xl1, u0, u1, kp, gstride, ldx, nv, row1, cst,
+                                 r0, r1);
+            if (nv == VX) {
+              sts_vec<T, VX>(Ub, r0);
+              if (row1) sts_vec<T, VX>(Ub + XT, r1);
+            } else {
+#pragma unroll
+              for (int i = 0; i < VX; ++i)
+                if (i < nv) {
+                  Ub[i] = r0[i];
+                  if (row1) Ub[XT + i] = r1[i];
+                }
             }
             if (fl & 12) {
               const uint32_t so = (uint32_t)(guo_[g] + sl * pe) * (uint32_t)sizeof(T);
-              if (fl & 4) {  // my left edge is the left neighbour's right halo
-                st_cluster(left_base + so + (uint32_t)(XW * (int)sizeof(T)), r0);
-                if (row1) st_cluster(left_base + so + (uint32_t)((XT + XW) * (int)sizeof(T)), r1);
-              }
-              if (fl & 8) {  // my right edge is the right neighbour's left halo
-                st_cluster(right_base + so - (uint32_t)(XW * (int)sizeof(T)), r0);
-                if (row1) st_cluster(right_base + so + (uint32_t)((XT - XW) * (int)sizeof(T)), r1);
+#pragma unroll
+              for (int i = 0; i < VX; ++i) {
+                if (i >= nv) continue;
+                const uint32_t oi = so + (uint32_t)(i * (int)sizeof(T));
+                const int colx = gx_[g] + i;  // slab column of lane i
+                if ((fl & 4) && colx < R) {  // my left edge is the left neighbour's right halo
+                  st_cluster(left_base + oi + (uint32_t)(XW * (int)sizeof(T)), r0[i]);
+                  if (row1) st_cluster(left_base + oi + (uint32_t)((XT + XW) * (int)sizeof(T)), r1[i]);
+                }
+                if ((fl & 8) && colx >= XW - R) {  // my right edge is the right neighbour's left halo
+                  st_cluster(right_base + oi - (uint32_t)(XW * (int)sizeof(T)), r0[i]);
+                  if (row1) st_cluster(right_base + oi + (uint32_t)((XT - XW) * (int)sizeof(T)), r1[i]);
+                }
               }
             }
           }
