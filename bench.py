@@ -188,6 +188,7 @@ def main():
     ap.add_argument("--nf", type=int, default=1)
     ap.add_argument("--cluster", type=int, default=0)
     ap.add_argument("--threads", type=int, default=256)
+    ap.add_argument("--variant", type=int, default=0, help="0 FED, 1 RELAXED, 2 FED_BULK")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-naive", action="store_true")
@@ -221,7 +222,8 @@ def main():
     if args.algo == "naive":
         cfg = girih.config(girih.NAIVE)
     elif args.algo == "mwd" and args.dw:
-        cfg = girih.config(girih.MWD, dw=args.dw, nf=args.nf, cluster=args.cluster or 1, threads=args.threads)
+        cfg = girih.config(girih.MWD, dw=args.dw, nf=args.nf, cluster=args.cluster or 1, threads=args.threads,
+                           variant=args.variant)
     else:
         tuned = _tuned(args.workload)
         cfg = girih.Config(**tuned) if tuned else p.config

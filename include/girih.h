@@ -50,8 +50,11 @@ typedef enum { GIRIH_ALGO_NAIVE = 0, GIRIH_ALGO_MWD = 1 } girih_algo;
  *              staged element by element (cp.async), any alignment.
  *   FED_BULK -- FED with whole rows moved by the bulk-copy (TMA) engine from a producer warp;
  *              needs ldx*elem to be a multiple of 16 bytes and 16-byte aligned buffers.
- *   RELAXED -- each time level of the tile only waits for its own predecessor level
- *              (left-neighbour hand-off), through per-level progress counters.            */
+ *   RELAXED -- no cluster-wide barrier: each block of the cluster publishes its completed
+ *              wavefront steps to its two x neighbours (progress counters in their shared
+ *              memory, release/acquire at cluster scope) and waits only for theirs, the
+ *              neighbour hand-off of the paper's relaxed synchronisation.  Element staging as
+ *              FED, any alignment; with a cluster of one block it is the same as FED.      */
 typedef enum { GIRIH_FED = 0, GIRIH_RELAXED = 1, GIRIH_FED_BULK = 2 } girih_variant;
 
 #define GIRIH_OK 0

@@ -66,8 +66,8 @@ int check_config(const Plan* p, const girih_config* c, int64_t* smem_out, int* x
     return GIRIH_OK;
   }
   if (c->algo != GIRIH_ALGO_MWD) return fail(GIRIH_EINVAL, "unknown algo %d", c->algo);
-  if (c->variant == GIRIH_RELAXED) return fail(GIRIH_ENOTIMPL, "the RELAXED wavefront variant is not built");
-  if (c->variant != GIRIH_FED && c->variant != GIRIH_FED_BULK) return fail(GIRIH_EINVAL, "unknown variant %d", c->variant);
+  if (c->variant != GIRIH_FED && c->variant != GIRIH_RELAXED && c->variant != GIRIH_FED_BULK)
+    return fail(GIRIH_EINVAL, "unknown variant %d", c->variant);
   const bool bulk = c->variant == GIRIH_FED_BULK;
   if (bulk && !p->bulk_layout)
     return fail(GIRIH_EINVAL, "FED_BULK needs ldx*elem to be a multiple of 16 bytes (ldx=%lld)", (long long)p->ldx);
@@ -178,6 +178,7 @@ int run_sweep(Plan* p, int64_t T, void* u, void* u_prev, const void* coeffs, con
     a.YW = sh.YW;
     a.XT = sh.XT;
     a.err = p->err;
+    a.relaxed = cfg.variant == GIRIH_RELAXED ? 1 : 0;
     const int64_t rows = mwd_rows(T, cfg.dw, p->R);
     for (int64_t rho = 0; rho < rows && e == cudaSuccess; ++rho) {  // one launch per diamond row
       int64_t a_min = 0, nd = 0;

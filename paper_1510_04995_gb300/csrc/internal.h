@@ -43,6 +43,7 @@ struct MwdArgs {
   int32_t C, XW;     // blocks per tile (cluster) and x slab width per block
   int32_t NZ, YW, XT;  // shared ring: planes, rows, columns per buffer
   int* err;          // device error word: bounded waits that ran out set GIRIH_ETIMEOUT here
+  int32_t relaxed;   // RELAXED variant: neighbour hand-off instead of the cluster barrier
 };
 
 struct MwdShape {

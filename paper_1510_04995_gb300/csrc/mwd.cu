@@ -25,7 +25,7 @@ MwdShape mwd_shape(int stencil, int dtype, int dw, int nf, int XW, bool bulk) {
   const int off = mwd_vx(stencil, dtype, bulk) == 1 ? R : a16;
   s.XT = (off + XW + R + a16 - 1) / a16 * a16;  // rows start on 16-byte boundaries
   const int64_t ring = 2LL * s.NZ * s.YW * s.XT * elem;
-  s.smem_bytes = (ring + 15) / 16 * 16 + 8LL * s.NZ + (3LL * H + 1 + s.YW) * 4;
+  s.smem_bytes = (ring + 15) / 16 * 16 + 8LL * s.NZ + (3LL * H + 1 + s.YW + 2) * 4;
   return s;
 }
 

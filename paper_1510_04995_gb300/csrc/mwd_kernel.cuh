@@ -127,6 +127,19 @@ __device__ __forceinline__ void cluster_arrive_release() {
 __device__ __forceinline__ void cluster_wait_acquire() {
   asm volatile("barrier.cluster.wait.acquire.aligned;" ::: "memory");
 }
+// Named barrier 1 of the block (barrier 0 is __syncthreads): arrive without waiting, or wait for
+// all `n` threads to have arrived.
+__device__ __forceinline__ void named_bar_arrive(int n) { asm volatile("bar.arrive 1, %0;" ::"r"(n) : "memory"); }
+__device__ __forceinline__ void named_bar_sync(int n) { asm volatile("bar.sync 1, %0;" ::"r"(n) : "memory"); }
+__device__ __forceinline__ void fence_acq_rel_cluster() { asm volatile("fence.acq_rel.cluster;" ::: "memory"); }
+__device__ __forceinline__ void st_cluster_u32(uint32_t addr, uint32_t v) {
+  asm volatile("st.relaxed.cluster.shared::cluster.u32 [%0], %1;" ::"r"(addr), "r"(v) : "memory");
+}
+__device__ __forceinline__ uint32_t ld_acquire_cluster_u32(const int* p) {
+  uint32_t v;
+  asm volatile("ld.acquire.cluster.shared::cta.u32 %0, [%1];" : "=r"(v) : "r"(smem_addr(p)) : "memory");
+  return v;
+}
 
 // ---- bulk-copy (TMA) and mbarrier helpers ---------------------------------------------------
 __device__ __forceinline__ void mbar_init(uint64_t* m, uint32_t count) {
@@ -218,6 +231,7 @@ __global__ void __launch_bounds__((1024 / (G * mwd_lbf<S, T, BULK>()) + (BULK ? 
   int* lev_w = lev_lo + A.H;
   int* lev_pp = lev_w + A.H;  // prefix count of row pairs per level
   int* row_mask = lev_pp + A.H + 1;
+  int* prog = row_mask + A.YW;  // RELAXED: steps completed by the left [0] and right [1] neighbour
 
   const int nx = (int)A.g.nx, ny = (int)A.g.ny, nz = (int)A.g.nz;
   const int64_t ldx = A.g.ldx;
@@ -253,6 +267,7 @@ __global__ void __launch_bounds__((1024 / (G * mwd_lbf<S, T, BULK>()) + (BULK ? 
       acc += (max(hi - lo, 0) + 1) / 2;
     }
     lev_pp[nlev] = acc;
+    prog[0] = prog[1] = 0;
     if constexpr (BULK) {
       for (int s = 0; s < NZ; ++s) mbar_init(&mbar[s], 1);
       asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -428,6 +443,8 @@ __global__ void __launch_bounds__((1024 / (G * mwd_lbf<S, T, BULK>()) + (BULK ? 
   const uint32_t sm_base = smem_addr(sm);
   const uint32_t left_base = (C > 1 && rank > 0) ? map_to_rank(sm_base, rank - 1) : 0u;
   const uint32_t right_base = (C > 1 && rank < C - 1) ? map_to_rank(sm_base, rank + 1) : 0u;
+  const bool relaxed = !BULK && C > 1 && A.relaxed;
+  const uint32_t prog_base = smem_addr(prog);
 
   const int W = (nz + smax * K + nf - 1) / nf;
   for (int w = 0; w < W; ++w) {
@@ -559,6 +576,44 @@ __global__ void __launch_bounds__((1024 / (G * mwd_lbf<S, T, BULK>()) + (BULK ? 
       }
       if (C > 1) cluster_barrier();
       else __syncthreads();
+    } else if (relaxed) {
+      // RELAXED: no cluster-wide barrier.  Once all warps of this block have finished the step's
+      // updates and pushes (named barrier 1, on which only warp 0 waits), one thread publishes
+      // the step count to the two x neighbours (release at cluster scope).  The block then
+      // writes back and stages, and before the next step waits only for its own neighbours'
+      // counts (acquire), i.e. for the blocks whose pushes it receives and into whose shared
+      // memory it pushes.  Neighbours thus stay within one step of each other, the same overlap
+      // the cluster barrier allows, without waiting for the rest of the cluster.
+      cp_async_wait_group<PD - 1>();
+      if (warp == 0) {
+        named_bar_sync(NT);
+        if (lane == 0) {
+          fence_acq_rel_cluster();
+          if (rank > 0) st_cluster_u32(map_to_rank(prog_base + 4u, rank - 1), (uint32_t)(w + 1));
+          if (rank < C - 1) st_cluster_u32(map_to_rank(prog_base, rank + 1), (uint32_t)(w + 1));
+        }
+        __syncwarp();
+      } else {
+        named_bar_arrive(NT);
+      }
+      if (xw > 0) {
+        if (w > 0)
+          for (int f = 0; f < nf; ++f, ++wz, wsl = (wsl + 1 == NZ) ? 0 : wsl + 1) plain_write(wz, wsl);
+        for (int f = 0; f < nf; ++f, ++lz, lsl = (lsl + 1 == NZ) ? 0 : lsl + 1) plain_stage(lz, lsl);
+      }
+      cp_async_commit();
+      if (tid == 0) {  // bounded wait for both neighbours; a timeout sets the error word
+        const uint32_t need = (uint32_t)(w + 1);
+        const uint64_t t0 = global_ns();
+        while ((rank > 0 && ld_acquire_cluster_u32(&prog[0]) < need) ||
+               (rank < C - 1 && ld_acquire_cluster_u32(&prog[1]) < need)) {
+          if (global_ns() - t0 > kMbarWaitNs) {
+            atomicOr(A.err, GIRIH_ETIMEOUT);
+            break;
+          }
+        }
+      }
+      __syncthreads();
     } else {
       cp_async_wait_group<PD - 1>();
       if (C > 1) cluster_arrive_release();

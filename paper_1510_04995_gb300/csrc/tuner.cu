@@ -128,7 +128,8 @@ std::vector<girih_config> candidates(Plan* p) {
     for (int nf : {1, 2})
       for (int C : {1, 2, 4, 8, 16})
         for (int th : {128, 256, 512, 1024})
-          for (int v : {GIRIH_FED, GIRIH_FED_BULK}) {
+          for (int v : {GIRIH_FED, GIRIH_RELAXED, GIRIH_FED_BULK}) {
+            if (v == GIRIH_RELAXED && C == 1) continue;  // a single block: RELAXED is FED
             // the bulk-copy variant adds a producer warp to the computing threads
             girih_config c{GIRIH_ALGO_MWD, dw, nf, C, v == GIRIH_FED_BULK ? th + 32 : th, v};
             if (c.threads > 1024) continue;

@@ -201,3 +201,28 @@ def test_bulk_copy_path_equals_element_path(stencil, dtype):
         assert np.all(gu[:, :, w:] == 0) and np.all(gup[:, :, w:] == 0)  # row padding keeps its (zero) values
         outs.append(gu[:, :, :w])
     assert np.array_equal(outs[0], outs[1])
+
+
+@pytest.mark.parametrize("stencil", [0, 1, 2, 3])
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+def test_relaxed_variant(stencil, dtype):
+    """The RELAXED synchronisation (neighbour hand-off between the blocks of a cluster instead of a
+    cluster barrier) reorders no arithmetic: bit-identical to FED and to the naive sweep, and
+    within the FP64 contract of the oracle, for clusters of 2 to 16 blocks."""
+    R = inputs.RADIUS[stencil]
+    nx, ny, nz = SIZES[R]
+    dw = 8 if R == 1 else 16
+    T = 2 * (dw // R) + 3
+    u, up, co, c, ru, rup = _ref(stencil, nx, ny, nz, T)
+    nu, nup = gpu_sweep(stencil, dtype, u, up, co, c, T, nx, ny, nz, girih.config(girih.NAIVE))
+    if dtype == "f64":
+        assert normwise(nu, ru, R) <= 1e-12
+    for cl in (2, 4, 8, 16):
+        kw = dict(dw=dw, nf=1 if cl != 4 else 2, cluster=cl, threads=256, variant=girih.RELAXED)
+        cfg = feasible_cfg(stencil, dtype, nx, ny, nz, kw)
+        assert cfg.variant == girih.RELAXED and cfg.cluster >= 2
+        bu, bup = gpu_sweep(stencil, dtype, u, up, co, c, T, nx, ny, nz, cfg)
+        assert np.array_equal(bu, nu) and np.array_equal(bup, nup), (cl, cfg)
+        fed = girih.config(girih.MWD, dw=cfg.dw, nf=cfg.nf, cluster=cfg.cluster, threads=cfg.threads)
+        fu, _ = gpu_sweep(stencil, dtype, u, up, co, c, T, nx, ny, nz, fed)
+        assert np.array_equal(bu, fu), (cl, cfg)
