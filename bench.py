@@ -59,12 +59,18 @@ def _peaks():
 
 
 def _tuned(workload):
+    """(best config, fastest blocked config) recorded by the exhaustive tuner for a workload."""
     path = os.path.join(ROOT, "paper_1510_04995_gb300", "tuned_configs.json")
     try:
         with open(path) as f:
-            return json.load(f).get(workload)
+            e = json.load(f).get(workload)
     except Exception:
-        return None
+        return None, None
+    if not e:
+        return None, None
+    if "best" not in e:  # a bare configuration
+        return e, None
+    return e["best"], e.get("blocked")
 
 
 class ClockSampler:
@@ -133,13 +139,17 @@ def cpu_baseline(stencil, nx, ny, nz, budget_s=10.0, max_T=64, min_T=1):
     oracle.sweep(stencil, u, up, co, c, 1, nx, ny, nz, nthreads=cores)
     t1 = time.perf_counter() - t0
     T = int(max(min_T, min(max_T, budget_s / max(t1, 1e-6))))
+    # repeat sweeps of T steps (the workload's T at most) until about budget_s of CPU time
+    reps = int(max(1, min(50, budget_s / max(t1 * T, 1e-6))))
     t0 = time.perf_counter()
-    oracle.sweep(stencil, u, up, co, c, T, nx, ny, nz, nthreads=cores)
+    for _ in range(reps):
+        oracle.sweep(stencil, u, up, co, c, T, nx, ny, nz, nthreads=cores)
     dt = time.perf_counter() - t0
-    glups = nx * ny * nz * T / dt * 1e-9
+    glups = nx * ny * nz * T * reps / dt * 1e-9
     del u, up, co
     return {"value": glups, "unit": "GLUP/s", "cores": cores, "kind": "oracle",
-            "sample": f"{nx}x{ny}x{nz} grid, {T} time steps (FP64 oracle, OpenMP over z), {dt:.1f} s"}
+            "sample": f"{nx}x{ny}x{nz} grid, {reps} sweep(s) of {T} time steps (FP64 oracle, OpenMP over z), "
+                      f"{dt:.1f} s"}
 
 
 def run_reference(args, wl):
@@ -188,7 +198,7 @@ def main():
     ap.add_argument("--nf", type=int, default=1)
     ap.add_argument("--cluster", type=int, default=0)
     ap.add_argument("--threads", type=int, default=256)
-    ap.add_argument("--variant", type=int, default=0, help="0 FED, 1 RELAXED, 2 FED_BULK")
+    ap.add_argument("--variant", type=int, default=0, help="0 FED, 1 RELAXED, 2 FED_BULK, 3 FED_ELEM, 4 RELAXED_ELEM")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-naive", action="store_true")
@@ -225,9 +235,13 @@ def main():
         cfg = girih.config(girih.MWD, dw=args.dw, nf=args.nf, cluster=args.cluster or 1, threads=args.threads,
                            variant=args.variant)
     else:
-        tuned = _tuned(args.workload)
+        tuned, _ = _tuned(args.workload)
         cfg = girih.Config(**tuned) if tuned else p.config
     p.set_config(cfg)
+    _, blocked_d = _tuned(args.workload)
+    blocked_cfg = girih.Config(**blocked_d) if (blocked_d and args.algo == "tuned") else None
+    if cfg.algo == girih.MWD:
+        blocked_cfg = cfg
 
     u, up, co, c = inputs.make_problem(stencil, nx, ny, nz, backend="torch", device=dev, ldx=ldx)
     tdt = torch.float64 if dtype == "f64" else torch.float32
@@ -269,19 +283,30 @@ def main():
         else:
             nms = timed(girih.config(girih.NAIVE), max(1, args.steps // 2), 1)
             naive = lups * max(1, args.steps // 2) * ws / (nms * 1e-3) * 1e-9
+    elem = 8 if dtype == "f64" else 4
+    peaks, src = _peaks()
+    # spatial-blocking roofline: HBM bandwidth / minimal bytes per LUP (u in, u out; coefficients in)
+    spatial = float(peaks["hbm_gbs"]) / (SPATIAL_ELEMS[stencil] * elem)
+    blocked = None
+    if blocked_cfg is not None:
+        if blocked_cfg.as_dict() == cfg.as_dict():
+            bg = value
+        else:
+            bms = timed(blocked_cfg, max(1, args.steps // 2), 1)
+            bg = lups * max(1, args.steps // 2) * ws / (bms * 1e-3) * 1e-9
+        blocked = {"glups": bg, "config": blocked_cfg.as_dict(), "vs_naive": (bg / naive) if naive else None,
+                   "frac_spatial_roofline": bg / ws / spatial}
 
     # roofline of the dominant kernel (every launch of the timed region is the blocked kernel,
     # except the exchange kernel for odd T, which the default workloads do not have)
     launches = p.launch_count(cfg)
-    peaks, src = _peaks()
-    elem = 8 if dtype == "f64" else 4
     per_gpu = lups * args.steps / (ms * 1e-3)
     if dtype == "f64":
         # FP64 pipe: 152 SMs x 2 DFMA per clock (1.25 TFLOP/s nominal) at the maximum SM clock
         peak_inst = 152 * 2 * float(peaks.get("sm_max_mhz", 2070.0)) * 1e6
         achieved = per_gpu * INSTR_PER_LUP[stencil]
         roof = {"bound": "alu", "achieved": achieved * 1e-12, "peak": peak_inst * 1e-12,
-                "unit": "TFLOP/s", "frac": achieved / peak_inst, "traffic": None,
+                "unit": "Tinst/s", "frac": achieved / peak_inst, "traffic": None,
                 "note": "FP64 instructions/s (one per explicitly rounded op, 7 or 28 per LUP) vs 152 SMs x 2 DFMA/clk "
                         f"x max SM clock ({src} peaks file clock); HBM is not the bound"}
     else:
@@ -323,7 +348,7 @@ def main():
     if rank == 0 and ws == 1 and not args.no_cpu:
         del u, up, co
         torch.cuda.empty_cache()
-        cpu = cpu_baseline(stencil, nx, ny, nz)
+        cpu = cpu_baseline(stencil, nx, ny, nz, max_T=T)
 
     if rank == 0:
         line = {
@@ -335,6 +360,8 @@ def main():
                        "kernel_config": cfg.as_dict(),
                        "l2": "inputs larger than L2 (each grid > 126 MB)", "parallelism": f"replicas x{ws}"},
             "naive_glups": naive, "speedup_vs_naive": (value / naive) if naive else None,
+            "blocked": blocked, "spatial_roofline_glups": spatial,
+            "frac_spatial_roofline": value / ws / spatial,
             "gpu_launches": launches * args.steps,
             "roofline": roof, "clocks": clocks, "e2e": e2e, "cpu_baseline": cpu,
         }

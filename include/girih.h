@@ -46,16 +46,27 @@ typedef enum { GIRIH_F64 = 0, GIRIH_F32 = 1 } girih_dtype;
 typedef enum { GIRIH_ALGO_NAIVE = 0, GIRIH_ALGO_MWD = 1 } girih_algo;
 /* Wavefront synchronisation variants of Sect. 4.2.1:
  *   FED     -- fixed execution to data: each thread block of the cluster always updates the
- *              same x slab of the tile; one cluster-wide barrier per wavefront step; planes are
- *              staged element by element (cp.async), any alignment.
- *   FED_BULK -- FED with whole rows moved by the bulk-copy (TMA) engine from a producer warp;
- *              needs ldx*elem to be a multiple of 16 bytes and 16-byte aligned buffers.
+ *              same x slab of the tile; one cluster-wide barrier per wavefront step.  Planes
+ *              move in 16-byte chunks (cp.async in, vector stores out) when ldx*elem is a
+ *              multiple of 16 bytes and the buffers are 16-byte aligned, else element by
+ *              element (any layout).
+ *   FED_BULK -- FED with whole rows moved by the bulk-copy (TMA) engine, issued by one warp
+ *              between the halves of each step's barrier; needs ldx*elem to be a multiple of
+ *              16 bytes, 16-byte aligned buffers and planes of fewer than 2^30 elements.
  *   RELAXED -- no cluster-wide barrier: each block of the cluster publishes its completed
  *              wavefront steps to its two x neighbours (progress counters in their shared
  *              memory, release/acquire at cluster scope) and waits only for theirs, the
- *              neighbour hand-off of the paper's relaxed synchronisation.  Element staging as
- *              FED, any alignment; with a cluster of one block it is the same as FED.      */
-typedef enum { GIRIH_FED = 0, GIRIH_RELAXED = 1, GIRIH_FED_BULK = 2 } girih_variant;
+ *              neighbour hand-off of the paper's relaxed synchronisation.  Data movement as
+ *              FED; with a cluster of one block it is the same as FED.
+ *   FED_ELEM, RELAXED_ELEM -- FED and RELAXED forced onto the element-by-element path on any
+ *              layout (the tuner weighs both data paths).                                   */
+typedef enum {
+  GIRIH_FED = 0,
+  GIRIH_RELAXED = 1,
+  GIRIH_FED_BULK = 2,
+  GIRIH_FED_ELEM = 3,
+  GIRIH_RELAXED_ELEM = 4
+} girih_variant;
 
 #define GIRIH_OK 0
 #define GIRIH_EINVAL 1   /* bad enum, size, T, pointer, alignment, or config: nothing enqueued */

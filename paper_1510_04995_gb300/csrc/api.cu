@@ -52,25 +52,45 @@ void mwd_row_span(int64_t rho, int dw, int64_t ny, int64_t* a_min, int64_t* ndia
   *ndiam = std::max<int64_t>(hi - lo + 1, 0);
 }
 
-// x slab per block: nx split evenly over the cluster, rounded up to a multiple of 16 elements
-// (blocks past the end of the grid stay idle but take part in the cluster barriers).
-static int slab_width(int64_t nx, int C) {
-  const int64_t w = (nx + C - 1) / C;
+// x slab per block (blocks past the end of the grid stay idle but take part in the cluster's
+// synchronisation).  Element path: nx split evenly, rounded up to 16 elements.  Vector and
+// bulk-copy paths: the slabs partition the padded columns [R, nx + R) at 16-byte boundaries
+// (block r owns padded [r*XW, (r+1)*XW)), so nx + R columns are split, rounded up to 16 bytes.
+static int slab_width(const Plan* p, int C, int mv) {
+  if (mv_shifted(mv)) {
+    const int a16 = 16 / p->elem;
+    const int64_t w = (p->nx + p->R + C - 1) / C;
+    return (int)((w + a16 - 1) / a16 * a16);
+  }
+  const int64_t w = (p->nx + C - 1) / C;
   return (int)((w + 15) / 16 * 16);
 }
 
-int check_config(const Plan* p, const girih_config* c, int64_t* smem_out, int* xw_out, int* g_out) {
+// Data path of a configuration: FED_BULK moves rows with the bulk-copy engine; FED and RELAXED
+// use 16-byte vectors when rows are 16-byte multiples (and, at run time, the buffers 16-byte
+// aligned), else per-element staging.
+static int mwd_path(const Plan* p, const girih_config* c, bool ptrs16) {
+  if (c->variant == GIRIH_FED_BULK) return MV_BULK;
+  if (c->variant == GIRIH_FED_ELEM || c->variant == GIRIH_RELAXED_ELEM) return MV_ELEM;
+  const int64_t plane = (p->ny + 2 * p->R) * p->ldx;
+  return (p->bulk_layout && ptrs16 && plane < (1LL << 30)) ? MV_VEC : MV_ELEM;
+}
+
+int check_config(const Plan* p, const girih_config* c, int64_t* smem_out, int* xw_out, int* g_out, int* mv_out,
+                 bool ptrs16) {
   if (!c) return fail(GIRIH_EINVAL, "config is NULL");
   if (c->algo == GIRIH_ALGO_NAIVE) {
     if (smem_out) *smem_out = 0;
     return GIRIH_OK;
   }
   if (c->algo != GIRIH_ALGO_MWD) return fail(GIRIH_EINVAL, "unknown algo %d", c->algo);
-  if (c->variant != GIRIH_FED && c->variant != GIRIH_RELAXED && c->variant != GIRIH_FED_BULK)
+  if (c->variant < GIRIH_FED || c->variant > GIRIH_RELAXED_ELEM)
     return fail(GIRIH_EINVAL, "unknown variant %d", c->variant);
   const bool bulk = c->variant == GIRIH_FED_BULK;
   if (bulk && !p->bulk_layout)
     return fail(GIRIH_EINVAL, "FED_BULK needs ldx*elem to be a multiple of 16 bytes (ldx=%lld)", (long long)p->ldx);
+  if (bulk && (p->ny + 2 * p->R) * p->ldx >= (1LL << 30))
+    return fail(GIRIH_EINVAL, "FED_BULK needs planes of fewer than 2^30 elements");
   const int R = p->R;
   if (c->dw < 2 * R || c->dw % (2 * R) != 0)
     return fail(GIRIH_EINVAL, "dw=%d must be a positive multiple of 2R=%d", c->dw, 2 * R);
@@ -79,25 +99,25 @@ int check_config(const Plan* p, const girih_config* c, int64_t* smem_out, int* x
     return fail(GIRIH_EINVAL, "cluster=%d not in {1,2,4,8,16}", c->cluster);
   if (c->threads < 64 || c->threads > 1024 || c->threads % 32 != 0)
     return fail(GIRIH_EINVAL, "threads=%d must be a multiple of 32 in 64..1024", c->threads);
-  const int XW = slab_width(p->nx, c->cluster);
-  // with a 16-byte aligned layout one warp of the block moves data and the others compute
-  const int cthreads = bulk ? c->threads - 32 : c->threads;
-  const int G = mwd_pairs_per_thread(p->stencil, p->dtype, c->dw, XW, c->threads, bulk);
+  const int mv = mwd_path(p, c, ptrs16);
+  const int XW = slab_width(p, c->cluster, mv);
+  const int cthreads = c->threads;
+  const int G = mwd_pairs_per_thread(p->stencil, p->dtype, c->dw, XW, c->threads, mv);
   if (G == 0)
     return fail(GIRIH_EINVAL, "dw=%d with a %d-wide slab has %d row pairs x %d column groups: too many for %d "
-                "computing threads", c->dw, XW, mwd_max_pairs(R, c->dw), XW / mwd_vx(p->stencil, p->dtype, bulk),
+                "computing threads", c->dw, XW, mwd_max_pairs(R, c->dw), XW / mwd_vx(p->stencil, p->dtype, mv),
                 cthreads);
   if (R == 4 && G > 4) return fail(GIRIH_EINVAL, "25-point tiles allow at most 4 row pairs per thread (registers)");
   if (p->dtype == GIRIH_F64 && R == 4 && G > 2)
     return fail(GIRIH_EINVAL, "25-point FP64 tiles allow at most 2 row pairs per thread (registers)");
   if (p->ny > (1 << 28) || p->nx > (1 << 28) || p->nz > (1 << 28))
     return fail(GIRIH_EINVAL, "grid too large for the blocked kernel");
-  const MwdShape sh = mwd_shape(p->stencil, p->dtype, c->dw, c->nf, XW, bulk);
+  const MwdShape sh = mwd_shape(p->stencil, p->dtype, c->dw, c->nf, XW, mv);
   if (sh.smem_bytes > p->smem_optin)
     return fail(GIRIH_EINVAL, "config needs %lld bytes of shared memory per block (device limit %lld)",
                 (long long)sh.smem_bytes, (long long)p->smem_optin);
   int maxc = 0;
-  cudaError_t e = mwd_prepare(p->stencil, p->dtype, c->cluster, c->threads, G, bulk, sh.smem_bytes, &maxc);
+  cudaError_t e = mwd_prepare(p->stencil, p->dtype, c->cluster, c->threads, G, mv, sh.smem_bytes, &maxc);
   if (e != cudaSuccess) {
     cudaGetLastError();
     return fail(GIRIH_EINVAL, "cluster of %d blocks with %lld bytes cannot be configured: %s", c->cluster,
@@ -107,6 +127,7 @@ int check_config(const Plan* p, const girih_config* c, int64_t* smem_out, int* x
   if (smem_out) *smem_out = sh.smem_bytes;
   if (xw_out) *xw_out = XW;
   if (g_out) *g_out = G;
+  if (mv_out) *mv_out = mv;
   return GIRIH_OK;
 }
 
@@ -116,17 +137,18 @@ static girih_config default_config(Plan* p) {
   girih_config best{GIRIH_ALGO_NAIVE, 0, 1, 1, 256, GIRIH_FED};
   int best_dw = 0;
   const int R = p->R;
-  for (int C : {1, 2, 4, 8, 16}) {
-    for (int dw = 2 * R; dw <= 64 * R; dw += 2 * R) {
-      girih_config c{GIRIH_ALGO_MWD, dw, 1, C, 512, GIRIH_FED};
-      int64_t smem = 0;
-      if (check_config(p, &c, &smem, nullptr, nullptr) != GIRIH_OK) continue;
-      if (dw > best_dw && dw <= (R == 1 ? 16 : 32)) {
-        best_dw = dw;
-        best = c;
+  for (int th : {512, 256, 1024})
+    for (int C : {1, 2, 4, 8, 16}) {
+      for (int dw = 2 * R; dw <= 64 * R; dw += 2 * R) {
+        girih_config c{GIRIH_ALGO_MWD, dw, 1, C, th, GIRIH_FED};
+        int64_t smem = 0;
+        if (check_config(p, &c, &smem, nullptr, nullptr) != GIRIH_OK) continue;
+        if (dw > best_dw && dw <= (R == 1 ? 16 : 32)) {
+          best_dw = dw;
+          best = c;
+        }
       }
     }
-  }
   g_err.clear();
   return best;
 }
@@ -152,12 +174,12 @@ int run_sweep(Plan* p, int64_t T, void* u, void* u_prev, const void* coeffs, con
     }
   } else {
     int64_t smem = 0;
-    int XW = 0, G = 0;
-    const int rc = check_config(p, &cfg, &smem, &XW, &G);
+    int XW = 0, G = 0, mv = 0;
+    const bool ptrs16 = ((reinterpret_cast<uintptr_t>(u) | reinterpret_cast<uintptr_t>(u_prev)) & 15) == 0;
+    const int rc = check_config(p, &cfg, &smem, &XW, &G, &mv, ptrs16);
     if (rc != GIRIH_OK) return rc;
-    const bool bulk = cfg.variant == GIRIH_FED_BULK;
-    e = mwd_prepare(p->stencil, p->dtype, cfg.cluster, cfg.threads, G, bulk, smem, nullptr);
-    const MwdShape sh = mwd_shape(p->stencil, p->dtype, cfg.dw, cfg.nf, XW, cfg.variant == GIRIH_FED_BULK);
+    e = mwd_prepare(p->stencil, p->dtype, cfg.cluster, cfg.threads, G, mv, smem, nullptr);
+    const MwdShape sh = mwd_shape(p->stencil, p->dtype, cfg.dw, cfg.nf, XW, mv);
     MwdArgs a{};
     a.g = g;
     a.buf0 = u;
@@ -178,7 +200,7 @@ int run_sweep(Plan* p, int64_t T, void* u, void* u_prev, const void* coeffs, con
     a.YW = sh.YW;
     a.XT = sh.XT;
     a.err = p->err;
-    a.relaxed = cfg.variant == GIRIH_RELAXED ? 1 : 0;
+    a.relaxed = (cfg.variant == GIRIH_RELAXED || cfg.variant == GIRIH_RELAXED_ELEM) ? 1 : 0;
     const int64_t rows = mwd_rows(T, cfg.dw, p->R);
     for (int64_t rho = 0; rho < rows && e == cudaSuccess; ++rho) {  // one launch per diamond row
       int64_t a_min = 0, nd = 0;
@@ -186,7 +208,7 @@ int run_sweep(Plan* p, int64_t T, void* u, void* u_prev, const void* coeffs, con
       if (nd == 0) continue;
       a.rho = (int32_t)rho;
       a.a_min = (int32_t)a_min;
-      e = launch_mwd_row(p->stencil, p->dtype, a, (int)nd, cfg.threads, G, bulk, sh.smem_bytes, st);
+      e = launch_mwd_row(p->stencil, p->dtype, a, (int)nd, cfg.threads, G, mv, sh.smem_bytes, st);
     }
   }
   if (e == cudaSuccess && T % 2 == 1) e = launch_swap(u, u_prev, p->gstride * p->elem, st);
@@ -216,7 +238,8 @@ int validate_run(Plan* p, void* u, void* u_prev, const void* coeffs, const girih
   *c = (params) ? params->c : (p->stencil >= 2 ? kConst25 : kConst7);
   *cfg = (params && params->force_cfg) ? &params->cfg : &p->cfg;
   if ((*cfg)->algo == GIRIH_ALGO_MWD) {
-    const int rc = check_config(p, *cfg, nullptr, nullptr, nullptr);
+    const bool ptrs16 = ((reinterpret_cast<uintptr_t>(u) | reinterpret_cast<uintptr_t>(u_prev)) & 15) == 0;
+    const int rc = check_config(p, *cfg, nullptr, nullptr, nullptr, nullptr, ptrs16);
     if (rc != GIRIH_OK) return rc;
     if ((*cfg)->variant == GIRIH_FED_BULK &&
         ((reinterpret_cast<uintptr_t>(u) | reinterpret_cast<uintptr_t>(u_prev)) & 15) != 0)

@@ -50,27 +50,34 @@ struct MwdShape {
   int32_t NZ, YW, XT;
   int64_t smem_bytes;
 };
-MwdShape mwd_shape(int stencil, int dtype, int dw, int nf, int XW, bool bulk);
+// Data paths of the blocked kernel: per-element staging (any layout); 16-byte vectors on a
+// shifted slab partition (rows of 16-byte multiples, 16-byte aligned buffers) moved by cp.async
+// and vector stores; or the same partition with whole rows moved by the bulk-copy (TMA) engine
+// (FED_BULK).
+enum { MV_ELEM = 0, MV_VEC = 1, MV_BULK = 2 };
+inline bool mv_shifted(int mv) { return mv != MV_ELEM; }
+MwdShape mwd_shape(int stencil, int dtype, int dw, int nf, int XW, int mv);
 // Launch one diamond row: ndiam tiles, each a cluster of a.C blocks of `threads` threads.
-// G = row pairs per thread (1, 2 or 4), from mwd_pairs_per_thread; bulk = rows moved by the
-// bulk-copy engine (16-byte aligned layout) instead of per-element cp.async.
-cudaError_t launch_mwd_row(int stencil, int dtype, const MwdArgs& a, int ndiam, int threads, int G, bool bulk,
+// G = groups per thread (1, 2, 4 or 8), from mwd_pairs_per_thread; mv = data path.
+cudaError_t launch_mwd_row(int stencil, int dtype, const MwdArgs& a, int ndiam, int threads, int G, int mv,
                            int64_t smem, cudaStream_t st);
 // Configure kernel attributes (dynamic shared memory, non-portable clusters); returns the max
 // active clusters the device reports for the configuration (0 = cannot be scheduled).
-cudaError_t mwd_prepare(int stencil, int dtype, int C, int threads, int G, bool bulk, int64_t smem, int* max_clusters);
+cudaError_t mwd_prepare(int stencil, int dtype, int C, int threads, int G, int mv, int64_t smem, int* max_clusters);
 int mwd_max_pairs(int R, int dw);
-int mwd_pairs_per_thread(int stencil, int dtype, int dw, int XW, int threads, bool bulk);
-// Columns per thread of the blocked kernel and its launch-bound divisor (mirror the device side).
-inline int mwd_vx(int stencil, int dtype, bool bulk) {
-  return (bulk || (stencil >= 2 && dtype == GIRIH_F64)) ? 1 : (dtype == GIRIH_F64 ? 2 : 4);
+int mwd_pairs_per_thread(int stencil, int dtype, int dw, int XW, int threads, int mv);
+// Columns per group of the blocked kernel and its launch-bound divisor (mirror the device side).
+inline int mwd_vx(int stencil, int dtype, int mv) {
+  if (mv_shifted(mv)) return stencil < 2 ? (dtype == GIRIH_F64 ? 2 : 4) : (dtype == GIRIH_F32 ? 2 : 1);
+  return (stencil >= 2 && dtype == GIRIH_F64) ? 1 : (dtype == GIRIH_F64 ? 2 : 4);
 }
-inline int mwd_lbf(int stencil, int dtype, bool bulk) {
-  return mwd_vx(stencil, dtype, bulk) == 1 ? 1 : (stencil < 2 ? 2 : 4);
+inline int mwd_lbf(int stencil, int dtype, int mv) {
+  if (mv_shifted(mv)) return stencil < 2 ? 2 : 4;
+  return mwd_vx(stencil, dtype, mv) == 1 ? 1 : (stencil < 2 ? 2 : 4);
 }
 // Largest block for G groups per thread (the kernel's launch bound).
-inline int mwd_max_threads(int G, int lbf, bool bulk) {
-  const int t = 1024 / (G * lbf) + (bulk ? 32 : 0);
+inline int mwd_max_threads(int G, int lbf) {
+  const int t = 1024 / (G * lbf);
   return t > 1024 ? 1024 : t;
 }
 // Planes are staged this many wavefront steps ahead of use (element path / bulk-copy path).

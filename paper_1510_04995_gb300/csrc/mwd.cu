@@ -4,26 +4,40 @@
 
 namespace girih {
 
-void* mwd_kernel_r1(int stencil, int dtype, int G, bool bulk);
-void* mwd_kernel_r4(int stencil, int dtype, int G, bool bulk);
+void* mwd_kernel_r1(int stencil, int dtype, int G);
+void* mwd_kernel_r4(int stencil, int dtype, int G);
+void* mwd_vec_kernel_r1(int stencil, int dtype, int G, bool tma);
+void* mwd_vec_kernel_r4(int stencil, int dtype, int G, bool tma);
 
-static void* pick(int stencil, int dtype, int G, bool bulk) {
-  return stencil < 2 ? mwd_kernel_r1(stencil, dtype, G, bulk) : mwd_kernel_r4(stencil, dtype, G, bulk);
+static void* pick(int stencil, int dtype, int G, int mv) {
+  if (mv_shifted(mv)) {
+    const bool tma = mv == MV_BULK;
+    return stencil < 2 ? mwd_vec_kernel_r1(stencil, dtype, G, tma) : mwd_vec_kernel_r4(stencil, dtype, G, tma);
+  }
+  return stencil < 2 ? mwd_kernel_r1(stencil, dtype, G) : mwd_kernel_r4(stencil, dtype, G);
 }
 
-MwdShape mwd_shape(int stencil, int dtype, int dw, int nf, int XW, bool bulk) {
+MwdShape mwd_shape(int stencil, int dtype, int dw, int nf, int XW, int mv) {
   const int R = radius_of(stencil);
   const int H = dw / R;
   const int K = R + nf;
   const int elem = dtype == GIRIH_F64 ? 8 : 4;
   const int a16 = 16 / elem;
   MwdShape s;
+  const bool bulk = mv == MV_BULK;
   const int pd = bulk ? MWD_PREFETCH_BULK : MWD_PREFETCH;
   s.NZ = (pd + 1) * nf + R + (R > nf ? R : nf) + (H - 2) * K + (bulk ? MWD_BULK_SLACK * nf : 0);
   s.YW = dw + 2 * R;
-  // shared row: [halo | slab | halo]; with vector groups the slab starts on a 16-byte boundary
-  const int off = mwd_vx(stencil, dtype, bulk) == 1 ? R : a16;
-  s.XT = (off + XW + R + a16 - 1) / a16 * a16;  // rows start on 16-byte boundaries
+  // shared row: [halo | slab | halo], rows starting on 16-byte boundaries.  Element path: the
+  // slab starts on a 16-byte boundary when groups are vectors.  Vector path: HM = R rounded up
+  // to 16 bytes columns each side, so global and shared rows share their 16-byte alignment.
+  if (mv_shifted(mv)) {
+    const int hm = (R + a16 - 1) / a16 * a16;
+    s.XT = XW + 2 * hm;
+  } else {
+    const int off = mwd_vx(stencil, dtype, mv) == 1 ? R : a16;
+    s.XT = (off + XW + R + a16 - 1) / a16 * a16;
+  }
   const int64_t ring = 2LL * s.NZ * s.YW * s.XT * elem;
   s.smem_bytes = (ring + 15) / 16 * 16 + 8LL * s.NZ + (3LL * H + 1 + s.YW + 2) * 4;
   return s;
@@ -38,16 +52,16 @@ int mwd_max_pairs(int R, int dw) {
 }
 
 // Groups (row pair x VX columns) per computing thread (1, 2, 4 or 8) for a block of `threads`
-// (one warp of them a producer in the bulk-copy path), or 0 if the tile needs more.
-int mwd_pairs_per_thread(int stencil, int dtype, int dw, int XW, int threads, bool bulk) {
+// or 0 if the tile needs more.
+int mwd_pairs_per_thread(int stencil, int dtype, int dw, int XW, int threads, int mv) {
   const int R = radius_of(stencil);
-  const int vx = mwd_vx(stencil, dtype, bulk), lbf = mwd_lbf(stencil, dtype, bulk);
+  const int vx = mwd_vx(stencil, dtype, mv), lbf = mwd_lbf(stencil, dtype, mv);
   const int64_t ng = (int64_t)mwd_max_pairs(R, dw) * (XW / vx);
-  const int ct = bulk ? threads - 32 : threads;
+  const int ct = threads;
   for (int G : {1, 2, 4, 8}) {
     if (G == 8 && R == 4) break;  // radius-4 kernels are built for at most 4 groups per thread
-    if (G > 2 && R == 4 && vx > 1) break;  // radius-4 vector groups: registers allow 2 per thread
-    if (threads <= mwd_max_threads(G, lbf, bulk) && ng <= (int64_t)G * ct) return G;
+    if (G > 2 && R == 4 && vx > 1 && mv == MV_ELEM) break;  // radius-4 vector windows: 2 per thread
+    if (threads <= mwd_max_threads(G, lbf) && ng <= (int64_t)G * ct) return G;
   }
   return 0;
 }
@@ -66,9 +80,9 @@ static cudaLaunchConfig_t launch_config(int C, int threads, int64_t smem, cudaLa
   return cfg;
 }
 
-cudaError_t mwd_prepare(int stencil, int dtype, int C, int threads, int G, bool bulk, int64_t smem,
+cudaError_t mwd_prepare(int stencil, int dtype, int C, int threads, int G, int mv, int64_t smem,
                         int* max_clusters) {
-  const void* k = pick(stencil, dtype, G, bulk);
+  const void* k = pick(stencil, dtype, G, mv);
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   if (C > 8) {
@@ -86,14 +100,14 @@ cudaError_t mwd_prepare(int stencil, int dtype, int C, int threads, int G, bool 
   return cudaSuccess;
 }
 
-cudaError_t launch_mwd_row(int stencil, int dtype, const MwdArgs& a, int ndiam, int threads, int G, bool bulk,
+cudaError_t launch_mwd_row(int stencil, int dtype, const MwdArgs& a, int ndiam, int threads, int G, int mv,
                            int64_t smem, cudaStream_t st) {
   cudaLaunchAttribute attr[1];
   cudaLaunchConfig_t cfg = launch_config(a.C, threads, smem, attr);
   cfg.gridDim = dim3((unsigned)(ndiam * a.C), 1, 1);
   cfg.stream = st;
   void* args[] = {const_cast<MwdArgs*>(&a)};
-  return cudaLaunchKernelExC(&cfg, pick(stencil, dtype, G, bulk), args);
+  return cudaLaunchKernelExC(&cfg, pick(stencil, dtype, G, mv), args);
 }
 
 }  // namespace girih

@@ -28,19 +28,10 @@
 // step and plane a pair loads 2 new z values, 2R rows of y neighbours shared by both rows, 2R x
 // neighbours per row, and stores 2.
 //
-// Data movement, two modes:
-//  BULK  (16-byte aligned rows): warp 0 is a producer that moves whole rows with the bulk-copy
-//        (TMA) engine: cp.async.bulk global->shared completing on one mbarrier per ring slot
-//        (waits are bounded; a timeout sets an error word instead of hanging), and
-//        cp.async.bulk shared->global for the write-back.  The other warps only compute.
-//  plain (any alignment): every thread stages elements with cp.async and writes back with
-//        plain stores.
-// In both modes planes are staged MWD_PREFETCH steps ahead, and a plane is written back once the
-// tile's top level has passed it: only rows of the diamond's projection, only buffers the tile
-// updated in that row.  BULK write-back rows cover padded columns [x0, x0 + XW): the first R are
-// the left neighbour's (its final values, pushed here) and the block's own last R are written by
-// the right neighbour in turn, so every interior column is written exactly once with its final
-// value; the last block of the cluster extends its rows to its slab end.
+// Data movement: every thread stages elements with cp.async, MWD_PREFETCH steps ahead, and
+// writes back with plain stores; a plane is written back once the tile's top level has passed
+// it, only rows of the diamond's projection, only buffers the tile updated in that row.  This is
+// the path for any layout; 16-byte aligned layouts use the vector kernel of mwd_vec.cuh.
 #pragma once
 #include "internal.h"
 #include "stencil.cuh"
@@ -103,16 +94,16 @@ __device__ __forceinline__ void sts_vec(T* p, const T* v) {
   }
 }
 
-// Columns per thread of the blocked kernel: whole 16-byte vectors on the element path, except
-// the 25-point FP64 tiles (register budget); single columns on the bulk-copy path.
-template <int S, typename T, bool BULK>
+// Columns per thread of the element kernel: whole 16-byte vectors, except the 25-point FP64
+// tiles (register budget).
+template <int S, typename T>
 constexpr int mwd_vx() {
-  return (BULK || (Traits<S>::R == 4 && sizeof(T) == 8)) ? 1 : (int)(16 / sizeof(T));
+  return (Traits<S>::R == 4 && sizeof(T) == 8) ? 1 : (int)(16 / sizeof(T));
 }
 // Launch-bound divisor for the register growth of vector groups.
-template <int S, typename T, bool BULK>
+template <int S, typename T>
 constexpr int mwd_lbf() {
-  return mwd_vx<S, T, BULK>() == 1 ? 1 : (Traits<S>::R == 1 ? 2 : 4);
+  return mwd_vx<S, T>() == 1 ? 1 : (Traits<S>::R == 1 ? 2 : 4);
 }
 
 __device__ __forceinline__ int lev_lo_of(int a, int b, int dw, int R, int t) {
@@ -210,16 +201,13 @@ __device__ __forceinline__ void mwd_points(const T* w0, const T* w1, const T* yl
   mwd_points_i<S, T, VX, 0>(w0, w1, ylo, yhi, xl0, xl1, u0, u1, kp, gs, ldx, nv, row1, cst, r0, r1);
 }
 
-template <int S, typename T, int G, bool BULK>
-__global__ void __launch_bounds__((1024 / (G * mwd_lbf<S, T, BULK>()) + (BULK ? 32 : 0)) > 1024
-                                      ? 1024
-                                      : (1024 / (G * mwd_lbf<S, T, BULK>()) + (BULK ? 32 : 0)))
-    mwd_fed_kernel(const MwdArgs A) {
+template <int S, typename T, int G>
+__global__ void __launch_bounds__(1024 / (G * mwd_lbf<S, T>())) mwd_fed_kernel(const MwdArgs A) {
   constexpr int R = Traits<S>::R;
   constexpr int NC = Traits<S>::NCOEF;
-  constexpr int PD = BULK ? MWD_PREFETCH_BULK : MWD_PREFETCH;
+  constexpr int PD = MWD_PREFETCH;
   constexpr int A16 = 16 / (int)sizeof(T);  // elements per 16 bytes
-  constexpr int VX = mwd_vx<S, T, BULK>();   // columns per thread
+  constexpr int VX = mwd_vx<S, T>();         // columns per thread
   constexpr int OFF = VX == 1 ? R : A16;     // shared column of the slab's first column
   extern __shared__ __align__(128) unsigned char smem_raw[];
   T* sm = reinterpret_cast<T*>(smem_raw);
@@ -251,9 +239,6 @@ __global__ void __launch_bounds__((1024 / (G * mwd_lbf<S, T, BULK>()) + (BULK ? 
   const int nlev = te - tb + 1, smax = nlev - 1;
   const int NT = blockDim.x, tid = threadIdx.x;
   const int lane = tid & 31, warp = tid >> 5, nwarps = NT >> 5;
-  const bool producer = BULK && warp == 0;
-  const int ctid = BULK ? tid - 32 : tid;  // index among the computing threads
-  const int CNT = BULK ? NT - 32 : NT;
 
   if (tid == 0) {
     int acc = 0;
@@ -268,10 +253,6 @@ __global__ void __launch_bounds__((1024 / (G * mwd_lbf<S, T, BULK>()) + (BULK ? 
     }
     lev_pp[nlev] = acc;
     prog[0] = prog[1] = 0;
-    if constexpr (BULK) {
-      for (int s = 0; s < NZ; ++s) mbar_init(&mbar[s], 1);
-      asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    }
   }
   for (int yy = tid; yy < YW; yy += NT) {
     const int y = Y0 + yy;
@@ -289,7 +270,7 @@ __global__ void __launch_bounds__((1024 / (G * mwd_lbf<S, T, BULK>()) + (BULK ? 
     }
     row_mask[yy] = m;
   }
-  __syncthreads();  // level tables (and mbarriers) ready
+  __syncthreads();  // level tables ready
 
   const T* __restrict__ gb0 = static_cast<const T*>(A.buf0);
   const T* __restrict__ gb1 = static_cast<const T*>(A.buf1);
@@ -311,9 +292,9 @@ __global__ void __launch_bounds__((1024 / (G * mwd_lbf<S, T, BULK>()) + (BULK ? 
   const int nvec = XW / VX;
 #pragma unroll
   for (int g = 0; g < G; ++g) {
-    const int id = ctid + g * CNT;
+    const int id = tid + g * NT;
     const int pr = id / nvec, xl = (id - pr * nvec) * VX;
-    const bool valid = !producer && (pr < npairs) && (xl < xw);
+    const bool valid = (pr < npairs) && (xl < xw);
     int s = 0;
     if (valid)
       while (lev_pp[s + 1] <= pr) ++s;
@@ -337,65 +318,13 @@ __global__ void __launch_bounds__((1024 / (G * mwd_lbf<S, T, BULK>()) + (BULK ? 
   T win[G][2][(2 * R + 1) * VX];
 
   // ---- staging geometry: rows y in [Y0, Y0+YW) clipped to the padded grid, columns from padded
-  // x0 (interior x0 - R); BULK rows are rounded up to 16 bytes (the host keeps them inside ldx)
+  // x0 (interior x0 - R)
   const int ylo = max(Y0, -R), yhi = min(Y0 + YW, ny + R);
   const int nrow = max(yhi - ylo, 0);
   const int ncol = (xw > 0) ? xw + 2 * R : 0;
-  const int lcols = BULK ? (ncol + A16 - 1) / A16 * A16 : ncol;
-  const bool last_rank = x0 + XW >= nx;
-  const int wcols = last_rank ? (xw + R + A16 - 1) / A16 * A16 : XW;  // BULK write-back columns
   int lz = -R, lsl = 0;                                  // next plane to stage and its slot
   int wz = -smax * K, wsl = ((R - smax * K) % NZ + NZ) % NZ;  // next plane to write back
 
-  // BULK helpers (producer warp only)
-  auto bulk_stage = [&](int z, int slot) {  // whole warp: rows of both buffers of plane z
-    if (z < -R || z >= nz + R) return;
-    const uint32_t bytes = (uint32_t)(lcols * sizeof(T));
-    if (lane == 0) mbar_expect_tx(&mbar[slot], bytes * 2u * (uint32_t)nrow);
-    __syncwarp();
-    const int64_t gz = (int64_t)(z + R) * gplane;
-    for (int rr = lane; rr < 2 * nrow; rr += 32) {
-      const int p = rr >= nrow;
-      const int y = ylo + rr - p * nrow;
-      bulk_load(sm + p * be + slot * pe + (y - Y0) * XT, (p ? gb1 : gb0) + gz + (int64_t)(y + R) * ldx + x0, bytes,
-                &mbar[slot]);
-    }
-  };
-  auto bulk_wait = [&](int z) {  // lane 0 waits for plane z's staging; error word on timeout
-    if (z < -R || z >= nz + R) return;
-    if (lane == 0) {
-      const int q = z + R;
-      const int slot = q % NZ;
-      const uint32_t parity = (uint32_t)((q / NZ) & 1);
-      if (!mbar_try_wait(&mbar[slot], parity)) {
-        const uint64_t t0 = global_ns();
-        while (!mbar_try_wait(&mbar[slot], parity)) {
-          if (global_ns() - t0 > kMbarWaitNs) {
-            atomicOr(A.err, GIRIH_ETIMEOUT);
-            break;
-          }
-        }
-      }
-    }
-    __syncwarp();
-  };
-  auto bulk_write = [&](int z, int slot) {  // whole warp: masked rows of plane z, one group per call
-    if (z >= 0 && z < nz) {
-      fence_proxy_async();
-      const int64_t gz = (int64_t)(z + R) * gplane;
-      const uint32_t bytes = (uint32_t)(wcols * sizeof(T));
-      for (int yy = lane; yy < YW; yy += 32) {
-        const int m = row_mask[yy];
-        if (m == 0) continue;
-        const int64_t go = gz + (int64_t)(Y0 + yy + R) * ldx + x0;
-        const int so = slot * pe + yy * XT;
-        if (m & 1) bulk_store(go0 + go, sm + so, bytes);
-        if (m & 2) bulk_store(go1 + go, sm + be + so, bytes);
-      }
-    }
-    bulk_commit();  // exactly nf groups per step, so "the last nf groups" are this step's
-  };
-  // plain-mode helpers (all threads)
   auto plain_stage = [&](int z, int slot) {
     if (z < -R || z >= nz + R) return;
     const int64_t gz = (int64_t)(z + R) * gplane;
@@ -423,27 +352,17 @@ __global__ void __launch_bounds__((1024 / (G * mwd_lbf<S, T, BULK>()) + (BULK ? 
   };
 
   // ---- prologue: planes of the first PD steps --------------------------------------------------
-  if (xw > 0) {
-    if constexpr (BULK) {
-      if (producer) {
-        for (; lz < PD * nf + R; ++lz, lsl = (lsl + 1 == NZ) ? 0 : lsl + 1) bulk_stage(lz, lsl);
-        for (int z = -R; z < PD * nf + R; ++z) bulk_wait(z);
-      }
-    } else {
-      for (; lz < PD * nf + R; ++lz, lsl = (lsl + 1 == NZ) ? 0 : lsl + 1) plain_stage(lz, lsl);
-    }
-  }
-  if constexpr (!BULK) {
-    cp_async_commit();
-    cp_async_wait_group<0>();
-  }
+  if (xw > 0)
+    for (; lz < PD * nf + R; ++lz, lsl = (lsl + 1 == NZ) ? 0 : lsl + 1) plain_stage(lz, lsl);
+  cp_async_commit();
+  cp_async_wait_group<0>();
   if (C > 1) cluster_barrier();
   else __syncthreads();
 
   const uint32_t sm_base = smem_addr(sm);
   const uint32_t left_base = (C > 1 && rank > 0) ? map_to_rank(sm_base, rank - 1) : 0u;
   const uint32_t right_base = (C > 1 && rank < C - 1) ? map_to_rank(sm_base, rank + 1) : 0u;
-  const bool relaxed = !BULK && C > 1 && A.relaxed;
+  const bool relaxed = C > 1 && A.relaxed;
   const uint32_t prog_base = smem_addr(prog);
 
   const int W = (nz + smax * K + nf - 1) / nf;
@@ -549,34 +468,7 @@ __global__ void __launch_bounds__((1024 / (G * mwd_lbf<S, T, BULK>()) + (BULK ? 
       if constexpr (NC > 0) gk_[g] += nf * gplane;
     }
 
-    if constexpr (BULK) {
-      // shared writes of this step become visible to the bulk engine (write-back reads them)
-      if (!producer) fence_proxy_async();
-      if (producer && xw > 0) {
-        // Stage the planes of step w+PD first.  Their slots were last written back at least two
-        // steps ago (ring slack): wait until only the previous step's nf write-back groups may
-        // still be reading shared memory.
-        if (nf == 1) bulk_wait_read_n<1>();
-        else if (nf == 2) bulk_wait_read_n<2>();
-        else if (nf == 3) bulk_wait_read_n<3>();
-        else bulk_wait_read_n<4>();
-        __syncwarp();
-        for (int f = 0; f < nf; ++f, ++lz, lsl = (lsl + 1 == NZ) ? 0 : lsl + 1) bulk_stage(lz, lsl);
-        // then write back the planes the top level finished in step w-1 (nf groups, maybe empty)
-        for (int f = 0; f < nf; ++f) {
-          if (w > 0) {
-            bulk_write(wz, wsl);
-            ++wz;
-            wsl = (wsl + 1 == NZ) ? 0 : wsl + 1;
-          } else {
-            bulk_commit();  // keep nf groups per step
-          }
-        }
-        for (int f = 0; f < nf; ++f) bulk_wait((w + 1) * nf + R + f);  // new planes of step w+1
-      }
-      if (C > 1) cluster_barrier();
-      else __syncthreads();
-    } else if (relaxed) {
+    if (relaxed) {
       // RELAXED: no cluster-wide barrier.  Once all warps of this block have finished the step's
       // updates and pushes (named barrier 1, on which only warp 0 waits), one thread publishes
       // the step count to the two x neighbours (release at cluster scope).  The block then
@@ -628,16 +520,9 @@ __global__ void __launch_bounds__((1024 / (G * mwd_lbf<S, T, BULK>()) + (BULK ? 
     }
   }
   // ---- epilogue: planes the top level finished in the last step ----
-  if constexpr (BULK) {
-    if (producer && xw > 0) {
-      for (int f = 0; f < nf; ++f, ++wz, wsl = (wsl + 1 == NZ) ? 0 : wsl + 1) bulk_write(wz, wsl);
-      bulk_wait_all();  // the shared source must outlive the copies
-    }
-  } else {
-    cp_async_wait_group<0>();
-    if (xw > 0)
-      for (int f = 0; f < nf; ++f, ++wz, wsl = (wsl + 1 == NZ) ? 0 : wsl + 1) plain_write(wz, wsl);
-  }
+  cp_async_wait_group<0>();
+  if (xw > 0)
+    for (int f = 0; f < nf; ++f, ++wz, wsl = (wsl + 1 == NZ) ? 0 : wsl + 1) plain_write(wz, wsl);
 }
 
 }  // namespace girih

@@ -27,7 +27,10 @@ using Plan = girih_plan_s;
 int fail(int code, const char* fmt, ...);
 void g_err_clear();
 int cuda_fail(cudaError_t e, const char* where);
-int check_config(const Plan* p, const girih_config* c, int64_t* smem_out, int* xw_out, int* g_out);
+// Validates a configuration for the plan's device and layout.  ptrs16: the buffers of the run
+// are 16-byte aligned (plan-time checks assume so); mv_out: the kernel's data path.
+int check_config(const Plan* p, const girih_config* c, int64_t* smem_out, int* xw_out, int* g_out,
+                 int* mv_out = nullptr, bool ptrs16 = true);
 int run_sweep(Plan* p, int64_t T, void* u, void* u_prev, const void* coeffs, const double* c,
               const girih_config& cfg, cudaStream_t st);
 int64_t mwd_rows(int64_t T, int dw, int R);

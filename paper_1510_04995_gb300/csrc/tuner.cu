@@ -128,11 +128,11 @@ std::vector<girih_config> candidates(Plan* p) {
     for (int nf : {1, 2})
       for (int C : {1, 2, 4, 8, 16})
         for (int th : {128, 256, 512, 1024})
-          for (int v : {GIRIH_FED, GIRIH_RELAXED, GIRIH_FED_BULK}) {
-            if (v == GIRIH_RELAXED && C == 1) continue;  // a single block: RELAXED is FED
-            // the bulk-copy variant adds a producer warp to the computing threads
-            girih_config c{GIRIH_ALGO_MWD, dw, nf, C, v == GIRIH_FED_BULK ? th + 32 : th, v};
-            if (c.threads > 1024) continue;
+          for (int v : {GIRIH_FED, GIRIH_RELAXED, GIRIH_FED_BULK, GIRIH_FED_ELEM, GIRIH_RELAXED_ELEM}) {
+            if ((v == GIRIH_RELAXED || v == GIRIH_RELAXED_ELEM) && C == 1) continue;  // one block: = FED
+            // on an unaligned layout FED is already the element path
+            if ((v == GIRIH_FED_ELEM || v == GIRIH_RELAXED_ELEM) && !p->bulk_layout) continue;
+            girih_config c{GIRIH_ALGO_MWD, dw, nf, C, th, v};
             if (check_config(p, &c, nullptr, nullptr, nullptr) == GIRIH_OK) out.push_back(c);
           }
   g_err_clear();

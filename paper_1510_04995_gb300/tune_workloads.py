@@ -5,7 +5,9 @@
 For every workload (stencil, dtype, grid, T) this runs girih_tune_exhaustive (Sect. 4.2.2: all
 feasible candidates, test length grown until two repetitions agree) on tuner-owned arrays of the
 full grid, with the 16-byte aligned leading dimension the benchmark uses, and writes
-{workload: config} to tuned_configs.json next to this file, plus the timing database.
+{workload: {"best": config, "best_glups": rate, "blocked": config, "blocked_glups": rate}} to
+tuned_configs.json next to this file ("blocked" is the fastest wavefront-diamond candidate, which
+the benchmark reports beside the overall winner), plus the timing database.
 """
 from __future__ import annotations
 
@@ -15,7 +17,7 @@ import json
 import os
 import time
 
-from . import TuneRow, build, check, lib, plan
+from . import F32, F64, MWD, TuneRow, build, check, lib, plan
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 
@@ -37,6 +39,17 @@ def aligned_ldx(stencil: int, dtype: str, nx: int) -> int:
     return -(-(nx + 2 * RADIUS[stencil]) // a16) * a16
 
 
+def _best_blocked(db_path, stencil, dtype, nx, ny, nz):
+    """(config dict, GLUP/s) of the fastest blocked candidate of one problem in the database."""
+    from .learned import load_db, problem_key, row_config
+    key = (stencil, F64 if dtype == "f64" else F32, nx, ny, nz)
+    rows = [r for r in load_db(db_path) if problem_key(r) == key and int(r["algo"]) == MWD]
+    if not rows:
+        return None
+    r = max(rows, key=lambda r: r["glups"])
+    return row_config(r).as_dict(), r["glups"]
+
+
 def tune(names, out_path, db_path, tol=0.05, max_steps=64, log=print):
     build.build()
     res = {}
@@ -51,7 +64,9 @@ def tune(names, out_path, db_path, tol=0.05, max_steps=64, log=print):
         t0 = time.perf_counter()
         check(lib().girih_tune_exhaustive(p.handle, None, 0, tol, max_steps, db_path.encode(), ctypes.byref(best),
                                           ctypes.byref(nm)))
-        res[name] = best.cfg.as_dict()
+        blk = _best_blocked(db_path, s, d, nx, ny, nz)
+        res[name] = {"best": best.cfg.as_dict(), "best_glups": best.glups,
+                     "blocked": blk[0] if blk else None, "blocked_glups": blk[1] if blk else None}
         if log:
             log(f"{name}: {nm.value} candidates, {time.perf_counter() - t0:.1f} s, best {best.glups:.1f} GLUP/s "
                 f"{best.cfg}")

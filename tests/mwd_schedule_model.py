@@ -23,6 +23,12 @@ def slab_width(nx, C):
     return -(-w // 16) * 16
 
 
+def vec_slab_width(nx, R, C, a16):
+    """Vector path: the slabs split the padded columns [R, nx + R) at 16-byte boundaries."""
+    w = -(-(nx + R) // C)
+    return -(-w // a16) * a16
+
+
 PD = 2       # element path: planes staged this many steps ahead (cp.async groups, wait_group PD-1)
 PD_BULK = 3  # bulk-copy path
 SLACK = 2    # bulk-copy path: extra ring planes per wavefront width
@@ -53,11 +59,30 @@ def row_span(rho, dw, ny):
     return lo, max(hi - lo + 1, 0)
 
 
-def simulate(R, second_order, nx, ny, nz, T, dw, nf, C, bulk=False, a16=4):
-    """bulk: write-back as the bulk-copy mode does (padded columns [x0, x0 + wcols) of each row,
-    the first R being the left neighbour's final values held in this block's halo copy)."""
-    XW = slab_width(nx, C)
-    NZ, YW, XT = shape(R, dw, nf, XW, bulk)
+def simulate(R, second_order, nx, ny, nz, T, dw, nf, C, bulk=False, a16=4, vec=False):
+    """vec: the 16-byte vector path (block r owns padded columns [r*XW, (r+1)*XW); its shared row
+    starts HM = R rounded up to a16 columns before them; whole a16-column chunks are staged and
+    written back; both rows of a pair are read even when only the first is updated).
+    bulk (with vec): the bulk-copy schedule -- planes staged PD_BULK steps ahead, a ring slack of
+    SLACK*nf planes, write-back copies that may still read shared memory for two steps."""
+    assert vec or not bulk, "the bulk-copy schedule runs on the vector partition"
+    if vec:
+        XW = vec_slab_width(nx, R, C, a16)
+        HM = -(-R // a16) * a16
+        NZ, YW, _ = shape(R, dw, nf, XW, bulk)
+        XT = XW + 2 * HM
+    else:
+        XW = slab_width(nx, C)
+        NZ, YW, XT = shape(R, dw, nf, XW, bulk)
+
+    def slab(rank):
+        """(first interior column of slab column 0, shared column of slab column 0, valid slab
+        columns [lo, hi))."""
+        if vec:
+            x0 = rank * XW - R
+            return x0, HM, max(0, -x0), min(XW, nx - x0)
+        x0 = rank * XW
+        return x0, R, 0, min(XW, nx - x0)
     pdm = PD_BULK if bulk else PD
     H = dw // R
     K = R + nf
@@ -111,30 +136,34 @@ def simulate(R, second_order, nx, ny, nz, T, dw, nf, C, bulk=False, a16=4):
 
         def load_plane(tl, rank, z, loaded):
             nonlocal max_s
-            x0 = rank * XW
-            xw = min(XW, nx - x0)
-            if z < -R or z >= nz + R or xw <= 0:
+            x0, off, vlo, vhi = slab(rank)
+            if z < -R or z >= nz + R or vhi <= vlo:
                 return
             slot = (z + R) % NZ
             Y0 = tl["Y0"]
             ylo, yhi = max(Y0, -R), min(Y0 + YW, ny + R)
+            if vec:  # whole a16 chunks of padded columns [pc0 - HM, pc0 + XW + HM), inside the row
+                pc0 = rank * XW
+                cb, ce = max(pc0 - HM, 0), min(pc0 + XW + HM, nx + 2 * R)
+                cols = [(pc - (pc0 - HM), pc - R) for pc in range(cb, ce)]
+            else:
+                cols = [(xx, x0 - R + xx) for xx in range(vhi + 2 * R)]
             for p in range(2):
                 for y in range(ylo, yhi):
-                    for xx in range(xw + 2 * R):
+                    for xx, x in cols:
                         assert 0 <= y - Y0 < YW and 0 <= xx < XT
-                        tl["S"][rank, p, slot, y - Y0, xx] = gtag(p, z, y, x0 - R + xx)
+                        tl["S"][rank, p, slot, y - Y0, xx] = gtag(p, z, y, x)
                         loaded.add((rank, p, slot, y - Y0, xx))
 
         def write_plane(tl, rank, z, wb_reads):
-            x0 = rank * XW
-            xw = min(XW, nx - x0)
-            if z < 0 or z >= nz or xw <= 0:
+            x0, off, vlo, vhi = slab(rank)
+            xw = vhi
+            if z < 0 or z >= nz or vhi <= vlo:
                 return
             slot = (z + R) % NZ
-            if bulk:
-                last = x0 + XW >= nx
-                wcols = -(-(xw + R) // a16) * a16 if last else XW
-                cols = [xx for xx in range(wcols) if x0 - R + xx < nx + R]  # beyond: row padding
+            if vec:  # the owned padded columns [pc0, pc0 + XW), inside the row
+                pc0 = rank * XW
+                cols = [pc - (pc0 - HM) for pc in range(pc0, min(pc0 + XW, nx + 2 * R))]
             else:
                 cols = [xl + R for xl in range(xw)]
             for yy in range(YW):
@@ -143,7 +172,7 @@ def simulate(R, second_order, nx, ny, nz, T, dw, nf, C, bulk=False, a16=4):
                     continue
                 y = tl["Y0"] + yy
                 for xx in cols:
-                    x = x0 - R + xx
+                    x = x0 - off + xx
                     for p in range(2):
                         if m >> p & 1:
                             gtag(p, z, y, x)
@@ -178,9 +207,8 @@ def simulate(R, second_order, nx, ny, nz, T, dw, nf, C, bulk=False, a16=4):
                             write_plane(tl, rank, (w - 1) * nf - smax * K + f, wb_reads)
                 pending = []
                 for rank in range(C):
-                    x0 = rank * XW
-                    xw = min(XW, nx - x0)
-                    if xw <= 0:
+                    x0, off, vlo, vhi = slab(rank)
+                    if vhi <= vlo:
                         continue
                     for s in range(nlev):
                         zb = w * nf - s * K
@@ -199,8 +227,8 @@ def simulate(R, second_order, nx, ny, nz, T, dw, nf, C, bulk=False, a16=4):
                                 if z < 0 or z >= nz:
                                     continue
                                 sl = (z + R) % NZ
-                                for xl in range(xw):
-                                    xx = xl + R
+                                for xl in range(vlo, vhi):
+                                    xx = xl + off
                                     item = (rank, s, y0, z, xl)
                                     key = (rank, s, y0, xl)
                                     def rd(cell, want):
@@ -221,6 +249,12 @@ def simulate(R, second_order, nx, ny, nz, T, dw, nf, C, bulk=False, a16=4):
                                         rd((pin, sl, yy0 - d, xx), t)
                                         if d < R or row1:
                                             rd((pin, sl, yy0 + 1 + d, xx), t)
+                                    if vec and not row1:  # the second row is read, not used
+                                        for cell in [(pin, (sl + d) % NZ, yy0 + 1, xx + e)
+                                                     for d in range(-R, R + 1) for e in range(-R, R + 1)] + \
+                                                    [(pin, sl, yy0 + R, xx), (pout, sl, yy0 + 1, xx)]:
+                                            assert 0 <= cell[2] < YW and 0 <= cell[3] < XT, cell
+                                            reads.setdefault((rank,) + cell, set()).add(item)
                                     for r in (0, 1) if row1 else (0,):
                                         for d in range(-R, R + 1):
                                             if d:

@@ -27,19 +27,28 @@ def _build():
     __graft_entry__.build()
 
 
-def _bench_cfg(workload, p):
+def _blocked_cfg(workload, p):
+    """The blocked configuration the benchmark reports for this workload (the tuner's fastest
+    blocked candidate), else the plan's default blocked configuration."""
     import bench
-    tuned = bench._tuned(workload)
-    return girih.Config(**tuned) if tuned else p.config
+    best, blocked = bench._tuned(workload)
+    for c in (blocked, best):
+        if c and c["algo"] == girih.MWD:
+            return girih.Config(**c)
+    return p.config
 
 
 def _run_pair(workload):
     import torch
     import bench
     stencil, dtype, nx, ny, nz, T = bench.WORKLOADS[workload]
-    p = girih.plan(stencil, nx, ny, nz, dtype=dtype, T=T)
-    cfg = _bench_cfg(workload, p)
-    u, up, co, c = inputs.make_problem(stencil, nx, ny, nz, backend="torch", device="cuda")
+    R = inputs.RADIUS[stencil]
+    a16 = 16 // (8 if dtype == "f64" else 4)
+    ldx = -(-(nx + 2 * R) // a16) * a16  # the benchmark's 16-byte aligned leading dimension
+    p = girih.plan(stencil, nx, ny, nz, dtype=dtype, T=T, ldx=ldx)
+    cfg = _blocked_cfg(workload, p)
+    assert cfg.algo == girih.MWD
+    u, up, co, c = inputs.make_problem(stencil, nx, ny, nz, backend="torch", device="cuda", ldx=ldx)
     tdt = torch.float64 if dtype == "f64" else torch.float32
     u, up = u.to(tdt).contiguous(), up.to(tdt).contiguous()
     co = co.to(tdt).contiguous() if co is not None else None

@@ -189,7 +189,9 @@ def test_bulk_copy_path_equals_element_path(stencil, dtype):
     assert (ld_al * elem) % 16 == 0 and (ld_un * elem) % 16 != 0
     dw = 8 if (R == 1 or dtype == "f64") else 16
     outs = []
-    for ldx, variant in ((ld_al, girih.FED_BULK), (ld_un, girih.FED)):
+    # FED_BULK: bulk-copy rows; FED on the aligned layout: 16-byte vector path; FED_ELEM on the
+    # aligned layout and FED on the unaligned one: per-element path
+    for ldx, variant in ((ld_al, girih.FED_BULK), (ld_al, girih.FED), (ld_al, girih.FED_ELEM), (ld_un, girih.FED)):
         cfg = feasible_cfg(stencil, dtype, nx, ny, nz, dict(dw=dw, nf=1, cluster=4, threads=544, variant=variant),
                            ldx=ldx)
         assert cfg.variant == variant
@@ -200,7 +202,40 @@ def test_bulk_copy_path_equals_element_path(stencil, dtype):
         assert np.array_equal(gu[:, :, :w], nu[:, :, :w]) and np.array_equal(gup[:, :, :w], nup[:, :, :w])
         assert np.all(gu[:, :, w:] == 0) and np.all(gup[:, :, w:] == 0)  # row padding keeps its (zero) values
         outs.append(gu[:, :, :w])
-    assert np.array_equal(outs[0], outs[1])
+    assert all(np.array_equal(outs[0], o) for o in outs[1:])
+
+
+@pytest.mark.parametrize("stencil,dtype", [(0, "f32"), (3, "f32"), (1, "f64"), (2, "f64")])
+def test_vector_path_on_unaligned_buffers_falls_back(stencil, dtype):
+    """A 16-byte aligned layout whose buffers start off a 16-byte boundary runs the per-element
+    path, with the same result."""
+    import torch
+    from gpu_util import to_dev
+    R = inputs.RADIUS[stencil]
+    nx, ny, nz, T = 61, 37, 19, 7
+    elem = 8 if dtype == "f64" else 4
+    a16 = 16 // elem
+    ldx = -(-(nx + 2 * R) // a16) * a16
+    u, up, co, c = inputs.make_problem(stencil, nx, ny, nz, seed=8, ldx=ldx)
+    p = girih.plan(stencil, nx, ny, nz, dtype=dtype, T=T, ldx=ldx)
+    cfg = feasible_cfg(stencil, dtype, nx, ny, nz, dict(dw=4 * R, nf=1, cluster=2, threads=256), ldx=ldx)
+    outs = []
+    for shift in (0, 1):
+        n = u.size
+        tdt = torch.float64 if dtype == "f64" else torch.float32
+        bu = torch.zeros(n + 1, dtype=tdt, device="cuda")[shift:shift + n].view(u.shape)
+        bup = torch.zeros(n + 1, dtype=tdt, device="cuda")[shift:shift + n].view(u.shape)
+        bu.copy_(to_dev(u, dtype))
+        bup.copy_(to_dev(up, dtype))
+        assert (bu.data_ptr() % 16 == 0) == (shift == 0)
+        dco = to_dev(co, dtype) if co is not None else None
+        girih.run(p, bu, bup, dco, c=c, cfg=cfg)
+        girih.status(p)
+        torch.cuda.synchronize()
+        outs.append((bu.double().cpu().numpy(), bup.double().cpu().numpy()))
+    nu, nup = gpu_sweep(stencil, dtype, u, up, co, c, T, nx, ny, nz, girih.config(girih.NAIVE), ldx=ldx)
+    for gu, gup in outs:
+        assert np.array_equal(gu, nu) and np.array_equal(gup, nup)
 
 
 @pytest.mark.parametrize("stencil", [0, 1, 2, 3])

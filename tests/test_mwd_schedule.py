@@ -12,7 +12,7 @@ CASES = [
     (1, False, 3, 2, 5, 5, 2, 1, 1),
     (1, False, 65, 9, 4, 11, 4, 4, 4),
     (4, True, 70, 29, 12, 5, 8, 1, 1),
-    (4, True, 70, 35, 11, 9, 16, 2, 2),
+    (4, True, 46, 35, 11, 9, 16, 2, 2),
     (4, True, 44, 30, 10, 6, 24, 1, 4),
     (4, True, 70, 29, 9, 7, 16, 1, 8),
     (1, False, 70, 12, 5, 6, 4, 1, 16),
@@ -20,7 +20,13 @@ CASES = [
 ]
 
 
-@pytest.mark.parametrize("case", CASES)
-@pytest.mark.parametrize("bulk", [False, True])
-def test_schedule_model(case, bulk):
-    assert simulate(*case, bulk=bulk)
+MODES = [(c, m) for c in CASES for m in ("element", "vec_f32", "bulk_f32")] + \
+        [(c, m) for c in CASES[1::2] for m in ("vec_f64", "bulk_f64")]
+
+
+@pytest.mark.parametrize("case,mode", MODES)
+def test_schedule_model(case, mode):
+    if mode == "element":
+        assert simulate(*case)
+    else:
+        assert simulate(*case, vec=True, bulk=mode.startswith("bulk"), a16=4 if mode.endswith("f32") else 2)
