@@ -104,9 +104,10 @@ int check_config(const Plan* p, const girih_config* c, int64_t* smem_out, int* x
   const int cthreads = c->threads;
   const int G = mwd_pairs_per_thread(p->stencil, p->dtype, c->dw, XW, c->threads, mv);
   if (G == 0)
-    return fail(GIRIH_EINVAL, "dw=%d with a %d-wide slab has %d row pairs x %d column groups: too many for %d "
-                "computing threads", c->dw, XW, mwd_max_pairs(R, c->dw), XW / mwd_vx(p->stencil, p->dtype, mv),
-                cthreads);
+    return fail(GIRIH_EINVAL, "dw=%d with a %d-wide slab has %d row pairs x %d column groups: no groups-per-thread "
+                "count fits %d threads within the kernel's launch bound (%d threads for one group per thread)",
+                c->dw, XW, mwd_max_pairs(R, c->dw), XW / mwd_vx(p->stencil, p->dtype, mv), cthreads,
+                mwd_max_threads(1, mwd_lbf(p->stencil, p->dtype, mv)));
   if (R == 4 && G > 4) return fail(GIRIH_EINVAL, "25-point tiles allow at most 4 row pairs per thread (registers)");
   if (p->dtype == GIRIH_F64 && R == 4 && G > 2)
     return fail(GIRIH_EINVAL, "25-point FP64 tiles allow at most 2 row pairs per thread (registers)");
@@ -166,6 +167,8 @@ int run_sweep(Plan* p, int64_t T, void* u, void* u_prev, const void* coeffs, con
       a.cf[i] = (float)c[i];
     }
     a.zc = 64;
+    a.v16 = (p->bulk_layout &&
+             ((reinterpret_cast<uintptr_t>(u) | reinterpret_cast<uintptr_t>(u_prev)) & 15) == 0) ? 1 : 0;
     void* buf[2] = {u, u_prev};
     for (int64_t t = 0; t < T && e == cudaSuccess; ++t) {
       a.V = buf[t % 2];

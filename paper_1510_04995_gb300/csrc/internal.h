@@ -24,6 +24,7 @@ struct NaiveArgs {
   double c[5];
   float cf[5];  // the same constants rounded to FP32 (FP32 kernels read these: no conversion on device)
   int32_t zc;  // z planes per block
+  int32_t v16;  // rows of 16-byte multiples and 16-byte aligned buffers: 16-byte staging
 };
 cudaError_t launch_naive_step(int stencil, int dtype, const NaiveArgs& a, cudaStream_t st);
 int naive_block_rows(int stencil, int dtype);  // threads per block = 32 * rows
@@ -80,11 +81,16 @@ inline int mwd_max_threads(int G, int lbf) {
   const int t = 1024 / (G * lbf);
   return t > 1024 ? 1024 : t;
 }
-// Planes are staged this many wavefront steps ahead of use (element path / bulk-copy path).
-#define MWD_PREFETCH 2
+// Planes are staged this many wavefront steps ahead of use (cp.async paths / bulk-copy path).
+// A cp.async group committed at step k is waited for (wait_group PD-2) before the barrier that
+// ends step k+PD-1, so it has PD-1 steps to land.
+#define MWD_PREFETCH 3
 #define MWD_PREFETCH_BULK 3
-// Extra ring planes per wavefront width in the bulk-copy path: a slot is restaged at least two
-// steps after its plane was written back, so only older write-backs need to have read it.
+// Extra ring planes per wavefront width, so that a slot is restaged only after every write-back
+// that may still read it: cp.async paths -- the previous step's write-back, which threads of the
+// block that have not yet passed that step's barrier may still be doing; bulk-copy path -- the
+// write-back copies of the two previous steps.
+#define MWD_PLAIN_SLACK 1
 #define MWD_BULK_SLACK 2
 
 

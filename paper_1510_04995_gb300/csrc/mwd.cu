@@ -26,7 +26,7 @@ MwdShape mwd_shape(int stencil, int dtype, int dw, int nf, int XW, int mv) {
   MwdShape s;
   const bool bulk = mv == MV_BULK;
   const int pd = bulk ? MWD_PREFETCH_BULK : MWD_PREFETCH;
-  s.NZ = (pd + 1) * nf + R + (R > nf ? R : nf) + (H - 2) * K + (bulk ? MWD_BULK_SLACK * nf : 0);
+  s.NZ = (pd + 1) * nf + R + (R > nf ? R : nf) + (H - 2) * K + (bulk ? MWD_BULK_SLACK : MWD_PLAIN_SLACK) * nf;
   s.YW = dw + 2 * R;
   // shared row: [halo | slab | halo], rows starting on 16-byte boundaries.  Element path: the
   // slab starts on a 16-byte boundary when groups are vectors.  Vector path: HM = R rounded up

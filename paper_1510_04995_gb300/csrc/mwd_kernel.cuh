@@ -476,7 +476,7 @@ __global__ void __launch_bounds__(1024 / (G * mwd_lbf<S, T>())) mwd_fed_kernel(c
       // counts (acquire), i.e. for the blocks whose pushes it receives and into whose shared
       // memory it pushes.  Neighbours thus stay within one step of each other, the same overlap
       // the cluster barrier allows, without waiting for the rest of the cluster.
-      cp_async_wait_group<PD - 1>();
+      cp_async_wait_group<PD - 2>();  // the planes of step w+1 are complete
       if (warp == 0) {
         named_bar_sync(NT);
         if (lane == 0) {
@@ -507,7 +507,7 @@ __global__ void __launch_bounds__(1024 / (G * mwd_lbf<S, T>())) mwd_fed_kernel(c
       }
       __syncthreads();
     } else {
-      cp_async_wait_group<PD - 1>();
+      cp_async_wait_group<PD - 2>();  // the planes of step w+1 are complete
       if (C > 1) cluster_arrive_release();
       else __syncthreads();  // a single block needs no second barrier
       if (xw > 0) {

@@ -43,11 +43,6 @@ constexpr int vec_lbf() {
 }
 constexpr int kVecItems = 4;  // precomputed staging / write-back items per thread
 
-// 16-byte copy global -> shared, completing with the thread's cp.async groups.
-__device__ __forceinline__ void cp_async16(void* smem_dst, const void* g) {
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_addr(smem_dst)), "l"(g) : "memory");
-}
-
 template <int S, typename T, int G, bool TMA>
 __global__ void __launch_bounds__(1024 / (G * vec_lbf<S>()), 1) mwd_vec_kernel(const MwdArgs A) {
   constexpr int R = Traits<S>::R;
@@ -220,7 +215,7 @@ __global__ void __launch_bounds__(1024 / (G * vec_lbf<S>()), 1) mwd_vec_kernel(c
       if (s_src[i] < 0) continue;
       const int p = s_src[i] >> 30;
       const T* src = reinterpret_cast<const T*>(p ? gb1 : gb0) + zo + (s_src[i] & 0x3fffffff);
-      cp_async16(dst + s_dst[i], src);
+      cp_async16_cg(dst + s_dst[i], src);
     }
     for (int idx = tid + kVecItems * NT; idx < nstage; idx += NT) {  // tiles wider than the items
       const int p = idx / (nrow * nch);
@@ -228,7 +223,7 @@ __global__ void __launch_bounds__(1024 / (G * vec_lbf<S>()), 1) mwd_vec_kernel(c
       const int r = rem / nch, ch = rem - r * nch;
       const int y = ylo + r, pc = cb + ch * A16;
       const T* src = reinterpret_cast<const T*>(p ? gb1 : gb0) + zo + (int64_t)(y + R) * ldx + pc;
-      cp_async16(dst + p * be + (y - Y0) * XT + (pc - (pc0 - HM)), src);
+      cp_async16_cg(dst + p * be + (y - Y0) * XT + (pc - (pc0 - HM)), src);
     }
   };
   auto write_back = [&](int z, int slot) {
@@ -428,6 +423,10 @@ __global__ void __launch_bounds__(1024 / (G * vec_lbf<S>()), 1) mwd_vec_kernel(c
 
     if constexpr (TMA) {
       fence_proxy_async();  // this step's shared-memory results become visible to bulk stores
+      // the planes of step w+1 (staged PD-1 steps ago) have landed before anyone may pass this
+      // step's barrier
+      if (warp == 0 && active)
+        for (int f = 0; f < nf; ++f) tma_wait((w + 1) * nf + R + f);
       cluster_arrive_release();
       if (warp == 0 && active) {
         // restage first: the slots of step w+PD were last written back two or more steps ago, so
@@ -447,11 +446,10 @@ __global__ void __launch_bounds__(1024 / (G * vec_lbf<S>()), 1) mwd_vec_kernel(c
             bulk_commit();
           }
         }
-        for (int f = 0; f < nf; ++f) tma_wait((w + 1) * nf + R + f);  // planes of step w+1
       }
       cluster_wait_acquire();
     } else if (relaxed) {
-      cp_async_wait_group<PD - 1>();
+      cp_async_wait_group<PD - 2>();  // the planes of step w+1 are complete
       if (warp == 0) {
         named_bar_sync(NT);
         if (lane == 0) {
@@ -480,7 +478,7 @@ __global__ void __launch_bounds__(1024 / (G * vec_lbf<S>()), 1) mwd_vec_kernel(c
       }
       __syncthreads();
     } else {
-      cp_async_wait_group<PD - 1>();
+      cp_async_wait_group<PD - 2>();  // the planes of step w+1 are complete
       if (C > 1) cluster_arrive_release();
       else __syncthreads();
       if (w > 0)

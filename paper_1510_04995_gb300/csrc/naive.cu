@@ -5,7 +5,6 @@
 // columns (rows ty and ty+8).  The tile's planes (with their R-wide halo) are staged into a
 // shared-memory ring by cp.async several planes ahead of use; each thread keeps its columns'
 // 2R+1 values along z in registers (rotated as the block walks up in z).  Every input is read
-// from HBM once per step (halo re-reads hit L2), every output written once.  Every input is read
 // from HBM once per step (halo re-reads hit L2), every output written once: 2s bytes per LUP
 // for the 7-point constant stencil, s = element size.
 #include <algorithm>
@@ -15,13 +14,12 @@
 
 namespace girih {
 
-template <int S, typename T>
+template <int S, typename T, int TW>
 struct NaiveAcc {
-  const T* tc;       // centre of this thread's cell in the shared plane tile
+  const T* tc;       // centre of this thread's cell in the shared plane tile (row stride TW)
   const T* w;        // register window, w[R] = centre
   const T* kv;       // coefficient values of this point (variable stencils)
   T uc;              // level t-1 centre (second order)
-  static constexpr int TW = 32 + 2 * Traits<S>::R;
   __device__ __forceinline__ T c() const { return w[Traits<S>::R]; }
   __device__ __forceinline__ T x(int d) const { return tc[d]; }
   __device__ __forceinline__ T y(int d) const { return tc[d * TW]; }
@@ -32,16 +30,20 @@ struct NaiveAcc {
 
 // Block = 32 x TY threads over a 32 x 2TY tile of (x, y) columns and a chunk of z planes; each
 // thread owns rows ty and ty + TY.  The tile's planes (with the R-wide halo) stream through a
-// ring of NP shared-memory slots filled by cp.async PD planes ahead of use (one commit group per
-// plane), so that many loads are in flight without holding registers.  The z window of each
-// owned column stays in registers; its new value and the x/y neighbours come from the ring.
-// One barrier per plane.
-template <int S, typename T, int TY, int PD>
+// ring of NP shared-memory slots filled PD planes ahead of use (one commit group per plane).
+// The z window of each owned column stays in registers; its new value and the x/y neighbours
+// come from the ring.  One barrier per plane.
+//
+// V16 (rows of 16-byte multiples, 16-byte aligned buffers): 16-byte cp.async.cg chunks, the tile
+// row widened to whole chunks.  Otherwise: element cp.async.
+template <int S, typename T, int TY, int PD, bool V16>
 __global__ void __launch_bounds__(32 * TY) naive_kernel(const NaiveArgs a) {
   constexpr int R = Traits<S>::R;
   constexpr int NC = Traits<S>::NCOEF;
   constexpr int ROWS = 2 * TY;
-  constexpr int TXW = 32 + 2 * R, TYW = ROWS + 2 * R, TP = TXW * TYW;
+  constexpr int A16 = 16 / (int)sizeof(T);
+  constexpr int TXW = V16 ? (32 + 2 * R + A16 - 1) / A16 * A16 : 32 + 2 * R;  // shared row width
+  constexpr int TYW = ROWS + 2 * R, TP = TXW * TYW;
   // ring slots: the first window needs planes 0..2R plus PD staged ahead (2R+PD+1 at once); in
   // the steady state planes z+R .. z+2R+PD+1 are live (R+PD+2), which is never more
   constexpr int NP = 2 * R + PD + 1;
@@ -67,28 +69,37 @@ __global__ void __launch_bounds__(32 * TY) naive_kernel(const NaiveArgs a) {
   const T* Vb = V + (int64_t)z0 * plane + (int64_t)by * ldx + bx;  // padded plane z0, tile corner
   T* Ub = U + (int64_t)(z0 + R) * plane + (int64_t)(by + R) * ldx + (bx + R);
 
-  // This thread's cells of one staged plane (fixed for the whole z walk): shared offset within a
-  // ring slot and offset within a global plane relative to the tile corner, -1 = none.
-  constexpr int CPT = (TP + 32 * TY - 1) / (32 * TY);
+  // This thread's items of one staged plane (fixed for the whole z walk): shared offset within a
+  // ring slot and offset within a global plane relative to the tile corner, -1 = none.  An item
+  // is one element, or (V16) one 16-byte chunk of a tile row inside the padded row [0, ldx).
+  constexpr int W = V16 ? A16 : 1;             // elements per item
+  constexpr int NCH = TXW / W;                 // items per tile row
+  constexpr int CPT = (NCH * TYW + 32 * TY - 1) / (32 * TY);
   int so[CPT], go[CPT];
 #pragma unroll
   for (int k = 0; k < CPT; ++k) {
     const int i = tid + k * 32 * TY;
-    const int r = i / TXW, c = i - r * TXW;
-    const bool ok = i < TP && r < trows && c < tcols;
-    so[k] = ok ? i : -1;
+    const int r = i / NCH, c = (i - r * NCH) * W;
+    const bool ok = i < NCH * TYW && r < trows && (V16 ? bx + c < ldx : c < tcols);
+    so[k] = ok ? r * TXW + c : -1;
     go[k] = ok ? r * ldx + c : 0;
   }
-  constexpr int UPT = (ROWS * 32 + 32 * TY - 1) / (32 * TY);  // level t-1 centres per thread
+  // level t-1 centres (second order, R = 4: interior columns bx+R.. start on a 16-byte boundary)
+  constexpr int UNC = 32 / W;                  // items per centre row
+  constexpr int UPT = (ROWS * UNC + 32 * TY - 1) / (32 * TY);
   int uso[UPT], ugo[UPT];
 #pragma unroll
   for (int k = 0; k < UPT; ++k) {
     const int i = tid + k * 32 * TY;
-    const int r = i / 32, c = i - r * 32;
-    const bool ok = Traits<S>::ORDER2 && i < ROWS * 32 && by + r < ny && bx + c < nx;
-    uso[k] = ok ? i : -1;
+    const int r = i / UNC, c = (i - r * UNC) * W;
+    const bool ok = Traits<S>::ORDER2 && i < ROWS * UNC && by + r < ny && (V16 ? bx + R + c < ldx : bx + c < nx);
+    uso[k] = ok ? r * 32 + c : -1;
     ugo[k] = ok ? r * ldx + c : 0;
   }
+  auto copy = [&](T* dst, const T* src) {
+    if constexpr (V16) cp_async16_cg(dst, src);
+    else cp_async(dst, src);
+  };
 
   // stage padded plane z0 + q (q = 0 .. nzb + 2R - 1) into ring slot q % NP
   auto stage = [&](int q) {
@@ -97,7 +108,7 @@ __global__ void __launch_bounds__(32 * TY) naive_kernel(const NaiveArgs a) {
       const T* src = Vb + (int64_t)q * plane;
 #pragma unroll
       for (int k = 0; k < CPT; ++k)
-        if (so[k] >= 0) cp_async(dst + so[k], src + go[k]);
+        if (so[k] >= 0) copy(dst + so[k], src + go[k]);
       if constexpr (Traits<S>::ORDER2) {
         // level t-1 centres of interior plane z0 + q - R (used when that plane is updated)
         const int zi = q - R;
@@ -106,7 +117,7 @@ __global__ void __launch_bounds__(32 * TY) naive_kernel(const NaiveArgs a) {
           const T* us = Ub + (int64_t)zi * plane;
 #pragma unroll
           for (int k = 0; k < UPT; ++k)
-            if (uso[k] >= 0) cp_async(ud + uso[k], us + ugo[k]);
+            if (uso[k] >= 0) copy(ud + uso[k], us + ugo[k]);
         }
       }
     }
@@ -129,6 +140,8 @@ __global__ void __launch_bounds__(32 * TY) naive_kernel(const NaiveArgs a) {
 #pragma unroll
     for (int i = 0; i <= 2 * R; ++i) w[r][i] = ring[i * TP + cofs[r]];
   }
+  // every thread has its first window before the first in-loop staging overwrites slot 0
+  __syncthreads();
   // coefficients of the first plane, then one plane ahead
   T kv[2][NC > 0 ? NC : 1], kn[2][NC > 0 ? NC : 1];
   const int64_t gs = a.g.gstride;
@@ -155,7 +168,7 @@ __global__ void __launch_bounds__(32 * TY) naive_kernel(const NaiveArgs a) {
 #pragma unroll
     for (int r = 0; r < 2; ++r) {
       if (act[r]) {
-        NaiveAcc<S, T> acc{tl + cofs[r], w[r], kv[r], T(0)};
+        NaiveAcc<S, T, TXW> acc{tl + cofs[r], w[r], kv[r], T(0)};
         if constexpr (Traits<S>::ORDER2) acc.uc = uring[((zr + R) % NP) * (ROWS * 32) + (ty + r * TY) * 32 + tx];
         Ub[(int64_t)zr * plane + (ty + r * TY) * ldx + tx] = point_update<S, T>(acc, cst);
       }
@@ -181,20 +194,21 @@ int naive_block_rows(int, int) { return 2 * kTY; }
 template <int S>
 constexpr int naive_pd() { return Traits<S>::R == 1 ? 4 : 2; }
 
-template <int S, typename T>
+template <int S, typename T, bool V16>
 static size_t naive_smem() {
-  constexpr int R = Traits<S>::R, PD = naive_pd<S>();
-  constexpr int NP = 2 * R + PD + 1, TP = (32 + 2 * R) * (2 * kTY + 2 * R);
+  constexpr int R = Traits<S>::R, PD = naive_pd<S>(), A16 = 16 / (int)sizeof(T);
+  constexpr int TXW = V16 ? (32 + 2 * R + A16 - 1) / A16 * A16 : 32 + 2 * R;
+  constexpr int NP = 2 * R + PD + 1, TP = TXW * (2 * kTY + 2 * R);
   return sizeof(T) * ((size_t)NP * TP + (Traits<S>::ORDER2 ? (size_t)NP * 2 * kTY * 32 : 0));
 }
 
-template <int S, typename T>
+template <int S, typename T, bool V16>
 static cudaError_t launch_one(const NaiveArgs& a, cudaStream_t st) {
   dim3 block(32, kTY);
   dim3 grid((unsigned)((a.g.nx + 31) / 32), (unsigned)((a.g.ny + 2 * kTY - 1) / (2 * kTY)),
             (unsigned)((a.g.nz + a.zc - 1) / a.zc));
-  const size_t sm = naive_smem<S, T>();
-  auto k = naive_kernel<S, T, kTY, naive_pd<S>()>;
+  const size_t sm = naive_smem<S, T, V16>();
+  auto k = naive_kernel<S, T, kTY, naive_pd<S>(), V16>;
   if (sm > 48 * 1024) {
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
@@ -203,13 +217,18 @@ static cudaError_t launch_one(const NaiveArgs& a, cudaStream_t st) {
   return cudaGetLastError();
 }
 
+template <int S, typename T>
+static cudaError_t launch_v(const NaiveArgs& a, cudaStream_t st) {
+  return a.v16 ? launch_one<S, T, true>(a, st) : launch_one<S, T, false>(a, st);
+}
+
 cudaError_t launch_naive_step(int stencil, int dtype, const NaiveArgs& a, cudaStream_t st) {
   const bool f64 = dtype == GIRIH_F64;
   switch (stencil) {
-    case 0: return f64 ? launch_one<0, double>(a, st) : launch_one<0, float>(a, st);
-    case 1: return f64 ? launch_one<1, double>(a, st) : launch_one<1, float>(a, st);
-    case 2: return f64 ? launch_one<2, double>(a, st) : launch_one<2, float>(a, st);
-    default: return f64 ? launch_one<3, double>(a, st) : launch_one<3, float>(a, st);
+    case 0: return f64 ? launch_v<0, double>(a, st) : launch_v<0, float>(a, st);
+    case 1: return f64 ? launch_v<1, double>(a, st) : launch_v<1, float>(a, st);
+    case 2: return f64 ? launch_v<2, double>(a, st) : launch_v<2, float>(a, st);
+    default: return f64 ? launch_v<3, double>(a, st) : launch_v<3, float>(a, st);
   }
 }
 

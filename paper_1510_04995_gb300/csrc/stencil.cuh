@@ -130,6 +130,11 @@ __device__ __forceinline__ void cp_async(void* smem_dst, const float* g) {
 __device__ __forceinline__ void cp_async(void* smem_dst, const double* g) {
   asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(smem_addr(smem_dst)), "l"(g) : "memory");
 }
+// 16-byte copy global -> shared through L2 only (cp.async.cg), completing with the thread's
+// cp.async groups.  Both addresses must be 16-byte aligned.
+__device__ __forceinline__ void cp_async16_cg(void* smem_dst, const void* g) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_addr(smem_dst)), "l"(g) : "memory");
+}
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 // Wait until at most N of this thread's committed cp.async groups are still pending.

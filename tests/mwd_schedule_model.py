@@ -29,16 +29,18 @@ def vec_slab_width(nx, R, C, a16):
     return -(-w // a16) * a16
 
 
-PD = 2       # element path: planes staged this many steps ahead (cp.async groups, wait_group PD-1)
+PD = 3       # cp.async paths: planes staged this many steps ahead (a group issued at step k is
+             # waited for before the barrier ending step k+PD-1: in flight during steps k..k+PD-1)
 PD_BULK = 3  # bulk-copy path
 SLACK = 2    # bulk-copy path: extra ring planes per wavefront width
+SLACK_PLAIN = 1  # cp.async paths
 
 
 def shape(R, dw, nf, XW, bulk=False):
     H = dw // R
     K = R + nf
     pd = PD_BULK if bulk else PD
-    NZ = (pd + 1) * nf + R + max(R, nf) + (H - 2) * K + (SLACK * nf if bulk else 0)
+    NZ = (pd + 1) * nf + R + max(R, nf) + (H - 2) * K + (SLACK if bulk else SLACK_PLAIN) * nf
     return NZ, dw + 2 * R, -(-(XW + 2 * R) // 4) * 4
 
 
@@ -245,6 +247,15 @@ def simulate(R, second_order, nx, ny, nz, T, dw, nf, C, bulk=False, a16=4, vec=F
                                             wv[r] = wv[r][1:] + [rd((pin, (sl + R) % NZ, yy0 + r, xx), t)]
                                     for r in (0, 1):  # centre of each row is its window's middle
                                         check_read(tl["win"][key][r][R], t)
+                                    if vec:  # the vector kernel re-reads the 2R+1 planes of both rows
+                                        for r in (0, 1):
+                                            for d in range(-R, R + 1):
+                                                cell = (pin, (sl + d) % NZ, yy0 + r, xx)
+                                                if r == 0 or row1:
+                                                    rd(cell, t)
+                                                else:
+                                                    assert 0 <= cell[2] < YW, cell
+                                                    reads.setdefault((rank,) + cell, set()).add(item)
                                     for d in range(1, R + 1):
                                         rd((pin, sl, yy0 - d, xx), t)
                                         if d < R or row1:
@@ -278,9 +289,11 @@ def simulate(R, second_order, nx, ny, nz, T, dw, nf, C, bulk=False, a16=4, vec=F
                     assert cell not in busy and cell not in wb_reads, ("write vs load/write-back", cell)
                     for old in tl["prev_wb"][(0 if bulk else 1):]:
                         assert cell not in old, ("write vs a recent step's write-back", cell)
-                if bulk:
-                    for old in tl["prev_wb"]:
-                        assert not (old & loaded), "slot restaged while a recent write-back may still read it"
+                # a slot restaged in this step may still be read by a write-back of the previous
+                # step (threads of the block that have not yet passed that step's barrier), and in
+                # the bulk-copy path by the write-back copies of the two previous steps
+                for old in tl["prev_wb"][(0 if bulk else 1):]:
+                    assert not (old & loaded), "slot restaged while a recent write-back may still read it"
                 tl["prev_wb"] = [tl["prev_wb"][1], wb_reads]
                 for cell in busy:
                     assert cell not in reads and cell not in wb_reads, ("slot read while its load is in flight", cell)
