@@ -45,6 +45,12 @@ DEFAULT = "7pt_const_f64_512"
 STENCIL_NAME = {0: "7-point constant", 1: "7-point variable", 2: "25-point constant", 3: "25-point variable"}
 # FP instructions per LUP of the point update (explicitly rounded ops, see csrc/stencil.cuh)
 INSTR_PER_LUP = {0: 7, 1: 7, 2: 28, 3: 28}
+# DRAM bytes per LUP measured by ncu (dram__bytes_read.sum + dram__bytes_write.sum of one launch
+# / LUPs of that launch) for a kernel on a smaller grid of the same workload, with the summary it
+# comes from; the roofline's "traffic" scales it to one launch of the benchmark grid
+MEASURED_BYTES_PER_LUP = {
+    ("naive", 0, "f64"): (15.61, "profiles/naive_7pt_const_f64_512x384x256.md"),
+}
 # domain-sized streams N_D of the code-balance model and the spatial minimum bytes per LUP (in elements)
 ND = {0: 2, 1: 9, 2: 2, 3: 15}
 SPATIAL_ELEMS = {0: 2, 1: 9, 2: 3, 3: 16}
@@ -140,7 +146,9 @@ def cpu_baseline(stencil, nx, ny, nz, budget_s=10.0, max_T=64, min_T=1):
     t1 = time.perf_counter() - t0
     T = int(max(min_T, min(max_T, budget_s / max(t1, 1e-6))))
     # repeat sweeps of T steps (the workload's T at most) until about budget_s of CPU time
-    reps = int(max(1, min(50, budget_s / max(t1 * T, 1e-6))))
+    t0 = time.perf_counter()
+    oracle.sweep(stencil, u, up, co, c, T, nx, ny, nz, nthreads=cores)
+    reps = int(max(1, min(50, budget_s / max(time.perf_counter() - t0, 1e-6))))
     t0 = time.perf_counter()
     for _ in range(reps):
         oracle.sweep(stencil, u, up, co, c, T, nx, ny, nz, nthreads=cores)
@@ -301,12 +309,18 @@ def main():
     # except the exchange kernel for odd T, which the default workloads do not have)
     launches = p.launch_count(cfg)
     per_gpu = lups * args.steps / (ms * 1e-3)
+    algo_name = "mwd" if cfg.algo == girih.MWD else "naive"
+    meas = MEASURED_BYTES_PER_LUP.get((algo_name, stencil, dtype))
+    # one launch of the naive sweep is one time step over the grid; of the blocked sweep, one
+    # diamond row (the sweep's LUPs over its launches, on average)
+    lups_per_launch = nx * ny * nz if cfg.algo == girih.NAIVE else lups / max(launches, 1)
+    traffic = meas[0] * lups_per_launch if meas else None
     if dtype == "f64":
         # FP64 pipe: 152 SMs x 2 DFMA per clock (1.25 TFLOP/s nominal) at the maximum SM clock
         peak_inst = 152 * 2 * float(peaks.get("sm_max_mhz", 2070.0)) * 1e6
         achieved = per_gpu * INSTR_PER_LUP[stencil]
         roof = {"bound": "alu", "achieved": achieved * 1e-12, "peak": peak_inst * 1e-12,
-                "unit": "Tinst/s", "frac": achieved / peak_inst, "traffic": None,
+                "unit": "Tinst/s", "frac": achieved / peak_inst, "traffic": traffic,
                 "note": "FP64 instructions/s (one per explicitly rounded op, 7 or 28 per LUP) vs 152 SMs x 2 DFMA/clk "
                         f"x max SM clock ({src} peaks file clock); HBM is not the bound"}
     else:
@@ -314,8 +328,11 @@ def main():
               if cfg.algo == girih.MWD else SPATIAL_ELEMS[stencil] * elem)
         achieved = per_gpu * bc
         roof = {"bound": "hbm", "achieved": achieved * 1e-9, "peak": float(peaks["hbm_gbs"]), "unit": "GB/s",
-                "frac": achieved * 1e-9 / float(peaks["hbm_gbs"]), "traffic": None,
+                "frac": achieved * 1e-9 / float(peaks["hbm_gbs"]), "traffic": traffic,
                 "note": f"algorithmic bytes = model code balance {bc:.2f} B/LUP x LUPs ({src} HBM peak)"}
+
+    if meas:
+        roof["traffic_source"] = f"{meas[1]}: {meas[0]} DRAM bytes/LUP x {lups_per_launch:.4g} LUPs per launch"
 
     e2e = None
     if not args.no_e2e:

@@ -26,7 +26,7 @@ import time
 
 import numpy as np
 
-from . import (F32, F64, FED, FED_BULK, FED_ELEM, MLP_FEATURES, MWD, NAIVE, RELAXED, Config, TuneRow, check,
+from . import (F32, F64, FED, FED_BULK, MLP_FEATURES, MWD, NAIVE, RELAXED, Config, TuneRow, check,
                config, config_array, lib, plan)
 
 # The 12 non-cubic grids of the learned-tuner sweep (nx, ny, nz), and the held-out ones (#3, #7, #10).
@@ -44,16 +44,17 @@ def _dt(d):
 
 def space(p) -> list:
     """The experiment's search space for a plan: the naive sweep and the feasible blocked sweeps
-    with diamond widths 2R..16R, wavefront widths 1 and 2, clusters 1..16, 256 or 512 threads and
-    the variants (FED and FED_BULK, FED on the element path, RELAXED where the cluster has more
-    than one block)."""
+    with diamond widths 2R, 4R, 8R, 16R, wavefront widths 1 and 2, clusters 1, 4, 8, 16, 256 or
+    512 threads, and the FED / FED_BULK data paths (RELAXED where the cluster has more than one
+    block, with 512 threads)."""
     R = p.R
     out = [config(NAIVE, 0, 1, 1, 256, FED)]
-    for dw in sorted({2 * R, 4 * R, 6 * R, 8 * R, 12 * R, 16 * R}):
+    for dw in (2 * R, 4 * R, 8 * R, 16 * R):
         for nf in (1, 2):
-            for cl in (1, 2, 4, 8, 16):
+            for cl in (1, 4, 8, 16):
                 for th in (256, 512):
-                    for v in ((FED, RELAXED, FED_BULK, FED_ELEM) if cl > 1 else (FED, FED_BULK, FED_ELEM)):
+                    vs = [FED, FED_BULK] + ([RELAXED] if cl > 1 and th == 512 else [])
+                    for v in vs:
                         c = config(MWD, dw, nf, cl, th, v)
                         if p.feasible(c):
                             out.append(c)
