@@ -78,3 +78,25 @@ def test_explicit_candidate_list(tmp_path):
     assert nm.value == 3
     bad, nb = girih.config_array([girih.config(girih.MWD, dw=3)])
     assert girih.lib().girih_tune_exhaustive(p.handle, bad, nb, 0.5, 8, None, ctypes.byref(best), ctypes.byref(nm)) == 1
+
+
+MODEL = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "paper_1510_04995_gb300",
+                     "learned_model", "mlp_params.npy")
+
+
+@pytest.mark.skipif(not os.path.exists(MODEL), reason="no trained network committed")
+@pytest.mark.parametrize("stencil,dtype", [(1, "f32"), (2, "f64")])
+def test_trained_network_gains_over_default_configuration(stencil, dtype):
+    """The network trained on the exhaustive tuner's timings (learned_model/) on a grid it was not
+    trained on: its top-5 candidates, measured, against the method without the network -- the
+    plan's default configuration (widest diamond whose tile fits, Sect. 4.2.2's cache-block
+    pruning) -- measured the same way."""
+    from paper_1510_04995_gb300 import learned
+    nx, ny, nz = learned.GRIDS[learned.HELD_OUT[0]]
+    p = girih.plan(stencil, nx, ny, nz, dtype=dtype, T=16)
+    default = girih.TuneRow()
+    girih.check(girih.lib().girih_tune_measure(p.handle, ctypes.byref(p.config), 0.1, 16, ctypes.byref(default)))
+    params = np.load(MODEL)
+    row, nm, _ = learned.tune(p, params, k=5, tol=0.1, max_steps=16)
+    assert nm == 5
+    assert row.glups >= default.glups, (row.glups, default.glups, row.cfg, p.config)
