@@ -155,6 +155,15 @@ GIRIH_API int girih_run_host(girih_plan_t plan, void* u_host, void* u_prev_host,
  * GIRIH_EKERNEL.  Clears the plan's error word.  girih_run_host calls it itself.            */
 GIRIH_API int girih_status(girih_plan_t plan, void* stream);
 
+/* Failure-path check of the device-side bounded waits (no counterpart in the paper; Sect. 4.2.1's
+ * relaxed synchronisation is the wait being checked): enqueues on `stream` one block that runs
+ * the RELAXED neighbour wait on progress counters nothing advances, limited to limit_ns
+ * nanoseconds of the GPU's global timer (1e3 .. 2e9).  The wait gives up and sets the plan's
+ * error word, so a following girih_status returns GIRIH_ETIMEOUT; the context stays usable.
+ * Returns GIRIH_EINVAL for a NULL plan or a limit outside the range (nothing enqueued), or
+ * GIRIH_ECUDA if the launch fails.                                                          */
+GIRIH_API int girih_check_bounded_wait(girih_plan_t plan, int64_t limit_ns, void* stream);
+
 /* Elements of one padded grid for the plan ((nz+2R)*(ny+2R)*ldx) and the halo width R. */
 GIRIH_API int girih_plan_layout(girih_plan_t plan, int64_t* elems_per_grid, int32_t* radius, int64_t* ldx);
 

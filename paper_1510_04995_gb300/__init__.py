@@ -84,6 +84,7 @@ _SIGS = {
     "girih_last_error": (ctypes.c_char_p, []),
     "girih_model_cache_block": (_F64, [_F64, _I32, _I32, _I32, _I32]),
     "girih_model_code_balance": (_F64, [_I32, _I32, _I32, _I32]),
+    "girih_check_bounded_wait": (ctypes.c_int, [_VP, _I64, _VP]),
     "girih_tune_candidates": (ctypes.c_int, [_VP, ctypes.POINTER(Config), _I32, ctypes.POINTER(_I32)]),
     "girih_tune_measure": (ctypes.c_int, [_VP, ctypes.POINTER(Config), _F64, _I64, ctypes.POINTER(TuneRow)]),
     "girih_tune_exhaustive": (ctypes.c_int, [_VP, ctypes.POINTER(Config), _I32, _F64, _I64, ctypes.c_char_p,

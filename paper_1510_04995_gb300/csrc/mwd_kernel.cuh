@@ -172,6 +172,21 @@ __device__ __forceinline__ uint64_t global_ns() {
 // arrived after this long sets GIRIH_ETIMEOUT in the error word and the kernel carries on.
 constexpr uint64_t kMbarWaitNs = 2000000000ull;
 
+// RELAXED hand-off: wait until the progress counters of the block's existing x neighbours
+// (prog[0] left, prog[1] right, written by them with release semantics) reach `need`, for at
+// most limit_ns of the global timer.  On timeout sets GIRIH_ETIMEOUT in *err and returns false.
+__device__ __forceinline__ bool wait_counts(const int* prog, bool left, bool right, uint32_t need,
+                                            uint64_t limit_ns, int* err) {
+  const uint64_t t0 = global_ns();
+  while ((left && ld_acquire_cluster_u32(&prog[0]) < need) || (right && ld_acquire_cluster_u32(&prog[1]) < need)) {
+    if (global_ns() - t0 > limit_ns) {
+      atomicOr(err, GIRIH_ETIMEOUT);
+      return false;
+    }
+  }
+  return true;
+}
+
 template <int N>
 __device__ __forceinline__ void bulk_wait_read_n() {
   asm volatile("cp.async.bulk.wait_group.read %0;" ::"n"(N) : "memory");
@@ -494,17 +509,8 @@ __global__ void __launch_bounds__(1024 / (G * mwd_lbf<S, T>())) mwd_fed_kernel(c
         for (int f = 0; f < nf; ++f, ++lz, lsl = (lsl + 1 == NZ) ? 0 : lsl + 1) plain_stage(lz, lsl);
       }
       cp_async_commit();
-      if (tid == 0) {  // bounded wait for both neighbours; a timeout sets the error word
-        const uint32_t need = (uint32_t)(w + 1);
-        const uint64_t t0 = global_ns();
-        while ((rank > 0 && ld_acquire_cluster_u32(&prog[0]) < need) ||
-               (rank < C - 1 && ld_acquire_cluster_u32(&prog[1]) < need)) {
-          if (global_ns() - t0 > kMbarWaitNs) {
-            atomicOr(A.err, GIRIH_ETIMEOUT);
-            break;
-          }
-        }
-      }
+      if (tid == 0)  // bounded wait for both neighbours; a timeout sets the error word
+        wait_counts(prog, rank > 0, rank < C - 1, (uint32_t)(w + 1), kMbarWaitNs, A.err);
       __syncthreads();
     } else {
       cp_async_wait_group<PD - 2>();  // the planes of step w+1 are complete

@@ -14,8 +14,11 @@
 //    costs fewer issue slots than sliding a register window, and frees the registers.
 //  * Both rows of a row pair are always computed (reads clamped inside the tile); the second
 //    row's stores are predicated, so a group's update is straight-line code.
-//  * Data movement, two modes.  Plain: every thread stages 16-byte chunks with cp.async and
-//    writes back 16-byte chunks with vector stores (work items precomputed per thread).  TMA
+//  * Data movement, two modes.  Plain: every thread stages 16-byte chunks with cp.async (global
+//    pointers and shared offsets precomputed per thread, only its valid items visited) and
+//    writes back 16-byte chunks with vector stores.  (Write-back by bulk stores from warp 0, which
+//    spares the barrier's release the wait for generic stores, measured 26 % slower here: the
+//    per-thread fence.proxy.async and warp 0's serial issue cost more than they saved.)  TMA
 //    (FED_BULK): between the two halves of each step's cluster barrier, warp 0 moves whole rows
 //    with the bulk-copy engine, global->shared completing on one mbarrier per ring slot (bounded
 //    waits: a timeout sets the error word) and shared->global in bulk groups; the computing
@@ -170,19 +173,24 @@ __global__ void __launch_bounds__(1024 / (G * vec_lbf<S>()), 1) mwd_vec_kernel(c
   const int cb = max(pc0 - HM, 0), ce = min(pc0 + XW + HM, ldx);
   const int nch = active ? (ce - cb) / A16 : 0;
   const int nstage = 2 * nrow * nch;
-  int s_src[kVecItems], s_dst[kVecItems];
+  // this thread's items: global address at plane 0 (buffer included) and shared byte offset in
+  // slot 0; items tid, tid + NT, ... so the valid ones are a prefix of length n_s
+  const T* s_ptr[kVecItems];
+  uint32_t s_off[kVecItems];
+  int n_s = 0;
 #pragma unroll
   for (int i = 0; i < kVecItems; ++i) {
     const int idx = tid + i * NT;
-    s_src[i] = -1;
-    s_dst[i] = 0;
+    s_ptr[i] = static_cast<const T*>(A.buf0);
+    s_off[i] = 0;
     if (idx < nstage) {
       const int p = idx / (nrow * nch);
       const int rem = idx - p * nrow * nch;
       const int r = rem / nch, ch = rem - r * nch;
       const int y = ylo + r, pc = cb + ch * A16;
-      s_src[i] = (p << 30) | ((y + R) * ldx + pc);  // buffer in bit 30 (plane offsets < 2^30)
-      s_dst[i] = p * be + (y - Y0) * XT + (pc - (pc0 - HM));
+      s_ptr[i] = static_cast<const T*>(p ? A.buf1 : A.buf0) + (int64_t)(y + R) * ldx + pc;
+      s_off[i] = (uint32_t)((p * be + (y - Y0) * XT + (pc - (pc0 - HM))) * (int)sizeof(T));
+      n_s = i + 1;
     }
   }
   // ---- write-back items: (row of the diamond's projection, 16-byte chunk of the owned columns) ----
@@ -206,26 +214,24 @@ __global__ void __launch_bounds__(1024 / (G * vec_lbf<S>()), 1) mwd_vec_kernel(c
 
   const char* gb0 = static_cast<const char*>(A.buf0);
   const char* gb1 = static_cast<const char*>(A.buf1);
+  const uint32_t sm_u32 = smem_addr(sm);
   auto stage = [&](int z, int slot) {
     if (z < -R || z >= nz + R) return;
     const int64_t zo = (int64_t)(z + R) * gplane;
-    T* dst = sm + slot * pe;
+    const uint32_t dst = sm_u32 + (uint32_t)(slot * pe * (int)sizeof(T));
 #pragma unroll
-    for (int i = 0; i < kVecItems; ++i) {
-      if (s_src[i] < 0) continue;
-      const int p = s_src[i] >> 30;
-      const T* src = reinterpret_cast<const T*>(p ? gb1 : gb0) + zo + (s_src[i] & 0x3fffffff);
-      cp_async16_cg(dst + s_dst[i], src);
-    }
+    for (int i = 0; i < kVecItems; ++i)
+      if (i < n_s) cp_async16_cg_u32(dst + s_off[i], s_ptr[i] + zo);
     for (int idx = tid + kVecItems * NT; idx < nstage; idx += NT) {  // tiles wider than the items
       const int p = idx / (nrow * nch);
       const int rem = idx - p * nrow * nch;
       const int r = rem / nch, ch = rem - r * nch;
       const int y = ylo + r, pc = cb + ch * A16;
       const T* src = reinterpret_cast<const T*>(p ? gb1 : gb0) + zo + (int64_t)(y + R) * ldx + pc;
-      cp_async16_cg(dst + p * be + (y - Y0) * XT + (pc - (pc0 - HM)), src);
+      cp_async16_cg(sm + slot * pe + p * be + (y - Y0) * XT + (pc - (pc0 - HM)), src);
     }
   };
+
   auto write_back = [&](int z, int slot) {
     if (z < 0 || z >= nz) return;
     const int64_t zo = (int64_t)(z + R) * gplane;
@@ -465,17 +471,7 @@ __global__ void __launch_bounds__(1024 / (G * vec_lbf<S>()), 1) mwd_vec_kernel(c
         for (int f = 0; f < nf; ++f, ++wz, wsl = (wsl + 1 == NZ) ? 0 : wsl + 1) write_back(wz, wsl);
       for (int f = 0; f < nf; ++f, ++lz, lsl = (lsl + 1 == NZ) ? 0 : lsl + 1) stage(lz, lsl);
       cp_async_commit();
-      if (tid == 0) {
-        const uint32_t need = (uint32_t)(w + 1);
-        const uint64_t t0 = global_ns();
-        while ((rank > 0 && ld_acquire_cluster_u32(&prog[0]) < need) ||
-               (rank < C - 1 && ld_acquire_cluster_u32(&prog[1]) < need)) {
-          if (global_ns() - t0 > kMbarWaitNs) {
-            atomicOr(A.err, GIRIH_ETIMEOUT);
-            break;
-          }
-        }
-      }
+      if (tid == 0) wait_counts(prog, rank > 0, rank < C - 1, (uint32_t)(w + 1), kMbarWaitNs, A.err);
       __syncthreads();
     } else {
       cp_async_wait_group<PD - 2>();  // the planes of step w+1 are complete

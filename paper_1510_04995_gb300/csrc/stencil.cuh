@@ -135,6 +135,9 @@ __device__ __forceinline__ void cp_async(void* smem_dst, const double* g) {
 __device__ __forceinline__ void cp_async16_cg(void* smem_dst, const void* g) {
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_addr(smem_dst)), "l"(g) : "memory");
 }
+__device__ __forceinline__ void cp_async16_cg_u32(uint32_t smem_dst, const void* g) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_dst), "l"(g) : "memory");
+}
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 // Wait until at most N of this thread's committed cp.async groups are still pending.

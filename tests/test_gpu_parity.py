@@ -261,3 +261,23 @@ def test_relaxed_variant(stencil, dtype):
         fed = girih.config(girih.MWD, dw=cfg.dw, nf=cfg.nf, cluster=cfg.cluster, threads=cfg.threads)
         fu, _ = gpu_sweep(stencil, dtype, u, up, co, c, T, nx, ny, nz, fed)
         assert np.array_equal(bu, fu), (cl, cfg)
+
+
+def test_bounded_wait_times_out_and_reports():
+    """The failure path of the device-side waits: a RELAXED neighbour wait on counters nothing
+    advances gives up after its limit, girih_status reports GIRIH_ETIMEOUT once (and clears it),
+    and the context stays usable for a correct sweep afterwards."""
+    import ctypes
+    import time
+    p = girih.plan(girih.S7C, 40, 30, 20, dtype="f64", T=4)
+    t0 = time.perf_counter()
+    girih.check(girih.lib().girih_check_bounded_wait(p.handle, ctypes.c_int64(20_000_000), None))  # 20 ms
+    rc = girih.lib().girih_status(p.handle, None)
+    assert rc == 5, (rc, girih.last_error())  # GIRIH_ETIMEOUT
+    assert time.perf_counter() - t0 < 10.0
+    assert girih.lib().girih_status(p.handle, None) == 0  # cleared
+    assert girih.lib().girih_check_bounded_wait(p.handle, ctypes.c_int64(10), None) == 1  # limit out of range
+    u, up, co, c, ru, rup = _ref(0, 40, 30, 20, 4)
+    gu, _ = gpu_sweep(0, "f64", u, up, co, c, 4, 40, 30, 20,
+                      feasible_cfg(0, "f64", 40, 30, 20, dict(dw=4, nf=1, cluster=2, threads=256, variant=girih.RELAXED)))
+    assert normwise(gu, ru, 1) <= 1e-12
