@@ -198,17 +198,18 @@ __global__ void __launch_bounds__(1024 / (G * vec_lbf<S>()), 1) mwd_vec_kernel(c
   const int wb = pc0, wcend = min(pc0 + XW, ldx);
   const int nchw = active ? max((wcend - wb) / A16, 0) : 0;
   const int nwb = max(wy1 - wy0, 0) * nchw;
-  int w_sm[kVecItems], w_gl[kVecItems];
+  int w_sm[kVecItems], w_gl[kVecItems], n_w = 0;  // valid items are a prefix of length n_w
 #pragma unroll
   for (int i = 0; i < kVecItems; ++i) {
     const int idx = tid + i * NT;
-    w_sm[i] = -1;
+    w_sm[i] = 0;
     w_gl[i] = 0;
     if (idx < nwb) {
       const int r = idx / nchw, ch = idx - r * nchw;
       const int yy = wy0 + r - Y0;
       w_sm[i] = (row_mask[yy] << 28) | (yy * XT + HM + ch * A16);  // mask in bits 28-29
       w_gl[i] = (wy0 + r + R) * ldx + wb + ch * A16;
+      n_w = i + 1;
     }
   }
 
@@ -220,8 +221,10 @@ __global__ void __launch_bounds__(1024 / (G * vec_lbf<S>()), 1) mwd_vec_kernel(c
     const int64_t zo = (int64_t)(z + R) * gplane;
     const uint32_t dst = sm_u32 + (uint32_t)(slot * pe * (int)sizeof(T));
 #pragma unroll
-    for (int i = 0; i < kVecItems; ++i)
-      if (i < n_s) cp_async16_cg_u32(dst + s_off[i], s_ptr[i] + zo);
+    for (int i = 0; i < kVecItems; ++i) {
+      if (i >= n_s) break;
+      cp_async16_cg_u32(dst + s_off[i], s_ptr[i] + zo);
+    }
     for (int idx = tid + kVecItems * NT; idx < nstage; idx += NT) {  // tiles wider than the items
       const int p = idx / (nrow * nch);
       const int rem = idx - p * nrow * nch;
@@ -238,7 +241,7 @@ __global__ void __launch_bounds__(1024 / (G * vec_lbf<S>()), 1) mwd_vec_kernel(c
     const T* src = sm + slot * pe;
 #pragma unroll
     for (int i = 0; i < kVecItems; ++i) {
-      if (w_sm[i] < 0) continue;
+      if (i >= n_w) break;
       const int m = (w_sm[i] >> 28) & 3, so = w_sm[i] & 0x0fffffff;
       if (m & 1) *reinterpret_cast<V16*>(go0 + zo + w_gl[i]) = *reinterpret_cast<const V16*>(src + so);
       if (m & 2) *reinterpret_cast<V16*>(go1 + zo + w_gl[i]) = *reinterpret_cast<const V16*>(src + be + so);

@@ -8,6 +8,8 @@
 // from HBM once per step (halo re-reads hit L2), every output written once: 2s bytes per LUP
 // for the 7-point constant stencil, s = element size.
 #include <algorithm>
+#include <cmath>
+#include <type_traits>
 
 #include "internal.h"
 #include "stencil.cuh"
@@ -191,15 +193,35 @@ constexpr int kTY = 8;
 
 int naive_block_rows(int, int) { return 2 * kTY; }
 
-template <int S>
+// Planes staged ahead of use (4 for the 7-point stencils, 2 for the radius-4 ones, whose ring of
+// 2R+PD+1 planes is larger).
+template <int S, typename T>
 constexpr int naive_pd() { return Traits<S>::R == 1 ? 4 : 2; }
 
 template <int S, typename T, bool V16>
 static size_t naive_smem() {
-  constexpr int R = Traits<S>::R, PD = naive_pd<S>(), A16 = 16 / (int)sizeof(T);
+  constexpr int R = Traits<S>::R, PD = naive_pd<S, T>(), A16 = 16 / (int)sizeof(T);
   constexpr int TXW = V16 ? (32 + 2 * R + A16 - 1) / A16 * A16 : 32 + 2 * R;
   constexpr int NP = 2 * R + PD + 1, TP = TXW * (2 * kTY + 2 * R);
   return sizeof(T) * ((size_t)NP * TP + (Traits<S>::ORDER2 ? (size_t)NP * 2 * kTY * 32 : 0));
+}
+
+// Resident blocks per SM of one naive kernel instance (occupancy query, cached per instance).
+template <int S, typename T, bool V16>
+static int resident_blocks() {
+  static int n = -1;
+  if (n < 0) {
+    const size_t sm = naive_smem<S, T, V16>();
+    auto k = naive_kernel<S, T, kTY, naive_pd<S, T>(), V16>;
+    if (sm > 48 * 1024) cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    int b = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k, 32 * kTY, sm) != cudaSuccess || b < 1) {
+      cudaGetLastError();
+      b = 1;
+    }
+    n = b;
+  }
+  return n;
 }
 
 template <int S, typename T, bool V16>
@@ -208,7 +230,7 @@ static cudaError_t launch_one(const NaiveArgs& a, cudaStream_t st) {
   dim3 grid((unsigned)((a.g.nx + 31) / 32), (unsigned)((a.g.ny + 2 * kTY - 1) / (2 * kTY)),
             (unsigned)((a.g.nz + a.zc - 1) / a.zc));
   const size_t sm = naive_smem<S, T, V16>();
-  auto k = naive_kernel<S, T, kTY, naive_pd<S>(), V16>;
+  auto k = naive_kernel<S, T, kTY, naive_pd<S, T>(), V16>;
   if (sm > 48 * 1024) {
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
@@ -220,6 +242,44 @@ static cudaError_t launch_one(const NaiveArgs& a, cudaStream_t st) {
 template <int S, typename T>
 static cudaError_t launch_v(const NaiveArgs& a, cudaStream_t st) {
   return a.v16 ? launch_one<S, T, true>(a, st) : launch_one<S, T, false>(a, st);
+}
+
+int naive_resident_blocks(int stencil, int dtype, bool v16) {
+  const bool f64 = dtype == GIRIH_F64;
+  auto pick = [&](auto s_tag) -> int {
+    constexpr int S = decltype(s_tag)::value;
+    if (f64) return v16 ? resident_blocks<S, double, true>() : resident_blocks<S, double, false>();
+    return v16 ? resident_blocks<S, float, true>() : resident_blocks<S, float, false>();
+  };
+  switch (stencil) {
+    case 0: return pick(std::integral_constant<int, 0>());
+    case 1: return pick(std::integral_constant<int, 1>());
+    case 2: return pick(std::integral_constant<int, 2>());
+    default: return pick(std::integral_constant<int, 3>());
+  }
+}
+
+// z planes per block, 16 to 64: the chunk count that maximises (fraction of the last wave of
+// blocks that is used) x (fraction of each block's staged planes that it updates, zc/(zc+2R)),
+// i.e. fills the device's resident block slots in whole waves without re-reading too many
+// z-halo planes (fewer chunks on ties).
+int naive_z_chunk(int64_t nx, int64_t ny, int64_t nz, int R, int resident_per_sm, int sm_count) {
+  const int64_t tiles = ((nx + 31) / 32) * ((ny + 2 * kTY - 1) / (2 * kTY));
+  const int64_t slots = (int64_t)std::max(resident_per_sm, 1) * std::max(sm_count, 1);
+  const int64_t cmin = std::max<int64_t>((nz + 63) / 64, 1), cmax = std::max<int64_t>((nz + 15) / 16, cmin);
+  int64_t best_c = cmin;
+  double best_eff = -1.0;
+  for (int64_t c = cmin; c <= cmax; ++c) {
+    const int64_t zc = (nz + c - 1) / c;
+    const int64_t blocks = tiles * ((nz + zc - 1) / zc);
+    const double waves = (double)blocks / (double)slots;
+    const double eff = waves / std::ceil(waves) * (double)zc / (double)(zc + 2 * R);
+    if (eff > best_eff + 1e-9) {
+      best_eff = eff;
+      best_c = c;
+    }
+  }
+  return (int)((nz + best_c - 1) / best_c);
 }
 
 cudaError_t launch_naive_step(int stencil, int dtype, const NaiveArgs& a, cudaStream_t st) {
