@@ -160,6 +160,42 @@ def cpu_baseline(stencil, nx, ny, nz, budget_s=10.0, max_T=64, min_T=1):
                       f"{dt:.1f} s"}
 
 
+def accuracy(stencil, dtype, nx, ny, nz, T, ldx, configs, p, device):
+    """Error of the GPU sweep after the full T steps against the FP64 oracle run on the FP64
+    inputs: FP64 max normwise relative error (bound 1e-12), FP32 relative L2 error (bound 1e-5
+    for the 7-point stencils, 1e-4 for the 25-point ones)."""
+    import numpy as np
+    import torch
+
+    import oracle
+    import paper_1510_04995_gb300 as girih
+    from paper_1510_04995_gb300 import inputs
+    oracle.build()
+    R = inputs.RADIUS[stencil]
+    u, up, co, c = inputs.make_problem(stencil, nx, ny, nz)
+    ru, rup = u.copy(), up.copy()
+    oracle.sweep(stencil, ru, rup, co, c, T, nx, ny, nz, nthreads=len(os.sched_getaffinity(0)))
+    ref = ru[R:-R, R:-R, R:-R]
+    del ru, rup, u, up, co
+    tdt = torch.float64 if dtype == "f64" else torch.float32
+    res = {}
+    for name, cfg in configs:
+        gu, gup, gco, _ = inputs.make_problem(stencil, nx, ny, nz, backend="torch", device=device, ldx=ldx)
+        gu, gup = gu.to(tdt).contiguous(), gup.to(tdt).contiguous()
+        gco = gco.to(tdt).contiguous() if gco is not None else None
+        girih.run(p, gu, gup, gco, c=c, cfg=cfg)
+        girih.status(p)
+        g = gu[R:-R, R:-R, R:R + nx].double().cpu().numpy()
+        del gu, gup, gco
+        if dtype == "f64":
+            res[name] = float(np.max(np.abs(g - ref)) / np.max(np.abs(ref)))
+        else:
+            res[name] = float(np.linalg.norm((g - ref).ravel()) / np.linalg.norm(ref.ravel()))
+    bound = 1e-12 if dtype == "f64" else (1e-5 if stencil < 2 else 1e-4)
+    return {"metric": "max normwise relative error" if dtype == "f64" else "relative L2 error",
+            "vs": "FP64 oracle, full T", "bound": bound, **res, "ok": all(v <= bound for v in res.values())}
+
+
 def run_reference(args, wl):
     ws, rank, _ = _dist()
     if rank != 0:
@@ -210,6 +246,7 @@ def main():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-naive", action="store_true")
+    ap.add_argument("--no-accuracy", action="store_true", help="skip the error check against the FP64 oracle")
     ap.add_argument("--grid", default="", help="override nx,ny,nz (profiling a smaller case of the same kernel)")
     args = ap.parse_args()
     if args.impl == "reference":
@@ -362,10 +399,16 @@ def main():
         del hu, hup, hco
 
     cpu = None
+    acc = None
     if rank == 0 and ws == 1 and not args.no_cpu:
         del u, up, co
         torch.cuda.empty_cache()
         cpu = cpu_baseline(stencil, nx, ny, nz, max_T=T)
+        if not args.no_accuracy:
+            cfgs = [("tuned" if args.algo == "tuned" else "measured", cfg)]
+            if blocked_cfg is not None and blocked_cfg.as_dict() != cfg.as_dict():
+                cfgs.append(("blocked", blocked_cfg))
+            acc = accuracy(stencil, dtype, nx, ny, nz, T, ldx, cfgs, p, dev)
 
     if rank == 0:
         line = {
@@ -380,7 +423,7 @@ def main():
             "blocked": blocked, "spatial_roofline_glups": spatial,
             "frac_spatial_roofline": value / ws / spatial,
             "gpu_launches": launches * args.steps,
-            "roofline": roof, "clocks": clocks, "e2e": e2e, "cpu_baseline": cpu,
+            "roofline": roof, "clocks": clocks, "e2e": e2e, "cpu_baseline": cpu, "accuracy": acc,
         }
         print(json.dumps(line))
     if ws > 1:

@@ -19,19 +19,24 @@
 // both buffers in shared memory: [2][NZ][YW = Dw + 2R][XT >= XW + 2R].  The wavefront walks up in
 // z (Sect. 2.1.1): at step w, local level s updates planes [w*nf - s*K, w*nf - s*K + nf) with the
 // level skew K = R + nf, which makes every input of a step come from earlier steps, so one
-// cluster barrier per step is the only synchronisation ("fixed execution to data": each block
-// always updates its own slab).  x-halo columns are kept fresh by pushing boundary results into
-// the neighbour blocks' shared memory (st.shared::cluster, DSMEM) before the barrier.
+// synchronisation per step suffices ("fixed execution to data": each block always updates its
+// own slab): a cluster barrier (FED), or (RELAXED) each block publishing its step count to its
+// two x neighbours and waiting only for theirs.  x-halo columns are kept fresh by pushing
+// boundary results into the neighbour blocks' shared memory (st.shared::cluster, DSMEM) in the
+// step that computes them.
 //
-// Work per thread: G row pairs (level s, rows y0 and y0+1, column xl), owned for the whole launch,
-// so the two rows' z windows stay in registers across steps (register-rotated z columns): per
-// step and plane a pair loads 2 new z values, 2R rows of y neighbours shared by both rows, 2R x
-// neighbours per row, and stores 2.
+// Work per thread: G groups (level s, rows y0 and y0+1, VX consecutive columns), owned for the
+// whole launch, so the two rows' z windows stay in registers across steps (register-rotated z
+// columns): per step and plane a group loads one new z plane per row, 2R rows of y neighbours
+// shared by both rows and 2R x neighbours per row, and stores one vector per row.
 //
-// Data movement: every thread stages elements with cp.async, MWD_PREFETCH steps ahead, and
-// writes back with plain stores; a plane is written back once the tile's top level has passed
-// it, only rows of the diamond's projection, only buffers the tile updated in that row.  This is
-// the path for any layout; 16-byte aligned layouts use the vector kernel of mwd_vec.cuh.
+// Data movement: every thread stages elements with cp.async, MWD_PREFETCH steps ahead (a group
+// committed at step k is waited for before the barrier that ends step k+PD-1), and writes back
+// with plain stores; a plane is written back once the tile's top level has passed it, only rows
+// of the diamond's projection, only buffers the tile updated in that row.  The ring holds
+// MWD_PLAIN_SLACK*nf planes more than the wavefront needs, so no slot is restaged while a thread
+// that has not yet passed the previous step's barrier still writes back from it.  This is the
+// path for any layout; 16-byte aligned layouts use the vector kernel of mwd_vec.cuh.
 #pragma once
 #include "internal.h"
 #include "stencil.cuh"

@@ -17,7 +17,7 @@
 namespace girih {
 
 template <int S, typename T, int TW>
-struct NaiveAcc {
+struct NaiveAcc {  // one column of the thread's VX columns
   const T* tc;       // centre of this thread's cell in the shared plane tile (row stride TW)
   const T* w;        // register window, w[R] = centre
   const T* kv;       // coefficient values of this point (variable stencils)
@@ -38,20 +38,25 @@ struct NaiveAcc {
 //
 // V16 (rows of 16-byte multiples, 16-byte aligned buffers): 16-byte cp.async.cg chunks, the tile
 // row widened to whole chunks.  Otherwise: element cp.async.
-template <int S, typename T, int TY, int PD, bool V16>
+//
+// VX columns per thread, 32 apart (the tile is 32*VX columns wide; a warp's accesses stay on
+// consecutive words, free of bank conflicts): VX > 1 shares each thread's per-plane work
+// (barrier, staging items, loop control) among VX*2 updates.
+template <int S, typename T, int TY, int PD, bool V16, int VX>
 __global__ void __launch_bounds__(32 * TY) naive_kernel(const NaiveArgs a) {
   constexpr int R = Traits<S>::R;
   constexpr int NC = Traits<S>::NCOEF;
   constexpr int ROWS = 2 * TY;
   constexpr int A16 = 16 / (int)sizeof(T);
-  constexpr int TXW = V16 ? (32 + 2 * R + A16 - 1) / A16 * A16 : 32 + 2 * R;  // shared row width
+  constexpr int TX = 32 * VX;                  // tile columns
+  constexpr int TXW = V16 ? (TX + 2 * R + A16 - 1) / A16 * A16 : TX + 2 * R;  // shared row width
   constexpr int TYW = ROWS + 2 * R, TP = TXW * TYW;
   // ring slots: the first window needs planes 0..2R plus PD staged ahead (2R+PD+1 at once); in
   // the steady state planes z+R .. z+2R+PD+1 are live (R+PD+2), which is never more
   constexpr int NP = 2 * R + PD + 1;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* ring = reinterpret_cast<T*>(smem_raw);       // [NP][TYW][TXW]
-  T* uring = ring + NP * TP;                       // second order: [NP][ROWS][32] level t-1 centres
+  T* uring = ring + NP * TP;                       // second order: [NP][ROWS][TX] level t-1 centres
   const T* __restrict__ V = static_cast<const T*>(a.V);
   T* __restrict__ U = static_cast<T*>(a.U);
   const T* __restrict__ coef = static_cast<const T*>(a.coef);
@@ -63,7 +68,7 @@ __global__ void __launch_bounds__(32 * TY) naive_kernel(const NaiveArgs a) {
   const int nx = (int)a.g.nx, ny = (int)a.g.ny, nz = (int)a.g.nz;
   const int ldx = (int)a.g.ldx;
   const int64_t plane = a.g.sy * a.g.ldx;
-  const int bx = blockIdx.x * 32, by = blockIdx.y * ROWS;  // padded coords of the tile's corner
+  const int bx = blockIdx.x * TX, by = blockIdx.y * ROWS;  // padded coords of the tile's corner
   const int z0 = blockIdx.z * a.zc;
   const int nzb = min(a.zc, nz - z0);
   // tile rows/cols that exist in the padded grid
@@ -87,7 +92,7 @@ __global__ void __launch_bounds__(32 * TY) naive_kernel(const NaiveArgs a) {
     go[k] = ok ? r * ldx + c : 0;
   }
   // level t-1 centres (second order, R = 4: interior columns bx+R.. start on a 16-byte boundary)
-  constexpr int UNC = 32 / W;                  // items per centre row
+  constexpr int UNC = TX / W;                  // items per centre row
   constexpr int UPT = (ROWS * UNC + 32 * TY - 1) / (32 * TY);
   int uso[UPT], ugo[UPT];
 #pragma unroll
@@ -95,7 +100,7 @@ __global__ void __launch_bounds__(32 * TY) naive_kernel(const NaiveArgs a) {
     const int i = tid + k * 32 * TY;
     const int r = i / UNC, c = (i - r * UNC) * W;
     const bool ok = Traits<S>::ORDER2 && i < ROWS * UNC && by + r < ny && (V16 ? bx + R + c < ldx : bx + c < nx);
-    uso[k] = ok ? r * 32 + c : -1;
+    uso[k] = ok ? r * TX + c : -1;
     ugo[k] = ok ? r * ldx + c : 0;
   }
   auto copy = [&](T* dst, const T* src) {
@@ -115,7 +120,7 @@ __global__ void __launch_bounds__(32 * TY) naive_kernel(const NaiveArgs a) {
         // level t-1 centres of interior plane z0 + q - R (used when that plane is updated)
         const int zi = q - R;
         if (zi >= 0 && zi < nzb) {
-          T* ud = uring + (q % NP) * (ROWS * 32);
+          T* ud = uring + (q % NP) * (ROWS * TX);
           const T* us = Ub + (int64_t)zi * plane;
 #pragma unroll
           for (int k = 0; k < UPT; ++k)
@@ -131,28 +136,34 @@ __global__ void __launch_bounds__(32 * TY) naive_kernel(const NaiveArgs a) {
   cp_async_wait_all();
   __syncthreads();
 
-  bool act[2];
-  int cofs[2];
-  T w[2][2 * R + 1];
+  bool act[2][VX];
+  int cofs[2];  // shared offset of the thread's first column in each row
+  T w[2][VX][2 * R + 1];
 #pragma unroll
   for (int r = 0; r < 2; ++r) {
     const int row = ty + r * TY;
-    act[r] = (bx + tx < nx) && (by + row < ny);
     cofs[r] = (row + R) * TXW + tx + R;
 #pragma unroll
-    for (int i = 0; i <= 2 * R; ++i) w[r][i] = ring[i * TP + cofs[r]];
+    for (int v = 0; v < VX; ++v) {
+      act[r][v] = (bx + v * 32 + tx < nx) && (by + row < ny);
+#pragma unroll
+      for (int i = 0; i <= 2 * R; ++i) w[r][v][i] = ring[i * TP + cofs[r] + v * 32];
+    }
   }
   // every thread has its first window before the first in-loop staging overwrites slot 0
   __syncthreads();
   // coefficients of the first plane, then one plane ahead
-  T kv[2][NC > 0 ? NC : 1], kn[2][NC > 0 ? NC : 1];
+  T kv[2][VX][NC > 0 ? NC : 1], kn[2][VX][NC > 0 ? NC : 1];
   const int64_t gs = a.g.gstride;
   const T* cb = coef ? coef + (int64_t)(z0 + R) * plane + (int64_t)(by + R) * ldx + (bx + R) : nullptr;
   if constexpr (NC > 0) {
 #pragma unroll
     for (int r = 0; r < 2; ++r)
 #pragma unroll
-      for (int g = 0; g < NC; ++g) kn[r][g] = act[r] ? __ldg(cb + g * gs + (ty + r * TY) * ldx + tx) : T(0);
+      for (int v = 0; v < VX; ++v)
+#pragma unroll
+        for (int g = 0; g < NC; ++g)
+          kn[r][v][g] = act[r][v] ? __ldg(cb + g * gs + (ty + r * TY) * ldx + v * 32 + tx) : T(0);
   }
 
   for (int zr = 0; zr < nzb; ++zr) {
@@ -160,19 +171,26 @@ __global__ void __launch_bounds__(32 * TY) naive_kernel(const NaiveArgs a) {
 #pragma unroll
       for (int r = 0; r < 2; ++r)
 #pragma unroll
-        for (int g = 0; g < NC; ++g) {
-          kv[r][g] = kn[r][g];
-          kn[r][g] = (act[r] && zr + 1 < nzb) ? __ldg(cb + g * gs + (int64_t)(zr + 1) * plane + (ty + r * TY) * ldx + tx)
-                                              : T(0);
-        }
+        for (int v = 0; v < VX; ++v)
+#pragma unroll
+          for (int g = 0; g < NC; ++g) {
+            kv[r][v][g] = kn[r][v][g];
+            kn[r][v][g] = (act[r][v] && zr + 1 < nzb)
+                              ? __ldg(cb + g * gs + (int64_t)(zr + 1) * plane + (ty + r * TY) * ldx + v * 32 + tx)
+                              : T(0);
+          }
     }
     const T* tl = ring + ((zr + R) % NP) * TP;  // padded plane z0 + zr + R = interior plane z0 + zr
 #pragma unroll
     for (int r = 0; r < 2; ++r) {
-      if (act[r]) {
-        NaiveAcc<S, T, TXW> acc{tl + cofs[r], w[r], kv[r], T(0)};
-        if constexpr (Traits<S>::ORDER2) acc.uc = uring[((zr + R) % NP) * (ROWS * 32) + (ty + r * TY) * 32 + tx];
-        Ub[(int64_t)zr * plane + (ty + r * TY) * ldx + tx] = point_update<S, T>(acc, cst);
+#pragma unroll
+      for (int v = 0; v < VX; ++v) {
+        if (act[r][v]) {
+          NaiveAcc<S, T, TXW> acc{tl + cofs[r] + v * 32, w[r][v], kv[r][v], T(0)};
+          if constexpr (Traits<S>::ORDER2)
+            acc.uc = uring[((zr + R) % NP) * (ROWS * TX) + (ty + r * TY) * TX + v * 32 + tx];
+          Ub[(int64_t)zr * plane + (ty + r * TY) * ldx + v * 32 + tx] = point_update<S, T>(acc, cst);
+        }
       }
     }
     // advance: stage the plane PD ahead, wait for the next window value, one barrier
@@ -183,8 +201,11 @@ __global__ void __launch_bounds__(32 * TY) naive_kernel(const NaiveArgs a) {
 #pragma unroll
     for (int r = 0; r < 2; ++r) {
 #pragma unroll
-      for (int i = 0; i < 2 * R; ++i) w[r][i] = w[r][i + 1];
-      w[r][2 * R] = nw[cofs[r]];
+      for (int v = 0; v < VX; ++v) {
+#pragma unroll
+        for (int i = 0; i < 2 * R; ++i) w[r][v][i] = w[r][v][i + 1];
+        w[r][v][2 * R] = nw[cofs[r] + v * 32];
+      }
     }
   }
 }
@@ -198,12 +219,22 @@ int naive_block_rows(int, int) { return 2 * kTY; }
 template <int S, typename T>
 constexpr int naive_pd() { return Traits<S>::R == 1 ? 4 : 2; }
 
+// Columns per thread: 4 for the FP32 7-point constant stencil on 16-byte aligned layouts (its
+// sweep was bound by instruction issue: 564 -> 715 GLUP/s at 512^3), else 1 (measured: the
+// FP64 sweeps are bound by the FP64 pipe and the 25-point FP32 sweep lost occupancy; the
+// variable stencils keep a plane of coefficients per column in registers).
+template <int S, typename T, bool V16>
+constexpr int naive_vx() {
+  return (V16 && S == 0 && sizeof(T) == 4) ? 4 : 1;
+}
+
 template <int S, typename T, bool V16>
 static size_t naive_smem() {
   constexpr int R = Traits<S>::R, PD = naive_pd<S, T>(), A16 = 16 / (int)sizeof(T);
-  constexpr int TXW = V16 ? (32 + 2 * R + A16 - 1) / A16 * A16 : 32 + 2 * R;
+  constexpr int TX = 32 * naive_vx<S, T, V16>();
+  constexpr int TXW = V16 ? (TX + 2 * R + A16 - 1) / A16 * A16 : TX + 2 * R;
   constexpr int NP = 2 * R + PD + 1, TP = TXW * (2 * kTY + 2 * R);
-  return sizeof(T) * ((size_t)NP * TP + (Traits<S>::ORDER2 ? (size_t)NP * 2 * kTY * 32 : 0));
+  return sizeof(T) * ((size_t)NP * TP + (Traits<S>::ORDER2 ? (size_t)NP * 2 * kTY * TX : 0));
 }
 
 // Resident blocks per SM of one naive kernel instance (occupancy query, cached per instance).
@@ -212,7 +243,7 @@ static int resident_blocks() {
   static int n = -1;
   if (n < 0) {
     const size_t sm = naive_smem<S, T, V16>();
-    auto k = naive_kernel<S, T, kTY, naive_pd<S, T>(), V16>;
+    auto k = naive_kernel<S, T, kTY, naive_pd<S, T>(), V16, naive_vx<S, T, V16>()>;
     if (sm > 48 * 1024) cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     int b = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k, 32 * kTY, sm) != cudaSuccess || b < 1) {
@@ -227,10 +258,11 @@ static int resident_blocks() {
 template <int S, typename T, bool V16>
 static cudaError_t launch_one(const NaiveArgs& a, cudaStream_t st) {
   dim3 block(32, kTY);
-  dim3 grid((unsigned)((a.g.nx + 31) / 32), (unsigned)((a.g.ny + 2 * kTY - 1) / (2 * kTY)),
+  constexpr int TX = 32 * naive_vx<S, T, V16>();
+  dim3 grid((unsigned)((a.g.nx + TX - 1) / TX), (unsigned)((a.g.ny + 2 * kTY - 1) / (2 * kTY)),
             (unsigned)((a.g.nz + a.zc - 1) / a.zc));
   const size_t sm = naive_smem<S, T, V16>();
-  auto k = naive_kernel<S, T, kTY, naive_pd<S, T>(), V16>;
+  auto k = naive_kernel<S, T, kTY, naive_pd<S, T>(), V16, naive_vx<S, T, V16>()>;
   if (sm > 48 * 1024) {
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
@@ -242,6 +274,21 @@ static cudaError_t launch_one(const NaiveArgs& a, cudaStream_t st) {
 template <int S, typename T>
 static cudaError_t launch_v(const NaiveArgs& a, cudaStream_t st) {
   return a.v16 ? launch_one<S, T, true>(a, st) : launch_one<S, T, false>(a, st);
+}
+
+int naive_tile_x(int stencil, int dtype, bool v16) {
+  const bool f64 = dtype == GIRIH_F64;
+  auto pick = [&](auto s_tag) -> int {
+    constexpr int S = decltype(s_tag)::value;
+    if (f64) return 32 * (v16 ? naive_vx<S, double, true>() : naive_vx<S, double, false>());
+    return 32 * (v16 ? naive_vx<S, float, true>() : naive_vx<S, float, false>());
+  };
+  switch (stencil) {
+    case 0: return pick(std::integral_constant<int, 0>());
+    case 1: return pick(std::integral_constant<int, 1>());
+    case 2: return pick(std::integral_constant<int, 2>());
+    default: return pick(std::integral_constant<int, 3>());
+  }
 }
 
 int naive_resident_blocks(int stencil, int dtype, bool v16) {
@@ -263,8 +310,8 @@ int naive_resident_blocks(int stencil, int dtype, bool v16) {
 // blocks that is used) x (fraction of each block's staged planes that it updates, zc/(zc+2R)),
 // i.e. fills the device's resident block slots in whole waves without re-reading too many
 // z-halo planes (fewer chunks on ties).
-int naive_z_chunk(int64_t nx, int64_t ny, int64_t nz, int R, int resident_per_sm, int sm_count) {
-  const int64_t tiles = ((nx + 31) / 32) * ((ny + 2 * kTY - 1) / (2 * kTY));
+int naive_z_chunk(int64_t nx, int64_t ny, int64_t nz, int R, int tile_x, int resident_per_sm, int sm_count) {
+  const int64_t tiles = ((nx + tile_x - 1) / tile_x) * ((ny + 2 * kTY - 1) / (2 * kTY));
   const int64_t slots = (int64_t)std::max(resident_per_sm, 1) * std::max(sm_count, 1);
   const int64_t cmin = std::max<int64_t>((nz + 63) / 64, 1), cmax = std::max<int64_t>((nz + 15) / 16, cmin);
   int64_t best_c = cmin;
