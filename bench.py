@@ -242,7 +242,7 @@ def main():
     ap.add_argument("--nf", type=int, default=1)
     ap.add_argument("--cluster", type=int, default=0)
     ap.add_argument("--threads", type=int, default=256)
-    ap.add_argument("--variant", type=int, default=0, help="0 FED, 1 RELAXED, 2 FED_BULK, 3 FED_ELEM, 4 RELAXED_ELEM")
+    ap.add_argument("--variant", type=int, default=0, help="0 FED, 1 RELAXED, 2 FED_BULK, 3 FED_ELEM, 4 RELAXED_ELEM, 5 FED_PERSISTENT")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-naive", action="store_true")

@@ -59,13 +59,19 @@ typedef enum { GIRIH_ALGO_NAIVE = 0, GIRIH_ALGO_MWD = 1 } girih_algo;
  *              neighbour hand-off of the paper's relaxed synchronisation.  Data movement as
  *              FED; with a cluster of one block it is the same as FED.
  *   FED_ELEM, RELAXED_ELEM -- FED and RELAXED forced onto the element-by-element path on any
- *              layout (the tuner weighs both data paths).                                   */
+ *              layout (the tuner weighs both data paths).
+ *   FED_PERSISTENT -- FED on the vector path with the FIFO runtime of Sect. 4.2.3: one launch
+ *              per sweep, clusters take diamonds in row-major order and start each once the
+ *              two diamonds of the previous row it depends on have completed (bounded waits
+ *              on per-diamond flags).  Needs the vector path's layout (16-byte rows, 16-byte
+ *              aligned buffers).                                                           */
 typedef enum {
   GIRIH_FED = 0,
   GIRIH_RELAXED = 1,
   GIRIH_FED_BULK = 2,
   GIRIH_FED_ELEM = 3,
-  GIRIH_RELAXED_ELEM = 4
+  GIRIH_RELAXED_ELEM = 4,
+  GIRIH_FED_PERSISTENT = 5
 } girih_variant;
 
 #define GIRIH_OK 0

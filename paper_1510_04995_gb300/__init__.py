@@ -21,7 +21,7 @@ HEADER = os.path.join(os.path.dirname(HERE), "include", "girih.h")
 S7C, S7V, S25C, S25V = 0, 1, 2, 3
 F64, F32 = 0, 1
 NAIVE, MWD = 0, 1
-FED, RELAXED, FED_BULK, FED_ELEM, RELAXED_ELEM = 0, 1, 2, 3, 4
+FED, RELAXED, FED_BULK, FED_ELEM, RELAXED_ELEM, FED_PERSISTENT = 0, 1, 2, 3, 4, 5
 RADIUS = {0: 1, 1: 1, 2: 4, 3: 4}
 NCOEF = {0: 0, 1: 7, 2: 0, 3: 13}
 STATUS = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "EKERNEL", 5: "ETIMEOUT", 6: "ENOTIMPL"}

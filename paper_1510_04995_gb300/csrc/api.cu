@@ -8,6 +8,7 @@
 #include <cstdio>
 #include <cstring>
 #include <string>
+#include <vector>
 
 #include "internal.h"
 #include "plan.h"
@@ -84,8 +85,10 @@ int check_config(const Plan* p, const girih_config* c, int64_t* smem_out, int* x
     return GIRIH_OK;
   }
   if (c->algo != GIRIH_ALGO_MWD) return fail(GIRIH_EINVAL, "unknown algo %d", c->algo);
-  if (c->variant < GIRIH_FED || c->variant > GIRIH_RELAXED_ELEM)
+  if (c->variant < GIRIH_FED || c->variant > GIRIH_FED_PERSISTENT)
     return fail(GIRIH_EINVAL, "unknown variant %d", c->variant);
+  if (c->variant == GIRIH_FED_PERSISTENT && mwd_path(p, c, ptrs16) != MV_VEC)
+    return fail(GIRIH_EINVAL, "FED_PERSISTENT needs rows of 16-byte multiples and 16-byte aligned buffers");
   const bool bulk = c->variant == GIRIH_FED_BULK;
   if (bulk && !p->bulk_layout)
     return fail(GIRIH_EINVAL, "FED_BULK needs ldx*elem to be a multiple of 16 bytes (ldx=%lld)", (long long)p->ldx);
@@ -154,6 +157,9 @@ static girih_config default_config(Plan* p) {
   return best;
 }
 
+static int launch_persistent(Plan* p, MwdArgs a, int64_t rows, const girih_config& cfg, int G, int mv,
+                             int64_t smem, cudaStream_t st, cudaError_t* e_out);
+
 int run_sweep(Plan* p, int64_t T, void* u, void* u_prev, const void* coeffs, const double* c,
               const girih_config& cfg, cudaStream_t st) {
   Grid g{p->nx, p->ny, p->nz, p->ldx, p->ny + 2 * p->R, p->gstride};
@@ -206,7 +212,11 @@ int run_sweep(Plan* p, int64_t T, void* u, void* u_prev, const void* coeffs, con
     a.err = p->err;
     a.relaxed = (cfg.variant == GIRIH_RELAXED || cfg.variant == GIRIH_RELAXED_ELEM) ? 1 : 0;
     const int64_t rows = mwd_rows(T, cfg.dw, p->R);
-    for (int64_t rho = 0; rho < rows && e == cudaSuccess; ++rho) {  // one launch per diamond row
+    if (cfg.variant == GIRIH_FED_PERSISTENT) {
+      const int rc2 = launch_persistent(p, a, rows, cfg, G, mv, sh.smem_bytes, st, &e);
+      if (rc2 != GIRIH_OK) return rc2;
+    }
+    for (int64_t rho = 0; rho < rows && e == cudaSuccess && cfg.variant != GIRIH_FED_PERSISTENT; ++rho) {
       int64_t a_min = 0, nd = 0;
       mwd_row_span(rho, cfg.dw, p->ny, &a_min, &nd);
       if (nd == 0) continue;
@@ -217,6 +227,86 @@ int run_sweep(Plan* p, int64_t T, void* u, void* u_prev, const void* coeffs, con
   }
   if (e == cudaSuccess && T % 2 == 1) e = launch_swap(u, u_prev, p->gstride * p->elem, st);
   if (e != cudaSuccess) return cuda_fail(e, "kernel launch");
+  return GIRIH_OK;
+}
+
+// FED_PERSISTENT: build the FIFO of diamonds (row-major) and the per-row table, reset the FIFO
+// counter, bump the epoch (flags of earlier sweeps never equal it) and launch as many clusters
+// as the device holds at once (all resident, so dependency waits cannot deadlock).
+static int launch_persistent(Plan* p, MwdArgs a, int64_t rows, const girih_config& cfg, int G, int mv,
+                             int64_t smem, cudaStream_t st, cudaError_t* e_out) {
+  std::vector<int> items, table;
+  for (int64_t rho = 0; rho < rows; ++rho) {
+    int64_t a_min = 0, nd = 0;
+    mwd_row_span(rho, cfg.dw, p->ny, &a_min, &nd);
+    table.push_back((int)(items.size() / 2));
+    table.push_back((int)a_min);
+    table.push_back((int)nd);
+    for (int64_t k = 0; k < nd; ++k) {
+      items.push_back((int)rho);
+      items.push_back((int)(a_min + k));
+    }
+  }
+  const int64_t n_items = (int64_t)items.size() / 2;
+  *e_out = cudaSuccess;
+  if (n_items == 0) return GIRIH_OK;
+  std::vector<int> host(items);
+  host.insert(host.end(), table.begin(), table.end());
+  cudaError_t e = cudaSuccess;
+  if ((int64_t)host.size() > p->sched_cap) {
+    if (p->sched) cudaFree(p->sched);
+    p->sched = nullptr;
+    p->sched_cap = 0;
+    e = cudaMalloc(&p->sched, host.size() * sizeof(int));
+    if (e != cudaSuccess) return fail(GIRIH_ENOMEM, "schedule buffer: %s", cudaGetErrorString(e));
+    p->sched_cap = (int64_t)host.size();
+    p->sched_T = -1;
+  }
+  if (n_items > p->flags_cap) {
+    if (p->flags) cudaFree(p->flags);
+    p->flags = nullptr;
+    p->flags_cap = 0;
+    e = cudaMalloc(&p->flags, n_items * sizeof(int));
+    if (e != cudaSuccess) return fail(GIRIH_ENOMEM, "flag buffer: %s", cudaGetErrorString(e));
+    e = cudaMemset(p->flags, 0, n_items * sizeof(int));
+    if (e != cudaSuccess) return cuda_fail(e, "flag reset");
+    p->flags_cap = n_items;
+    p->epoch = 0;
+  }
+  if (!p->fifo) {
+    e = cudaMalloc(&p->fifo, sizeof(int));
+    if (e != cudaSuccess) return fail(GIRIH_ENOMEM, "FIFO counter: %s", cudaGetErrorString(e));
+  }
+  // the list depends on (T, dw) only: upload it when they change (a pageable copy has taken
+  // the host data when it returns, and is ordered before the launch on the stream)
+  if (p->sched_T != rows || p->sched_dw != cfg.dw) {
+    e = cudaMemcpyAsync(p->sched, host.data(), host.size() * sizeof(int), cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) return cuda_fail(e, "schedule upload");
+    p->sched_T = rows;
+    p->sched_dw = cfg.dw;
+  }
+  e = cudaMemsetAsync(p->fifo, 0, sizeof(int), st);
+  if (e != cudaSuccess) return cuda_fail(e, "schedule upload");
+  if (++p->epoch == 0x7fffffff) {  // wrap: clear the flags so that no stale one matches
+    p->epoch = 1;
+    e = cudaMemsetAsync(p->flags, 0, p->flags_cap * sizeof(int), st);
+    if (e != cudaSuccess) return cuda_fail(e, "flag reset");
+  }
+  int max_clusters = 0;
+  e = mwd_prepare(p->stencil, p->dtype, cfg.cluster, cfg.threads, G, mv, smem, &max_clusters);
+  if (e != cudaSuccess) return cuda_fail(e, "persistent launch configuration");
+  if (max_clusters < 1) return fail(GIRIH_EINVAL, "no cluster of the configuration fits the device");
+  a.persist = 1;
+  a.n_items = (int32_t)n_items;
+  a.epoch = p->epoch;
+  a.items = p->sched;
+  a.rows = p->sched + 2 * n_items;
+  a.flags = p->flags;
+  a.fifo = p->fifo;
+  a.rho = 0;
+  a.a_min = 0;
+  const int ngrid = (int)std::min<int64_t>(n_items, max_clusters);
+  *e_out = launch_mwd_row(p->stencil, p->dtype, a, ngrid, cfg.threads, G, mv, smem, st);
   return GIRIH_OK;
 }
 
@@ -311,7 +401,8 @@ int girih_plan(girih_plan_t* out, int32_t stencil, int64_t nx, int64_t ny, int64
 int girih_plan_destroy(girih_plan_t plan) {
   if (!plan) return GIRIH_OK;
   Plan* p = plan;
-  for (void* d : {p->host_u, p->host_up, p->host_co, p->tune_u, p->tune_up, p->tune_co, (void*)p->err})
+  for (void* d : {p->host_u, p->host_up, p->host_co, p->tune_u, p->tune_up, p->tune_co, (void*)p->err,
+                  (void*)p->sched, (void*)p->flags, (void*)p->fifo})
     if (d) cudaFree(d);
   delete p;
   return GIRIH_OK;
@@ -349,6 +440,7 @@ int girih_plan_launch_count(girih_plan_t plan, const girih_config* cfg, int64_t*
   const girih_config& c = cfg ? *cfg : plan->cfg;
   const int64_t T = plan->T;
   int64_t n = (c.algo == GIRIH_ALGO_NAIVE) ? T : mwd_rows(T, c.dw, plan->R);
+  if (c.algo != GIRIH_ALGO_NAIVE && c.variant == GIRIH_FED_PERSISTENT && T > 0) n = 1;
   if (T % 2 == 1) ++n;
   *launches = n;
   return GIRIH_OK;

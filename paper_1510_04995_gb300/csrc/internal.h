@@ -50,6 +50,13 @@ struct MwdArgs {
   int32_t NZ, YW, XT;  // shared ring: planes, rows, columns per buffer
   int* err;          // device error word: bounded waits that ran out set GIRIH_ETIMEOUT here
   int32_t relaxed;   // RELAXED variant: neighbour hand-off instead of the cluster barrier
+  // persistent schedule (FED_PERSISTENT): diamonds (rho, a) in FIFO order, per row
+  // (first item, a_min, count), completion flags (= epoch when done), the FIFO counter
+  int32_t persist, n_items, epoch;
+  const int* items;
+  const int* rows;
+  int* flags;
+  int* fifo;
 };
 
 struct MwdShape {

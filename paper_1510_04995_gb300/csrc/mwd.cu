@@ -39,7 +39,9 @@ MwdShape mwd_shape(int stencil, int dtype, int dw, int nf, int XW, int mv) {
     s.XT = (off + XW + R + a16 - 1) / a16 * a16;
   }
   const int64_t ring = 2LL * s.NZ * s.YW * s.XT * elem;
-  s.smem_bytes = (ring + 15) / 16 * 16 + 8LL * s.NZ + (3LL * H + 1 + s.YW + 2) * 4;
+  // ring, one mbarrier per plane, level tables (3H+1), row masks (YW), RELAXED progress
+  // counters (2), persistent-schedule item slot (1)
+  s.smem_bytes = (ring + 15) / 16 * 16 + 8LL * s.NZ + (3LL * H + 1 + s.YW + 3) * 4;
   return s;
 }
 

@@ -46,8 +46,9 @@ constexpr int vec_lbf() {
 }
 constexpr int kVecItems = 4;  // precomputed staging / write-back items per thread
 
+// One tile (diamond (a, a - rho) of row rho, this block's x slab) from staging to write-back.
 template <int S, typename T, int G, bool TMA>
-__global__ void __launch_bounds__(1024 / (G * vec_lbf<S>()), 1) mwd_vec_kernel(const MwdArgs A) {
+__device__ __forceinline__ void mwd_vec_tile(const MwdArgs& A, const int rho, const int a) {
   constexpr int R = Traits<S>::R;
   constexpr int NC = Traits<S>::NCOEF;
   constexpr int PD = TMA ? MWD_PREFETCH_BULK : MWD_PREFETCH;
@@ -72,9 +73,8 @@ __global__ void __launch_bounds__(1024 / (G * vec_lbf<S>()), 1) mwd_vec_kernel(c
   const int ldx = (int)A.g.ldx;
   const int64_t gplane = A.g.sy * A.g.ldx;
   const int rank = (C > 1) ? (int)cluster_ctarank() : 0;
-  const int tile = blockIdx.x / C;
-  const int dw = A.dw, rho = A.rho;
-  const int a = A.a_min + tile, b = a - rho;
+  const int dw = A.dw;
+  const int b = a - rho;
   const int P0 = a * dw - rho * (dw / 2);
   const int Y0 = P0 - R;
   const int pc0 = rank * XW;          // padded column of slab column 0
@@ -495,6 +495,65 @@ __global__ void __launch_bounds__(1024 / (G * vec_lbf<S>()), 1) mwd_vec_kernel(c
   } else {
     cp_async_wait_group<0>();
     for (int f = 0; f < nf; ++f, ++wz, wsl = (wsl + 1 == NZ) ? 0 : wsl + 1) write_back(wz, wsl);
+  }
+}
+
+// The kernel: one tile per cluster per launch (one launch per diamond row), or, persistent
+// (FED_PERSISTENT), every cluster of a grid that fits the device at once takes diamonds from a
+// FIFO in row-major order -- the runtime of Sect. 4.2.3 -- and starts a diamond once the two
+// diamonds of the previous row it depends on ((a-1, b) and (a, b+1)) have published completion.
+// Their y projections cover the diamond's projection plus R rows each side, so every value the
+// diamond reads is final; diamonds that are not dependencies are at least Dw/2 rows away.  The
+// FIFO order is a topological order and all clusters are resident, so the waits cannot
+// deadlock; each is bounded (a timeout sets GIRIH_ETIMEOUT) all the same.  Completion: after a
+// cluster barrier (all blocks' write-back stores ordered at cluster scope), one thread releases
+// the diamond's flag at GPU scope (fence.acq_rel.gpu); the waiting cluster acquires it.
+template <int S, typename T, int G, bool TMA>
+__global__ void __launch_bounds__(1024 / (G * vec_lbf<S>()), 1) mwd_vec_kernel(const MwdArgs A) {
+  if (!A.persist) {
+    mwd_vec_tile<S, T, G, TMA>(A, A.rho, A.a_min + (int)blockIdx.x / A.C);
+    return;
+  }
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  const int C = A.C;
+  const int rank = (C > 1) ? (int)cluster_ctarank() : 0;
+  const size_t ring_bytes = (((size_t)2 * A.NZ * A.YW * A.XT * sizeof(T) + 15) / 16) * 16;
+  int* slot = reinterpret_cast<int*>(smem_raw + ring_bytes + 8 * (size_t)A.NZ) + 3 * A.H + 1 + A.YW + 2;
+  for (;;) {
+    if (rank == 0 && threadIdx.x == 0) {
+      const int it = atomicAdd(A.fifo, 1);
+      for (int r = 0; r < C; ++r) st_cluster_u32(map_to_rank(smem_addr(slot), (uint32_t)r), (uint32_t)it);
+    }
+    cluster_barrier();
+    const int it = *reinterpret_cast<volatile int*>(slot);
+    if (it >= A.n_items) break;
+    const int rho = A.items[2 * it], a = A.items[2 * it + 1];
+    if (rank == 0 && threadIdx.x == 0 && rho > 0) {
+      const int first = A.rows[3 * (rho - 1)], amin = A.rows[3 * (rho - 1) + 1], nd = A.rows[3 * (rho - 1) + 2];
+      const uint64_t t0 = global_ns();
+      // after a timeout anywhere in the sweep the result is void: stop waiting so the launch ends
+      const bool gave_up = *reinterpret_cast<volatile int*>(A.err) != 0;
+      for (int d = a - 1; d <= a && !gave_up; ++d) {
+        if (d < amin || d >= amin + nd) continue;  // outside the grid: nothing to wait for
+        const int* f = A.flags + first + (d - amin);
+        int v;
+        for (;;) {
+          asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(f) : "memory");
+          if (v == A.epoch) break;
+          if (global_ns() - t0 > kMbarWaitNs) {
+            atomicOr(A.err, GIRIH_ETIMEOUT);
+            break;
+          }
+        }
+      }
+    }
+    cluster_barrier();
+    mwd_vec_tile<S, T, G, TMA>(A, rho, a);
+    cluster_barrier();
+    if (rank == 0 && threadIdx.x == 0) {
+      asm volatile("fence.acq_rel.gpu;" ::: "memory");
+      asm volatile("st.relaxed.gpu.global.u32 [%0], %1;" ::"l"(A.flags + it), "r"(A.epoch) : "memory");
+    }
   }
 }
 

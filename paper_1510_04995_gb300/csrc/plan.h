@@ -19,6 +19,15 @@ struct girih_plan_s {
   void* tune_up = nullptr;
   void* tune_co = nullptr;
   int* err = nullptr;  // device error word of the kernels' bounded waits
+  // persistent schedule: item list + per-row table, completion flags, FIFO counter, run epoch
+  int* sched = nullptr;
+  int64_t sched_cap = 0;  // ints
+  int64_t sched_T = -1;   // diamond rows and width of the uploaded list
+  int32_t sched_dw = 0;
+  int* flags = nullptr;
+  int64_t flags_cap = 0;  // ints
+  int* fifo = nullptr;
+  int32_t epoch = 0;
   bool bulk_layout = false;  // rows are 16-byte multiples: the blocked kernel may use bulk copies
 };
 

@@ -128,7 +128,8 @@ std::vector<girih_config> candidates(Plan* p) {
     for (int nf : {1, 2})
       for (int C : {1, 2, 4, 8, 16})
         for (int th : {128, 256, 512, 1024})
-          for (int v : {GIRIH_FED, GIRIH_RELAXED, GIRIH_FED_BULK, GIRIH_FED_ELEM, GIRIH_RELAXED_ELEM}) {
+          for (int v : {GIRIH_FED, GIRIH_RELAXED, GIRIH_FED_BULK, GIRIH_FED_ELEM, GIRIH_RELAXED_ELEM,
+                        GIRIH_FED_PERSISTENT}) {
             if ((v == GIRIH_RELAXED || v == GIRIH_RELAXED_ELEM) && C == 1) continue;  // one block: = FED
             // on an unaligned layout FED is already the element path
             if ((v == GIRIH_FED_ELEM || v == GIRIH_RELAXED_ELEM) && !p->bulk_layout) continue;

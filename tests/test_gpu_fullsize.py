@@ -87,7 +87,7 @@ def test_sampled_points_against_oracle_cones():
         assert abs(got - ref) <= 1e-12 * scale, ((i, j, k), got, ref)
 
 
-@pytest.mark.parametrize("variant", ["NAIVE", "FED", "FED_BULK", "FED_ELEM", "RELAXED"])
+@pytest.mark.parametrize("variant", ["NAIVE", "FED", "FED_BULK", "FED_ELEM", "RELAXED", "FED_PERSISTENT"])
 def test_blocked_repeatable_under_load(variant):
     """Repeated large sweeps in each data path, bit for bit against one naive sweep: a staging or
     synchronisation race shows up as a rare, localised difference, so several long runs with many

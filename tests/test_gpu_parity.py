@@ -281,3 +281,60 @@ def test_bounded_wait_times_out_and_reports():
     gu, _ = gpu_sweep(0, "f64", u, up, co, c, 4, 40, 30, 20,
                       feasible_cfg(0, "f64", 40, 30, 20, dict(dw=4, nf=1, cluster=2, threads=256, variant=girih.RELAXED)))
     assert normwise(gu, ru, 1) <= 1e-12
+
+
+def _aligned_ldx(nx, R, dtype):
+    a16 = 16 // (8 if dtype == "f64" else 4)
+    return -(-(nx + 2 * R) // a16) * a16
+
+
+@pytest.mark.parametrize("stencil", [0, 1, 2, 3])
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+def test_persistent_schedule(stencil, dtype):
+    """FED_PERSISTENT (one launch per sweep; clusters take diamonds from a FIFO and start each once
+    its two parent diamonds have completed, Sect. 4.2.3) changes the order tiles run in, not their
+    arithmetic: bit-identical to the naive sweep and to the row-by-row FED launches, for truncated
+    and full diamond rows, clusters of 1 to 8 blocks, and repeated sweeps on one plan."""
+    R = inputs.RADIUS[stencil]
+    nx, ny, nz = SIZES[R]
+    ldx = _aligned_ldx(nx, R, dtype)
+    dws = (4, 8) if R == 1 else (8, 16)
+    for dw, cl, nf in ((dws[0], 1, 1), (dws[1], 2, 2), (dws[1], 8, 1)):
+        H = dw // R
+        for T in (1, H - 1, 2 * H + 3):
+            u, up, co, c = inputs.make_problem(stencil, nx, ny, nz, seed=31 + T, ldx=ldx)
+            nu, nup = gpu_sweep(stencil, dtype, u, up, co, c, T, nx, ny, nz, girih.config(girih.NAIVE), ldx=ldx)
+            kw = dict(dw=dw, nf=nf, cluster=cl, threads=256, variant=girih.FED_PERSISTENT)
+            cfg = feasible_cfg(stencil, dtype, nx, ny, nz, kw, ldx=ldx)
+            assert cfg.variant == girih.FED_PERSISTENT
+            pu, pup = gpu_sweep(stencil, dtype, u, up, co, c, T, nx, ny, nz, cfg, ldx=ldx)
+            assert np.array_equal(pu, nu) and np.array_equal(pup, nup), (dw, cl, T, cfg)
+            fed = girih.config(girih.MWD, dw=cfg.dw, nf=cfg.nf, cluster=cfg.cluster, threads=cfg.threads)
+            fu, _ = gpu_sweep(stencil, dtype, u, up, co, c, T, nx, ny, nz, fed, ldx=ldx)
+            assert np.array_equal(pu, fu)
+
+
+def test_persistent_schedule_reuse_and_rejects_unaligned():
+    """One plan runs several persistent sweeps (the completion flags of a sweep carry its epoch,
+    so earlier sweeps' flags never release a diamond) and switches diamond width (the diamond list
+    is rebuilt); the variant needs the vector layout and says so otherwise."""
+    import torch
+    from gpu_util import to_dev
+    stencil, dtype, nx, ny, nz, T = 0, "f64", 70, 45, 33, 11
+    ldx = _aligned_ldx(nx, 1, dtype)
+    u, up, co, c = inputs.make_problem(stencil, nx, ny, nz, seed=5, ldx=ldx)
+    p = girih.plan(stencil, nx, ny, nz, dtype=dtype, T=T, ldx=ldx)
+    du, dup = to_dev(u, dtype), to_dev(up, dtype)
+    cur_u, cur_up = u, up
+    for i, dw in enumerate((8, 8, 4, 8, 4)):
+        cfg = girih.config(girih.MWD, dw=dw, nf=1, cluster=2, threads=256, variant=girih.FED_PERSISTENT)
+        girih.run(p, du, dup, None, c=c, cfg=cfg)
+        girih.status(p)
+        torch.cuda.synchronize()
+        cur_u, cur_up = gpu_sweep(stencil, dtype, cur_u, cur_up, co, c, T, nx, ny, nz, girih.config(girih.NAIVE),
+                                  ldx=ldx)
+        assert np.array_equal(du.cpu().numpy(), cur_u) and np.array_equal(dup.cpu().numpy(), cur_up), i
+    pun = girih.plan(stencil, nx, ny, nz, dtype=dtype, T=T, ldx=ldx + 1)
+    bad = girih.config(girih.MWD, dw=8, nf=1, cluster=2, threads=256, variant=girih.FED_PERSISTENT)
+    assert not pun.feasible(bad)
+    assert p.launch_count(bad) == 2  # one persistent launch + the exchange for odd T
