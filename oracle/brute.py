@@ -1,9 +1,10 @@
 """Brute-force per-point evaluator -- TEST INFRASTRUCTURE ONLY.
 
-An independent restatement of the four operators of Listings 1-4 (arXiv 1510.04995, Sect. 2.2)
+An independent restatement of the five operators of Listings 1-4 (arXiv 1510.04995, Sect. 2.2)
 as a table of terms.  Each term is (coefficient source, list of neighbour offsets (dx, dy, dz));
 a point's update is the running sum, in table order, of coefficient * (sum of the neighbours in
-list order).  Every level is recomputed point by point over the whole interior in pure Python,
+list order).  The 25-point stencil with the factor grid (Listing 3 as printed) uses the 25-point
+constant table and multiplies the sum by the point's factor before the leapfrog terms.  Every level is recomputed point by point over the whole interior in pure Python,
 so it is only meant for tiny grids (8^3, T <= 3), where it must agree bit for bit with the C loop
 nests (same terms, same order, one rounding per operation).
 """
@@ -25,7 +26,7 @@ def term_table(stencil: int):
         return [(("C", 0), [(0, 0, 0)]), (("C", 1), [(1, 0, 0)]), (("C", 2), [(-1, 0, 0)]),
                 (("C", 3), [(0, 1, 0)]), (("C", 4), [(0, -1, 0)]), (("C", 5), [(0, 0, 1)]),
                 (("C", 6), [(0, 0, -1)])]
-    if stencil == 2:
+    if stencil in (2, 4):
         tab = [(("c", 0), [(0, 0, 0)])]
         for r in range(1, 5):
             x, y, z = _axis(r)
@@ -44,7 +45,7 @@ def sweep(stencil: int, u, u_prev, coeffs, c, T: int, R: int):
     """Return (level T, level T-1) as new arrays; inputs are padded [nz+2R][ny+2R][nx+2R]."""
     a = [u.copy(), u_prev.copy()]
     nz, ny, nx = (s - 2 * R for s in u.shape)
-    second = stencil in (2, 3)
+    second = stencil in (2, 3, 4)
     tab = term_table(stencil)
     for t in range(T):
         V, U = a[t % 2], a[(t + 1) % 2]
@@ -61,6 +62,8 @@ def sweep(stencil: int, u, u_prev, coeffs, c, T: int, R: int):
                         w = float(c[q]) if kind == "c" else float(coeffs[q, k, j, i])
                         term = w * s
                         acc = term if acc is None else acc + term
+                    if stencil == 4:  # Listing 3's per-point factor on the whole bracket
+                        acc = float(coeffs[0, k, j, i]) * acc
                     if second:
                         acc = (2.0 * float(V[k, j, i]) - float(U[k, j, i])) + acc
                     new[k, j, i] = acc

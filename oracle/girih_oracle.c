@@ -4,7 +4,7 @@
  * Only the tests, the smoke check and the benchmark's CPU-baseline leg may load this code.  It
  * shares nothing with the CUDA library: no headers, no helpers, no tables.
  *
- * What it computes: T applications of one of the four stencil operators of Listings 1-4 of
+ * What it computes: T applications of one of the five stencil operators of Listings 1-4 of
  * Malas et al. (arXiv 1510.04995, Sect. 2.2) to the interior of a padded 3D grid, in FP64, in the
  * plain lexicographic ("naive") order of the 1D example of Sect. 2.1.1: every time step reads the
  * level-t array and writes the level-(t+1) array; the two arrays swap roles after each step.  The
@@ -21,6 +21,8 @@
  *   25pt var   (Listing 4's 13 axis-symmetric coefficient grids, with the second-order-in-time
  *       update of Listing 3):  (2*V - U) + (C00*V + C01*(x+1 + x-1) + C02*(y+1 + y-1)
  *       + C03*(z+1 + z-1) + C04*(x+2 pair) + ... + C12*(z+4 pair))
+ *   25pt C grid (Listing 3 as printed, with its per-point factor grid C):
+ *       (2*V - U) + C * (c0*V + c1*(x+1 + x-1 + y+1 + y-1 + z+1 + z-1) + ... + c4*(... r=4 ...))
  * For the second-order stencils U is the level t-1 array, overwritten in place by level t+1
  * (Listing 3 writes U = 2V - U + ...).
  *
@@ -108,14 +110,32 @@ static void step_25v(int64_t nx, int64_t ny, int64_t nz, int64_t ldx, const doub
       }
 }
 
+static void step_25cg(int64_t nx, int64_t ny, int64_t nz, int64_t ldx, const double* V, double* U,
+                      const double* C, const double* c, int nthreads) {
+  const int64_t R = 4, sy = ny + 2 * R;
+#pragma omp parallel for num_threads(nthreads) schedule(static)
+  for (int64_t k = R; k < R + nz; k++)
+    for (int64_t j = R; j < R + ny; j++)
+      for (int64_t i = R; i < R + nx; i++) {
+        const int64_t p = IDX(i, j, k);
+        /* the bracket of Listing 3, then scaled by the factor of this point */
+        double lap = c[0] * V[p];
+        for (int64_t r = 1; r <= 4; r++)
+          lap = lap + c[r] * (V[IDX(i + r, j, k)] + V[IDX(i - r, j, k)]
+                            + V[IDX(i, j + r, k)] + V[IDX(i, j - r, k)]
+                            + V[IDX(i, j, k + r)] + V[IDX(i, j, k - r)]);
+        U[p] = 2.0 * V[p] - U[p] + C[p] * lap;
+      }
+}
+
 /* Returns 0 on success, 1 on invalid arguments. */
 int oracle_sweep(int stencil, int64_t nx, int64_t ny, int64_t nz, int64_t ldx, int64_t T,
                  double* u, double* u_prev, const double* coeffs, const double* c, int nthreads) {
-  if (stencil < 0 || stencil > 3 || nx < 1 || ny < 1 || nz < 1 || T < 0 || !u || !u_prev) return 1;
+  if (stencil < 0 || stencil > 4 || nx < 1 || ny < 1 || nz < 1 || T < 0 || !u || !u_prev) return 1;
   const int64_t R = (stencil >= 2) ? 4 : 1;
   if (ldx < nx + 2 * R) return 1;
-  if ((stencil == 1 || stencil == 3) && !coeffs) return 1;
-  if ((stencil == 0 || stencil == 2) && !c) return 1;
+  if ((stencil == 1 || stencil == 3 || stencil == 4) && !coeffs) return 1;
+  if ((stencil == 0 || stencil == 2 || stencil == 4) && !c) return 1;
   if (nthreads < 1) nthreads = 1;
   double* buf[2] = {u, u_prev};
   for (int64_t t = 0; t < T; t++) {
@@ -125,7 +145,8 @@ int oracle_sweep(int stencil, int64_t nx, int64_t ny, int64_t nz, int64_t ldx, i
       case 0: step_7c(nx, ny, nz, ldx, V, U, c, nthreads); break;
       case 1: step_7v(nx, ny, nz, ldx, V, U, coeffs, nthreads); break;
       case 2: step_25c(nx, ny, nz, ldx, V, U, c, nthreads); break;
-      default: step_25v(nx, ny, nz, ldx, V, U, coeffs, nthreads); break;
+      case 3: step_25v(nx, ny, nz, ldx, V, U, coeffs, nthreads); break;
+      default: step_25cg(nx, ny, nz, ldx, V, U, coeffs, c, nthreads); break;
     }
   }
   if (T % 2 == 1) { /* level T sits in u_prev: exchange contents so that u holds level T */

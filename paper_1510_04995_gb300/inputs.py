@@ -21,6 +21,7 @@ Workload recipes (the configurations the sweeps are measured and tested on):
   7v  : u0 ~ U[-1,1]; C1..C6 ~ U[0,1/7] (streams 2..7); C0 = 1 - (C1+...+C6) summed in that order in FP64.
   25c : u0 ~ U[-1,1]; u_prev = u0 (zero initial velocity); c0 = -0.9, c_r = 0.1/2^r.
   25v : u0 ~ U[-1,1]; u_prev = u0; C00..C12 ~ U[0,0.01] (streams 1..13).
+  25cg: u0 ~ U[-1,1]; u_prev = u0; c as 25c; the per-point factor C ~ U[0.5,1] (stream 1).
 """
 from __future__ import annotations
 
@@ -33,11 +34,12 @@ M1 = 0xBF58476D1CE4E5B9
 M2 = 0x94D049BB133111EB
 DEFAULT_SEED = 20151016
 
-RADIUS = {0: 1, 1: 1, 2: 4, 3: 4}
-NCOEF = {0: 0, 1: 7, 2: 0, 3: 13}
-SECOND_ORDER = {0: False, 1: False, 2: True, 3: True}
-STENCIL_NAMES = {0: "7pt_const", 1: "7pt_var", 2: "25pt_const", 3: "25pt_var"}
-CONST_COEFFS = {0: (0.4, 0.1), 2: (-0.9, 0.1 / 2, 0.1 / 4, 0.1 / 8, 0.1 / 16)}
+RADIUS = {0: 1, 1: 1, 2: 4, 3: 4, 4: 4}
+NCOEF = {0: 0, 1: 7, 2: 0, 3: 13, 4: 1}
+SECOND_ORDER = {0: False, 1: False, 2: True, 3: True, 4: True}
+STENCIL_NAMES = {0: "7pt_const", 1: "7pt_var", 2: "25pt_const", 3: "25pt_var", 4: "25pt_cgrid"}
+CONST_COEFFS = {0: (0.4, 0.1), 2: (-0.9, 0.1 / 2, 0.1 / 4, 0.1 / 8, 0.1 / 16),
+                4: (-0.9, 0.1 / 2, 0.1 / 4, 0.1 / 8, 0.1 / 16)}
 
 
 def _mix_int(z: int) -> int:
@@ -117,10 +119,10 @@ def _field(seed, stream, nx, ny, nz, R, ldx, a, b, backend, device):
 
 def make_problem(stencil: int, nx: int, ny: int, nz: int, seed: int = DEFAULT_SEED,
                  ldx: int | None = None, backend: str = "numpy", device=None):
-    """Return (u, u_prev, coeffs, c) in FP64 for one of the four workloads.
+    """Return (u, u_prev, coeffs, c) in FP64 for one of the five workloads.
 
     u, u_prev: padded grids.  coeffs: None or an array [ncoef, *padded] (coefficient halo = 0).
-    c: tuple of the constant coefficients (empty for variable-coefficient stencils).
+    c: tuple of the constant coefficients (empty for the variable-coefficient stencils 1 and 3).
     """
     R = RADIUS[stencil]
     u = _field(seed, 0, nx, ny, nz, R, ldx, -1.0, 1.0, backend, device)
@@ -139,6 +141,9 @@ def make_problem(stencil: int, nx: int, ny: int, nz: int, seed: int = DEFAULT_SE
         grids = [_field(seed, 1 + m, nx, ny, nz, R, ldx, 0.0, 0.01, backend, device) for m in range(13)]
         lib = np if backend == "numpy" else __import__("torch")
         coeffs = lib.stack(grids)
+    elif stencil == 4:
+        lib = np if backend == "numpy" else __import__("torch")
+        coeffs = lib.stack([_field(seed, 1, nx, ny, nz, R, ldx, 0.5, 1.0, backend, device)])
     c = CONST_COEFFS.get(stencil, ())
     return u, u_prev, coeffs, c
 

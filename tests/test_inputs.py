@@ -36,3 +36,8 @@ def test_problem_recipes():
     assert np.array_equal(u, up)
     assert c == ()
     assert inputs.make_problem(2, 4, 4, 4)[3] == (-0.9, 0.05, 0.025, 0.0125, 0.00625)
+    u, up, co, c = inputs.make_problem(4, 5, 4, 3)
+    assert co.shape == (1, 11, 12, 13) and np.array_equal(u, up)
+    inner = co[0][4:-4, 4:-4, 4:-4]
+    assert inner.min() >= 0.5 and inner.max() < 1.0 and co[0].sum() == inner.sum()  # zero halo
+    assert c == (-0.9, 0.05, 0.025, 0.0125, 0.00625)

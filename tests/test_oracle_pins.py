@@ -7,7 +7,9 @@ index, a transposed axis, a wrong coefficient grid) fails at least one of them:
   and sine modes of the 25-point leapfrog follow their scalar recurrence inside the light cone;
 * invariants: constant fields are preserved when the weights sum to one (7-point) or when the
   Laplacian part annihilates constants (25-point), linearity, impulse responses;
-* special cases: uniform coefficient grids reduce the variable stencils to the constant ones.
+* special cases: uniform coefficient grids reduce the variable stencils to the constant ones,
+  and a unit factor grid reduces Listing 3 as printed (25-point with the factor grid C) to the
+  25-point constant stencil.
 """
 import math
 
@@ -23,13 +25,13 @@ def _grid(stencil, n, seed=7, ldx=None):
     return inputs.make_problem(stencil, n, n, n, seed=seed, ldx=ldx)
 
 
-@pytest.mark.parametrize("stencil", [0, 1, 2, 3])
+@pytest.mark.parametrize("stencil", [0, 1, 2, 3, 4])
 @pytest.mark.parametrize("T", [1, 2, 3])
 def test_brute_force_bitwise(stencil, T):
     """Oracle loop nests == table-driven per-point evaluation on 8^3 (Listings 1-4)."""
     R = inputs.RADIUS[stencil]
     u, up, co, c = _grid(stencil, 8)
-    if stencil in (2, 3):  # a non-trivial u_prev so the 2V - U term is exercised
+    if stencil in (2, 3, 4):  # a non-trivial u_prev so the 2V - U term is exercised
         up = up.copy()
         up[R:-R, R:-R, R:-R] *= 0.5
     bu, bup = brute.sweep(stencil, u, up, co, c, T, R)
@@ -87,14 +89,15 @@ def test_constant_preserved_7pt(stencil):
     assert np.max(np.abs(u - cval)) <= 4 * T * np.finfo(float).eps
 
 
-@pytest.mark.parametrize("stencil", [2, 3])
+@pytest.mark.parametrize("stencil", [2, 3, 4])
 def test_constant_preserved_25pt(stencil):
-    """Leapfrog with a Laplacian part that annihilates constants keeps u = u_prev = const."""
+    """Leapfrog with a Laplacian part that annihilates constants keeps u = u_prev = const (with the
+    factor grid: whatever the factors, since they multiply a zero bracket)."""
     n, T, cval = 12, 4, -0.3
     u, up, co, c = _grid(stencil, n)
     u[:] = cval
     up[:] = cval
-    if stencil == 2:
+    if stencil in (2, 4):
         c = (-6 * (0.05 + 0.025 + 0.0125 + 0.00625), 0.05, 0.025, 0.0125, 0.00625)
     else:
         co = co.copy()
@@ -130,6 +133,52 @@ def test_25c_light_cone_sine_mode():
     assert err < 1e-12
     # outside the cone the wall is felt: the identity must NOT hold everywhere (the test has teeth)
     assert np.max(np.abs(u[R:-R, R:-R, R:-R] - aT * phi[R:-R, R:-R, R:-R])) > 1e-6
+
+
+@pytest.mark.parametrize("kappa", [0.75, 0.5])
+def test_25cg_light_cone_sine_mode(kappa):
+    """Listing 3 as printed with a uniform factor grid C = kappa: inside the light cone a sine mode
+    follows a_{t+1} = (2 + kappa*lam) a_t - a_{t-1}, a_0 = a_{-1} = 1 (the factor scales the whole
+    bracket, centre term included, and not the leapfrog terms 2V - U)."""
+    n, T, R = 72, 6, 4
+    c = (-0.9, 0.05, 0.025, 0.0125, 0.00625)
+    th = (2 * math.pi / 13, 2 * math.pi / 19, 2 * math.pi / 29)
+    idx = np.arange(n + 2 * R, dtype=np.float64)
+    f = [np.sin(t * idx + 0.7) for t in th]
+    phi = f[2][:, None, None] * f[1][None, :, None] * f[0][None, None, :]
+    u = np.zeros_like(phi)
+    u[R:-R, R:-R, R:-R] = phi[R:-R, R:-R, R:-R]
+    up = u.copy()
+    co = np.zeros((1,) + u.shape)
+    co[0, R:-R, R:-R, R:-R] = kappa
+    oracle.sweep(4, u, up, co, c, T, n, n, n)
+    lam = c[0] + 2 * sum(c[r] * sum(math.cos(r * t) for t in th) for r in range(1, 5))
+    from decimal import Decimal, getcontext
+    getcontext().prec = 50
+    a_prev, a = Decimal(1), Decimal(1)
+    L = Decimal(2) + Decimal(kappa) * Decimal(lam)
+    for _ in range(T):
+        a_prev, a = a, L * a - a_prev
+    aT = float(a)
+    m = R + R * T + 1
+    core = (slice(m, n + 2 * R - m),) * 3
+    err = np.max(np.abs(u[core] - aT * phi[core])) / np.max(np.abs(aT * phi[core]))
+    assert err < 1e-12
+    assert np.max(np.abs(u[R:-R, R:-R, R:-R] - aT * phi[R:-R, R:-R, R:-R])) > 1e-6
+
+
+def test_25cg_unit_factor_equals_25c():
+    """A factor grid of ones reduces Listing 3 as printed to the 25-point constant stencil, bit for
+    bit (multiplying by 1 is exact)."""
+    n, T = 12, 4
+    u, up, _, c = _grid(2, n)
+    up = up.copy()
+    up[4:-4, 4:-4, 4:-4] *= 0.25
+    u2, up2 = u.copy(), up.copy()
+    co = np.ones((1,) + u.shape)
+    oracle.sweep(2, u, up, None, c, T, n, n, n)
+    oracle.sweep(4, u2, up2, co, c, T, n, n, n)
+    assert np.array_equal(u, u2) and np.array_equal(up, up2)
 
 
 def test_7v_uniform_equals_7c():
@@ -175,6 +224,13 @@ def _impulse_pattern(stencil, co, c, R, n):
         for r in range(1, 5):
             for d in [(r, 0, 0), (-r, 0, 0), (0, r, 0), (0, -r, 0), (0, 0, r), (0, 0, -r)]:
                 exp[d] = c[r]
+    elif stencil == 4:
+        # the point at p + d updates with its own factor C(p + d) times c_r (the impulse is its
+        # neighbour at -d); the centre keeps 2V and gains C(p) * c0
+        exp[(0, 0, 0)] = 2.0 + co[0, m, m, m] * c[0]
+        for r in range(1, 5):
+            for d in [(r, 0, 0), (-r, 0, 0), (0, r, 0), (0, -r, 0), (0, 0, r), (0, 0, -r)]:
+                exp[d] = co[0, m + d[2], m + d[1], m + d[0]] * c[r]
     else:
         exp[(0, 0, 0)] = 2.0 + co[0, m, m, m]
         g = 1
@@ -188,7 +244,7 @@ def _impulse_pattern(stencil, co, c, R, n):
     return m, exp
 
 
-@pytest.mark.parametrize("stencil", [0, 1, 2, 3])
+@pytest.mark.parametrize("stencil", [0, 1, 2, 3, 4])
 def test_impulse_response(stencil):
     R = inputs.RADIUS[stencil]
     n = 11
@@ -204,7 +260,7 @@ def test_impulse_response(stencil):
     assert np.array_equal(u, ref)
 
 
-@pytest.mark.parametrize("stencil", [0, 1, 2, 3])
+@pytest.mark.parametrize("stencil", [0, 1, 2, 3, 4])
 def test_linearity(stencil):
     n, T = 10, 3
     u1, up1, co, c = _grid(stencil, n, seed=1)
@@ -220,7 +276,7 @@ def test_linearity(stencil):
 def test_padded_leading_dimension_matches_dense():
     """A padded x pitch (ldx > nx + 2R) changes nothing in the interior."""
     n, T = 9, 4
-    for stencil in range(4):
+    for stencil in range(5):
         u, up, co, c = _grid(stencil, n)
         R = inputs.RADIUS[stencil]
         u2, up2, co2, _ = _grid(stencil, n, ldx=n + 2 * R + 5)
