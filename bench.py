@@ -40,11 +40,14 @@ WORKLOADS = {
     "25pt_const_f32_384": (2, "f32", 384, 384, 384, 32),
     "25pt_var_f64_384": (3, "f64", 384, 384, 384, 32),
     "25pt_var_f32_384": (3, "f32", 384, 384, 384, 32),
+    "25pt_cgrid_f64_384": (4, "f64", 384, 384, 384, 32),
+    "25pt_cgrid_f32_384": (4, "f32", 384, 384, 384, 32),
 }
 DEFAULT = "7pt_const_f64_512"
-STENCIL_NAME = {0: "7-point constant", 1: "7-point variable", 2: "25-point constant", 3: "25-point variable"}
+STENCIL_NAME = {0: "7-point constant", 1: "7-point variable", 2: "25-point constant", 3: "25-point variable",
+                4: "25-point constant with factor grid"}
 # FP instructions per LUP of the point update (explicitly rounded ops, see csrc/stencil.cuh)
-INSTR_PER_LUP = {0: 7, 1: 7, 2: 28, 3: 28}
+INSTR_PER_LUP = {0: 7, 1: 7, 2: 28, 3: 28, 4: 28}
 # DRAM bytes per LUP measured by ncu (dram__bytes_read.sum + dram__bytes_write.sum of one launch
 # / LUPs of that launch) for a kernel on a smaller grid of the same workload, with the summary it
 # comes from; the roofline's "traffic" scales it to one launch of the benchmark grid
@@ -52,8 +55,8 @@ MEASURED_BYTES_PER_LUP = {
     ("naive", 0, "f64"): (15.61, "profiles/naive_7pt_const_f64_512x384x256.md"),
 }
 # domain-sized streams N_D of the code-balance model and the spatial minimum bytes per LUP (in elements)
-ND = {0: 2, 1: 9, 2: 2, 3: 15}
-SPATIAL_ELEMS = {0: 2, 1: 9, 2: 3, 3: 16}
+ND = {0: 2, 1: 9, 2: 2, 3: 15, 4: 3}
+SPATIAL_ELEMS = {0: 2, 1: 9, 2: 3, 3: 16, 4: 4}
 
 
 def _peaks():

@@ -356,7 +356,7 @@ int girih_plan(girih_plan_t* out, int32_t stencil, int64_t nx, int64_t ny, int64
                int64_t T) {
   if (!out) return fail(GIRIH_EINVAL, "out is NULL");
   *out = nullptr;
-  if (stencil < 0 || stencil > 3) return fail(GIRIH_EINVAL, "unknown stencil %d", stencil);
+  if (stencil < 0 || stencil > 4) return fail(GIRIH_EINVAL, "unknown stencil %d", stencil);
   if (dtype != GIRIH_F64 && dtype != GIRIH_F32) return fail(GIRIH_EINVAL, "unknown dtype %d", dtype);
   if (nx < 1 || ny < 1 || nz < 1) return fail(GIRIH_EINVAL, "sizes must be >= 1");
   if (T < 0 || T > (1LL << 30)) return fail(GIRIH_EINVAL, "T=%lld out of range", (long long)T);

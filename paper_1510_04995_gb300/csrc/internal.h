@@ -110,6 +110,6 @@ inline int mwd_max_threads(int G, int lbf) {
 cudaError_t launch_swap(void* a, void* b, int64_t bytes, cudaStream_t st);
 
 inline int radius_of(int stencil) { return stencil >= 2 ? 4 : 1; }
-inline int ncoef_of(int stencil) { return stencil == 1 ? 7 : (stencil == 3 ? 13 : 0); }
+inline int ncoef_of(int stencil) { return stencil == 1 ? 7 : (stencil == 3 ? 13 : (stencil == 4 ? 1 : 0)); }
 
 }  // namespace girih

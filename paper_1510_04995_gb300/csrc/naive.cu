@@ -287,7 +287,8 @@ int naive_tile_x(int stencil, int dtype, bool v16) {
     case 0: return pick(std::integral_constant<int, 0>());
     case 1: return pick(std::integral_constant<int, 1>());
     case 2: return pick(std::integral_constant<int, 2>());
-    default: return pick(std::integral_constant<int, 3>());
+    case 3: return pick(std::integral_constant<int, 3>());
+    default: return pick(std::integral_constant<int, 4>());
   }
 }
 
@@ -302,7 +303,8 @@ int naive_resident_blocks(int stencil, int dtype, bool v16) {
     case 0: return pick(std::integral_constant<int, 0>());
     case 1: return pick(std::integral_constant<int, 1>());
     case 2: return pick(std::integral_constant<int, 2>());
-    default: return pick(std::integral_constant<int, 3>());
+    case 3: return pick(std::integral_constant<int, 3>());
+    default: return pick(std::integral_constant<int, 4>());
   }
 }
 
@@ -335,7 +337,8 @@ cudaError_t launch_naive_step(int stencil, int dtype, const NaiveArgs& a, cudaSt
     case 0: return f64 ? launch_v<0, double>(a, st) : launch_v<0, float>(a, st);
     case 1: return f64 ? launch_v<1, double>(a, st) : launch_v<1, float>(a, st);
     case 2: return f64 ? launch_v<2, double>(a, st) : launch_v<2, float>(a, st);
-    default: return f64 ? launch_v<3, double>(a, st) : launch_v<3, float>(a, st);
+    case 3: return f64 ? launch_v<3, double>(a, st) : launch_v<3, float>(a, st);
+    default: return f64 ? launch_v<4, double>(a, st) : launch_v<4, float>(a, st);
   }
 }
 

@@ -1,4 +1,4 @@
-// Point updates of the four stencils (arXiv 1510.04995, Sect. 2.2, Listings 1-4) and the small
+// Point updates of the five stencils (arXiv 1510.04995, Sect. 2.2, Listings 1-4) and the small
 // device helpers the sweep kernels share.
 //
 // Every kernel of the library computes a lattice-site update (LUP) through exactly one of the
@@ -14,6 +14,7 @@
 //               U' = ((V + V) - U) + lap      (Listing 3 with the per-point factor equal to 1)
 //   25pt var  : acc = C00*V; for r=1..4: acc += C(3r-2)*(x pair) + C(3r-1)*(y pair) + C(3r)*(z pair)
 //               U' = ((V + V) - U) + acc
+//   25pt Cgrid: lap as 25pt const; U' = fma(C, lap, (V + V) - U)   (Listing 3 as printed)
 #pragma once
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -30,6 +31,8 @@ template <>
 struct Traits<2> { static constexpr int R = 4, NCOEF = 0; static constexpr bool ORDER2 = true; };
 template <>
 struct Traits<3> { static constexpr int R = 4, NCOEF = 13; static constexpr bool ORDER2 = true; };
+template <>
+struct Traits<4> { static constexpr int R = 4, NCOEF = 1; static constexpr bool ORDER2 = true; };
 
 template <typename T>
 struct Ops;
@@ -70,7 +73,7 @@ __device__ __forceinline__ T point_update(const A& a, const T* cst) {
     acc = O::fma(a.k(5), a.z(1), acc);
     acc = O::fma(a.k(6), a.z(-1), acc);
     return acc;
-  } else if constexpr (S == 2) {
+  } else if constexpr (S == 2 || S == 4) {
     const T v = a.c();
     T lap = O::mul(cst[0], v);
 #pragma unroll
@@ -82,6 +85,7 @@ __device__ __forceinline__ T point_update(const A& a, const T* cst) {
       s = O::add(s, a.z(-r));
       lap = O::fma(cst[r], s, lap);
     }
+    if constexpr (S == 4) return O::fma(a.k(0), lap, O::sub(O::add(v, v), a.u()));
     return O::add(O::sub(O::add(v, v), a.u()), lap);
   } else {
     const T v = a.c();
@@ -97,7 +101,8 @@ __device__ __forceinline__ T point_update(const A& a, const T* cst) {
 }
 
 // Arithmetic instructions per LUP of point_update (each intrinsic is one FP instruction):
-// 7pt const 7, 7pt var 7, 25pt const 1 + 4*6 + 3 = 28, 25pt var 1 + 12*2 + 3 = 28.
+// 7pt const 7, 7pt var 7, 25pt const 1 + 4*6 + 3 = 28, 25pt var 1 + 12*2 + 3 = 28, 25pt Cgrid
+// 1 + 4*6 + 3 = 28.
 __host__ __device__ constexpr int fp_instructions_per_lup(int s) { return s < 2 ? 7 : 28; }
 
 // ---- small PTX helpers (sm_90+ cluster features, cp.async) -------------------------------------

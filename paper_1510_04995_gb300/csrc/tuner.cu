@@ -36,7 +36,7 @@ __global__ void tune_fill(T* u, T* up, T* co, int64_t n, int ncoef) {
     const T v = (T)((double)(z >> 11) * (2.0 / 9007199254740992.0) - 1.0);
     u[i] = v;
     up[i] = v;
-    for (int g = 0; g < ncoef; ++g) co[g * n + i] = (ncoef == 7) ? (T)(1.0 / 7.0) : (T)0.003;
+    for (int g = 0; g < ncoef; ++g) co[g * n + i] = (ncoef == 7) ? (T)(1.0 / 7.0) : (ncoef == 1 ? (T)0.75 : (T)0.003);
   }
 }
 
@@ -216,9 +216,9 @@ int girih_tune_exhaustive(girih_plan_t plan, const girih_config* cand_list, int3
 
 int girih_mlp_features(int32_t stencil, int32_t dtype, int64_t nx, int64_t ny, int64_t nz, const girih_config* cfg,
                        float* out) {
-  if (!cfg || !out || stencil < 0 || stencil > 3) return fail(GIRIH_EINVAL, "bad feature arguments");
+  if (!cfg || !out || stencil < 0 || stencil > 4) return fail(GIRIH_EINVAL, "bad feature arguments");
   for (int i = 0; i < GIRIH_MLP_FEATURES; ++i) out[i] = 0.f;
-  out[stencil] = 1.f;
+  out[stencil == GIRIH_25PT_CGRID ? GIRIH_25PT_CONST : stencil] = 1.f;
   out[4] = dtype == GIRIH_F32 ? 1.f : 0.f;
   out[5] = (float)(std::log2((double)nx) / 10.0);
   out[6] = (float)(std::log2((double)ny) / 10.0);

@@ -30,8 +30,10 @@ WORKLOADS = {
     "25pt_const_f32_384": (2, "f32", 384, 384, 384, 32),
     "25pt_var_f64_384": (3, "f64", 384, 384, 384, 32),
     "25pt_var_f32_384": (3, "f32", 384, 384, 384, 32),
+    "25pt_cgrid_f64_384": (4, "f64", 384, 384, 384, 32),
+    "25pt_cgrid_f32_384": (4, "f32", 384, 384, 384, 32),
 }
-RADIUS = {0: 1, 1: 1, 2: 4, 3: 4}
+RADIUS = {0: 1, 1: 1, 2: 4, 3: 4, 4: 4}
 
 
 def aligned_ldx(stencil: int, dtype: str, nx: int) -> int:

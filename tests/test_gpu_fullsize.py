@@ -60,16 +60,17 @@ def _run_pair(workload):
 
 
 @pytest.mark.parametrize("workload", ["7pt_const_f64_512", "7pt_const_f32_512", "7pt_var_f32_480",
-                                      "25pt_const_f32_384", "25pt_var_f32_384", "25pt_const_f64_384"])
+                                      "25pt_const_f32_384", "25pt_var_f32_384", "25pt_const_f64_384",
+                                      "25pt_cgrid_f32_384"])
 def test_blocked_equals_naive_full_size(workload):
     import torch
     p, cfg, (bu, bup), (nu, nup), _ = _run_pair(workload)
     assert torch.equal(bu, nu) and torch.equal(bup, nup), (workload, cfg)
 
 
-def test_sampled_points_against_oracle_cones():
+@pytest.mark.parametrize("workload", ["7pt_const_f64_512", "25pt_cgrid_f64_384"])
+def test_sampled_points_against_oracle_cones(workload):
     import torch
-    workload = "7pt_const_f64_512"
     p, cfg, (bu, _), _, (stencil, dtype, nx, ny, nz, T) = _run_pair(workload)
     R = inputs.RADIUS[stencil]
     h = R * T
@@ -81,7 +82,9 @@ def test_sampled_points_against_oracle_cones():
         hi = [min(q + h + 1, n) for q, n in zip((i, j, k), (nx, ny, nz))]
         sub = np.ascontiguousarray(u0[lo[2]:hi[2] + 2 * R, lo[1]:hi[1] + 2 * R, lo[0]:hi[0] + 2 * R])
         sup = sub.copy()
-        oracle.sweep(stencil, sub, sup, None, c, T, hi[0] - lo[0], hi[1] - lo[1], hi[2] - lo[2], nthreads=16)
+        sco = None if co is None else np.ascontiguousarray(
+            co[:, lo[2]:hi[2] + 2 * R, lo[1]:hi[1] + 2 * R, lo[0]:hi[0] + 2 * R])
+        oracle.sweep(stencil, sub, sup, sco, c, T, hi[0] - lo[0], hi[1] - lo[1], hi[2] - lo[2], nthreads=16)
         ref = sub[k - lo[2] + R, j - lo[1] + R, i - lo[0] + R]
         got = float(bu[k + R, j + R, i + R])
         assert abs(got - ref) <= 1e-12 * scale, ((i, j, k), got, ref)
