@@ -32,9 +32,12 @@ struct NaiveAcc {  // one column of the thread's VX columns
 
 // Block = 32 x TY threads over a 32 x 2TY tile of (x, y) columns and a chunk of z planes; each
 // thread owns rows ty and ty + TY.  The tile's planes (with the R-wide halo) stream through a
-// ring of NP shared-memory slots filled PD planes ahead of use (one commit group per plane).
-// The z window of each owned column stays in registers; its new value and the x/y neighbours
-// come from the ring.  One barrier per plane.
+// ring of NP = R + PD + 2 shared-memory slots filled PD planes ahead of use (one commit group
+// per plane): at the update of plane z the ring holds padded planes z+R (the x/y neighbours)
+// up to z+2R+PD+1 and one slot that is being refilled.  The z window of each owned column
+// stays in registers: its R lowest planes are loaded from global memory at the start, the rest
+// and every new value come from the ring.  The level t-1 centres of the second-order stencils
+// and the coefficients are loaded into registers one plane ahead.  One barrier per plane.
 //
 // V16 (rows of 16-byte multiples, 16-byte aligned buffers): 16-byte cp.async.cg chunks, the tile
 // row widened to whole chunks.  Otherwise: element cp.async.
@@ -51,12 +54,10 @@ __global__ void __launch_bounds__(32 * TY) naive_kernel(const NaiveArgs a) {
   constexpr int TX = 32 * VX;                  // tile columns
   constexpr int TXW = V16 ? (TX + 2 * R + A16 - 1) / A16 * A16 : TX + 2 * R;  // shared row width
   constexpr int TYW = ROWS + 2 * R, TP = TXW * TYW;
-  // ring slots: the first window needs planes 0..2R plus PD staged ahead (2R+PD+1 at once); in
-  // the steady state planes z+R .. z+2R+PD+1 are live (R+PD+2), which is never more
-  constexpr int NP = 2 * R + PD + 1;
+  // ring slots: planes z+R .. z+2R+PD+1 are live at the update of plane z (R+PD+2)
+  constexpr int NP = R + PD + 2;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* ring = reinterpret_cast<T*>(smem_raw);       // [NP][TYW][TXW]
-  T* uring = ring + NP * TP;                       // second order: [NP][ROWS][TX] level t-1 centres
   const T* __restrict__ V = static_cast<const T*>(a.V);
   T* __restrict__ U = static_cast<T*>(a.U);
   const T* __restrict__ coef = static_cast<const T*>(a.coef);
@@ -91,18 +92,6 @@ __global__ void __launch_bounds__(32 * TY) naive_kernel(const NaiveArgs a) {
     so[k] = ok ? r * TXW + c : -1;
     go[k] = ok ? r * ldx + c : 0;
   }
-  // level t-1 centres (second order, R = 4: interior columns bx+R.. start on a 16-byte boundary)
-  constexpr int UNC = TX / W;                  // items per centre row
-  constexpr int UPT = (ROWS * UNC + 32 * TY - 1) / (32 * TY);
-  int uso[UPT], ugo[UPT];
-#pragma unroll
-  for (int k = 0; k < UPT; ++k) {
-    const int i = tid + k * 32 * TY;
-    const int r = i / UNC, c = (i - r * UNC) * W;
-    const bool ok = Traits<S>::ORDER2 && i < ROWS * UNC && by + r < ny && (V16 ? bx + R + c < ldx : bx + c < nx);
-    uso[k] = ok ? r * TX + c : -1;
-    ugo[k] = ok ? r * ldx + c : 0;
-  }
   auto copy = [&](T* dst, const T* src) {
     if constexpr (V16) cp_async16_cg(dst, src);
     else cp_async(dst, src);
@@ -116,25 +105,12 @@ __global__ void __launch_bounds__(32 * TY) naive_kernel(const NaiveArgs a) {
 #pragma unroll
       for (int k = 0; k < CPT; ++k)
         if (so[k] >= 0) copy(dst + so[k], src + go[k]);
-      if constexpr (Traits<S>::ORDER2) {
-        // level t-1 centres of interior plane z0 + q - R (used when that plane is updated)
-        const int zi = q - R;
-        if (zi >= 0 && zi < nzb) {
-          T* ud = uring + (q % NP) * (ROWS * TX);
-          const T* us = Ub + (int64_t)zi * plane;
-#pragma unroll
-          for (int k = 0; k < UPT; ++k)
-            if (uso[k] >= 0) copy(ud + uso[k], us + ugo[k]);
-        }
-      }
     }
     cp_async_commit();
   };
 
-  // planes z0 .. z0+2R fill the windows; planes up to z0 + 2R + PD are staged ahead
-  for (int q = 0; q <= 2 * R + PD; ++q) stage(q);
-  cp_async_wait_all();
-  __syncthreads();
+  // planes z0+R .. z0+2R fill the upper windows; planes up to z0 + 2R + PD are staged ahead
+  for (int q = R; q <= 2 * R + PD; ++q) stage(q);
 
   bool act[2][VX];
   int cofs[2];  // shared offset of the thread's first column in each row
@@ -146,11 +122,21 @@ __global__ void __launch_bounds__(32 * TY) naive_kernel(const NaiveArgs a) {
 #pragma unroll
     for (int v = 0; v < VX; ++v) {
       act[r][v] = (bx + v * 32 + tx < nx) && (by + row < ny);
+      // the R planes below the first updated one, straight from global memory
 #pragma unroll
-      for (int i = 0; i <= 2 * R; ++i) w[r][v][i] = ring[i * TP + cofs[r] + v * 32];
+      for (int i = 0; i < R; ++i)
+        w[r][v][i] = act[r][v] ? Vb[(int64_t)i * plane + (row + R) * ldx + tx + R + v * 32] : T(0);
     }
   }
-  // every thread has its first window before the first in-loop staging overwrites slot 0
+  cp_async_wait_all();
+  __syncthreads();
+#pragma unroll
+  for (int r = 0; r < 2; ++r)
+#pragma unroll
+    for (int v = 0; v < VX; ++v)
+#pragma unroll
+      for (int i = R; i <= 2 * R; ++i) w[r][v][i] = ring[(i % NP) * TP + cofs[r] + v * 32];
+  // every thread has its first window before the first in-loop staging refills a slot
   __syncthreads();
   // coefficients of the first plane, then one plane ahead
   T kv[2][VX][NC > 0 ? NC : 1], kn[2][VX][NC > 0 ? NC : 1];
@@ -164,6 +150,15 @@ __global__ void __launch_bounds__(32 * TY) naive_kernel(const NaiveArgs a) {
 #pragma unroll
         for (int g = 0; g < NC; ++g)
           kn[r][v][g] = act[r][v] ? __ldg(cb + g * gs + (ty + r * TY) * ldx + v * 32 + tx) : T(0);
+  }
+  // level t-1 centres (second order): read from the output buffer before this thread overwrites
+  // them, one plane ahead (each is read and written by its owning thread only)
+  T un[2][VX];
+  if constexpr (Traits<S>::ORDER2) {
+#pragma unroll
+    for (int r = 0; r < 2; ++r)
+#pragma unroll
+      for (int v = 0; v < VX; ++v) un[r][v] = act[r][v] ? __ldcg(Ub + (ty + r * TY) * ldx + v * 32 + tx) : T(0);
   }
 
   for (int zr = 0; zr < nzb; ++zr) {
@@ -180,6 +175,18 @@ __global__ void __launch_bounds__(32 * TY) naive_kernel(const NaiveArgs a) {
                               : T(0);
           }
     }
+    T uc[2][VX];
+    if constexpr (Traits<S>::ORDER2) {
+#pragma unroll
+      for (int r = 0; r < 2; ++r)
+#pragma unroll
+        for (int v = 0; v < VX; ++v) {
+          uc[r][v] = un[r][v];
+          un[r][v] = (act[r][v] && zr + 1 < nzb)
+                         ? __ldcg(Ub + (int64_t)(zr + 1) * plane + (ty + r * TY) * ldx + v * 32 + tx)
+                         : T(0);
+        }
+    }
     const T* tl = ring + ((zr + R) % NP) * TP;  // padded plane z0 + zr + R = interior plane z0 + zr
 #pragma unroll
     for (int r = 0; r < 2; ++r) {
@@ -187,8 +194,7 @@ __global__ void __launch_bounds__(32 * TY) naive_kernel(const NaiveArgs a) {
       for (int v = 0; v < VX; ++v) {
         if (act[r][v]) {
           NaiveAcc<S, T, TXW> acc{tl + cofs[r] + v * 32, w[r][v], kv[r][v], T(0)};
-          if constexpr (Traits<S>::ORDER2)
-            acc.uc = uring[((zr + R) % NP) * (ROWS * TX) + (ty + r * TY) * TX + v * 32 + tx];
+          if constexpr (Traits<S>::ORDER2) acc.uc = uc[r][v];
           Ub[(int64_t)zr * plane + (ty + r * TY) * ldx + v * 32 + tx] = point_update<S, T>(acc, cst);
         }
       }
@@ -214,8 +220,8 @@ constexpr int kTY = 8;
 
 int naive_block_rows(int, int) { return 2 * kTY; }
 
-// Planes staged ahead of use (4 for the 7-point stencils, 2 for the radius-4 ones, whose ring of
-// 2R+PD+1 planes is larger).
+// Planes staged ahead of use (4 for the 7-point stencils, 2 for the radius-4 ones, whose planes
+// are larger).
 template <int S, typename T>
 constexpr int naive_pd() { return Traits<S>::R == 1 ? 4 : 2; }
 
@@ -233,8 +239,8 @@ static size_t naive_smem() {
   constexpr int R = Traits<S>::R, PD = naive_pd<S, T>(), A16 = 16 / (int)sizeof(T);
   constexpr int TX = 32 * naive_vx<S, T, V16>();
   constexpr int TXW = V16 ? (TX + 2 * R + A16 - 1) / A16 * A16 : TX + 2 * R;
-  constexpr int NP = 2 * R + PD + 1, TP = TXW * (2 * kTY + 2 * R);
-  return sizeof(T) * ((size_t)NP * TP + (Traits<S>::ORDER2 ? (size_t)NP * 2 * kTY * TX : 0));
+  constexpr int NP = R + PD + 2, TP = TXW * (2 * kTY + 2 * R);
+  return sizeof(T) * (size_t)NP * TP;
 }
 
 // Resident blocks per SM of one naive kernel instance (occupancy query, cached per instance).
