@@ -138,18 +138,30 @@ __global__ void __launch_bounds__(32 * TY) naive_kernel(const NaiveArgs a) {
       for (int i = R; i <= 2 * R; ++i) w[r][v][i] = ring[(i % NP) * TP + cofs[r] + v * 32];
   // every thread has its first window before the first in-loop staging refills a slot
   __syncthreads();
+  // per-column pointers, advanced one plane per update: the output point (also the level t-1
+  // centre of the second-order stencils) and coefficient grid 0 of the next plane
+  T* up[2][VX];
+  const T* kp[2][VX];
+  const int64_t gs = a.g.gstride;
+#pragma unroll
+  for (int r = 0; r < 2; ++r)
+#pragma unroll
+    for (int v = 0; v < VX; ++v) {
+      const int64_t o = (int64_t)(ty + r * TY) * ldx + v * 32 + tx;
+      up[r][v] = Ub + o;
+      kp[r][v] = coef ? coef + (int64_t)(z0 + R) * plane + (int64_t)(by + R) * ldx + (bx + R) + o : nullptr;
+    }
   // coefficients of the first plane, then one plane ahead
   T kv[2][VX][NC > 0 ? NC : 1], kn[2][VX][NC > 0 ? NC : 1];
-  const int64_t gs = a.g.gstride;
-  const T* cb = coef ? coef + (int64_t)(z0 + R) * plane + (int64_t)(by + R) * ldx + (bx + R) : nullptr;
   if constexpr (NC > 0) {
 #pragma unroll
     for (int r = 0; r < 2; ++r)
 #pragma unroll
-      for (int v = 0; v < VX; ++v)
+      for (int v = 0; v < VX; ++v) {
 #pragma unroll
-        for (int g = 0; g < NC; ++g)
-          kn[r][v][g] = act[r][v] ? __ldg(cb + g * gs + (ty + r * TY) * ldx + v * 32 + tx) : T(0);
+        for (int g = 0; g < NC; ++g) kn[r][v][g] = act[r][v] ? __ldg(kp[r][v] + g * gs) : T(0);
+        kp[r][v] += plane;
+      }
   }
   // level t-1 centres (second order): read from the output buffer before this thread overwrites
   // them, one plane ahead (each is read and written by its owning thread only)
@@ -158,22 +170,24 @@ __global__ void __launch_bounds__(32 * TY) naive_kernel(const NaiveArgs a) {
 #pragma unroll
     for (int r = 0; r < 2; ++r)
 #pragma unroll
-      for (int v = 0; v < VX; ++v) un[r][v] = act[r][v] ? __ldcg(Ub + (ty + r * TY) * ldx + v * 32 + tx) : T(0);
+      for (int v = 0; v < VX; ++v) un[r][v] = act[r][v] ? __ldcg(up[r][v]) : T(0);
   }
 
   for (int zr = 0; zr < nzb; ++zr) {
+    const bool more = zr + 1 < nzb;
     if constexpr (NC > 0) {
 #pragma unroll
       for (int r = 0; r < 2; ++r)
 #pragma unroll
-        for (int v = 0; v < VX; ++v)
+        for (int v = 0; v < VX; ++v) {
+          const bool ld = act[r][v] && more;
 #pragma unroll
           for (int g = 0; g < NC; ++g) {
             kv[r][v][g] = kn[r][v][g];
-            kn[r][v][g] = (act[r][v] && zr + 1 < nzb)
-                              ? __ldg(cb + g * gs + (int64_t)(zr + 1) * plane + (ty + r * TY) * ldx + v * 32 + tx)
-                              : T(0);
+            kn[r][v][g] = ld ? __ldg(kp[r][v] + g * gs) : T(0);
           }
+          kp[r][v] += plane;
+        }
     }
     T uc[2][VX];
     if constexpr (Traits<S>::ORDER2) {
@@ -182,9 +196,7 @@ __global__ void __launch_bounds__(32 * TY) naive_kernel(const NaiveArgs a) {
 #pragma unroll
         for (int v = 0; v < VX; ++v) {
           uc[r][v] = un[r][v];
-          un[r][v] = (act[r][v] && zr + 1 < nzb)
-                         ? __ldcg(Ub + (int64_t)(zr + 1) * plane + (ty + r * TY) * ldx + v * 32 + tx)
-                         : T(0);
+          un[r][v] = (act[r][v] && more) ? __ldcg(up[r][v] + plane) : T(0);
         }
     }
     const T* tl = ring + ((zr + R) % NP) * TP;  // padded plane z0 + zr + R = interior plane z0 + zr
@@ -195,8 +207,9 @@ __global__ void __launch_bounds__(32 * TY) naive_kernel(const NaiveArgs a) {
         if (act[r][v]) {
           NaiveAcc<S, T, TXW> acc{tl + cofs[r] + v * 32, w[r][v], kv[r][v], T(0)};
           if constexpr (Traits<S>::ORDER2) acc.uc = uc[r][v];
-          Ub[(int64_t)zr * plane + (ty + r * TY) * ldx + v * 32 + tx] = point_update<S, T>(acc, cst);
+          *up[r][v] = point_update<S, T>(acc, cst);
         }
+        up[r][v] += plane;
       }
     }
     // advance: stage the plane PD ahead, wait for the next window value, one barrier
@@ -220,18 +233,21 @@ constexpr int kTY = 8;
 
 int naive_block_rows(int, int) { return 2 * kTY; }
 
-// Planes staged ahead of use (4 for the 7-point stencils, 2 for the radius-4 ones, whose planes
-// are larger).
+// Planes staged ahead of use: 4 for the 7-point stencils; for the radius-4 ones, whose planes
+// are larger, 2 (25-point constant) or 3 (the stencils with coefficient grids, which also wait
+// on their coefficient loads).  Measured at 384^3.
 template <int S, typename T>
-constexpr int naive_pd() { return Traits<S>::R == 1 ? 4 : 2; }
+constexpr int naive_pd() { return Traits<S>::R == 1 ? 4 : (S == 2 ? 2 : 3); }
 
-// Columns per thread: 4 for the FP32 7-point constant stencil on 16-byte aligned layouts (its
-// sweep was bound by instruction issue: 564 -> 715 GLUP/s at 512^3), else 1 (measured: the
-// FP64 sweeps are bound by the FP64 pipe and the 25-point FP32 sweep lost occupancy; the
-// variable stencils keep a plane of coefficients per column in registers).
+// Columns per thread (16-byte aligned layouts): 4 for the FP32 7-point constant stencil and 2
+// for the FP32 25-point constant one, whose sweeps were bound by instruction issue (the
+// thread's per-plane work -- barrier, staging items, loop and address bookkeeping -- is then
+// shared by 2*VX updates: 564 -> 715 and 291 -> 336 GLUP/s); else 1 (measured: the FP64
+// sweeps are bound by the FP64 pipe, and the stencils with coefficient grids keep a plane of
+// coefficients per column in registers, so more columns cost occupancy).
 template <int S, typename T, bool V16>
 constexpr int naive_vx() {
-  return (V16 && S == 0 && sizeof(T) == 4) ? 4 : 1;
+  return (V16 && sizeof(T) == 4) ? (S == 0 ? 4 : (S == 2 ? 2 : 1)) : 1;
 }
 
 template <int S, typename T, bool V16>
