@@ -52,7 +52,16 @@ INSTR_PER_LUP = {0: 7, 1: 7, 2: 28, 3: 28, 4: 28}
 # / LUPs of that launch) for a kernel on a smaller grid of the same workload, with the summary it
 # comes from; the roofline's "traffic" scales it to one launch of the benchmark grid
 MEASURED_BYTES_PER_LUP = {
-    ("naive", 0, "f64"): (15.61, "profiles/naive_7pt_const_f64_512x384x256.md"),
+    ("naive", 0, "f64"): (15.69, "profiles/naive_7pt_const_f64_512x384x256.md"),
+    ("naive", 0, "f32"): (7.28, "profiles/naive_7pt_const_f32_512x384x256.md"),
+    ("naive", 1, "f64"): (72.84, "profiles/naive_7pt_var_f64_480x384x192.md"),
+    ("naive", 1, "f32"): (36.46, "profiles/naive_7pt_var_f32_480x384x256.md"),
+    ("naive", 2, "f64"): (24.05, "profiles/naive_25pt_const_f64_384x384x192.md"),
+    ("naive", 2, "f32"): (11.66, "profiles/naive_25pt_const_f32_384x384x256.md"),
+    ("naive", 3, "f64"): (132.13, "profiles/naive_25pt_var_f64_384x384x128.md"),
+    ("naive", 3, "f32"): (65.91, "profiles/naive_25pt_var_f32_384x384x192.md"),
+    ("naive", 4, "f64"): (32.35, "profiles/naive_25pt_cgrid_f64_384x384x192.md"),
+    ("naive", 4, "f32"): (16.14, "profiles/naive_25pt_cgrid_f32_384x384x256.md"),
 }
 # domain-sized streams N_D of the code-balance model and the spatial minimum bytes per LUP (in elements)
 ND = {0: 2, 1: 9, 2: 2, 3: 15, 4: 3}
