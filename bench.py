@@ -144,6 +144,24 @@ def _dist():
     return ws, rank, local
 
 
+def max_over_ranks(x, ws, device):
+    """The largest value of x over the ranks (the slowest rank's time); x itself with one rank.
+    Used with NCCL on the GPUs, and with gloo on the host in the multi-rank tests."""
+    if ws <= 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_glups(lups_per_rank, steps, ws, ms):
+    """Whole-job throughput: the updates all ranks made (each rank runs its own replica of the
+    workload) divided by the slowest rank's time."""
+    return lups_per_rank * steps * ws / (ms * 1e-3) * 1e-9
+
+
 def cpu_baseline(stencil, nx, ny, nz, budget_s=10.0, max_T=64, min_T=1):
     """Time the FP64 oracle on this host's cores on the workload's grid for a bounded number of steps."""
     import numpy as np
@@ -321,25 +339,20 @@ def main():
             girih.run(p, u, up, co, c=c, cfg=config, stream=stream)
         ev1.record(stream)
         barrier()
-        ms = ev0.elapsed_time(ev1)
-        if ws > 1:
-            t = torch.tensor([ms], device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ms = float(t.item())
-        return ms
+        return max_over_ranks(ev0.elapsed_time(ev1), ws, dev)
 
     lups = nx * ny * nz * T
     with ClockSampler(local) as clk:
         ms = timed(cfg, args.steps, args.warmup)
     clocks = clk.summary()
-    value = lups * args.steps * ws / (ms * 1e-3) * 1e-9
+    value = whole_job_glups(lups, args.steps, ws, ms)
     naive = None
     if not args.no_naive:
         if cfg.algo == girih.NAIVE:
             naive = value
         else:
             nms = timed(girih.config(girih.NAIVE), max(1, args.steps // 2), 1)
-            naive = lups * max(1, args.steps // 2) * ws / (nms * 1e-3) * 1e-9
+            naive = whole_job_glups(lups, max(1, args.steps // 2), ws, nms)
     elem = 8 if dtype == "f64" else 4
     peaks, src = _peaks()
     # spatial-blocking roofline: HBM bandwidth / minimal bytes per LUP (u in, u out; coefficients in)
@@ -350,7 +363,7 @@ def main():
             bg = value
         else:
             bms = timed(blocked_cfg, max(1, args.steps // 2), 1)
-            bg = lups * max(1, args.steps // 2) * ws / (bms * 1e-3) * 1e-9
+            bg = whole_job_glups(lups, max(1, args.steps // 2), ws, bms)
         blocked = {"glups": bg, "config": blocked_cfg.as_dict(), "vs_naive": (bg / naive) if naive else None,
                    "frac_spatial_roofline": bg / ws / spatial}
 
@@ -399,11 +412,7 @@ def main():
         for _ in range(n_e2e):
             girih.run_host(p, hu, hup, hco, c=c, stream=stream)
         barrier()
-        et = time.perf_counter() - t0
-        if ws > 1:
-            t = torch.tensor([et], device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            et = float(t.item())
+        et = max_over_ranks(time.perf_counter() - t0, ws, dev)
         nbytes = u.numel() * elem
         e2e = {"value": lups * n_e2e * ws / et * 1e-9, "unit": "GLUP/s",
                "h2d_bytes_per_step": 2 * nbytes + (co.numel() * elem if co is not None else 0),
