@@ -1,10 +1,11 @@
 """Brute-force per-point evaluator -- TEST INFRASTRUCTURE ONLY.
 
-An independent restatement of the five operators of Listings 1-4 (arXiv 1510.04995, Sect. 2.2)
+An independent restatement of the six operators of Listings 1-4 (arXiv 1510.04995, Sect. 2.2)
 as a table of terms.  Each term is (coefficient source, list of neighbour offsets (dx, dy, dz));
 a point's update is the running sum, in table order, of coefficient * (sum of the neighbours in
 list order).  The 25-point stencil with the factor grid (Listing 3 as printed) uses the 25-point
-constant table and multiplies the sum by the point's factor before the leapfrog terms.  Every level is recomputed point by point over the whole interior in pure Python,
+constant table and multiplies the sum by the point's factor before the leapfrog terms.  The
+27-point box operator (Sect. 7) groups its 26 neighbours by class (face, edge, corner).  Every level is recomputed point by point over the whole interior in pure Python,
 so it is only meant for tiny grids (8^3, T <= 3), where it must agree bit for bit with the C loop
 nests (same terms, same order, one rounding per operation).
 """
@@ -26,6 +27,13 @@ def term_table(stencil: int):
         return [(("C", 0), [(0, 0, 0)]), (("C", 1), [(1, 0, 0)]), (("C", 2), [(-1, 0, 0)]),
                 (("C", 3), [(0, 1, 0)]), (("C", 4), [(0, -1, 0)]), (("C", 5), [(0, 0, 1)]),
                 (("C", 6), [(0, 0, -1)])]
+    if stencil == 5:
+        # box: centre, then the face, edge and corner classes, offsets in (dz, dy, dx) order
+        offs = [(dx, dy, dz) for dz in (-1, 0, 1) for dy in (-1, 0, 1) for dx in (-1, 0, 1)]
+        tab = [(("c", 0), [(0, 0, 0)])]
+        for m in (1, 2, 3):
+            tab.append((("c", m), [o for o in offs if sum(v != 0 for v in o) == m]))
+        return tab
     if stencil in (2, 4):
         tab = [(("c", 0), [(0, 0, 0)])]
         for r in range(1, 5):

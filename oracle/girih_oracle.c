@@ -4,7 +4,7 @@
  * Only the tests, the smoke check and the benchmark's CPU-baseline leg may load this code.  It
  * shares nothing with the CUDA library: no headers, no helpers, no tables.
  *
- * What it computes: T applications of one of the five stencil operators of Listings 1-4 of
+ * What it computes: T applications of one of the six stencil operators of Listings 1-4 of
  * Malas et al. (arXiv 1510.04995, Sect. 2.2) to the interior of a padded 3D grid, in FP64, in the
  * plain lexicographic ("naive") order of the 1D example of Sect. 2.1.1: every time step reads the
  * level-t array and writes the level-(t+1) array; the two arrays swap roles after each step.  The
@@ -23,6 +23,12 @@
  *       + C03*(z+1 + z-1) + C04*(x+2 pair) + ... + C12*(z+4 pair))
  *   25pt C grid (Listing 3 as printed, with its per-point factor grid C):
  *       (2*V - U) + C * (c0*V + c1*(x+1 + x-1 + y+1 + y-1 + z+1 + z-1) + ... + c4*(... r=4 ...))
+ *   27pt box   (the box-shaped operator of Sect. 7: all 26 neighbours at Chebyshev distance 1,
+ *       first order in time, constants by neighbour class):
+ *       c0*V + c1*(sum of the 6 face neighbours) + c2*(sum of the 12 edge neighbours)
+ *            + c3*(sum of the 8 corner neighbours)
+ *       each sum taken over the offsets (dx, dy, dz) in lexicographic order (dz outermost, then
+ *       dy, then dx, each from -1 to 1).
  * For the second-order stencils U is the level t-1 array, overwritten in place by level t+1
  * (Listing 3 writes U = 2V - U + ...).
  *
@@ -128,14 +134,36 @@ static void step_25cg(int64_t nx, int64_t ny, int64_t nz, int64_t ldx, const dou
       }
 }
 
+static void step_27b(int64_t nx, int64_t ny, int64_t nz, int64_t ldx, const double* V, double* U,
+                     const double* c, int nthreads) {
+  const int64_t R = 1, sy = ny + 2 * R;
+#pragma omp parallel for num_threads(nthreads) schedule(static)
+  for (int64_t k = R; k < R + nz; k++)
+    for (int64_t j = R; j < R + ny; j++)
+      for (int64_t i = R; i < R + nx; i++) {
+        double cls[4] = {0.0, 0.0, 0.0, 0.0}; /* sums by class: 1 = face, 2 = edge, 3 = corner */
+        int first[4] = {1, 1, 1, 1};
+        for (int dz = -1; dz <= 1; dz++)
+          for (int dy = -1; dy <= 1; dy++)
+            for (int dx = -1; dx <= 1; dx++) {
+              const int m = (dx != 0) + (dy != 0) + (dz != 0);
+              if (m == 0) continue;
+              const double v = V[IDX(i + dx, j + dy, k + dz)];
+              cls[m] = first[m] ? v : cls[m] + v;
+              first[m] = 0;
+            }
+        U[IDX(i, j, k)] = c[0] * V[IDX(i, j, k)] + c[1] * cls[1] + c[2] * cls[2] + c[3] * cls[3];
+      }
+}
+
 /* Returns 0 on success, 1 on invalid arguments. */
 int oracle_sweep(int stencil, int64_t nx, int64_t ny, int64_t nz, int64_t ldx, int64_t T,
                  double* u, double* u_prev, const double* coeffs, const double* c, int nthreads) {
-  if (stencil < 0 || stencil > 4 || nx < 1 || ny < 1 || nz < 1 || T < 0 || !u || !u_prev) return 1;
-  const int64_t R = (stencil >= 2) ? 4 : 1;
+  if (stencil < 0 || stencil > 5 || nx < 1 || ny < 1 || nz < 1 || T < 0 || !u || !u_prev) return 1;
+  const int64_t R = (stencil >= 2 && stencil <= 4) ? 4 : 1;
   if (ldx < nx + 2 * R) return 1;
   if ((stencil == 1 || stencil == 3 || stencil == 4) && !coeffs) return 1;
-  if ((stencil == 0 || stencil == 2 || stencil == 4) && !c) return 1;
+  if ((stencil == 0 || stencil == 2 || stencil == 4 || stencil == 5) && !c) return 1;
   if (nthreads < 1) nthreads = 1;
   double* buf[2] = {u, u_prev};
   for (int64_t t = 0; t < T; t++) {
@@ -146,7 +174,8 @@ int oracle_sweep(int stencil, int64_t nx, int64_t ny, int64_t nz, int64_t ldx, i
       case 1: step_7v(nx, ny, nz, ldx, V, U, coeffs, nthreads); break;
       case 2: step_25c(nx, ny, nz, ldx, V, U, c, nthreads); break;
       case 3: step_25v(nx, ny, nz, ldx, V, U, coeffs, nthreads); break;
-      default: step_25cg(nx, ny, nz, ldx, V, U, coeffs, c, nthreads); break;
+      case 4: step_25cg(nx, ny, nz, ldx, V, U, coeffs, c, nthreads); break;
+      default: step_27b(nx, ny, nz, ldx, V, U, c, nthreads); break;
     }
   }
   if (T % 2 == 1) { /* level T sits in u_prev: exchange contents so that u holds level T */

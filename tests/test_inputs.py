@@ -41,3 +41,6 @@ def test_problem_recipes():
     inner = co[0][4:-4, 4:-4, 4:-4]
     assert inner.min() >= 0.5 and inner.max() < 1.0 and co[0].sum() == inner.sum()  # zero halo
     assert c == (-0.9, 0.05, 0.025, 0.0125, 0.00625)
+    u, up, co, c = inputs.make_problem(5, 4, 5, 6)
+    assert co is None and u.shape == (8, 7, 6) and c == (0.4, 0.05, 0.02, 0.0075)
+    assert abs(c[0] + 6 * c[1] + 12 * c[2] + 8 * c[3] - 1.0) < 1e-15

@@ -25,7 +25,7 @@ def _grid(stencil, n, seed=7, ldx=None):
     return inputs.make_problem(stencil, n, n, n, seed=seed, ldx=ldx)
 
 
-@pytest.mark.parametrize("stencil", [0, 1, 2, 3, 4])
+@pytest.mark.parametrize("stencil", [0, 1, 2, 3, 4, 5])
 @pytest.mark.parametrize("T", [1, 2, 3])
 def test_brute_force_bitwise(stencil, T):
     """Oracle loop nests == table-driven per-point evaluation on 8^3 (Listings 1-4)."""
@@ -181,6 +181,42 @@ def test_25cg_unit_factor_equals_25c():
     assert np.array_equal(u, u2) and np.array_equal(up, up2)
 
 
+@pytest.mark.parametrize("modes", [(1, 1, 1), (3, 5, 7), (16, 2, 9)])
+def test_27b_dirichlet_sine_mode(modes):
+    """With a zero halo at index 0 and n+1, sin modes are exact eigenvectors of the 27-point box
+    operator: mu = c0 + 2 c1 (cx+cy+cz) + 4 c2 (cx cy + cx cz + cy cz) + 8 c3 cx cy cz, c = cos(m pi/(n+1))."""
+    n, T = 16, 6
+    c = (0.4, 0.05, 0.02, 0.0075)
+    u = _sine(n, modes, 1)
+    up = u.copy()
+    oracle.sweep(5, u, up, None, c, T, n, n, n)
+    cx, cy, cz = (math.cos(m * math.pi / (n + 1)) for m in modes)
+    mu = c[0] + 2 * c[1] * (cx + cy + cz) + 4 * c[2] * (cx * cy + cx * cz + cy * cz) + 8 * c[3] * cx * cy * cz
+    ref = _sine(n, modes, 1) * mu ** T
+    scale = max(np.max(np.abs(ref)), 1e-300)
+    assert np.max(np.abs(u - ref)) <= 1e-13 * max(scale, abs(mu) ** T)
+    # the same field with the 7-point operator decays differently (the corners and edges count)
+    u7 = _sine(n, modes, 1)
+    oracle.sweep(0, u7, u7.copy(), None, (0.4, 0.1), T, n, n, n)
+    assert np.max(np.abs(u7 - ref)) > 1e-6 * np.max(np.abs(_sine(n, modes, 1)))
+
+
+def test_27b_constant_preserved_and_reduces_to_7c():
+    """Weights summing to one keep a constant field; with zero edge and corner weights the box
+    operator is the 7-point constant one (up to the rounding of its six-term face sum)."""
+    n, T, cval = 10, 4, 0.7
+    u, up, _, c = _grid(5, n)
+    u[1:-1, 1:-1, 1:-1] = cval
+    oracle.sweep(5, u, up, None, c, T, n, n, n)
+    core = u[1 + T:-1 - T, 1 + T:-1 - T, 1 + T:-1 - T]
+    assert np.max(np.abs(core - cval)) <= 1e-14
+    u, up, _, _ = _grid(5, n)
+    u2, up2 = u.copy(), up.copy()
+    oracle.sweep(5, u, up, None, (0.4, 0.1, 0.0, 0.0), T, n, n, n)
+    oracle.sweep(0, u2, up2, None, (0.4, 0.1), T, n, n, n)
+    assert np.max(np.abs(u - u2)) <= 4e-16 * T * np.max(np.abs(u2))
+
+
 def test_7v_uniform_equals_7c():
     n, T = 9, 4
     u, up, _, c = _grid(0, n)
@@ -224,6 +260,14 @@ def _impulse_pattern(stencil, co, c, R, n):
         for r in range(1, 5):
             for d in [(r, 0, 0), (-r, 0, 0), (0, r, 0), (0, -r, 0), (0, 0, r), (0, 0, -r)]:
                 exp[d] = c[r]
+    elif stencil == 5:
+        exp[(0, 0, 0)] = c[0]
+        for dz in (-1, 0, 1):
+            for dy in (-1, 0, 1):
+                for dx in (-1, 0, 1):
+                    m = (dx != 0) + (dy != 0) + (dz != 0)
+                    if m:
+                        exp[(dx, dy, dz)] = c[m]
     elif stencil == 4:
         # the point at p + d updates with its own factor C(p + d) times c_r (the impulse is its
         # neighbour at -d); the centre keeps 2V and gains C(p) * c0
@@ -244,7 +288,7 @@ def _impulse_pattern(stencil, co, c, R, n):
     return m, exp
 
 
-@pytest.mark.parametrize("stencil", [0, 1, 2, 3, 4])
+@pytest.mark.parametrize("stencil", [0, 1, 2, 3, 4, 5])
 def test_impulse_response(stencil):
     R = inputs.RADIUS[stencil]
     n = 11
@@ -260,7 +304,7 @@ def test_impulse_response(stencil):
     assert np.array_equal(u, ref)
 
 
-@pytest.mark.parametrize("stencil", [0, 1, 2, 3, 4])
+@pytest.mark.parametrize("stencil", [0, 1, 2, 3, 4, 5])
 def test_linearity(stencil):
     n, T = 10, 3
     u1, up1, co, c = _grid(stencil, n, seed=1)
@@ -276,7 +320,7 @@ def test_linearity(stencil):
 def test_padded_leading_dimension_matches_dense():
     """A padded x pitch (ldx > nx + 2R) changes nothing in the interior."""
     n, T = 9, 4
-    for stencil in range(5):
+    for stencil in range(6):
         u, up, co, c = _grid(stencil, n)
         R = inputs.RADIUS[stencil]
         u2, up2, co2, _ = _grid(stencil, n, ldx=n + 2 * R + 5)
