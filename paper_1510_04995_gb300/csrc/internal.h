@@ -80,13 +80,19 @@ cudaError_t mwd_prepare(int stencil, int dtype, int C, int threads, int G, int m
 int mwd_max_pairs(int R, int dw);
 int mwd_pairs_per_thread(int stencil, int dtype, int dw, int XW, int threads, int mv);
 // Columns per group of the blocked kernel and its launch-bound divisor (mirror the device side).
+inline int radius_of(int stencil) { return (stencil >= 2 && stencil <= 4) ? 4 : 1; }
+inline int ncoef_of(int stencil) { return stencil == 1 ? 7 : (stencil == 3 ? 13 : (stencil == 4 ? 1 : 0)); }
+inline bool is_box(int stencil) { return stencil == GIRIH_27PT_BOX; }
+inline bool second_order(int stencil) { return stencil >= 2 && stencil <= 4; }
 inline int mwd_vx(int stencil, int dtype, int mv) {
-  if (mv_shifted(mv)) return stencil < 2 ? (dtype == GIRIH_F64 ? 2 : 4) : (dtype == GIRIH_F32 ? 2 : 1);
-  return (stencil >= 2 && dtype == GIRIH_F64) ? 1 : (dtype == GIRIH_F64 ? 2 : 4);
+  const bool r1 = radius_of(stencil) == 1;
+  if (mv_shifted(mv)) return r1 ? (dtype == GIRIH_F64 ? 2 : 4) : (dtype == GIRIH_F32 ? 2 : 1);
+  return (!r1 && dtype == GIRIH_F64) ? 1 : (dtype == GIRIH_F64 ? 2 : 4);
 }
 inline int mwd_lbf(int stencil, int dtype, int mv) {
-  if (mv_shifted(mv)) return stencil < 2 ? 2 : 4;
-  return mwd_vx(stencil, dtype, mv) == 1 ? 1 : (stencil < 2 ? 2 : 4);
+  const bool r1 = radius_of(stencil) == 1;
+  if (mv_shifted(mv)) return (r1 && !is_box(stencil)) ? 2 : 4;
+  return mwd_vx(stencil, dtype, mv) == 1 ? 1 : (r1 ? 2 : 4);
 }
 // Largest block for G groups per thread (the kernel's launch bound).
 inline int mwd_max_threads(int G, int lbf) {
@@ -109,7 +115,5 @@ inline int mwd_max_threads(int G, int lbf) {
 // In-place exchange of two device arrays (odd T puts level T back into u).
 cudaError_t launch_swap(void* a, void* b, int64_t bytes, cudaStream_t st);
 
-inline int radius_of(int stencil) { return stencil >= 2 ? 4 : 1; }
-inline int ncoef_of(int stencil) { return stencil == 1 ? 7 : (stencil == 3 ? 13 : (stencil == 4 ? 1 : 0)); }
 
 }  // namespace girih

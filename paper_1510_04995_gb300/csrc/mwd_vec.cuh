@@ -42,9 +42,22 @@ constexpr int vec_vx() {
 }
 template <int S>
 constexpr int vec_lbf() {
-  return Traits<S>::R == 1 ? 2 : 4;
+  return (Traits<S>::R == 1 && !Traits<S>::BOX) ? 2 : 4;
 }
 constexpr int kVecItems = 4;  // precomputed staging / write-back items per thread
+
+// Box-stencil accessor over a group's register block [3 planes][4 rows][VX+2 columns] (planes
+// z-1..z+1, rows y0-1..y0+2, columns xl-1..xl+VX) for the point in row `row` (0 or 1) and
+// column `col` of the group.
+template <typename T, int VX>
+struct BoxAcc {
+  const T* blk;
+  int row, col;
+  __device__ __forceinline__ T b(int dx, int dy, int dz) const {
+    return blk[((1 + dz) * 4 + 1 + row + dy) * (VX + 2) + 1 + col + dx];
+  }
+  __device__ __forceinline__ T c() const { return b(0, 0, 0); }
+};
 
 // One tile (diamond (a, a - rho) of row rho, this block's x slab) from staging to write-back.
 template <int S, typename T, int G, bool TMA>
@@ -347,42 +360,65 @@ __device__ __forceinline__ void mwd_vec_tile(const MwdArgs& A, const int rho, co
               od[R - d] = dn < 0 ? dn + ring : dn;
             }
             const T* Vb = sm + gin_[g];
-            T w0[(2 * R + 1) * VX], w1[(2 * R + 1) * VX];
-#pragma unroll
-            for (int d = 0; d <= 2 * R; ++d) {
-              lds_vec<T, VX>(Vb + od[d], &w0[d * VX]);
-              lds_vec<T, VX>(Vb + od[d] + XT, &w1[d * VX]);
-            }
             const bool row1 = fl & 2;
-            const T* P = Vb + po;
-            T ylo_[R * VX], yhi_[R * VX], xl0[VX + 2 * R], xl1[VX + 2 * R];
-#pragma unroll
-            for (int j = 0; j < R; ++j) {
-              lds_vec<T, VX>(P + (j - R) * XT, &ylo_[j * VX]);
-              // without a second row, row y0+1+R may lie past the tile: read row y0+R instead
-              const int yo = (j == R - 1 && !row1) ? (1 + j) * XT : (2 + j) * XT;
-              lds_vec<T, VX>(P + yo, &yhi_[j * VX]);
-            }
-#pragma unroll
-            for (int d = 1; d <= R; ++d) {
-              xl0[R - d] = P[-d];
-              xl0[R + VX - 1 + d] = P[VX - 1 + d];
-              xl1[R - d] = P[XT - d];
-              xl1[R + VX - 1 + d] = P[XT + VX - 1 + d];
-            }
-#pragma unroll
-            for (int i = 0; i < VX; ++i) {
-              xl0[R + i] = w0[R * VX + i];
-              xl1[R + i] = w1[R * VX + i];
-            }
             T* Ub = sm + gout_[g] + po;
-            T r0[VX], r1[VX], u0[VX], u1[VX];
-            if constexpr (Traits<S>::ORDER2) {
-              lds_vec<T, VX>(Ub, u0);
-              lds_vec<T, VX>(Ub + XT, u1);
-            }
+            T r0[VX], r1[VX];
             const int lo = glo_[g], hi = ghi_[g];
-            mwd_points<S, T, VX>(w0, w1, ylo_, yhi_, xl0, xl1, u0, u1, kp, gstride, ldx, hi, true, cst, r0, r1);
+            if constexpr (Traits<S>::BOX) {
+              // planes z-1 .. z+1 x rows y0-1 .. y0+2 x columns xl-1 .. xl+VX around the group
+              // (without a second row, row y0+2 may lie past the tile: read row y0+1 instead)
+              T blk[3 * 4 * (VX + 2)];
+#pragma unroll
+              for (int d = 0; d < 3; ++d)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                  const int yo = (j == 3 && !row1) ? 2 : j;
+                  const T* q = Vb + od[d] + (yo - 1) * XT;
+                  T* bl = &blk[(d * 4 + j) * (VX + 2)];
+                  lds_vec<T, VX>(q, bl + 1);
+                  bl[0] = q[-1];
+                  bl[VX + 1] = q[VX];
+                }
+#pragma unroll
+              for (int i = 0; i < VX; ++i) {
+                r0[i] = point_update<S, T>(BoxAcc<T, VX>{blk, 0, i}, cst);
+                r1[i] = point_update<S, T>(BoxAcc<T, VX>{blk, 1, i}, cst);
+              }
+            } else {
+              T w0[(2 * R + 1) * VX], w1[(2 * R + 1) * VX];
+#pragma unroll
+              for (int d = 0; d <= 2 * R; ++d) {
+                lds_vec<T, VX>(Vb + od[d], &w0[d * VX]);
+                lds_vec<T, VX>(Vb + od[d] + XT, &w1[d * VX]);
+              }
+              const T* P = Vb + po;
+              T ylo_[R * VX], yhi_[R * VX], xl0[VX + 2 * R], xl1[VX + 2 * R];
+#pragma unroll
+              for (int j = 0; j < R; ++j) {
+                lds_vec<T, VX>(P + (j - R) * XT, &ylo_[j * VX]);
+                // without a second row, row y0+1+R may lie past the tile: read row y0+R instead
+                const int yo = (j == R - 1 && !row1) ? (1 + j) * XT : (2 + j) * XT;
+                lds_vec<T, VX>(P + yo, &yhi_[j * VX]);
+              }
+#pragma unroll
+              for (int d = 1; d <= R; ++d) {
+                xl0[R - d] = P[-d];
+                xl0[R + VX - 1 + d] = P[VX - 1 + d];
+                xl1[R - d] = P[XT - d];
+                xl1[R + VX - 1 + d] = P[XT + VX - 1 + d];
+              }
+#pragma unroll
+              for (int i = 0; i < VX; ++i) {
+                xl0[R + i] = w0[R * VX + i];
+                xl1[R + i] = w1[R * VX + i];
+              }
+              T u0[VX], u1[VX];
+              if constexpr (Traits<S>::ORDER2) {
+                lds_vec<T, VX>(Ub, u0);
+                lds_vec<T, VX>(Ub + XT, u1);
+              }
+              mwd_points<S, T, VX>(w0, w1, ylo_, yhi_, xl0, xl1, u0, u1, kp, gstride, ldx, hi, true, cst, r0, r1);
+            }
             if (lo == 0 && hi == VX) {
               sts_vec<T, VX>(Ub, r0);
               if (row1) sts_vec<T, VX>(Ub + XT, r1);

@@ -22,21 +22,28 @@ struct NaiveAcc {  // one column of the thread's VX columns
   const T* w;        // register window, w[R] = centre
   const T* kv;       // coefficient values of this point (variable stencils)
   T uc;              // level t-1 centre (second order)
+  const T* tcm;      // box stencil: the same cell in the planes below and above
+  const T* tcp;
   __device__ __forceinline__ T c() const { return w[Traits<S>::R]; }
   __device__ __forceinline__ T x(int d) const { return tc[d]; }
   __device__ __forceinline__ T y(int d) const { return tc[d * TW]; }
   __device__ __forceinline__ T z(int d) const { return w[Traits<S>::R + d]; }
   __device__ __forceinline__ T u() const { return uc; }
   __device__ __forceinline__ T k(int g) const { return kv[g]; }
+  __device__ __forceinline__ T b(int dx, int dy, int dz) const {
+    if (dx == 0 && dy == 0) return w[Traits<S>::R + dz];
+    return (dz < 0 ? tcm : (dz > 0 ? tcp : tc))[dy * TW + dx];
+  }
 };
 
 // Block = 32 x TY threads over a 32 x 2TY tile of (x, y) columns and a chunk of z planes; each
 // thread owns rows ty and ty + TY.  The tile's planes (with the R-wide halo) stream through a
-// ring of NP = R + PD + 2 shared-memory slots filled PD planes ahead of use (one commit group
-// per plane): at the update of plane z the ring holds padded planes z+R (the x/y neighbours)
-// up to z+2R+PD+1 and one slot that is being refilled.  The z window of each owned column
-// stays in registers: its R lowest planes are loaded from global memory at the start, the rest
-// and every new value come from the ring.  The level t-1 centres of the second-order stencils
+// ring of NP = R + PD + 2 (+1 for the box stencil) shared-memory slots filled PD planes ahead of
+// use (one commit group per plane): at the update of plane z the ring holds padded planes z+R
+// (the x/y neighbours; from z+R-1 for the box stencil, whose diagonal neighbours also lie in the
+// planes below and above) up to z+2R+PD+1 and one slot that is being refilled.  The z window of
+// each owned column stays in registers: its lowest planes that are not in the ring are loaded
+// from global memory at the start, the rest and every new value come from the ring.  The level t-1 centres of the second-order stencils
 // and the coefficients are loaded into registers one plane ahead.  One barrier per plane.
 //
 // V16 (rows of 16-byte multiples, 16-byte aligned buffers): 16-byte cp.async.cg chunks, the tile
@@ -54,8 +61,10 @@ __global__ void __launch_bounds__(32 * TY) naive_kernel(const NaiveArgs a) {
   constexpr int TX = 32 * VX;                  // tile columns
   constexpr int TXW = V16 ? (TX + 2 * R + A16 - 1) / A16 * A16 : TX + 2 * R;  // shared row width
   constexpr int TYW = ROWS + 2 * R, TP = TXW * TYW;
-  // ring slots: planes z+R .. z+2R+PD+1 are live at the update of plane z (R+PD+2)
-  constexpr int NP = R + PD + 2;
+  // ring slots: planes z+R-ZB .. z+2R+PD+1 are live at the update of plane z (R+PD+2+ZB), ZB = 1
+  // for the box stencil, whose diagonal neighbours need the x-y tiles of the planes below and above
+  constexpr int ZB = Traits<S>::BOX ? 1 : 0;
+  constexpr int NP = R + PD + 2 + ZB;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* ring = reinterpret_cast<T*>(smem_raw);       // [NP][TYW][TXW]
   const T* __restrict__ V = static_cast<const T*>(a.V);
@@ -109,8 +118,8 @@ __global__ void __launch_bounds__(32 * TY) naive_kernel(const NaiveArgs a) {
     cp_async_commit();
   };
 
-  // planes z0+R .. z0+2R fill the upper windows; planes up to z0 + 2R + PD are staged ahead
-  for (int q = R; q <= 2 * R + PD; ++q) stage(q);
+  // planes z0+R-ZB .. z0+2R fill the upper windows; planes up to z0 + 2R + PD are staged ahead
+  for (int q = R - ZB; q <= 2 * R + PD; ++q) stage(q);
 
   bool act[2][VX];
   int cofs[2];  // shared offset of the thread's first column in each row
@@ -122,9 +131,9 @@ __global__ void __launch_bounds__(32 * TY) naive_kernel(const NaiveArgs a) {
 #pragma unroll
     for (int v = 0; v < VX; ++v) {
       act[r][v] = (bx + v * 32 + tx < nx) && (by + row < ny);
-      // the R planes below the first updated one, straight from global memory
+      // the R-ZB lowest planes of the window, straight from global memory
 #pragma unroll
-      for (int i = 0; i < R; ++i)
+      for (int i = 0; i < R - ZB; ++i)
         w[r][v][i] = act[r][v] ? Vb[(int64_t)i * plane + (row + R) * ldx + tx + R + v * 32] : T(0);
     }
   }
@@ -135,7 +144,7 @@ __global__ void __launch_bounds__(32 * TY) naive_kernel(const NaiveArgs a) {
 #pragma unroll
     for (int v = 0; v < VX; ++v)
 #pragma unroll
-      for (int i = R; i <= 2 * R; ++i) w[r][v][i] = ring[(i % NP) * TP + cofs[r] + v * 32];
+      for (int i = R - ZB; i <= 2 * R; ++i) w[r][v][i] = ring[(i % NP) * TP + cofs[r] + v * 32];
   // every thread has its first window before the first in-loop staging refills a slot
   __syncthreads();
   // per-column pointers, advanced one plane per update: the output point (also the level t-1
@@ -200,12 +209,15 @@ __global__ void __launch_bounds__(32 * TY) naive_kernel(const NaiveArgs a) {
         }
     }
     const T* tl = ring + ((zr + R) % NP) * TP;  // padded plane z0 + zr + R = interior plane z0 + zr
+    const T* tlm = ring + ((zr + R - ZB) % NP) * TP;  // box: the planes below and above
+    const T* tlp = ring + ((zr + R + ZB) % NP) * TP;
 #pragma unroll
     for (int r = 0; r < 2; ++r) {
 #pragma unroll
       for (int v = 0; v < VX; ++v) {
         if (act[r][v]) {
-          NaiveAcc<S, T, TXW> acc{tl + cofs[r] + v * 32, w[r][v], kv[r][v], T(0)};
+          NaiveAcc<S, T, TXW> acc{tl + cofs[r] + v * 32, w[r][v], kv[r][v], T(0), tlm + cofs[r] + v * 32,
+                                  tlp + cofs[r] + v * 32};
           if constexpr (Traits<S>::ORDER2) acc.uc = uc[r][v];
           *up[r][v] = point_update<S, T>(acc, cst);
         }
@@ -255,7 +267,7 @@ static size_t naive_smem() {
   constexpr int R = Traits<S>::R, PD = naive_pd<S, T>(), A16 = 16 / (int)sizeof(T);
   constexpr int TX = 32 * naive_vx<S, T, V16>();
   constexpr int TXW = V16 ? (TX + 2 * R + A16 - 1) / A16 * A16 : TX + 2 * R;
-  constexpr int NP = R + PD + 2, TP = TXW * (2 * kTY + 2 * R);
+  constexpr int NP = R + PD + 2 + (Traits<S>::BOX ? 1 : 0), TP = TXW * (2 * kTY + 2 * R);
   return sizeof(T) * (size_t)NP * TP;
 }
 
@@ -310,7 +322,8 @@ int naive_tile_x(int stencil, int dtype, bool v16) {
     case 1: return pick(std::integral_constant<int, 1>());
     case 2: return pick(std::integral_constant<int, 2>());
     case 3: return pick(std::integral_constant<int, 3>());
-    default: return pick(std::integral_constant<int, 4>());
+    case 4: return pick(std::integral_constant<int, 4>());
+    default: return pick(std::integral_constant<int, 5>());
   }
 }
 
@@ -326,7 +339,8 @@ int naive_resident_blocks(int stencil, int dtype, bool v16) {
     case 1: return pick(std::integral_constant<int, 1>());
     case 2: return pick(std::integral_constant<int, 2>());
     case 3: return pick(std::integral_constant<int, 3>());
-    default: return pick(std::integral_constant<int, 4>());
+    case 4: return pick(std::integral_constant<int, 4>());
+    default: return pick(std::integral_constant<int, 5>());
   }
 }
 
@@ -360,7 +374,8 @@ cudaError_t launch_naive_step(int stencil, int dtype, const NaiveArgs& a, cudaSt
     case 1: return f64 ? launch_v<1, double>(a, st) : launch_v<1, float>(a, st);
     case 2: return f64 ? launch_v<2, double>(a, st) : launch_v<2, float>(a, st);
     case 3: return f64 ? launch_v<3, double>(a, st) : launch_v<3, float>(a, st);
-    default: return f64 ? launch_v<4, double>(a, st) : launch_v<4, float>(a, st);
+    case 4: return f64 ? launch_v<4, double>(a, st) : launch_v<4, float>(a, st);
+    default: return f64 ? launch_v<5, double>(a, st) : launch_v<5, float>(a, st);
   }
 }
 

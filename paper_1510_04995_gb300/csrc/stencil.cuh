@@ -1,4 +1,5 @@
-// Point updates of the five stencils (arXiv 1510.04995, Sect. 2.2, Listings 1-4) and the small
+// Point updates of the six stencils (arXiv 1510.04995, Sect. 2.2, Listings 1-4, and the 27-point
+// box operator of Sect. 7) and the small
 // device helpers the sweep kernels share.
 //
 // Every kernel of the library computes a lattice-site update (LUP) through exactly one of the
@@ -15,24 +16,31 @@
 //   25pt var  : acc = C00*V; for r=1..4: acc += C(3r-2)*(x pair) + C(3r-1)*(y pair) + C(3r)*(z pair)
 //               U' = ((V + V) - U) + acc
 //   25pt Cgrid: lap as 25pt const; U' = fma(C, lap, (V + V) - U)   (Listing 3 as printed)
+//   27pt box  : F, E, K = sums of the face, edge and corner neighbours, each taken over the
+//               offsets in (dz, dy, dx) lexicographic order; acc = c0*V; acc += c1*F; += c2*E;
+//               += c3*K
 #pragma once
 #include <cuda_runtime.h>
 #include <stdint.h>
 
 namespace girih {
 
+// R: radius; NCOEF: coefficient grids; ORDER2: second order in time; BOX: diagonal neighbours
+// (read through the accessor's b(dx, dy, dz)).
 template <int S>
 struct Traits;
 template <>
-struct Traits<0> { static constexpr int R = 1, NCOEF = 0; static constexpr bool ORDER2 = false; };
+struct Traits<0> { static constexpr int R = 1, NCOEF = 0; static constexpr bool ORDER2 = false, BOX = false; };
 template <>
-struct Traits<1> { static constexpr int R = 1, NCOEF = 7; static constexpr bool ORDER2 = false; };
+struct Traits<1> { static constexpr int R = 1, NCOEF = 7; static constexpr bool ORDER2 = false, BOX = false; };
 template <>
-struct Traits<2> { static constexpr int R = 4, NCOEF = 0; static constexpr bool ORDER2 = true; };
+struct Traits<2> { static constexpr int R = 4, NCOEF = 0; static constexpr bool ORDER2 = true, BOX = false; };
 template <>
-struct Traits<3> { static constexpr int R = 4, NCOEF = 13; static constexpr bool ORDER2 = true; };
+struct Traits<3> { static constexpr int R = 4, NCOEF = 13; static constexpr bool ORDER2 = true, BOX = false; };
 template <>
-struct Traits<4> { static constexpr int R = 4, NCOEF = 1; static constexpr bool ORDER2 = true; };
+struct Traits<4> { static constexpr int R = 4, NCOEF = 1; static constexpr bool ORDER2 = true, BOX = false; };
+template <>
+struct Traits<5> { static constexpr int R = 1, NCOEF = 0; static constexpr bool ORDER2 = false, BOX = true; };
 
 template <typename T>
 struct Ops;
@@ -54,6 +62,7 @@ struct Ops<double> {
 // An accessor A provides, for the point being updated:
 //   A.c()       centre value of level t                 A.x(d), A.y(d), A.z(d)  neighbours at offset d
 //   A.u()       centre value of level t-1 (ORDER2 only) A.k(g)                  coefficient grid g
+//   A.b(dx, dy, dz)  neighbour at any offset in [-1, 1]^3 (BOX only)
 template <int S, typename T, typename A>
 __device__ __forceinline__ T point_update(const A& a, const T* cst) {
   using O = Ops<T>;
@@ -72,6 +81,26 @@ __device__ __forceinline__ T point_update(const A& a, const T* cst) {
     acc = O::fma(a.k(4), a.y(-1), acc);
     acc = O::fma(a.k(5), a.z(1), acc);
     acc = O::fma(a.k(6), a.z(-1), acc);
+    return acc;
+  } else if constexpr (S == 5) {
+    T cls[4];
+    bool first[4] = {true, true, true, true};
+#pragma unroll
+    for (int dz = -1; dz <= 1; ++dz)
+#pragma unroll
+      for (int dy = -1; dy <= 1; ++dy)
+#pragma unroll
+        for (int dx = -1; dx <= 1; ++dx) {
+          const int m = (dx != 0) + (dy != 0) + (dz != 0);
+          if (m == 0) continue;
+          const T v = a.b(dx, dy, dz);
+          cls[m] = first[m] ? v : O::add(cls[m], v);
+          first[m] = false;
+        }
+    T acc = O::mul(cst[0], a.c());
+    acc = O::fma(cst[1], cls[1], acc);
+    acc = O::fma(cst[2], cls[2], acc);
+    acc = O::fma(cst[3], cls[3], acc);
     return acc;
   } else if constexpr (S == 2 || S == 4) {
     const T v = a.c();
@@ -103,7 +132,8 @@ __device__ __forceinline__ T point_update(const A& a, const T* cst) {
 // Arithmetic instructions per LUP of point_update (each intrinsic is one FP instruction):
 // 7pt const 7, 7pt var 7, 25pt const 1 + 4*6 + 3 = 28, 25pt var 1 + 12*2 + 3 = 28, 25pt Cgrid
 // 1 + 4*6 + 3 = 28.
-__host__ __device__ constexpr int fp_instructions_per_lup(int s) { return s < 2 ? 7 : 28; }
+// 27pt box 5 + 11 + 7 + 1 + 3 = 27.
+__host__ __device__ constexpr int fp_instructions_per_lup(int s) { return s < 2 ? 7 : (s == 5 ? 27 : 28); }
 
 // ---- small PTX helpers (sm_90+ cluster features, cp.async) -------------------------------------
 __device__ __forceinline__ uint32_t smem_addr(const void* p) {

@@ -32,8 +32,10 @@ WORKLOADS = {
     "25pt_var_f32_384": (3, "f32", 384, 384, 384, 32),
     "25pt_cgrid_f64_384": (4, "f64", 384, 384, 384, 32),
     "25pt_cgrid_f32_384": (4, "f32", 384, 384, 384, 32),
+    "27pt_box_f64_512": (5, "f64", 512, 512, 512, 64),
+    "27pt_box_f32_512": (5, "f32", 512, 512, 512, 64),
 }
-RADIUS = {0: 1, 1: 1, 2: 4, 3: 4, 4: 4}
+RADIUS = {0: 1, 1: 1, 2: 4, 3: 4, 4: 4, 5: 1}
 
 
 def aligned_ldx(stencil: int, dtype: str, nx: int) -> int:

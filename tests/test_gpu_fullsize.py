@@ -61,14 +61,14 @@ def _run_pair(workload):
 
 @pytest.mark.parametrize("workload", ["7pt_const_f64_512", "7pt_const_f32_512", "7pt_var_f32_480",
                                       "25pt_const_f32_384", "25pt_var_f32_384", "25pt_const_f64_384",
-                                      "25pt_cgrid_f32_384"])
+                                      "25pt_cgrid_f32_384", "27pt_box_f32_512"])
 def test_blocked_equals_naive_full_size(workload):
     import torch
     p, cfg, (bu, bup), (nu, nup), _ = _run_pair(workload)
     assert torch.equal(bu, nu) and torch.equal(bup, nup), (workload, cfg)
 
 
-@pytest.mark.parametrize("workload", ["7pt_const_f64_512", "25pt_cgrid_f64_384"])
+@pytest.mark.parametrize("workload", ["7pt_const_f64_512", "25pt_cgrid_f64_384", "27pt_box_f64_512"])
 def test_sampled_points_against_oracle_cones(workload):
     import torch
     p, cfg, (bu, _), _, (stencil, dtype, nx, ny, nz, T) = _run_pair(workload)
