@@ -252,14 +252,14 @@ template <int S, typename T>
 constexpr int naive_pd() { return Traits<S>::R == 1 ? 4 : (S == 2 ? 2 : 3); }
 
 // Columns per thread (16-byte aligned layouts): 4 for the FP32 7-point constant stencil and 2
-// for the FP32 25-point constant one, whose sweeps were bound by instruction issue (the
-// thread's per-plane work -- barrier, staging items, loop and address bookkeeping -- is then
-// shared by 2*VX updates: 564 -> 715 and 291 -> 336 GLUP/s); else 1 (measured: the FP64
+// for the FP32 25-point constant and 27-point box ones, whose sweeps were bound by instruction
+// issue (the thread's per-plane work -- barrier, staging items, loop and address bookkeeping --
+// is then shared by 2*VX updates: 564 -> 715, 291 -> 336 and 304 -> 320 GLUP/s); else 1 (measured: the FP64
 // sweeps are bound by the FP64 pipe, and the stencils with coefficient grids keep a plane of
 // coefficients per column in registers, so more columns cost occupancy).
 template <int S, typename T, bool V16>
 constexpr int naive_vx() {
-  return (V16 && sizeof(T) == 4) ? (S == 0 ? 4 : (S == 2 ? 2 : 1)) : 1;
+  return (V16 && sizeof(T) == 4) ? (S == 0 ? 4 : ((S == 2 || S == 5) ? 2 : 1)) : 1;
 }
 
 template <int S, typename T, bool V16>
