@@ -45,7 +45,7 @@ def _load():
     return _lib
 
 
-RADIUS = {0: 1, 1: 1, 2: 4, 3: 4, 4: 4, 5: 1}
+RADIUS = {0: 1, 1: 1, 2: 4, 3: 4, 4: 4, 5: 1, 6: 1}
 
 
 def _ptr(a):

@@ -5,7 +5,9 @@ as a table of terms.  Each term is (coefficient source, list of neighbour offset
 a point's update is the running sum, in table order, of coefficient * (sum of the neighbours in
 list order).  The 25-point stencil with the factor grid (Listing 3 as printed) uses the 25-point
 constant table and multiplies the sum by the point's factor before the leapfrog terms.  The
-27-point box operator (Sect. 7) groups its 26 neighbours by class (face, edge, corner).  Every level is recomputed point by point over the whole interior in pure Python,
+27-point box operator (Sect. 7) groups its 26 neighbours by class (face, edge, corner).  Red-black
+Gauss-Seidel is evaluated as Sect. 7 states it, in place on one array (``rbgs_in_place``), which
+checks the oracle's two-buffer half-step form.  Every level is recomputed point by point over the whole interior in pure Python,
 so it is only meant for tiny grids (8^3, T <= 3), where it must agree bit for bit with the C loop
 nests (same terms, same order, one rounding per operation).
 """
@@ -49,8 +51,33 @@ def term_table(stencil: int):
     return tab
 
 
+def rbgs_in_place(u, c, T: int):
+    """Red-black Gauss-Seidel written the way Sect. 7 states it: ONE array, updated in place, half
+    sweep t visiting the points with (x + y + z + t) even (interior coordinates) in lexicographic
+    order and replacing each by c0*u + c1*(x pair) + c1*(y pair) + c1*(z pair) of the current
+    array.  Returns (array after T half-sweeps, array after T-1)."""
+    a = u.copy()
+    prev = u.copy()
+    nz, ny, nx = (s - 2 for s in u.shape)
+    for t in range(T):
+        prev = a.copy()
+        for k in range(1, nz + 1):
+            for j in range(1, ny + 1):
+                for i in range(1, nx + 1):
+                    if ((i - 1) + (j - 1) + (k - 1) + t) % 2:
+                        continue
+                    v = float(c[0]) * float(a[k, j, i])
+                    v = v + float(c[1]) * (float(a[k, j, i + 1]) + float(a[k, j, i - 1]))
+                    v = v + float(c[1]) * (float(a[k, j + 1, i]) + float(a[k, j - 1, i]))
+                    v = v + float(c[1]) * (float(a[k + 1, j, i]) + float(a[k - 1, j, i]))
+                    a[k, j, i] = v
+    return a, prev
+
+
 def sweep(stencil: int, u, u_prev, coeffs, c, T: int, R: int):
     """Return (level T, level T-1) as new arrays; inputs are padded [nz+2R][ny+2R][nx+2R]."""
+    if stencil == 6:
+        return rbgs_in_place(u, c, T)
     a = [u.copy(), u_prev.copy()]
     nz, ny, nx = (s - 2 * R for s in u.shape)
     second = stencil in (2, 3, 4)

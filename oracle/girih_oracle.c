@@ -4,7 +4,7 @@
  * Only the tests, the smoke check and the benchmark's CPU-baseline leg may load this code.  It
  * shares nothing with the CUDA library: no headers, no helpers, no tables.
  *
- * What it computes: T applications of one of the six stencil operators of Listings 1-4 of
+ * What it computes: T applications of one of the seven stencil operators of Listings 1-4 of
  * Malas et al. (arXiv 1510.04995, Sect. 2.2) to the interior of a padded 3D grid, in FP64, in the
  * plain lexicographic ("naive") order of the 1D example of Sect. 2.1.1: every time step reads the
  * level-t array and writes the level-(t+1) array; the two arrays swap roles after each step.  The
@@ -29,6 +29,12 @@
  *            + c3*(sum of the 8 corner neighbours)
  *       each sum taken over the offsets (dx, dy, dz) in lexicographic order (dz outermost, then
  *       dy, then dx, each from -1 to 1).
+ *   7pt red-black Gauss-Seidel (Sect. 7): time step t is a half-sweep that updates, in place,
+ *       the points whose interior coordinates have (x + y + z + t) even with the 7-point constant
+ *       formula (c0*V + c1*(x pair) + c1*(y pair) + c1*(z pair)) and leaves the others; the
+ *       updated points' neighbours all have the other colour, so the half-sweep reads only
+ *       values of the previous half-step and the in-place order within it does not matter.
+ *       Two consecutive time steps make one red-black iteration.
  * For the second-order stencils U is the level t-1 array, overwritten in place by level t+1
  * (Listing 3 writes U = 2V - U + ...).
  *
@@ -156,14 +162,34 @@ static void step_27b(int64_t nx, int64_t ny, int64_t nz, int64_t ldx, const doub
       }
 }
 
+static void step_rbgs(int64_t nx, int64_t ny, int64_t nz, int64_t ldx, const double* V, double* U,
+                      const double* c, int64_t t, int nthreads) {
+  const int64_t R = 1, sy = ny + 2 * R;
+  const double c0 = c[0], c1 = c[1];
+#pragma omp parallel for num_threads(nthreads) schedule(static)
+  for (int64_t k = R; k < R + nz; k++)
+    for (int64_t j = R; j < R + ny; j++)
+      for (int64_t i = R; i < R + nx; i++) {
+        const int64_t colour = ((i - R) + (j - R) + (k - R) + t) % 2;
+        if (colour != 0) {
+          U[IDX(i, j, k)] = V[IDX(i, j, k)];
+          continue;
+        }
+        U[IDX(i, j, k)] = c0 * V[IDX(i, j, k)]
+                        + c1 * (V[IDX(i + 1, j, k)] + V[IDX(i - 1, j, k)])
+                        + c1 * (V[IDX(i, j + 1, k)] + V[IDX(i, j - 1, k)])
+                        + c1 * (V[IDX(i, j, k + 1)] + V[IDX(i, j, k - 1)]);
+      }
+}
+
 /* Returns 0 on success, 1 on invalid arguments. */
 int oracle_sweep(int stencil, int64_t nx, int64_t ny, int64_t nz, int64_t ldx, int64_t T,
                  double* u, double* u_prev, const double* coeffs, const double* c, int nthreads) {
-  if (stencil < 0 || stencil > 5 || nx < 1 || ny < 1 || nz < 1 || T < 0 || !u || !u_prev) return 1;
+  if (stencil < 0 || stencil > 6 || nx < 1 || ny < 1 || nz < 1 || T < 0 || !u || !u_prev) return 1;
   const int64_t R = (stencil >= 2 && stencil <= 4) ? 4 : 1;
   if (ldx < nx + 2 * R) return 1;
   if ((stencil == 1 || stencil == 3 || stencil == 4) && !coeffs) return 1;
-  if ((stencil == 0 || stencil == 2 || stencil == 4 || stencil == 5) && !c) return 1;
+  if ((stencil == 0 || stencil == 2 || stencil == 4 || stencil == 5 || stencil == 6) && !c) return 1;
   if (nthreads < 1) nthreads = 1;
   double* buf[2] = {u, u_prev};
   for (int64_t t = 0; t < T; t++) {
@@ -175,7 +201,8 @@ int oracle_sweep(int stencil, int64_t nx, int64_t ny, int64_t nz, int64_t ldx, i
       case 2: step_25c(nx, ny, nz, ldx, V, U, c, nthreads); break;
       case 3: step_25v(nx, ny, nz, ldx, V, U, coeffs, nthreads); break;
       case 4: step_25cg(nx, ny, nz, ldx, V, U, coeffs, c, nthreads); break;
-      default: step_27b(nx, ny, nz, ldx, V, U, c, nthreads); break;
+      case 5: step_27b(nx, ny, nz, ldx, V, U, c, nthreads); break;
+      default: step_rbgs(nx, ny, nz, ldx, V, U, c, t, nthreads); break;
     }
   }
   if (T % 2 == 1) { /* level T sits in u_prev: exchange contents so that u holds level T */

@@ -23,6 +23,7 @@ Workload recipes (the configurations the sweeps are measured and tested on):
   25v : u0 ~ U[-1,1]; u_prev = u0; C00..C12 ~ U[0,0.01] (streams 1..13).
   25cg: u0 ~ U[-1,1]; u_prev = u0; c as 25c; the per-point factor C ~ U[0.5,1] (stream 1).
   27b : u0 ~ U[-1,1]; centre 0.4, faces 0.05, edges 0.02, corners 0.0075 (weights sum to 1).
+  rbgs: u0 ~ U[-1,1]; c0 = 0, c1 = 1/6 (red-black Gauss-Seidel for the 7-point Laplace equation).
 """
 from __future__ import annotations
 
@@ -35,13 +36,14 @@ M1 = 0xBF58476D1CE4E5B9
 M2 = 0x94D049BB133111EB
 DEFAULT_SEED = 20151016
 
-RADIUS = {0: 1, 1: 1, 2: 4, 3: 4, 4: 4, 5: 1}
-NCOEF = {0: 0, 1: 7, 2: 0, 3: 13, 4: 1, 5: 0}
-SECOND_ORDER = {0: False, 1: False, 2: True, 3: True, 4: True, 5: False}
-STENCIL_NAMES = {0: "7pt_const", 1: "7pt_var", 2: "25pt_const", 3: "25pt_var", 4: "25pt_cgrid", 5: "27pt_box"}
+RADIUS = {0: 1, 1: 1, 2: 4, 3: 4, 4: 4, 5: 1, 6: 1}
+NCOEF = {0: 0, 1: 7, 2: 0, 3: 13, 4: 1, 5: 0, 6: 0}
+SECOND_ORDER = {0: False, 1: False, 2: True, 3: True, 4: True, 5: False, 6: False}
+STENCIL_NAMES = {0: "7pt_const", 1: "7pt_var", 2: "25pt_const", 3: "25pt_var", 4: "25pt_cgrid", 5: "27pt_box",
+                 6: "7pt_rbgs"}
 CONST_COEFFS = {0: (0.4, 0.1), 2: (-0.9, 0.1 / 2, 0.1 / 4, 0.1 / 8, 0.1 / 16),
                 4: (-0.9, 0.1 / 2, 0.1 / 4, 0.1 / 8, 0.1 / 16),
-                5: (0.4, 0.05, 0.02, 0.0075)}
+                5: (0.4, 0.05, 0.02, 0.0075), 6: (0.0, 1.0 / 6.0)}
 
 
 def _mix_int(z: int) -> int:
@@ -121,7 +123,7 @@ def _field(seed, stream, nx, ny, nz, R, ldx, a, b, backend, device):
 
 def make_problem(stencil: int, nx: int, ny: int, nz: int, seed: int = DEFAULT_SEED,
                  ldx: int | None = None, backend: str = "numpy", device=None):
-    """Return (u, u_prev, coeffs, c) in FP64 for one of the six workloads.
+    """Return (u, u_prev, coeffs, c) in FP64 for one of the seven workloads.
 
     u, u_prev: padded grids.  coeffs: None or an array [ncoef, *padded] (coefficient halo = 0).
     c: tuple of the constant coefficients (empty for the variable-coefficient stencils 1 and 3).

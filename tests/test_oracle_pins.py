@@ -25,7 +25,7 @@ def _grid(stencil, n, seed=7, ldx=None):
     return inputs.make_problem(stencil, n, n, n, seed=seed, ldx=ldx)
 
 
-@pytest.mark.parametrize("stencil", [0, 1, 2, 3, 4, 5])
+@pytest.mark.parametrize("stencil", [0, 1, 2, 3, 4, 5, 6])
 @pytest.mark.parametrize("T", [1, 2, 3])
 def test_brute_force_bitwise(stencil, T):
     """Oracle loop nests == table-driven per-point evaluation on 8^3 (Listings 1-4)."""
@@ -217,6 +217,63 @@ def test_27b_constant_preserved_and_reduces_to_7c():
     assert np.max(np.abs(u - u2)) <= 4e-16 * T * np.max(np.abs(u2))
 
 
+def test_rbgs_impulse_two_half_sweeps():
+    """One red-black iteration (two half-sweeps) of an impulse on a black point, hand-derived:
+    the red half-sweep gives its six red neighbours c1; the black half-sweep then reads those NEW
+    values (Gauss-Seidel, not Jacobi): the impulse point becomes c0 + 6 c1^2, the black points two
+    steps away along an axis c1^2 and the black points at face-diagonal offsets 2 c1^2."""
+    n = 11
+    c0, c1 = 0.25, 0.125                       # exact in binary: every product and sum below is exact
+    u = np.zeros((n + 2,) * 3)
+    m = 6                                      # interior coordinate 5: (5+5+5) odd -> black
+    u[m, m, m] = 1.0
+    up = u.copy()
+    oracle.sweep(6, u, up, None, (c0, c1), 2, n, n, n)
+    ref = np.zeros_like(u)
+    ref[m, m, m] = c0 + 6 * c1 * c1
+    for ax in range(3):
+        for sg in (1, -1):
+            d = [0, 0, 0]
+            d[ax] = sg
+            ref[m + d[0], m + d[1], m + d[2]] = c1               # red neighbours, from half-sweep 0
+            d[ax] = 2 * sg
+            ref[m + d[0], m + d[1], m + d[2]] = c1 * c1          # black, one red neighbour updated
+    for a in range(3):
+        for b in range(a + 1, 3):
+            for sa in (1, -1):
+                for sb in (1, -1):
+                    d = [0, 0, 0]
+                    d[a], d[b] = sa, sb
+                    ref[m + d[0], m + d[1], m + d[2]] = 2 * c1 * c1  # black, two red neighbours
+    assert np.array_equal(u, ref)
+    # Jacobi on the same two steps differs (the black half-sweep would read the old red values)
+    uj = np.zeros_like(ref)
+    uj[m, m, m] = 1.0
+    oracle.sweep(0, uj, uj.copy(), None, (c0, c1), 2, n, n, n)
+    assert not np.array_equal(uj, ref)
+
+
+def test_rbgs_harmonic_fixed_point_and_convergence():
+    """A discrete harmonic field (linear in x, y, z, with matching Dirichlet halo) is a fixed point
+    of the Laplace red-black iteration (c0 = 0, c1 = 1/6); from random interior values the
+    iteration converges towards it, faster than Jacobi (the spectral radius of red-black
+    Gauss-Seidel is the square of Jacobi's)."""
+    n = 12
+    idx = np.arange(n + 2, dtype=np.float64)
+    lin = (0.5 * idx[None, None, :] + 0.25 * idx[None, :, None] + 0.125 * idx[:, None, None])
+    u = lin.copy()
+    oracle.sweep(6, u, u.copy(), None, (0.0, 1.0 / 6.0), 8, n, n, n)
+    assert np.max(np.abs(u - lin)) <= 4e-15 * np.max(np.abs(lin))
+    rnd, _, _, _ = _grid(6, n)
+    u0 = lin.copy()
+    u0[1:-1, 1:-1, 1:-1] += rnd[1:-1, 1:-1, 1:-1]
+    ug, uj = u0.copy(), u0.copy()
+    oracle.sweep(6, ug, ug.copy(), None, (0.0, 1.0 / 6.0), 40, n, n, n)     # 20 iterations
+    oracle.sweep(0, uj, uj.copy(), None, (0.0, 1.0 / 6.0), 20, n, n, n)     # 20 Jacobi steps
+    eg, ej = np.max(np.abs(ug - lin)), np.max(np.abs(uj - lin))
+    assert eg < 0.5 * ej and eg < np.max(np.abs(u0 - lin))
+
+
 def test_7v_uniform_equals_7c():
     n, T = 9, 4
     u, up, _, c = _grid(0, n)
@@ -304,7 +361,7 @@ def test_impulse_response(stencil):
     assert np.array_equal(u, ref)
 
 
-@pytest.mark.parametrize("stencil", [0, 1, 2, 3, 4, 5])
+@pytest.mark.parametrize("stencil", [0, 1, 2, 3, 4, 5, 6])
 def test_linearity(stencil):
     n, T = 10, 3
     u1, up1, co, c = _grid(stencil, n, seed=1)
@@ -320,7 +377,7 @@ def test_linearity(stencil):
 def test_padded_leading_dimension_matches_dense():
     """A padded x pitch (ldx > nx + 2R) changes nothing in the interior."""
     n, T = 9, 4
-    for stencil in range(6):
+    for stencil in range(7):
         u, up, co, c = _grid(stencil, n)
         R = inputs.RADIUS[stencil]
         u2, up2, co2, _ = _grid(stencil, n, ldx=n + 2 * R + 5)
