@@ -44,30 +44,37 @@ WORKLOADS = {
     "25pt_cgrid_f32_384": (4, "f32", 384, 384, 384, 32),
     "27pt_box_f64_512": (5, "f64", 512, 512, 512, 64),
     "27pt_box_f32_512": (5, "f32", 512, 512, 512, 64),
+    "7pt_rbgs_f64_512": (6, "f64", 512, 512, 512, 64),
+    "7pt_rbgs_f32_512": (6, "f32", 512, 512, 512, 64),
 }
 DEFAULT = "7pt_const_f64_512"
 STENCIL_NAME = {0: "7-point constant", 1: "7-point variable", 2: "25-point constant", 3: "25-point variable",
-                4: "25-point constant with factor grid", 5: "27-point box"}
+                4: "25-point constant with factor grid", 5: "27-point box",
+                6: "7-point red-black Gauss-Seidel (T half-sweeps)"}
 # FP instructions per LUP of the point update (explicitly rounded ops, see csrc/stencil.cuh)
-INSTR_PER_LUP = {0: 7, 1: 7, 2: 28, 3: 28, 4: 28, 5: 27}
+INSTR_PER_LUP = {0: 7, 1: 7, 2: 28, 3: 28, 4: 28, 5: 27, 6: 7}
 # DRAM bytes per LUP measured by ncu (dram__bytes_read.sum + dram__bytes_write.sum of one launch
 # / LUPs of that launch) for a kernel on a smaller grid of the same workload, with the summary it
 # comes from; the roofline's "traffic" scales it to one launch of the benchmark grid
 MEASURED_BYTES_PER_LUP = {
     ("naive", 0, "f64"): (15.69, "profiles/naive_7pt_const_f64_512x384x256.md"),
-    ("naive", 0, "f32"): (7.28, "profiles/naive_7pt_const_f32_512x384x256.md"),
-    ("naive", 1, "f64"): (72.84, "profiles/naive_7pt_var_f64_480x384x192.md"),
-    ("naive", 1, "f32"): (36.46, "profiles/naive_7pt_var_f32_480x384x256.md"),
+    ("naive", 0, "f32"): (7.27, "profiles/naive_7pt_const_f32_512x384x256.md"),
+    ("naive", 1, "f64"): (72.81, "profiles/naive_7pt_var_f64_480x384x192.md"),
+    ("naive", 1, "f32"): (36.45, "profiles/naive_7pt_var_f32_480x384x256.md"),
     ("naive", 2, "f64"): (24.05, "profiles/naive_25pt_const_f64_384x384x192.md"),
     ("naive", 2, "f32"): (11.66, "profiles/naive_25pt_const_f32_384x384x256.md"),
-    ("naive", 3, "f64"): (132.13, "profiles/naive_25pt_var_f64_384x384x128.md"),
+    ("naive", 3, "f64"): (132.12, "profiles/naive_25pt_var_f64_384x384x128.md"),
     ("naive", 3, "f32"): (65.91, "profiles/naive_25pt_var_f32_384x384x192.md"),
     ("naive", 4, "f64"): (32.35, "profiles/naive_25pt_cgrid_f64_384x384x192.md"),
-    ("naive", 4, "f32"): (16.14, "profiles/naive_25pt_cgrid_f32_384x384x256.md"),
+    ("naive", 4, "f32"): (16.12, "profiles/naive_25pt_cgrid_f32_384x384x256.md"),
+    ("naive", 5, "f64"): (15.33, "profiles/naive_27pt_box_f64_512x384x256.md"),
+    ("naive", 5, "f32"): (7.26, "profiles/naive_27pt_box_f32_512x384x256.md"),
+    ("naive", 6, "f64"): (15.7, "profiles/naive_7pt_rbgs_f64_512x384x256.md"),
+    ("naive", 6, "f32"): (7.29, "profiles/naive_7pt_rbgs_f32_512x384x256.md"),
 }
 # domain-sized streams N_D of the code-balance model and the spatial minimum bytes per LUP (in elements)
-ND = {0: 2, 1: 9, 2: 2, 3: 15, 4: 3, 5: 2}
-SPATIAL_ELEMS = {0: 2, 1: 9, 2: 3, 3: 16, 4: 4, 5: 2}
+ND = {0: 2, 1: 9, 2: 2, 3: 15, 4: 3, 5: 2, 6: 2}
+SPATIAL_ELEMS = {0: 2, 1: 9, 2: 3, 3: 16, 4: 4, 5: 2, 6: 2}
 
 
 def _peaks():

@@ -1,7 +1,7 @@
 /*
  * girih.h -- C ABI of the GB300 (sm_103a) temporally blocked stencil sweep library.
  *
- * The library advances a 3D grid by T time steps of one of six Jacobi-style stencils
+ * The library advances a 3D grid by T time steps of one of seven Jacobi-style stencils
  * (Malas, Hager, Ltaief, Keyes, "Multi-dimensional intra-tile parallelization for
  * memory-starved stencil computations", arXiv 1510.04995):
  *   GIRIH_7PT_CONST  Listing 1: first order in time, radius 1, constants c0, c1.
@@ -17,6 +17,12 @@
  *                    neighbours), c2 (the 12 edge neighbours), c3 (the 8 corner neighbours).
  *                    Its blocked sweep runs on the 16-byte vector path only (rows of 16-byte
  *                    multiples, 16-byte aligned buffers); the naive sweep takes any layout.
+ *   GIRIH_7PT_RBGS   red-black Gauss-Seidel on the 7-point constant operator (Sect. 7): time
+ *                    step t is a half-sweep updating the points whose interior coordinates have
+ *                    x + y + z + t even (c0*V + c1*(neighbour pairs)) and keeping the others;
+ *                    T = 2 x the red-black iterations.  Computed in the two-buffer form (the
+ *                    kept colour is copied), bit for bit the in-place sweep.  Blocked sweep on
+ *                    the vector path only, as for 27PT_BOX.
  * Two algorithms reach the same result (Sect. 2.1): the naive sweep (one pass over the grid per
  * time step, Sect. 2.1.1) and the multi-threaded wavefront-diamond sweep (MWD, Sect. 4.2.1):
  * diamond tiles along y (Sect. 2.1.2), a wavefront along z, several time steps per pass over
@@ -55,7 +61,8 @@ typedef enum {
   GIRIH_25PT_CONST = 2,
   GIRIH_25PT_VAR = 3,
   GIRIH_25PT_CGRID = 4,
-  GIRIH_27PT_BOX = 5
+  GIRIH_27PT_BOX = 5,
+  GIRIH_7PT_RBGS = 6
 } girih_stencil;
 typedef enum { GIRIH_F64 = 0, GIRIH_F32 = 1 } girih_dtype;
 typedef enum { GIRIH_ALGO_NAIVE = 0, GIRIH_ALGO_MWD = 1 } girih_algo;
@@ -117,7 +124,7 @@ typedef struct girih_config {
 /* Per-call parameters.  c[] holds the constant coefficients: 7PT_CONST uses c[0]=c0 (centre),
  * c[1]=c1 (the six neighbours); 25PT_CONST and 25PT_CGRID use c[0] (centre) and c[r] for the six
  * neighbours at distance r = 1..4; 27PT_BOX uses c[0] (centre), c[1] (faces), c[2] (edges) and
- * c[3] (corners).  Ignored by the variable-coefficient stencils.  If force_cfg is non-zero,
+ * c[3] (corners); 7PT_RBGS c[0] and c[1] like 7PT_CONST.  Ignored by the variable-coefficient stencils.  If force_cfg is non-zero,
  * cfg replaces the plan's configuration for this call.                                     */
 typedef struct girih_params {
   double c[5];
@@ -130,7 +137,7 @@ typedef struct girih_plan_s* girih_plan_t;
 /* ---- plan / run ---------------------------------------------------------------------------- */
 
 /* Create a plan for T steps of `stencil` on an nx*ny*nz interior (halo R implied: 1 for the
- * 7-point and box stencils, 4 for the 25-point ones) in `dtype`, leading dimension ldx (0 = dense).
+ * 7-point, box and red-black stencils, 4 for the 25-point ones) in `dtype`, leading dimension ldx (0 = dense).
  * Queries the current device and picks a default configuration (largest feasible diamond).
  * Writes *out = NULL on failure.  EINVAL: bad enum, nx/ny/nz < 1, T < 0, ldx < nx + 2R.    */
 GIRIH_API int girih_plan(girih_plan_t* out, int32_t stencil, int64_t nx, int64_t ny, int64_t nz, int64_t ldx,
@@ -153,14 +160,14 @@ GIRIH_API int girih_config_check(girih_plan_t plan, const girih_config* cfg, int
  *   u_prev  device buffer: for the second-order stencils level -1 on entry and level T-1 on
  *           return; for the first-order stencils scratch whose halo must equal u's halo (on
  *           return it holds level T-1, or is unchanged when T = 0).
- *   coeffs  NULL for 7PT_CONST, 25PT_CONST and 27PT_BOX; else 7 (7PT_VAR: C0 centre, C1 x+1, C2 x-1,
+ *   coeffs  NULL for 7PT_CONST, 25PT_CONST, 27PT_BOX and 7PT_RBGS; else 7 (7PT_VAR: C0 centre, C1 x+1, C2 x-1,
  *           C3 y+1, C4 y-1, C5 z+1, C6 z-1; Listing 2), 13 (25PT_VAR: C00 centre, then for
  *           r = 1..4 the x, y, z pairs at distance r; Listing 4) or 1 (25PT_CGRID: the factor C
  *           of Listing 3) grids of the padded layout, back to back; their halo cells are never
  *           read.
  *   params  coefficients and optional forced configuration (NULL: 7PT_CONST uses the workload
  *           constants c0=0.4, c1=0.1; 25PT_CONST and 25PT_CGRID c0=-0.9, c_r=0.1/2^r; 27PT_BOX
- *           0.4, 0.05, 0.02, 0.0075).
+ *           0.4, 0.05, 0.02, 0.0075; 7PT_RBGS c0=0, c1=1/6, the Laplace equation).
  * Pointers must be 8-byte (F64) or 4-byte (F32) aligned (16-byte for GIRIH_FED_BULK) and
  * u != u_prev.  The two buffers'
  * roles alternate every step (Listing 3's pointer swap); for odd T one in-place exchange kernel
@@ -243,7 +250,7 @@ GIRIH_API int girih_tune_exhaustive(girih_plan_t plan, const girih_config* cands
 
 /* Features of a configuration for the network (writes GIRIH_MLP_FEATURES floats): stencil
  * one-hot in [0, 4) (25PT_CGRID shares the 25PT_CONST slot, its third stream showing in the
- * model code balance, feature 14; 27PT_BOX shares the 7PT_CONST slot), dtype, log sizes, algorithm, diamond width, wavefront width,
+ * model code balance, feature 14; 27PT_BOX and 7PT_RBGS share the 7PT_CONST slot), dtype, log sizes, algorithm, diamond width, wavefront width,
  * cluster, threads, variant, log code balance, log slab width.                                */
 #define GIRIH_MLP_FEATURES 16
 #define GIRIH_MLP_HIDDEN 64

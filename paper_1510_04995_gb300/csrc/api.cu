@@ -89,9 +89,9 @@ int check_config(const Plan* p, const girih_config* c, int64_t* smem_out, int* x
     return fail(GIRIH_EINVAL, "unknown variant %d", c->variant);
   if (c->variant == GIRIH_FED_PERSISTENT && mwd_path(p, c, ptrs16) != MV_VEC)
     return fail(GIRIH_EINVAL, "FED_PERSISTENT needs rows of 16-byte multiples and 16-byte aligned buffers");
-  if (is_box(p->stencil) && mwd_path(p, c, ptrs16) == MV_ELEM)
-    return fail(GIRIH_EINVAL, "the box stencil's blocked sweep needs the vector path: rows of 16-byte multiples, "
-                "16-byte aligned buffers and a variant other than FED_ELEM / RELAXED_ELEM");
+  if (vec_only(p->stencil) && mwd_path(p, c, ptrs16) == MV_ELEM)
+    return fail(GIRIH_EINVAL, "the blocked sweep of the box and red-black stencils needs the vector path: rows of "
+                "16-byte multiples, 16-byte aligned buffers and a variant other than FED_ELEM / RELAXED_ELEM");
   const bool bulk = c->variant == GIRIH_FED_BULK;
   if (bulk && !p->bulk_layout)
     return fail(GIRIH_EINVAL, "FED_BULK needs ldx*elem to be a multiple of 16 bytes (ldx=%lld)", (long long)p->ldx);
@@ -183,6 +183,7 @@ int run_sweep(Plan* p, int64_t T, void* u, void* u_prev, const void* coeffs, con
     for (int64_t t = 0; t < T && e == cudaSuccess; ++t) {
       a.V = buf[t % 2];
       a.U = buf[(t + 1) % 2];
+      a.t = (int32_t)t;
       e = launch_naive_step(p->stencil, p->dtype, a, st);
     }
   } else {
@@ -316,6 +317,7 @@ static int launch_persistent(Plan* p, MwdArgs a, int64_t rows, const girih_confi
 static const double kConst7[5] = {0.4, 0.1, 0, 0, 0};
 static const double kConst25[5] = {-0.9, 0.05, 0.025, 0.0125, 0.00625};
 static const double kConstBox[5] = {0.4, 0.05, 0.02, 0.0075, 0};
+static const double kConstRB[5] = {0.0, 1.0 / 6.0, 0, 0, 0};
 
 int validate_run(Plan* p, void* u, void* u_prev, const void* coeffs, const girih_params* params,
                  const double** c, const girih_config** cfg) {
@@ -333,7 +335,10 @@ int validate_run(Plan* p, void* u, void* u_prev, const void* coeffs, const girih
   const char* cu = static_cast<const char*>(u);
   const char* cp = static_cast<const char*>(u_prev);
   if (cu < cp + bytes && cp < cu + bytes) return fail(GIRIH_EINVAL, "u and u_prev overlap");
-  *c = (params) ? params->c : (is_box(p->stencil) ? kConstBox : (radius_of(p->stencil) == 4 ? kConst25 : kConst7));
+  *c = (params) ? params->c
+                 : (is_box(p->stencil) ? kConstBox
+                                       : (p->stencil == GIRIH_7PT_RBGS ? kConstRB
+                                                                       : (radius_of(p->stencil) == 4 ? kConst25 : kConst7)));
   *cfg = (params && params->force_cfg) ? &params->cfg : &p->cfg;
   if ((*cfg)->algo == GIRIH_ALGO_MWD) {
     const bool ptrs16 = ((reinterpret_cast<uintptr_t>(u) | reinterpret_cast<uintptr_t>(u_prev)) & 15) == 0;
@@ -360,7 +365,7 @@ int girih_plan(girih_plan_t* out, int32_t stencil, int64_t nx, int64_t ny, int64
                int64_t T) {
   if (!out) return fail(GIRIH_EINVAL, "out is NULL");
   *out = nullptr;
-  if (stencil < 0 || stencil > 5) return fail(GIRIH_EINVAL, "unknown stencil %d", stencil);
+  if (stencil < 0 || stencil > 6) return fail(GIRIH_EINVAL, "unknown stencil %d", stencil);
   if (dtype != GIRIH_F64 && dtype != GIRIH_F32) return fail(GIRIH_EINVAL, "unknown dtype %d", dtype);
   if (nx < 1 || ny < 1 || nz < 1) return fail(GIRIH_EINVAL, "sizes must be >= 1");
   if (T < 0 || T > (1LL << 30)) return fail(GIRIH_EINVAL, "T=%lld out of range", (long long)T);

@@ -25,6 +25,7 @@ struct NaiveArgs {
   float cf[5];  // the same constants rounded to FP32 (FP32 kernels read these: no conversion on device)
   int32_t zc;  // z planes per block
   int32_t v16;  // rows of 16-byte multiples and 16-byte aligned buffers: 16-byte staging
+  int32_t t;    // the time step this launch makes (the red-black colour mask depends on it)
 };
 cudaError_t launch_naive_step(int stencil, int dtype, const NaiveArgs& a, cudaStream_t st);
 // Resident blocks per SM of the naive kernel, and the z chunk (planes per block) that fills the
@@ -83,6 +84,8 @@ int mwd_pairs_per_thread(int stencil, int dtype, int dw, int XW, int threads, in
 inline int radius_of(int stencil) { return (stencil >= 2 && stencil <= 4) ? 4 : 1; }
 inline int ncoef_of(int stencil) { return stencil == 1 ? 7 : (stencil == 3 ? 13 : (stencil == 4 ? 1 : 0)); }
 inline bool is_box(int stencil) { return stencil == GIRIH_27PT_BOX; }
+// stencils whose blocked sweep exists on the 16-byte vector path only
+inline bool vec_only(int stencil) { return stencil == GIRIH_27PT_BOX || stencil == GIRIH_7PT_RBGS; }
 inline bool second_order(int stencil) { return stencil >= 2 && stencil <= 4; }
 inline int mwd_vx(int stencil, int dtype, int mv) {
   const bool r1 = radius_of(stencil) == 1;

@@ -11,12 +11,14 @@ void* mwd_vec_kernel_r4(int stencil, int dtype, int G, bool tma);
 void* mwd_kernel_cg(int dtype, int G);
 void* mwd_vec_kernel_cg(int dtype, int G, bool tma);
 void* mwd_vec_kernel_box(int dtype, int G, bool tma);
+void* mwd_vec_kernel_rb(int dtype, int G, bool tma);
 
 static void* pick(int stencil, int dtype, int G, int mv) {
   if (mv_shifted(mv)) {
     const bool tma = mv == MV_BULK;
     if (stencil == GIRIH_25PT_CGRID) return mwd_vec_kernel_cg(dtype, G, tma);
     if (stencil == GIRIH_27PT_BOX) return mwd_vec_kernel_box(dtype, G, tma);
+    if (stencil == GIRIH_7PT_RBGS) return mwd_vec_kernel_rb(dtype, G, tma);
     return stencil < 2 ? mwd_vec_kernel_r1(stencil, dtype, G, tma) : mwd_vec_kernel_r4(stencil, dtype, G, tma);
   }
   if (stencil == GIRIH_25PT_CGRID) return mwd_kernel_cg(dtype, G);

@@ -148,6 +148,7 @@ __device__ __forceinline__ void mwd_vec_tile(const MwdArgs& A, const int rho, co
 
   // ---- groups: row pair (level s, rows y0, y0+1) x VX columns, owned for the whole launch ----
   int gin_[G], gout_[G], gzb_[G], gpo_[G], gfl_[G], glo_[G], ghi_[G], gx_[G];
+  int gpar_[G];  // red-black: parity of (x + y0 + t) at the group's first column
   const T* gk_[G];
   const int npairs = lev_pp[nlev];
   const int nvec = XW / VX;
@@ -169,6 +170,7 @@ __device__ __forceinline__ void mwd_vec_tile(const MwdArgs& A, const int rho, co
     gpo_[g] = sl * pe;
     glo_[g] = max(0, vlo - xl);
     gx_[g] = xl;
+    gpar_[g] = (x0 + xl + y0 + t) & 1;
     ghi_[g] = min(VX, vhi - xl);
     const bool row1 = valid && (y0 + 1 < lev_lo[s] + lev_w[s]);
     // x-halo pushes: the slab's first R columns to the left neighbour, its last R columns to the
@@ -418,6 +420,16 @@ __device__ __forceinline__ void mwd_vec_tile(const MwdArgs& A, const int rho, co
                 lds_vec<T, VX>(Ub + XT, u1);
               }
               mwd_points<S, T, VX>(w0, w1, ylo_, yhi_, xl0, xl1, u0, u1, kp, gstride, ldx, hi, true, cst, r0, r1);
+              if constexpr (Traits<S>::RB) {
+                // red-black: only points with (x + y + z + t) even are updated, the others keep
+                // their value (row y0+1 has the other colour)
+#pragma unroll
+                for (int i = 0; i < VX; ++i) {
+                  const bool odd0 = (gpar_[g] + i + z) & 1;
+                  if (odd0) r0[i] = w0[R * VX + i];
+                  else r1[i] = w1[R * VX + i];
+                }
+              }
             }
             if (lo == 0 && hi == VX) {
               sts_vec<T, VX>(Ub, r0);

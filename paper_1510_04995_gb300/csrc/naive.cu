@@ -219,7 +219,10 @@ __global__ void __launch_bounds__(32 * TY) naive_kernel(const NaiveArgs a) {
           NaiveAcc<S, T, TXW> acc{tl + cofs[r] + v * 32, w[r][v], kv[r][v], T(0), tlm + cofs[r] + v * 32,
                                   tlp + cofs[r] + v * 32};
           if constexpr (Traits<S>::ORDER2) acc.uc = uc[r][v];
-          *up[r][v] = point_update<S, T>(acc, cst);
+          T res = point_update<S, T>(acc, cst);
+          if constexpr (Traits<S>::RB)  // red-black: only (x + y + z + t) even is updated
+            if ((bx + v * 32 + tx + by + ty + r * TY + z0 + zr + a.t) & 1) res = w[r][v][R];
+          *up[r][v] = res;
         }
         up[r][v] += plane;
       }
@@ -259,7 +262,7 @@ constexpr int naive_pd() { return Traits<S>::R == 1 ? 4 : (S == 2 ? 2 : 3); }
 // coefficients per column in registers, so more columns cost occupancy).
 template <int S, typename T, bool V16>
 constexpr int naive_vx() {
-  return (V16 && sizeof(T) == 4) ? (S == 0 ? 4 : ((S == 2 || S == 5) ? 2 : 1)) : 1;
+  return (V16 && sizeof(T) == 4) ? ((S == 0 || S == 6) ? 4 : ((S == 2 || S == 5) ? 2 : 1)) : 1;
 }
 
 template <int S, typename T, bool V16>
@@ -323,7 +326,8 @@ int naive_tile_x(int stencil, int dtype, bool v16) {
     case 2: return pick(std::integral_constant<int, 2>());
     case 3: return pick(std::integral_constant<int, 3>());
     case 4: return pick(std::integral_constant<int, 4>());
-    default: return pick(std::integral_constant<int, 5>());
+    case 5: return pick(std::integral_constant<int, 5>());
+    default: return pick(std::integral_constant<int, 6>());
   }
 }
 
@@ -340,7 +344,8 @@ int naive_resident_blocks(int stencil, int dtype, bool v16) {
     case 2: return pick(std::integral_constant<int, 2>());
     case 3: return pick(std::integral_constant<int, 3>());
     case 4: return pick(std::integral_constant<int, 4>());
-    default: return pick(std::integral_constant<int, 5>());
+    case 5: return pick(std::integral_constant<int, 5>());
+    default: return pick(std::integral_constant<int, 6>());
   }
 }
 
@@ -375,7 +380,8 @@ cudaError_t launch_naive_step(int stencil, int dtype, const NaiveArgs& a, cudaSt
     case 2: return f64 ? launch_v<2, double>(a, st) : launch_v<2, float>(a, st);
     case 3: return f64 ? launch_v<3, double>(a, st) : launch_v<3, float>(a, st);
     case 4: return f64 ? launch_v<4, double>(a, st) : launch_v<4, float>(a, st);
-    default: return f64 ? launch_v<5, double>(a, st) : launch_v<5, float>(a, st);
+    case 5: return f64 ? launch_v<5, double>(a, st) : launch_v<5, float>(a, st);
+    default: return f64 ? launch_v<6, double>(a, st) : launch_v<6, float>(a, st);
   }
 }
 

@@ -1,5 +1,5 @@
-// Point updates of the six stencils (arXiv 1510.04995, Sect. 2.2, Listings 1-4, and the 27-point
-// box operator of Sect. 7) and the small
+// Point updates of the seven stencils (arXiv 1510.04995, Sect. 2.2, Listings 1-4, and the
+// 27-point box operator and red-black Gauss-Seidel of Sect. 7) and the small
 // device helpers the sweep kernels share.
 //
 // Every kernel of the library computes a lattice-site update (LUP) through exactly one of the
@@ -19,6 +19,8 @@
 //   27pt box  : F, E, K = sums of the face, edge and corner neighbours, each taken over the
 //               offsets in (dz, dy, dx) lexicographic order; acc = c0*V; acc += c1*F; += c2*E;
 //               += c3*K
+//   7pt RB-GS : the 7pt const formula for the points whose interior (x + y + z + t) is even at
+//               time step (half-sweep) t; the others keep their value (the kernels select)
 #pragma once
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -26,21 +28,23 @@
 namespace girih {
 
 // R: radius; NCOEF: coefficient grids; ORDER2: second order in time; BOX: diagonal neighbours
-// (read through the accessor's b(dx, dy, dz)).
+// (read through the accessor's b(dx, dy, dz)); RB: red-black colour mask on the update.
 template <int S>
 struct Traits;
 template <>
-struct Traits<0> { static constexpr int R = 1, NCOEF = 0; static constexpr bool ORDER2 = false, BOX = false; };
+struct Traits<0> { static constexpr int R = 1, NCOEF = 0; static constexpr bool ORDER2 = false, BOX = false, RB = false; };
 template <>
-struct Traits<1> { static constexpr int R = 1, NCOEF = 7; static constexpr bool ORDER2 = false, BOX = false; };
+struct Traits<1> { static constexpr int R = 1, NCOEF = 7; static constexpr bool ORDER2 = false, BOX = false, RB = false; };
 template <>
-struct Traits<2> { static constexpr int R = 4, NCOEF = 0; static constexpr bool ORDER2 = true, BOX = false; };
+struct Traits<2> { static constexpr int R = 4, NCOEF = 0; static constexpr bool ORDER2 = true, BOX = false, RB = false; };
 template <>
-struct Traits<3> { static constexpr int R = 4, NCOEF = 13; static constexpr bool ORDER2 = true, BOX = false; };
+struct Traits<3> { static constexpr int R = 4, NCOEF = 13; static constexpr bool ORDER2 = true, BOX = false, RB = false; };
 template <>
-struct Traits<4> { static constexpr int R = 4, NCOEF = 1; static constexpr bool ORDER2 = true, BOX = false; };
+struct Traits<4> { static constexpr int R = 4, NCOEF = 1; static constexpr bool ORDER2 = true, BOX = false, RB = false; };
 template <>
-struct Traits<5> { static constexpr int R = 1, NCOEF = 0; static constexpr bool ORDER2 = false, BOX = true; };
+struct Traits<5> { static constexpr int R = 1, NCOEF = 0; static constexpr bool ORDER2 = false, BOX = true, RB = false; };
+template <>
+struct Traits<6> { static constexpr int R = 1, NCOEF = 0; static constexpr bool ORDER2 = false, BOX = false, RB = true; };
 
 template <typename T>
 struct Ops;
@@ -66,7 +70,7 @@ struct Ops<double> {
 template <int S, typename T, typename A>
 __device__ __forceinline__ T point_update(const A& a, const T* cst) {
   using O = Ops<T>;
-  if constexpr (S == 0) {
+  if constexpr (S == 0 || S == 6) {
     const T c0 = cst[0], c1 = cst[1];
     T acc = O::mul(c0, a.c());
     acc = O::fma(c1, O::add(a.x(1), a.x(-1)), acc);
@@ -132,8 +136,10 @@ __device__ __forceinline__ T point_update(const A& a, const T* cst) {
 // Arithmetic instructions per LUP of point_update (each intrinsic is one FP instruction):
 // 7pt const 7, 7pt var 7, 25pt const 1 + 4*6 + 3 = 28, 25pt var 1 + 12*2 + 3 = 28, 25pt Cgrid
 // 1 + 4*6 + 3 = 28.
-// 27pt box 5 + 11 + 7 + 1 + 3 = 27.
-__host__ __device__ constexpr int fp_instructions_per_lup(int s) { return s < 2 ? 7 : (s == 5 ? 27 : 28); }
+// 27pt box 5 + 11 + 7 + 1 + 3 = 27; 7pt RB-GS 7 (computed for every point, kept for one colour).
+__host__ __device__ constexpr int fp_instructions_per_lup(int s) {
+  return (s < 2 || s == 6) ? 7 : (s == 5 ? 27 : 28);
+}
 
 // ---- small PTX helpers (sm_90+ cluster features, cp.async) -------------------------------------
 __device__ __forceinline__ uint32_t smem_addr(const void* p) {

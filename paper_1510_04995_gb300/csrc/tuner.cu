@@ -69,6 +69,7 @@ static cudaError_t fill(Plan* p, cudaStream_t st) {
 static const double kC7[5] = {0.4, 0.1, 0, 0, 0};
 static const double kC25[5] = {-0.9, 0.05, 0.025, 0.0125, 0.00625};
 static const double kCBox[5] = {0.4, 0.05, 0.02, 0.0075, 0};
+static const double kCRB[5] = {0.0, 1.0 / 6.0, 0, 0, 0};
 
 int measure(Plan* p, const girih_config& cfg, double tol, int64_t max_steps, girih_tune_row* row) {
   const auto wall0 = std::chrono::steady_clock::now();
@@ -76,7 +77,7 @@ int measure(Plan* p, const girih_config& cfg, double tol, int64_t max_steps, gir
   if (rc != GIRIH_OK) return rc;
   rc = ensure_tune_arrays(p);
   if (rc != GIRIH_OK) return rc;
-  const double* c = is_box(p->stencil) ? kCBox : (p->R == 4 ? kC25 : kC7);
+  const double* c = is_box(p->stencil) ? kCBox : (p->stencil == GIRIH_7PT_RBGS ? kCRB : (p->R == 4 ? kC25 : kC7));
   // one diamond row advances H/2 steps; grow the test in units of two rows (Sect. 4.2.2)
   const int64_t unit = (cfg.algo == GIRIH_ALGO_MWD) ? std::max<int64_t>(cfg.dw / p->R, 2) : 2;
   int64_t steps = unit;
@@ -217,9 +218,9 @@ int girih_tune_exhaustive(girih_plan_t plan, const girih_config* cand_list, int3
 
 int girih_mlp_features(int32_t stencil, int32_t dtype, int64_t nx, int64_t ny, int64_t nz, const girih_config* cfg,
                        float* out) {
-  if (!cfg || !out || stencil < 0 || stencil > 5) return fail(GIRIH_EINVAL, "bad feature arguments");
+  if (!cfg || !out || stencil < 0 || stencil > 6) return fail(GIRIH_EINVAL, "bad feature arguments");
   for (int i = 0; i < GIRIH_MLP_FEATURES; ++i) out[i] = 0.f;
-  out[stencil == GIRIH_25PT_CGRID ? GIRIH_25PT_CONST : (stencil == GIRIH_27PT_BOX ? GIRIH_7PT_CONST : stencil)] = 1.f;
+  out[stencil == GIRIH_25PT_CGRID ? GIRIH_25PT_CONST : (stencil >= GIRIH_27PT_BOX ? GIRIH_7PT_CONST : stencil)] = 1.f;
   out[4] = dtype == GIRIH_F32 ? 1.f : 0.f;
   out[5] = (float)(std::log2((double)nx) / 10.0);
   out[6] = (float)(std::log2((double)ny) / 10.0);

@@ -34,8 +34,10 @@ WORKLOADS = {
     "25pt_cgrid_f32_384": (4, "f32", 384, 384, 384, 32),
     "27pt_box_f64_512": (5, "f64", 512, 512, 512, 64),
     "27pt_box_f32_512": (5, "f32", 512, 512, 512, 64),
+    "7pt_rbgs_f64_512": (6, "f64", 512, 512, 512, 64),
+    "7pt_rbgs_f32_512": (6, "f32", 512, 512, 512, 64),
 }
-RADIUS = {0: 1, 1: 1, 2: 4, 3: 4, 4: 4, 5: 1}
+RADIUS = {0: 1, 1: 1, 2: 4, 3: 4, 4: 4, 5: 1, 6: 1}
 
 
 def aligned_ldx(stencil: int, dtype: str, nx: int) -> int:

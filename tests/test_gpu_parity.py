@@ -17,7 +17,7 @@ from gpu_util import feasible_cfg, gpu_sweep, normwise, rel_l2
 pytestmark = pytest.mark.gpu
 
 SIZES = {1: (70, 45, 33), 4: (70, 50, 29)}
-FP32_TOL = {0: 1e-5, 1: 1e-5, 2: 1e-4, 3: 1e-4, 4: 1e-4, 5: 1e-5}
+FP32_TOL = {0: 1e-5, 1: 1e-5, 2: 1e-4, 3: 1e-4, 4: 1e-4, 5: 1e-5, 6: 1e-5}
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -41,7 +41,7 @@ MWD_CFGS = {
 }
 
 
-@pytest.mark.parametrize("stencil", [0, 1, 2, 3, 4, 5])
+@pytest.mark.parametrize("stencil", [0, 1, 2, 3, 4, 5, 6])
 def test_naive_fp64_vs_oracle(stencil):
     R = inputs.RADIUS[stencil]
     nx, ny, nz = SIZES[R]
@@ -56,7 +56,7 @@ def test_naive_fp64_vs_oracle(stencil):
     assert np.array_equal(gu[m], u[m]) and np.array_equal(gup[m], up[m])
 
 
-@pytest.mark.parametrize("stencil", [0, 1, 2, 3, 4, 5])
+@pytest.mark.parametrize("stencil", [0, 1, 2, 3, 4, 5, 6])
 @pytest.mark.parametrize("ci", [0, 1, 2, 3])
 def test_mwd_fp64_vs_oracle_and_naive(stencil, ci):
     R = inputs.RADIUS[stencil]
@@ -78,7 +78,7 @@ def test_mwd_fp64_vs_oracle_and_naive(stencil, ci):
         assert np.array_equal(bup, nup), (T, kw)
 
 
-@pytest.mark.parametrize("stencil", [0, 1, 2, 3, 4, 5])
+@pytest.mark.parametrize("stencil", [0, 1, 2, 3, 4, 5, 6])
 @pytest.mark.parametrize("algo", ["naive", "mwd"])
 def test_fp32_error_vs_fp64_oracle(stencil, algo):
     R = inputs.RADIUS[stencil]
@@ -90,7 +90,7 @@ def test_fp32_error_vs_fp64_oracle(stencil, algo):
     assert rel_l2(gu, ru, R) <= FP32_TOL[stencil]
 
 
-@pytest.mark.parametrize("stencil", [0, 3, 4, 5])
+@pytest.mark.parametrize("stencil", [0, 3, 4, 5, 6])
 def test_fp32_mwd_bitwise_equals_naive(stencil):
     R = inputs.RADIUS[stencil]
     nx, ny, nz = SIZES[R]
@@ -238,7 +238,7 @@ def test_vector_path_on_unaligned_buffers_falls_back(stencil, dtype):
         assert np.array_equal(gu, nu) and np.array_equal(gup, nup)
 
 
-@pytest.mark.parametrize("stencil", [0, 1, 2, 3, 4, 5])
+@pytest.mark.parametrize("stencil", [0, 1, 2, 3, 4, 5, 6])
 @pytest.mark.parametrize("dtype", ["f64", "f32"])
 def test_relaxed_variant(stencil, dtype):
     """The RELAXED synchronisation (neighbour hand-off between the blocks of a cluster instead of a
@@ -288,7 +288,7 @@ def _aligned_ldx(nx, R, dtype):
     return -(-(nx + 2 * R) // a16) * a16
 
 
-@pytest.mark.parametrize("stencil", [0, 1, 2, 3, 4, 5])
+@pytest.mark.parametrize("stencil", [0, 1, 2, 3, 4, 5, 6])
 @pytest.mark.parametrize("dtype", ["f64", "f32"])
 def test_persistent_schedule(stencil, dtype):
     """FED_PERSISTENT (one launch per sweep; clusters take diamonds from a FIFO and start each once
@@ -340,49 +340,52 @@ def test_persistent_schedule_reuse_and_rejects_unaligned():
     assert p.launch_count(bad) == 2  # one persistent launch + the exchange for odd T
 
 
+@pytest.mark.parametrize("stencil", [5, 6])
 @pytest.mark.parametrize("dtype", ["f64", "f32"])
-def test_box_blocked_paths_and_layouts(dtype):
-    """The 27-point box stencil: its diagonal dependencies (edges and corners of the tile, Sect. 7)
-    are met by the same diamonds and wavefront.  The vector path (FED), the bulk-copy path
+def test_vector_only_stencils_paths_and_layouts(stencil, dtype):
+    """The 27-point box stencil and red-black Gauss-Seidel (Sect. 7): the box stencil's diagonal
+    dependencies (edges and corners of the tile) and red-black's colour-masked half-sweeps are
+    met by the same diamonds and wavefront.  The vector path (FED), the bulk-copy path
     (FED_BULK) and the persistent schedule agree with the naive sweep bit for bit, including
     truncated diamond rows and clusters that split x; layouts the vector path cannot take are
     rejected for the blocked sweep, while the naive sweep takes them."""
     nx, ny, nz = 61, 47, 29
     ldx = _aligned_ldx(nx, 1, dtype) + (16 // (8 if dtype == "f64" else 4))   # spare columns
     for T in (1, 3, 4, 5, 11):
-        u, up, co, c = inputs.make_problem(5, nx, ny, nz, seed=40 + T, ldx=ldx)
-        nu, nup = gpu_sweep(5, dtype, u, up, co, c, T, nx, ny, nz, girih.config(girih.NAIVE), ldx=ldx)
+        u, up, co, c = inputs.make_problem(stencil, nx, ny, nz, seed=40 + T, ldx=ldx)
+        nu, nup = gpu_sweep(stencil, dtype, u, up, co, c, T, nx, ny, nz, girih.config(girih.NAIVE), ldx=ldx)
         if dtype == "f64":
             ru, rup = u.copy(), up.copy()
-            oracle.sweep(5, ru, rup, None, c, T, nx, ny, nz, nthreads=8)
+            oracle.sweep(stencil, ru, rup, None, c, T, nx, ny, nz, nthreads=8)
             assert normwise(nu[:, :, :nx + 2], ru[:, :, :nx + 2], 1) <= 1e-12
         for kw in (dict(dw=4, nf=1, cluster=2, threads=256, variant=girih.FED),
                    dict(dw=8, nf=2, cluster=4, threads=256, variant=girih.FED_BULK),
                    dict(dw=6, nf=1, cluster=8, threads=256, variant=girih.FED_PERSISTENT),
                    dict(dw=2, nf=1, cluster=1, threads=256, variant=girih.FED_PERSISTENT)):
-            cfg = feasible_cfg(5, dtype, nx, ny, nz, kw, ldx=ldx)
+            cfg = feasible_cfg(stencil, dtype, nx, ny, nz, kw, ldx=ldx)
             assert cfg.variant == kw["variant"]
-            bu, bup = gpu_sweep(5, dtype, u, up, co, c, T, nx, ny, nz, cfg, ldx=ldx)
+            bu, bup = gpu_sweep(stencil, dtype, u, up, co, c, T, nx, ny, nz, cfg, ldx=ldx)
             assert np.array_equal(bu, nu) and np.array_equal(bup, nup), (T, kw)
-    p_un = girih.plan(5, nx, ny, nz, dtype=dtype, T=3, ldx=ldx + 1)
+    p_un = girih.plan(stencil, nx, ny, nz, dtype=dtype, T=3, ldx=ldx + 1)
     assert not p_un.feasible(girih.config(girih.MWD, dw=4, nf=1, cluster=2, threads=256))
-    assert not girih.plan(5, nx, ny, nz, dtype=dtype, T=3, ldx=ldx).feasible(
+    assert not girih.plan(stencil, nx, ny, nz, dtype=dtype, T=3, ldx=ldx).feasible(
         girih.config(girih.MWD, dw=4, nf=1, cluster=2, threads=256, variant=girih.FED_ELEM))
-    u, up, co, c = inputs.make_problem(5, nx, ny, nz, seed=3, ldx=ldx + 1)
+    u, up, co, c = inputs.make_problem(stencil, nx, ny, nz, seed=3, ldx=ldx + 1)
     ru, rup = u.copy(), up.copy()
-    oracle.sweep(5, ru, rup, None, c, 3, nx, ny, nz)
-    gu, _ = gpu_sweep(5, "f64", u, up, co, c, 3, nx, ny, nz, girih.config(girih.NAIVE), ldx=ldx + 1)
+    oracle.sweep(stencil, ru, rup, None, c, 3, nx, ny, nz)
+    gu, _ = gpu_sweep(stencil, "f64", u, up, co, c, 3, nx, ny, nz, girih.config(girih.NAIVE), ldx=ldx + 1)
     assert normwise(gu[:, :, :nx + 2], ru[:, :, :nx + 2], 1) <= 1e-12
 
 
+@pytest.mark.parametrize("stencil", [5, 6])
 @pytest.mark.parametrize("shape", [(1, 1, 1), (3, 2, 5), (33, 1, 9), (1, 40, 3), (5, 7, 1)])
-def test_box_degenerate_shapes(shape):
+def test_vector_only_stencils_degenerate_shapes(stencil, shape):
     nx, ny, nz = shape
     ldx = _aligned_ldx(nx, 1, "f64")
-    u, up, co, c = inputs.make_problem(5, nx, ny, nz, ldx=ldx)
+    u, up, co, c = inputs.make_problem(stencil, nx, ny, nz, ldx=ldx)
     ru, rup = u.copy(), up.copy()
-    oracle.sweep(5, ru, rup, None, c, 5, nx, ny, nz)
-    mwd = feasible_cfg(5, "f64", nx, ny, nz, dict(dw=2, nf=1, cluster=1, threads=256), ldx=ldx)
+    oracle.sweep(stencil, ru, rup, None, c, 5, nx, ny, nz)
+    mwd = feasible_cfg(stencil, "f64", nx, ny, nz, dict(dw=2, nf=1, cluster=1, threads=256), ldx=ldx)
     for cfg in (girih.config(girih.NAIVE), mwd):
-        gu, _ = gpu_sweep(5, "f64", u, up, co, c, 5, nx, ny, nz, cfg, ldx=ldx)
+        gu, _ = gpu_sweep(stencil, "f64", u, up, co, c, 5, nx, ny, nz, cfg, ldx=ldx)
         assert np.max(np.abs(gu - ru)) <= 1e-12 * max(1.0, np.max(np.abs(ru))), (shape, cfg)
