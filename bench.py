@@ -424,7 +424,8 @@ def main():
         et = max_over_ranks(time.perf_counter() - t0, ws, dev)
         nbytes = u.numel() * elem
         e2e = {"value": lups * n_e2e * ws / et * 1e-9, "unit": "GLUP/s",
-               "h2d_bytes_per_step": 2 * nbytes + (co.numel() * elem if co is not None else 0),
+               "h2d_bytes_per_step": (2 if inputs.SECOND_ORDER[stencil] else 1) * nbytes
+                                     + (co.numel() * elem if co is not None else 0),
                "d2h_bytes_per_step": 2 * nbytes}
         del hu, hup, hco
 

@@ -177,7 +177,10 @@ GIRIH_API int girih_run(girih_plan_t plan, void* u, void* u_prev, const void* co
 
 /* Convenience for callers holding HOST arrays (pinned or pageable): copies u, u_prev and coeffs
  * to device buffers the plan owns (allocated on first use, freed by girih_plan_destroy), runs
- * girih_run on `stream`, copies u and u_prev back, and synchronises the stream.               */
+ * girih_run on `stream`, copies u and u_prev back, and synchronises the stream.  For the
+ * first-order stencils u_prev_host is not read: its device copy is made from u on the device
+ * (the scratch buffer's halo must equal u's), which saves one host-to-device transfer.  T = 0
+ * copies nothing and leaves both host arrays as they are.                                     */
 GIRIH_API int girih_run_host(girih_plan_t plan, void* u_host, void* u_prev_host, const void* coeffs_host,
                    const girih_params* params, void* stream);
 

@@ -495,8 +495,12 @@ int girih_run_host(girih_plan_t plan, void* u_host, void* u_prev_host, const voi
     cudaGetLastError();
     return fail(GIRIH_ENOMEM, "device buffers for host run: %s", cudaGetErrorString(e));
   }
+  if (p->T == 0) return GIRIH_OK;  // nothing to advance (as girih_run)
   e = cudaMemcpyAsync(p->host_u, u_host, bytes, cudaMemcpyHostToDevice, st);
-  if (e == cudaSuccess) e = cudaMemcpyAsync(p->host_up, u_prev_host, bytes, cudaMemcpyHostToDevice, st);
+  // first-order stencils: u_prev is scratch whose halo equals u's, so it is made on the device
+  if (e == cudaSuccess)
+    e = second_order(p->stencil) ? cudaMemcpyAsync(p->host_up, u_prev_host, bytes, cudaMemcpyHostToDevice, st)
+                                 : cudaMemcpyAsync(p->host_up, p->host_u, bytes, cudaMemcpyDeviceToDevice, st);
   if (e == cudaSuccess && nc > 0) e = cudaMemcpyAsync(p->host_co, coeffs_host, bytes * nc, cudaMemcpyHostToDevice, st);
   if (e != cudaSuccess) return cuda_fail(e, "host to device copy");
   int rc = girih_run(plan, p->host_u, p->host_up, nc > 0 ? p->host_co : nullptr, params, stream);

@@ -168,6 +168,26 @@ def test_run_host_matches_device_run():
     assert np.array_equal(hu, gu) and np.array_equal(hup, gup)
 
 
+def test_run_host_first_order_reads_only_u():
+    """For a first-order stencil the host entry point builds u_prev on the device from u (its
+    halo must equal u's anyway): whatever the host u_prev holds inside, the result equals the
+    device run from a u_prev that is a copy of u.  T = 0 leaves both host arrays untouched."""
+    stencil, nx, ny, nz, T = 0, 30, 26, 22, 5
+    u, up, co, c = inputs.make_problem(stencil, nx, ny, nz, seed=6)
+    p = girih.plan(stencil, nx, ny, nz, dtype="f64", T=T)
+    hu, hup = u.copy(), up.copy()
+    hup[1:-1, 1:-1, 1:-1] = 123.0
+    girih.run_host(p, hu, hup, None, c=c)
+    gu, gup = gpu_sweep(stencil, "f64", u, u.copy(), co, c, T, nx, ny, nz, p.config)
+    assert np.array_equal(hu, gu) and np.array_equal(hup, gup)
+    p0 = girih.plan(stencil, nx, ny, nz, dtype="f64", T=0)
+    a, b = u.copy(), up.copy()
+    b[1:-1, 1:-1, 1:-1] = 7.0
+    b0 = b.copy()
+    girih.run_host(p0, a, b, None, c=c)
+    assert np.array_equal(a, u) and np.array_equal(b, b0)
+
+
 def test_launch_count():
     p = girih.plan(0, 64, 64, 64, dtype="f64", T=9)
     assert p.launch_count(girih.config(girih.NAIVE)) == 10  # 9 steps + one exchange for odd T
