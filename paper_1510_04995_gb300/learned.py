@@ -260,6 +260,39 @@ def experiment(out_dir: str, stencils=(0, 1, 2, 3), dtypes=("f64", "f32"), grids
     return report
 
 
+def unseen(out_dir: str, params_path: str, stencils=(4, 5, 6), dtypes=("f64", "f32"), grids=None, T: int = 16,
+           tol: float = 0.05, max_steps: int = 32, k: int = 5, log=print):
+    """The trained network on stencils it never saw (the 25-point stencil with the factor grid,
+    the 27-point box stencil, red-black Gauss-Seidel): exhaustive timings as the judge, the
+    network's top k offline and live, regret and measurement-time fraction."""
+    import json
+    grids = grids or [GRIDS[i] for i in HELD_OUT]
+    os.makedirs(out_dir, exist_ok=True)
+    db = os.path.join(out_dir, "unseen_db.csv")
+    times = os.path.join(out_dir, "unseen_times.csv")
+    problems = [(s, d, *g) for s in stencils for d in dtypes for g in grids]
+    done = {problem_key(r) for r in load_db(db)} if os.path.exists(db) else set()
+    todo = [q for q in problems if (q[0], _dt(q[1]), q[2], q[3], q[4]) not in done]
+    collect(db, todo, T=T, tol=tol, max_steps=max_steps, times_path=times, log=log)
+    rows = load_db(db)
+    params = np.load(params_path)
+    res = evaluate(rows, predict(params, features(rows)), k)
+    live_res = []
+    for key in sorted({problem_key(r) for r in rows}):
+        s, d, nx, ny, nz = key
+        rs = [r for r in rows if problem_key(r) == key]
+        p = plan(s, nx, ny, nz, dtype=d, T=T)
+        row, nm, secs = tune(p, params, k=k, tol=tol, max_steps=max_steps)
+        live_res.append({"problem": key, "learned_glups": row.glups, "learned_config": row.cfg.as_dict(),
+                         "measured": nm, "seconds": secs, "exhaustive_best": max(r["glups"] for r in rs),
+                         "exhaustive_seconds": sum(r["tune_seconds"] for r in rs)})
+        p.close()
+    report = {"params": os.path.basename(params_path), "k": k, "offline": res, "live": live_res}
+    with open(os.path.join(out_dir, "report_unseen.json"), "w") as f:
+        json.dump(report, f, indent=1)
+    return report
+
+
 if __name__ == "__main__":
     import argparse
     import json
@@ -274,10 +307,17 @@ if __name__ == "__main__":
     ap.add_argument("--k", type=int, default=5)
     ap.add_argument("--epochs", type=int, default=3000)
     ap.add_argument("--no-live", action="store_true")
+    ap.add_argument("--unseen-from", default="", help="trained parameters (.npy): evaluate them on --stencils "
+                    "instead of training (stencils the network never saw)")
     a = ap.parse_args()
     from . import build as _b
     _b.build()
     gl = [GRIDS[int(i)] for i in a.grids.split(",")] if a.grids else None
+    if a.unseen_from:
+        rep = unseen(a.out_dir, a.unseen_from, tuple(int(s) for s in a.stencils.split(",")), tuple(a.dtypes.split(",")),
+                     gl, a.T, a.tol, a.max_steps, a.k)
+        print(json.dumps(rep, indent=1))
+        raise SystemExit(0)
     rep = experiment(a.out_dir, tuple(int(s) for s in a.stencils.split(",")), tuple(a.dtypes.split(",")), gl, a.T,
                      a.tol, a.max_steps, a.k, a.epochs, not a.no_live)
     print(json.dumps({k: rep[k] for k in ("train_problems", "train_rows", "train_seconds", "offline", "default",
