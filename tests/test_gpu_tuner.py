@@ -100,3 +100,22 @@ def test_trained_network_gains_over_default_configuration(stencil, dtype):
     row, nm, _ = learned.tune(p, params, k=5, tol=0.1, max_steps=16)
     assert nm == 5
     assert row.glups >= default.glups, (row.glups, default.glups, row.cfg, p.config)
+
+
+@pytest.mark.skipif(not os.path.exists(MODEL), reason="no trained network committed")
+@pytest.mark.parametrize("stencil,dtype", [(4, "f32"), (6, "f64")])
+def test_trained_network_on_an_unseen_stencil(stencil, dtype, tmp_path):
+    """The network never saw the factor-grid or red-black stencils: on a small grid its top 5,
+    measured, reach 90 % of the exhaustive best over the same search space (exhaustive search is
+    the judge of its regret)."""
+    from paper_1510_04995_gb300 import learned
+    p = girih.plan(stencil, 128, 96, 64, dtype=dtype, T=16)
+    cands = learned.space(p)
+    arr, n = girih.config_array(cands)
+    best = girih.TuneRow()
+    nm = ctypes.c_int32()
+    girih.check(girih.lib().girih_tune_exhaustive(p.handle, arr, n, 0.1, 16, None, ctypes.byref(best),
+                                                   ctypes.byref(nm)))
+    row, k, _ = learned.tune(p, np.load(MODEL), k=5, tol=0.1, max_steps=16)
+    assert k == min(5, len(cands))
+    assert row.glups >= 0.9 * best.glups, (row.glups, best.glups, row.cfg, best.cfg)
