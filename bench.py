@@ -63,7 +63,7 @@ MEASURED_BYTES_PER_LUP = {
     ("naive", 1, "f32"): (36.45, "profiles/naive_7pt_var_f32_480x384x256.md"),
     ("naive", 2, "f64"): (24.05, "profiles/naive_25pt_const_f64_384x384x192.md"),
     ("naive", 2, "f32"): (11.66, "profiles/naive_25pt_const_f32_384x384x256.md"),
-    ("naive", 3, "f64"): (132.12, "profiles/naive_25pt_var_f64_384x384x128.md"),
+    ("naive", 3, "f64"): (132.06, "profiles/naive_25pt_var_f64_384x384x128.md"),
     ("naive", 3, "f32"): (65.91, "profiles/naive_25pt_var_f32_384x384x192.md"),
     ("naive", 4, "f64"): (32.35, "profiles/naive_25pt_cgrid_f64_384x384x192.md"),
     ("naive", 4, "f32"): (16.12, "profiles/naive_25pt_cgrid_f32_384x384x256.md"),

@@ -178,6 +178,7 @@ int run_sweep(Plan* p, int64_t T, void* u, void* u_prev, const void* coeffs, con
     a.v16 = (p->bulk_layout &&
              ((reinterpret_cast<uintptr_t>(u) | reinterpret_cast<uintptr_t>(u_prev)) & 15) == 0) ? 1 : 0;
     a.zc = naive_z_chunk(p->nx, p->ny, p->nz, p->R, naive_tile_x(p->stencil, p->dtype, a.v16 != 0),
+                         naive_tile_y(p->stencil, p->dtype),
                          naive_resident_blocks(p->stencil, p->dtype, a.v16 != 0), p->sm_count);
     void* buf[2] = {u, u_prev};
     for (int64_t t = 0; t < T && e == cudaSuccess; ++t) {

@@ -32,8 +32,9 @@ cudaError_t launch_naive_step(int stencil, int dtype, const NaiveArgs& a, cudaSt
 // device's block slots in whole waves best.
 int naive_resident_blocks(int stencil, int dtype, bool v16);
 int naive_tile_x(int stencil, int dtype, bool v16);  // tile columns of the naive kernel
-int naive_z_chunk(int64_t nx, int64_t ny, int64_t nz, int R, int tile_x, int resident_per_sm, int sm_count);
-int naive_block_rows(int stencil, int dtype);  // threads per block = 32 * rows
+int naive_tile_y(int stencil, int dtype);             // tile rows (threads per block = 16 * rows)
+int naive_z_chunk(int64_t nx, int64_t ny, int64_t nz, int R, int tile_x, int tile_y, int resident_per_sm,
+                  int sm_count);
 
 // One row of diamonds of the multi-threaded wavefront-diamond sweep (Sect. 4.2.1).
 struct MwdArgs {

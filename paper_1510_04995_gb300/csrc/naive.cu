@@ -1,8 +1,8 @@
 // Naive sweep (arXiv 1510.04995, Sect. 2.1.1): one full pass over the grid per time step.
 //
 // On the GPU this is the "optimal spatial blocking" reference of Sect. 5 (diamond width 0):
-// every block owns a 32 x 16 tile of x-y columns over a chunk of z planes, each thread two
-// columns (rows ty and ty+8).  The tile's planes (with their R-wide halo) are staged into a
+// every block owns a (32*VX) x 2TY tile of x-y columns over a chunk of z planes, each thread two
+// rows (ty and ty+TY) of VX columns.  The tile's planes (with their R-wide halo) are staged into a
 // shared-memory ring by cp.async several planes ahead of use; each thread keeps its columns'
 // 2R+1 values along z in registers (rotated as the block walks up in z).  Every input is read
 // from HBM once per step (halo re-reads hit L2), every output written once: 2s bytes per LUP
@@ -244,9 +244,12 @@ __global__ void __launch_bounds__(32 * TY) naive_kernel(const NaiveArgs a) {
   }
 }
 
-constexpr int kTY = 8;
-
-int naive_block_rows(int, int) { return 2 * kTY; }
+// Thread rows per block (each thread owns two rows of the tile): 8, or 4 for the FP64 25-point
+// variable stencil, whose 26 coefficient registers per thread allow one 256-thread block per SM
+// only; two 128-thread blocks keep the same warps but desynchronise their barriers (measured:
+// 16.9 -> 18.4 GLUP/s at 384^3; the other stencils were as fast or faster with 8).
+template <int S, typename T>
+constexpr int naive_ty() { return (S == 3 && sizeof(T) == 8) ? 4 : 8; }
 
 // Planes staged ahead of use: 4 for the 7-point stencils; for the radius-4 ones, whose planes
 // are larger, 2 (25-point constant) or 3 (the stencils with coefficient grids, which also wait
@@ -270,7 +273,7 @@ static size_t naive_smem() {
   constexpr int R = Traits<S>::R, PD = naive_pd<S, T>(), A16 = 16 / (int)sizeof(T);
   constexpr int TX = 32 * naive_vx<S, T, V16>();
   constexpr int TXW = V16 ? (TX + 2 * R + A16 - 1) / A16 * A16 : TX + 2 * R;
-  constexpr int NP = R + PD + 2 + (Traits<S>::BOX ? 1 : 0), TP = TXW * (2 * kTY + 2 * R);
+  constexpr int NP = R + PD + 2 + (Traits<S>::BOX ? 1 : 0), TP = TXW * (2 * naive_ty<S, T>() + 2 * R);
   return sizeof(T) * (size_t)NP * TP;
 }
 
@@ -280,10 +283,10 @@ static int resident_blocks() {
   static int n = -1;
   if (n < 0) {
     const size_t sm = naive_smem<S, T, V16>();
-    auto k = naive_kernel<S, T, kTY, naive_pd<S, T>(), V16, naive_vx<S, T, V16>()>;
+    auto k = naive_kernel<S, T, naive_ty<S, T>(), naive_pd<S, T>(), V16, naive_vx<S, T, V16>()>;
     if (sm > 48 * 1024) cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     int b = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k, 32 * kTY, sm) != cudaSuccess || b < 1) {
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k, 32 * naive_ty<S, T>(), sm) != cudaSuccess || b < 1) {
       cudaGetLastError();
       b = 1;
     }
@@ -294,12 +297,13 @@ static int resident_blocks() {
 
 template <int S, typename T, bool V16>
 static cudaError_t launch_one(const NaiveArgs& a, cudaStream_t st) {
-  dim3 block(32, kTY);
+  constexpr int TY = naive_ty<S, T>();
+  dim3 block(32, TY);
   constexpr int TX = 32 * naive_vx<S, T, V16>();
-  dim3 grid((unsigned)((a.g.nx + TX - 1) / TX), (unsigned)((a.g.ny + 2 * kTY - 1) / (2 * kTY)),
+  dim3 grid((unsigned)((a.g.nx + TX - 1) / TX), (unsigned)((a.g.ny + 2 * TY - 1) / (2 * TY)),
             (unsigned)((a.g.nz + a.zc - 1) / a.zc));
   const size_t sm = naive_smem<S, T, V16>();
-  auto k = naive_kernel<S, T, kTY, naive_pd<S, T>(), V16, naive_vx<S, T, V16>()>;
+  auto k = naive_kernel<S, T, TY, naive_pd<S, T>(), V16, naive_vx<S, T, V16>()>;
   if (sm > 48 * 1024) {
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
@@ -311,6 +315,14 @@ static cudaError_t launch_one(const NaiveArgs& a, cudaStream_t st) {
 template <int S, typename T>
 static cudaError_t launch_v(const NaiveArgs& a, cudaStream_t st) {
   return a.v16 ? launch_one<S, T, true>(a, st) : launch_one<S, T, false>(a, st);
+}
+
+int naive_tile_y(int stencil, int dtype) {
+  const bool f64 = dtype == GIRIH_F64;
+  switch (stencil) {
+    case 3: return 2 * (f64 ? naive_ty<3, double>() : naive_ty<3, float>());
+    default: return 2 * naive_ty<0, float>();
+  }
 }
 
 int naive_tile_x(int stencil, int dtype, bool v16) {
@@ -353,8 +365,9 @@ int naive_resident_blocks(int stencil, int dtype, bool v16) {
 // blocks that is used) x (fraction of each block's staged planes that it updates, zc/(zc+2R)),
 // i.e. fills the device's resident block slots in whole waves without re-reading too many
 // z-halo planes (fewer chunks on ties).
-int naive_z_chunk(int64_t nx, int64_t ny, int64_t nz, int R, int tile_x, int resident_per_sm, int sm_count) {
-  const int64_t tiles = ((nx + tile_x - 1) / tile_x) * ((ny + 2 * kTY - 1) / (2 * kTY));
+int naive_z_chunk(int64_t nx, int64_t ny, int64_t nz, int R, int tile_x, int tile_y, int resident_per_sm,
+                  int sm_count) {
+  const int64_t tiles = ((nx + tile_x - 1) / tile_x) * ((ny + tile_y - 1) / tile_y);
   const int64_t slots = (int64_t)std::max(resident_per_sm, 1) * std::max(sm_count, 1);
   const int64_t cmin = std::max<int64_t>((nz + 63) / 64, 1), cmax = std::max<int64_t>((nz + 15) / 16, cmin);
   int64_t best_c = cmin;
