@@ -1,0 +1,84 @@
+"""Host-side pieces of the learned tuner (no GPU): database parsing, targets, the regret and
+cost evaluation, the feature slots of the stencils the network never saw, and the consistency
+of the committed experiment records with their timing databases."""
+import json
+import os
+
+import numpy as np
+import pytest
+
+import paper_1510_04995_gb300 as girih
+from paper_1510_04995_gb300 import learned
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    from paper_1510_04995_gb300 import build as gbuild
+    gbuild.build()
+
+
+MODEL_DIR = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "paper_1510_04995_gb300",
+                         "learned_model")
+
+
+def _rows():
+    base = dict(dtype=0, nx=64, ny=64, nz=64, nf=1, cluster=1, threads=256, variant=0, seconds=0.1, steps=8,
+                smem=0)
+    rows = []
+    for s, gl in ((0, [10.0, 20.0, 40.0]), (2, [5.0, 1.0, 2.0])):
+        for i, g in enumerate(gl):
+            rows.append(dict(base, stencil=s, algo=int(i > 0), dw=2 * i, glups=g, tune_seconds=1.0 + i))
+    return rows
+
+
+def test_targets_are_centred_per_problem():
+    y = learned.targets(_rows())
+    assert abs(y[:3].sum()) < 1e-6 and abs(y[3:].sum()) < 1e-6
+    assert y[2] > y[1] > y[0] and y[3] > y[5] > y[4]
+
+
+def test_evaluate_regret_and_cost():
+    rows = _rows()
+    scores = np.array([0.0, 1.0, 2.0, 0.0, 2.0, 1.0])      # problem 0: best ranked first; 1: worst first
+    res = {r["problem"][0]: r for r in learned.evaluate(rows, scores, k=1)}
+    assert res[0]["ratio"] == 1.0 and res[0]["cost_fraction"] == pytest.approx(3.0 / 6.0)
+    assert res[2]["ratio"] == pytest.approx(1.0 / 5.0) and res[2]["cost_fraction"] == pytest.approx(2.0 / 6.0)
+    res2 = {r["problem"][0]: r for r in learned.evaluate(rows, scores, k=3)}
+    assert all(r["ratio"] == 1.0 and r["cost_fraction"] == pytest.approx(1.0) for r in res2.values())
+
+
+def test_db_round_trip(tmp_path):
+    p = tmp_path / "db.csv"
+    rows = _rows()
+    with open(p, "w") as f:
+        f.write("# comment\n")
+        for r in rows:
+            f.write(",".join(str(r[k]) for k in learned.FIELDS) + "\n")
+    back = learned.load_db(str(p))
+    assert [learned.problem_key(r) for r in back] == [learned.problem_key(r) for r in rows]
+    assert [learned.row_config(r).as_dict() for r in back] == [learned.row_config(r).as_dict() for r in rows]
+
+
+@pytest.mark.parametrize("stencil,slot", [(0, 0), (2, 2), (4, 2), (5, 0), (6, 0)])
+def test_unseen_stencils_share_slots(stencil, slot):
+    rows = [dict(stencil=stencil, dtype=1, nx=128, ny=96, nz=64, algo=0, dw=0, nf=1, cluster=1, threads=256,
+                 variant=0)]
+    X = learned.features(rows)
+    assert X[0, :4].tolist() == [1.0 if i == slot else 0.0 for i in range(4)]
+
+
+@pytest.mark.parametrize("report,db", [("report.json", "tune_db.csv"), ("report_unseen.json", "unseen_db.csv")])
+def test_committed_reports_match_their_databases(report, db):
+    rp, dp = os.path.join(MODEL_DIR, report), os.path.join(MODEL_DIR, db)
+    if not (os.path.exists(rp) and os.path.exists(dp)):
+        pytest.skip("experiment records not committed")
+    rep = json.load(open(rp))
+    rows = learned.load_db(dp)
+    best = {}
+    for r in rows:
+        k = learned.problem_key(r)
+        best[k] = max(best.get(k, 0.0), r["glups"])
+    for e in rep["live"]:
+        assert e["exhaustive_best"] == pytest.approx(best[tuple(e["problem"])], rel=1e-6)
+        assert e["measured"] <= rep["k"]
+    for e in rep["offline"]:
+        assert 0 < e["ratio"] <= 1.0 and e["exhaustive_best"] == pytest.approx(best[tuple(e["problem"])], rel=1e-6)
