@@ -61,13 +61,16 @@ def row_span(rho, dw, ny):
     return lo, max(hi - lo + 1, 0)
 
 
-def simulate(R, second_order, nx, ny, nz, T, dw, nf, C, bulk=False, a16=4, vec=False):
+def simulate(R, second_order, nx, ny, nz, T, dw, nf, C, bulk=False, a16=4, vec=False, box=False):
     """vec: the 16-byte vector path (block r owns padded columns [r*XW, (r+1)*XW); its shared row
     starts HM = R rounded up to a16 columns before them; whole a16-column chunks are staged and
     written back; both rows of a pair are read even when only the first is updated).
     bulk (with vec): the bulk-copy schedule -- planes staged PD_BULK steps ahead, a ring slack of
-    SLACK*nf planes, write-back copies that may still read shared memory for two steps."""
+    SLACK*nf planes, write-back copies that may still read shared memory for two steps.
+    box (R = 1, vec): the 27-point box stencil also reads the diagonal neighbours -- every cell of
+    planes z-1..z+1, rows y-1..y+1, columns x-1..x+1 -- which must all hold level t."""
     assert vec or not bulk, "the bulk-copy schedule runs on the vector partition"
+    assert not box or (vec and R == 1), "the box stencil runs on the vector path, radius 1"
     if vec:
         XW = vec_slab_width(nx, R, C, a16)
         HM = -(-R // a16) * a16
@@ -270,6 +273,12 @@ def simulate(R, second_order, nx, ny, nz, T, dw, nf, C, bulk=False, a16=4, vec=F
                                         for d in range(-R, R + 1):
                                             if d:
                                                 rd((pin, sl, yy0 + r, xx + d), t)
+                                        if box:  # edges and corners, in the planes below and above too
+                                            for dz in (-1, 0, 1):
+                                                for dy in (-1, 0, 1):
+                                                    for dx in (-1, 0, 1):
+                                                        if dy and (dx or dz) or (dx and dz):
+                                                            rd((pin, (sl + dz) % NZ, yy0 + r + dy, xx + dx), t)
                                         if second_order:
                                             rd((pout, sl, yy0 + r, xx), t - 1)
                                         outs = [(rank, pout, sl, yy0 + r, xx)]

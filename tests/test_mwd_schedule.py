@@ -24,6 +24,14 @@ MODES = [(c, m) for c in CASES for m in ("element", "vec_f32", "bulk_f32")] + \
         [(c, m) for c in CASES[1::2] for m in ("vec_f64", "bulk_f64")]
 
 
+@pytest.mark.parametrize("case", [c for c in CASES if c[0] == 1])
+def test_schedule_model_box_stencil(case):
+    """The 27-point box stencil's diagonal reads (Sect. 7: the tiles already cover edge and corner
+    dependencies) find level t in every ring slot and halo column they touch."""
+    for a16 in (4, 2):
+        assert simulate(*case, vec=True, a16=a16, box=True)
+
+
 @pytest.mark.parametrize("case,mode", MODES)
 def test_schedule_model(case, mode):
     if mode == "element":
