@@ -86,7 +86,10 @@ typedef enum { GIRIH_ALGO_NAIVE = 0, GIRIH_ALGO_MWD = 1 } girih_algo;
  *              per sweep, clusters take diamonds in row-major order and start each once the
  *              two diamonds of the previous row it depends on have completed (bounded waits
  *              on per-diamond flags).  Needs the vector path's layout (16-byte rows, 16-byte
- *              aligned buffers).                                                           */
+ *              aligned buffers).  The plan owns the diamond list, the flags and the FIFO
+ *              counter (allocated on first use, freed by girih_plan_destroy), so sweeps of one
+ *              plan must not run concurrently on different streams.  A wait that runs out
+ *              (2 s) makes girih_status return GIRIH_ETIMEOUT.                             */
 typedef enum {
   GIRIH_FED = 0,
   GIRIH_RELAXED = 1,
