@@ -12,12 +12,12 @@
  *   GIRIH_25PT_CGRID Listing 3 as printed: second order in time, radius 4, constants c0..c4
  *                    and one per-point factor grid C multiplying the bracket (U = 2V - U +
  *                    C*(c0*V + sum_r c_r*pairs_r)); three domain-sized streams (Sect. 3.5).
- *   GIRIH_27PT_BOX   the box-shaped operator of Sect. 7: first order in time, radius 1, all 26
+ *   GIRIH_27PT_BOX   the box-shaped operator of Sect. 8.4: first order in time, radius 1, all 26
  *                    neighbours at Chebyshev distance 1, constants c0 (centre), c1 (the 6 face
  *                    neighbours), c2 (the 12 edge neighbours), c3 (the 8 corner neighbours).
  *                    Its blocked sweep runs on the 16-byte vector path only (rows of 16-byte
  *                    multiples, 16-byte aligned buffers); the naive sweep takes any layout.
- *   GIRIH_7PT_RBGS   red-black Gauss-Seidel on the 7-point constant operator (Sect. 7): time
+ *   GIRIH_7PT_RBGS   red-black Gauss-Seidel on the 7-point constant operator (Sect. 8.4): time
  *                    step t is a half-sweep updating the points whose interior coordinates have
  *                    x + y + z + t even (c0*V + c1*(neighbour pairs)) and keeping the others;
  *                    T = 2 x the red-black iterations.  Computed in the two-buffer form (the
@@ -89,14 +89,23 @@ typedef enum { GIRIH_ALGO_NAIVE = 0, GIRIH_ALGO_MWD = 1 } girih_algo;
  *              aligned buffers).  The plan owns the diamond list, the flags and the FIFO
  *              counter (allocated on first use, freed by girih_plan_destroy), so sweeps of one
  *              plan must not run concurrently on different streams.  A wait that runs out
- *              (2 s) makes girih_status return GIRIH_ETIMEOUT.                             */
+ *              (2 s) makes girih_status return GIRIH_ETIMEOUT.
+ *   RELAXED_PERSISTENT -- the persistent FIFO schedule of FED_PERSISTENT with the relaxed
+ *              synchronisation of Sect. 4.2.1 instead of a cluster barrier per wavefront step:
+ *              a block waits, per step, for its own results (block barrier) and for exactly the
+ *              x-halo bytes its two neighbours computed in that step, which they store into its
+ *              shared memory asynchronously (st.async, counted on an mbarrier).  Radius-1
+ *              first-order stencils (7PT_CONST, 7PT_VAR, 7PT_RBGS) on the vector path's
+ *              layout (16-byte rows, 16-byte aligned buffers and coefficient grids); EINVAL
+ *              otherwise.  Buffers and bounded waits as FED_PERSISTENT.                    */
 typedef enum {
   GIRIH_FED = 0,
   GIRIH_RELAXED = 1,
   GIRIH_FED_BULK = 2,
   GIRIH_FED_ELEM = 3,
   GIRIH_RELAXED_ELEM = 4,
-  GIRIH_FED_PERSISTENT = 5
+  GIRIH_FED_PERSISTENT = 5,
+  GIRIH_RELAXED_PERSISTENT = 6
 } girih_variant;
 
 #define GIRIH_OK 0
@@ -200,6 +209,15 @@ GIRIH_API int girih_status(girih_plan_t plan, void* stream);
  * Returns GIRIH_EINVAL for a NULL plan or a limit outside the range (nothing enqueued), or
  * GIRIH_ECUDA if the launch fails.                                                          */
 GIRIH_API int girih_check_bounded_wait(girih_plan_t plan, int64_t limit_ns, void* stream);
+
+/* Measured fused multiply-add throughput of the current GPU in `dtype` (no counterpart in the
+ * paper: it is the denominator of the arithmetic roofline of the FP64 sweeps, which this GPU's
+ * FP64 pipe bounds before HBM does).  Runs eight independent FMA chains per thread on every SM
+ * (a short calibration launch, then one of about 0.1 s) on `stream`, synchronises it, and writes
+ * the rate in FMA instructions per second (thread level; 2 flops each) to *fma_per_s and the
+ * timed launch's duration to *seconds (may be NULL).  Allocates and frees a small device
+ * buffer.  EINVAL for a NULL fma_per_s or an unknown dtype; ECUDA if a launch fails.          */
+GIRIH_API int girih_measure_fma_rate(int32_t dtype, double* fma_per_s, double* seconds, void* stream);
 
 /* Elements of one padded grid for the plan ((nz+2R)*(ny+2R)*ldx) and the halo width R. */
 GIRIH_API int girih_plan_layout(girih_plan_t plan, int64_t* elems_per_grid, int32_t* radius, int64_t* ldx);

@@ -5,8 +5,8 @@ as a table of terms.  Each term is (coefficient source, list of neighbour offset
 a point's update is the running sum, in table order, of coefficient * (sum of the neighbours in
 list order).  The 25-point stencil with the factor grid (Listing 3 as printed) uses the 25-point
 constant table and multiplies the sum by the point's factor before the leapfrog terms.  The
-27-point box operator (Sect. 7) groups its 26 neighbours by class (face, edge, corner).  Red-black
-Gauss-Seidel is evaluated as Sect. 7 states it, in place on one array (``rbgs_in_place``), which
+27-point box operator (Sect. 8.4) groups its 26 neighbours by class (face, edge, corner).  Red-black
+Gauss-Seidel is evaluated as Sect. 8.4 states it, in place on one array (``rbgs_in_place``), which
 checks the oracle's two-buffer half-step form.  Every level is recomputed point by point over the whole interior in pure Python,
 so it is only meant for tiny grids (8^3, T <= 3), where it must agree bit for bit with the C loop
 nests (same terms, same order, one rounding per operation).
@@ -52,7 +52,7 @@ def term_table(stencil: int):
 
 
 def rbgs_in_place(u, c, T: int):
-    """Red-black Gauss-Seidel written the way Sect. 7 states it: ONE array, updated in place, half
+    """Red-black Gauss-Seidel written the way Sect. 8.4 states it: ONE array, updated in place, half
     sweep t visiting the points with (x + y + z + t) even (interior coordinates) in lexicographic
     order and replacing each by c0*u + c1*(x pair) + c1*(y pair) + c1*(z pair) of the current
     array.  Returns (array after T half-sweeps, array after T-1)."""

@@ -21,7 +21,7 @@ HEADER = os.path.join(os.path.dirname(HERE), "include", "girih.h")
 S7C, S7V, S25C, S25V, S25CG, S27B, S7RB = 0, 1, 2, 3, 4, 5, 6
 F64, F32 = 0, 1
 NAIVE, MWD = 0, 1
-FED, RELAXED, FED_BULK, FED_ELEM, RELAXED_ELEM, FED_PERSISTENT = 0, 1, 2, 3, 4, 5
+FED, RELAXED, FED_BULK, FED_ELEM, RELAXED_ELEM, FED_PERSISTENT, RELAXED_PERSISTENT = 0, 1, 2, 3, 4, 5, 6
 RADIUS = {0: 1, 1: 1, 2: 4, 3: 4, 4: 4, 5: 1, 6: 1}
 NCOEF = {0: 0, 1: 7, 2: 0, 3: 13, 4: 1, 5: 0, 6: 0}
 STATUS = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "EKERNEL", 5: "ETIMEOUT", 6: "ENOTIMPL"}
@@ -85,6 +85,7 @@ _SIGS = {
     "girih_model_cache_block": (_F64, [_F64, _I32, _I32, _I32, _I32]),
     "girih_model_code_balance": (_F64, [_I32, _I32, _I32, _I32]),
     "girih_check_bounded_wait": (ctypes.c_int, [_VP, _I64, _VP]),
+    "girih_measure_fma_rate": (ctypes.c_int, [_I32, ctypes.POINTER(_F64), ctypes.POINTER(_F64), _VP]),
     "girih_tune_candidates": (ctypes.c_int, [_VP, ctypes.POINTER(Config), _I32, ctypes.POINTER(_I32)]),
     "girih_tune_measure": (ctypes.c_int, [_VP, ctypes.POINTER(Config), _F64, _I64, ctypes.POINTER(TuneRow)]),
     "girih_tune_exhaustive": (ctypes.c_int, [_VP, ctypes.POINTER(Config), _I32, _F64, _I64, ctypes.c_char_p,
@@ -251,6 +252,13 @@ def run_host(p: Plan, u, u_prev, coeffs=None, c=None, cfg: Config | None = None,
     prm = _params(c if c is not None else _default_c(p.stencil), cfg)
     check(lib().girih_run_host(p.handle, ptr(u), ptr(u_prev), ptr(coeffs), ctypes.byref(prm),
                                _stream_handle(stream)))
+
+
+def measure_fma_rate(dtype="f64", stream=None):
+    """(FMA instructions per second, seconds of the timed launch) of the current GPU in dtype."""
+    rate, secs = _F64(), _F64()
+    check(lib().girih_measure_fma_rate(_DT[dtype], ctypes.byref(rate), ctypes.byref(secs), _stream_handle(stream)))
+    return rate.value, secs.value
 
 
 def model_cache_block(n_xb, dw, nf, r, nd) -> float:

@@ -57,7 +57,7 @@ void mwd_row_span(int64_t rho, int dw, int64_t ny, int64_t* a_min, int64_t* ndia
 // synchronisation).  Element path: nx split evenly, rounded up to 16 elements.  Vector and
 // bulk-copy paths: the slabs partition the padded columns [R, nx + R) at 16-byte boundaries
 // (block r owns padded [r*XW, (r+1)*XW)), so nx + R columns are split, rounded up to 16 bytes.
-static int slab_width(const Plan* p, int C, int mv) {
+int slab_width(const Plan* p, int C, int mv) {
   if (mv_shifted(mv)) {
     const int a16 = 16 / p->elem;
     const int64_t w = (p->nx + p->R + C - 1) / C;
@@ -74,21 +74,35 @@ static int mwd_path(const Plan* p, const girih_config* c, bool ptrs16) {
   if (c->variant == GIRIH_FED_BULK) return MV_BULK;
   if (c->variant == GIRIH_FED_ELEM || c->variant == GIRIH_RELAXED_ELEM) return MV_ELEM;
   const int64_t plane = (p->ny + 2 * p->R) * p->ldx;
-  return (p->bulk_layout && ptrs16 && plane < (1LL << 30)) ? MV_VEC : MV_ELEM;
+  const bool vec = p->bulk_layout && ptrs16 && plane < (1LL << 30);
+  if (c->variant == GIRIH_RELAXED_PERSISTENT) return vec ? MV_ASYNC : MV_ELEM;
+  return vec ? MV_VEC : MV_ELEM;
 }
 
+static bool persistent_variant(int v) { return v == GIRIH_FED_PERSISTENT || v == GIRIH_RELAXED_PERSISTENT; }
+
 int check_config(const Plan* p, const girih_config* c, int64_t* smem_out, int* xw_out, int* g_out, int* mv_out,
-                 bool ptrs16) {
+                 bool ptrs16, int* lead_out) {
   if (!c) return fail(GIRIH_EINVAL, "config is NULL");
   if (c->algo == GIRIH_ALGO_NAIVE) {
     if (smem_out) *smem_out = 0;
     return GIRIH_OK;
   }
   if (c->algo != GIRIH_ALGO_MWD) return fail(GIRIH_EINVAL, "unknown algo %d", c->algo);
-  if (c->variant < GIRIH_FED || c->variant > GIRIH_FED_PERSISTENT)
+  if (c->variant < GIRIH_FED || c->variant > GIRIH_RELAXED_PERSISTENT)
     return fail(GIRIH_EINVAL, "unknown variant %d", c->variant);
   if (c->variant == GIRIH_FED_PERSISTENT && mwd_path(p, c, ptrs16) != MV_VEC)
     return fail(GIRIH_EINVAL, "FED_PERSISTENT needs rows of 16-byte multiples and 16-byte aligned buffers");
+  if (c->variant == GIRIH_RELAXED_PERSISTENT) {
+    if (!async_stencil(p->stencil))
+      return fail(GIRIH_EINVAL, "RELAXED_PERSISTENT is built for the radius-1 first-order stencils (7-point "
+                  "constant, 7-point variable, red-black Gauss-Seidel)");
+    if (mwd_path(p, c, ptrs16) != MV_ASYNC)
+      return fail(GIRIH_EINVAL, "RELAXED_PERSISTENT needs rows of 16-byte multiples and 16-byte aligned buffers");
+    if (c->nf != 1) return fail(GIRIH_EINVAL, "RELAXED_PERSISTENT advances one plane per level and step (nf = 1)");
+    if (c->threads <= kAsyncMovers)
+      return fail(GIRIH_EINVAL, "RELAXED_PERSISTENT needs more than %d threads (two warps move data)", kAsyncMovers);
+  }
   if (vec_only(p->stencil) && mwd_path(p, c, ptrs16) == MV_ELEM)
     return fail(GIRIH_EINVAL, "the blocked sweep of the box and red-black stencils needs the vector path: rows of "
                 "16-byte multiples, 16-byte aligned buffers and a variant other than FED_ELEM / RELAXED_ELEM");
@@ -109,6 +123,12 @@ int check_config(const Plan* p, const girih_config* c, int64_t* smem_out, int* x
   const int XW = slab_width(p, c->cluster, mv);
   const int cthreads = c->threads;
   const int G = mwd_pairs_per_thread(p->stencil, p->dtype, c->dw, XW, c->threads, mv);
+  if (G == 0 && mv == MV_ASYNC)
+    return fail(GIRIH_EINVAL, "dw=%d with a %d-wide slab has %d row pairs x %d vectors: more tasks than the %d "
+                "computing threads of a %d-thread block hold (blocks of at most %d, %d, %d threads for 1, 2, 4 tasks "
+                "per thread)", c->dw, XW, mwd_max_pairs(R, c->dw), XW / mwd_vx(p->stencil, p->dtype, mv),
+                c->threads - kAsyncMovers, c->threads, async_max_threads(1), async_max_threads(2),
+                async_max_threads(4));
   if (G == 0)
     return fail(GIRIH_EINVAL, "dw=%d with a %d-wide slab has %d row pairs x %d column groups: no groups-per-thread "
                 "count fits %d threads within the kernel's launch bound (%d threads for one group per thread)",
@@ -119,7 +139,9 @@ int check_config(const Plan* p, const girih_config* c, int64_t* smem_out, int* x
     return fail(GIRIH_EINVAL, "25-point FP64 tiles allow at most 2 row pairs per thread (registers)");
   if (p->ny > (1 << 28) || p->nx > (1 << 28) || p->nz > (1 << 28))
     return fail(GIRIH_EINVAL, "grid too large for the blocked kernel");
-  const MwdShape sh = mwd_shape(p->stencil, p->dtype, c->dw, c->nf, XW, mv);
+  const int lead = mv == MV_ASYNC ? mwd_async_lead(p->stencil, p->dtype, c->dw, c->nf, XW, c->threads, G, p->smem_optin)
+                                  : kAsyncLeadMin;
+  const MwdShape sh = mwd_shape(p->stencil, p->dtype, c->dw, c->nf, XW, mv, lead);
   if (sh.smem_bytes > p->smem_optin)
     return fail(GIRIH_EINVAL, "config needs %lld bytes of shared memory per block (device limit %lld)",
                 (long long)sh.smem_bytes, (long long)p->smem_optin);
@@ -135,6 +157,7 @@ int check_config(const Plan* p, const girih_config* c, int64_t* smem_out, int* x
   if (xw_out) *xw_out = XW;
   if (g_out) *g_out = G;
   if (mv_out) *mv_out = mv;
+  if (lead_out) *lead_out = lead;
   return GIRIH_OK;
 }
 
@@ -189,12 +212,12 @@ int run_sweep(Plan* p, int64_t T, void* u, void* u_prev, const void* coeffs, con
     }
   } else {
     int64_t smem = 0;
-    int XW = 0, G = 0, mv = 0;
+    int XW = 0, G = 0, mv = 0, lead = 0;
     const bool ptrs16 = ((reinterpret_cast<uintptr_t>(u) | reinterpret_cast<uintptr_t>(u_prev)) & 15) == 0;
-    const int rc = check_config(p, &cfg, &smem, &XW, &G, &mv, ptrs16);
+    const int rc = check_config(p, &cfg, &smem, &XW, &G, &mv, ptrs16, &lead);
     if (rc != GIRIH_OK) return rc;
     e = mwd_prepare(p->stencil, p->dtype, cfg.cluster, cfg.threads, G, mv, smem, nullptr);
-    const MwdShape sh = mwd_shape(p->stencil, p->dtype, cfg.dw, cfg.nf, XW, mv);
+    const MwdShape sh = mwd_shape(p->stencil, p->dtype, cfg.dw, cfg.nf, XW, mv, lead);
     MwdArgs a{};
     a.g = g;
     a.buf0 = u;
@@ -215,13 +238,14 @@ int run_sweep(Plan* p, int64_t T, void* u, void* u_prev, const void* coeffs, con
     a.YW = sh.YW;
     a.XT = sh.XT;
     a.err = p->err;
+    a.lead = lead;
     a.relaxed = (cfg.variant == GIRIH_RELAXED || cfg.variant == GIRIH_RELAXED_ELEM) ? 1 : 0;
     const int64_t rows = mwd_rows(T, cfg.dw, p->R);
-    if (cfg.variant == GIRIH_FED_PERSISTENT) {
+    if (persistent_variant(cfg.variant)) {
       const int rc2 = launch_persistent(p, a, rows, cfg, G, mv, sh.smem_bytes, st, &e);
       if (rc2 != GIRIH_OK) return rc2;
     }
-    for (int64_t rho = 0; rho < rows && e == cudaSuccess && cfg.variant != GIRIH_FED_PERSISTENT; ++rho) {
+    for (int64_t rho = 0; rho < rows && e == cudaSuccess && !persistent_variant(cfg.variant); ++rho) {
       int64_t a_min = 0, nd = 0;
       mwd_row_span(rho, cfg.dw, p->ny, &a_min, &nd);
       if (nd == 0) continue;
@@ -273,7 +297,9 @@ static int launch_persistent(Plan* p, MwdArgs a, int64_t rows, const girih_confi
     p->flags_cap = 0;
     e = cudaMalloc(&p->flags, n_items * sizeof(int));
     if (e != cudaSuccess) return fail(GIRIH_ENOMEM, "flag buffer: %s", cudaGetErrorString(e));
-    e = cudaMemset(p->flags, 0, n_items * sizeof(int));
+    // cleared on the sweep's own stream, so the clear is ordered before the kernel on any stream
+    // (a recycled allocation may still hold an epoch of an earlier plan)
+    e = cudaMemsetAsync(p->flags, 0, n_items * sizeof(int), st);
     if (e != cudaSuccess) return cuda_fail(e, "flag reset");
     p->flags_cap = n_items;
     p->epoch = 0;
@@ -348,6 +374,9 @@ int validate_run(Plan* p, void* u, void* u_prev, const void* coeffs, const girih
     if ((*cfg)->variant == GIRIH_FED_BULK &&
         ((reinterpret_cast<uintptr_t>(u) | reinterpret_cast<uintptr_t>(u_prev)) & 15) != 0)
       return fail(GIRIH_EINVAL, "FED_BULK needs 16-byte aligned buffers");
+    if ((*cfg)->variant == GIRIH_RELAXED_PERSISTENT && nc > 0 && (reinterpret_cast<uintptr_t>(coeffs) & 15) != 0)
+      return fail(GIRIH_EINVAL, "RELAXED_PERSISTENT reads coefficient grids in 16-byte vectors: coeffs must be "
+                  "16-byte aligned");
   } else if ((*cfg)->algo != GIRIH_ALGO_NAIVE) {
     return fail(GIRIH_EINVAL, "unknown algo %d", (*cfg)->algo);
   }
@@ -397,7 +426,9 @@ int girih_plan(girih_plan_t* out, int32_t stencil, int64_t nx, int64_t ny, int64
   p->smem_optin = optin;
   p->bulk_layout = (ldx * p->elem) % 16 == 0;
   e = cudaMalloc(&p->err, sizeof(int));
-  if (e == cudaSuccess) e = cudaMemset(p->err, 0, sizeof(int));
+  // cleared and waited for here, so the word is zero before any stream of the caller uses it
+  if (e == cudaSuccess) e = cudaMemsetAsync(p->err, 0, sizeof(int), nullptr);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(nullptr);
   if (e != cudaSuccess) {
     delete p;
     cudaGetLastError();
@@ -450,7 +481,7 @@ int girih_plan_launch_count(girih_plan_t plan, const girih_config* cfg, int64_t*
   const girih_config& c = cfg ? *cfg : plan->cfg;
   const int64_t T = plan->T;
   int64_t n = (c.algo == GIRIH_ALGO_NAIVE) ? T : mwd_rows(T, c.dw, plan->R);
-  if (c.algo != GIRIH_ALGO_NAIVE && c.variant == GIRIH_FED_PERSISTENT && T > 0) n = 1;
+  if (c.algo != GIRIH_ALGO_NAIVE && persistent_variant(c.variant) && T > 0) n = 1;
   if (T % 2 == 1) ++n;
   *launches = n;
   return GIRIH_OK;
@@ -471,8 +502,11 @@ int girih_status(girih_plan_t plan, void* stream) {
   cudaError_t e = cudaStreamSynchronize(static_cast<cudaStream_t>(stream));
   if (e != cudaSuccess) return cuda_fail(e, "stream synchronize");
   int v = 0;
-  e = cudaMemcpy(&v, plan->err, sizeof(int), cudaMemcpyDeviceToHost);
-  if (e == cudaSuccess && v != 0) e = cudaMemset(plan->err, 0, sizeof(int));
+  e = cudaMemcpyAsync(&v, plan->err, sizeof(int), cudaMemcpyDeviceToHost, static_cast<cudaStream_t>(stream));
+  if (e == cudaSuccess) e = cudaStreamSynchronize(static_cast<cudaStream_t>(stream));
+  // cleared on the caller's stream: ordered before the plan's next sweep on that stream
+  if (e == cudaSuccess && v != 0) e = cudaMemsetAsync(plan->err, 0, sizeof(int), static_cast<cudaStream_t>(stream));
+  if (e == cudaSuccess && v != 0) e = cudaStreamSynchronize(static_cast<cudaStream_t>(stream));
   if (e != cudaSuccess) return cuda_fail(e, "reading the error word");
   if (v & GIRIH_ETIMEOUT) return fail(GIRIH_ETIMEOUT, "a bounded device wait ran out (a staged plane never arrived)");
   if (v) return fail(GIRIH_EKERNEL, "kernel error word %d", v);

@@ -59,6 +59,7 @@ struct MwdArgs {
   const int* rows;
   int* flags;
   int* fifo;
+  int32_t lead;  // RELAXED_PERSISTENT: steps between a plane's staging and its first use (3..8)
 };
 
 struct MwdShape {
@@ -69,9 +70,27 @@ struct MwdShape {
 // shifted slab partition (rows of 16-byte multiples, 16-byte aligned buffers) moved by cp.async
 // and vector stores; or the same partition with whole rows moved by the bulk-copy (TMA) engine
 // (FED_BULK).
-enum { MV_ELEM = 0, MV_VEC = 1, MV_BULK = 2 };
+// MV_ASYNC: the vector path's partition and data movement with neighbour-only synchronisation
+// and the persistent schedule (RELAXED_PERSISTENT, mwd_async.cuh; radius-1 first-order stencils).
+enum { MV_ELEM = 0, MV_VEC = 1, MV_BULK = 2, MV_ASYNC = 3 };
+// stencils the RELAXED_PERSISTENT kernel is built for
+inline bool async_stencil(int stencil) {
+  return stencil == GIRIH_7PT_CONST || stencil == GIRIH_7PT_VAR || stencil == GIRIH_7PT_RBGS;
+}
+// Staging lead (steps) of the RELAXED_PERSISTENT kernel: the host takes the deepest lead in
+// [kAsyncLeadMin, kAsyncLeadMax] whose ring still fits as many blocks per SM as the shallowest.
+#ifndef GIRIH_ASYNC_LEAD_MAX
+#define GIRIH_ASYNC_LEAD_MAX 8
+#endif
+constexpr int kAsyncLeadMin = 3;
+constexpr int kAsyncMovers = 64;  // threads of the RELAXED_PERSISTENT block that move data
+constexpr int kAsyncLeadMax = GIRIH_ASYNC_LEAD_MAX;
+// Largest block of the RELAXED_PERSISTENT kernel for G tasks per thread (its launch bound).
+inline int async_max_threads(int G) { return G == 1 ? 640 : (G == 2 ? 512 : 256); }
 inline bool mv_shifted(int mv) { return mv != MV_ELEM; }
-MwdShape mwd_shape(int stencil, int dtype, int dw, int nf, int XW, int mv);
+MwdShape mwd_shape(int stencil, int dtype, int dw, int nf, int XW, int mv, int lead = kAsyncLeadMin);
+// RELAXED_PERSISTENT: the staging lead for a configuration (see kAsyncLeadMax) and its shape.
+int mwd_async_lead(int stencil, int dtype, int dw, int nf, int XW, int threads, int G, int64_t smem_optin);
 // Launch one diamond row: ndiam tiles, each a cluster of a.C blocks of `threads` threads.
 // G = groups per thread (1, 2, 4 or 8), from mwd_pairs_per_thread; mv = data path.
 cudaError_t launch_mwd_row(int stencil, int dtype, const MwdArgs& a, int ndiam, int threads, int G, int mv,

@@ -1,5 +1,7 @@
 // Host side of the wavefront-diamond sweep: tile shapes, kernel selection, cluster launches.
 // The kernel itself is in mwd_kernel.cuh (instantiated in mwd_r1.cu and mwd_r4.cu).
+#include <algorithm>
+
 #include "internal.h"
 
 namespace girih {
@@ -13,7 +15,10 @@ void* mwd_vec_kernel_cg(int dtype, int G, bool tma);
 void* mwd_vec_kernel_box(int dtype, int G, bool tma);
 void* mwd_vec_kernel_rb(int dtype, int G, bool tma);
 
+void* mwd_async_kernel_ptr(int stencil, int dtype, int G);
+
 static void* pick(int stencil, int dtype, int G, int mv) {
+  if (mv == MV_ASYNC) return mwd_async_kernel_ptr(stencil, dtype, G);
   if (mv_shifted(mv)) {
     const bool tma = mv == MV_BULK;
     if (stencil == GIRIH_25PT_CGRID) return mwd_vec_kernel_cg(dtype, G, tma);
@@ -25,13 +30,26 @@ static void* pick(int stencil, int dtype, int G, int mv) {
   return stencil < 2 ? mwd_kernel_r1(stencil, dtype, G) : mwd_kernel_r4(stencil, dtype, G);
 }
 
-MwdShape mwd_shape(int stencil, int dtype, int dw, int nf, int XW, int mv) {
+MwdShape mwd_shape(int stencil, int dtype, int dw, int nf, int XW, int mv, int lead) {
   const int R = radius_of(stencil);
   const int H = dw / R;
   const int K = R + nf;
   const int elem = dtype == GIRIH_F64 ? 8 : 4;
   const int a16 = 16 / elem;
   MwdShape s;
+  if (mv == MV_ASYNC) {
+    // ring (one plane per level and step): a slot is restaged, L steps ahead and while the
+    // computing warps run the current step, once its plane is below every level's read window and
+    // has been written back in an earlier step (mwd_async.cuh); halo mbarriers (2), level tables
+    // (3H+1), row masks (YW), item slot (1)
+    const int L = lead;
+    s.NZ = L + 2 * R + 1 + (H - 2) * K;
+    s.YW = dw + 2 * R;
+    s.XT = XW + 2 * ((R + a16 - 1) / a16 * a16);
+    const int64_t ring = 2LL * s.NZ * s.YW * s.XT * elem;
+    s.smem_bytes = (ring + 15) / 16 * 16 + 16 + (3LL * H + 1 + s.YW + 1) * 4;
+    return s;
+  }
   const bool bulk = mv == MV_BULK;
   const int pd = bulk ? MWD_PREFETCH_BULK : MWD_PREFETCH;
   s.NZ = (pd + 1) * nf + R + (R > nf ? R : nf) + (H - 2) * K + (bulk ? MWD_BULK_SLACK : MWD_PLAIN_SLACK) * nf;
@@ -53,6 +71,29 @@ MwdShape mwd_shape(int stencil, int dtype, int dw, int nf, int XW, int mv) {
   return s;
 }
 
+int mwd_async_lead(int stencil, int dtype, int dw, int nf, int XW, int threads, int G, int64_t smem_optin) {
+  const void* k = mwd_async_kernel_ptr(stencil, dtype, G);
+  auto per_sm = [&](int L) {
+    const MwdShape sh = mwd_shape(stencil, dtype, dw, nf, XW, MV_ASYNC, L);
+    if (sh.smem_bytes > smem_optin) return 0;
+    if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh.smem_bytes) != cudaSuccess) {
+      cudaGetLastError();
+      return 0;
+    }
+    int n = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k, threads, (size_t)sh.smem_bytes) != cudaSuccess) {
+      cudaGetLastError();
+      return 0;
+    }
+    return n;
+  };
+  const int base = per_sm(kAsyncLeadMin);
+  if (base < 1) return kAsyncLeadMin;
+  for (int L = kAsyncLeadMax; L > kAsyncLeadMin; --L)
+    if (per_sm(L) >= base) return L;
+  return kAsyncLeadMin;
+}
+
 // Row pairs of the widest (unclipped) diamond: levels k = 1..H-1 have 2R*min(k, H-k) rows.
 int mwd_max_pairs(int R, int dw) {
   const int H = dw / R;
@@ -67,6 +108,11 @@ int mwd_pairs_per_thread(int stencil, int dtype, int dw, int XW, int threads, in
   const int R = radius_of(stencil);
   const int vx = mwd_vx(stencil, dtype, mv), lbf = mwd_lbf(stencil, dtype, mv);
   const int64_t ng = (int64_t)mwd_max_pairs(R, dw) * (XW / vx);
+  if (mv == MV_ASYNC) {  // the block's last two warps move data; the others compute
+    for (int G : {1, 2, 4})
+      if (threads <= async_max_threads(G) && ng <= (int64_t)G * (threads - kAsyncMovers)) return G;
+    return 0;
+  }
   const int ct = threads;
   for (int G : {1, 2, 4, 8}) {
     if (G == 8 && R == 4) break;  // radius-4 kernels are built for at most 4 groups per thread

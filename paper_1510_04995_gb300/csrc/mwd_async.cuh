@@ -1,0 +1,568 @@
+// Wavefront-diamond sweep with neighbour-only synchronisation (variant RELAXED_PERSISTENT): the
+// tiling, wavefront and persistent FIFO schedule of the FED_PERSISTENT kernel (mwd_vec.cuh,
+// Sects. 4.2.1 and 4.2.3), with the per-step synchronisation reduced to what the data flow needs.
+//
+// A wavefront step of a tile needs, besides the block's own results of the previous step (a
+// block-local barrier), only the x-halo columns its two neighbours in the cluster computed in
+// that step.  Those arrive as asynchronous remote stores (st.async) that count their bytes on an
+// mbarrier of the receiving block, which waits for exactly that many bytes: the relaxed
+// synchronisation of Sect. 4.2.1 (a thread group member waits for its neighbour, not for the
+// whole group), here along x where the halo exchange goes both ways.  No cluster-wide barrier and
+// no release fence is taken per step, so nothing waits for the write-back stores or the staging
+// copies in flight to reach memory; a cluster barrier (with release) is taken once per tile.
+//
+// Step w of a block (every thread):
+//   1. update its tasks (level s, row pair, one 16-byte vector; planes w*nf - s*K ...) from the
+//      shared ring;
+//   2. wait for its own staging copies of the planes step w+1 reads; block barrier (A);
+//   3. push the results of its edge tasks to the neighbours (st.async, the neighbour's halo
+//      mbarrier of step w); arm this block's halo mbarrier for step w+1;
+//   4. write back (16-byte loads and stores) the planes the top level finished in step w;
+//   5. stage (cp.async) the planes first read at step w + L into the ring;
+//   6. wait (bounded) until the neighbours' halo bytes of step w have arrived.
+// A block can therefore run at most one step ahead of a neighbour; pushes are issued after the
+// pusher's own reads of that step are done (barrier A), so a push never overwrites a value its
+// receiver still reads, and a plane's staging copy completes (step 2 of the step before it is
+// first read) before any neighbour can push into it.
+//
+// Staging lead L (A.lead, 3..8 steps): the host takes the deepest lead whose ring keeps as many
+// blocks per SM as the shallowest; at a few hundred nanoseconds per step a plane needs several
+// steps to arrive from HBM.  Ring depth: a slot is restaged (step 5) once its previous plane is
+// below every level's read window and its write-back (step 4 of an earlier step) is done:
+//     NZ = max(L nf + 2R, (L + 1) nf + R) + smax K,   K = R + nf, smax = H - 2.
+//
+// Radius-1 first-order stencils (7-point constant, 7-point variable, red-black Gauss-Seidel) on
+// rows of 16-byte multiples with 16-byte aligned buffers.  Every point goes through point_update
+// (stencil.cuh), so the result equals the naive sweep bit for bit.
+#pragma once
+#include <type_traits>
+
+#include "mwd_kernel.cuh"
+
+namespace girih {
+
+
+// Wait until at most n (0..7) of this thread's committed cp.async groups are still pending.
+__device__ __forceinline__ void cp_async_wait_pending(int n) {
+  switch (n) {
+    case 0: cp_async_wait_group<0>(); break;
+    case 1: cp_async_wait_group<1>(); break;
+    case 2: cp_async_wait_group<2>(); break;
+    case 3: cp_async_wait_group<3>(); break;
+    case 4: cp_async_wait_group<4>(); break;
+    case 5: cp_async_wait_group<5>(); break;
+    case 6: cp_async_wait_group<6>(); break;
+    default: cp_async_wait_group<7>(); break;
+  }
+}
+
+// Accessor of one point of a task: row ROW (0: y0, 1: y0+1) and column I of the vector (both
+// compile-time after unrolling, so every access is a register):
+//   yr[0..3]  rows y0-1 .. y0+2 of plane z;  zm[ROW], zp[ROW]  planes z-1, z+1 of the row;
+//   xm[ROW], xp[ROW]  the columns left and right of the vector;  kv[g]  coefficient grid g of the row.
+template <typename T, int VX, int ROW, int I>
+struct TaskAcc {
+  const T (*yr)[VX];
+  const T (*zm)[VX];
+  const T (*zp)[VX];
+  const T* xm;
+  const T* xp;
+  const T (*kv)[VX];
+  __device__ __forceinline__ T c() const { return yr[1 + ROW][I]; }
+  __device__ __forceinline__ T x(int d) const {
+    return d < 0 ? (I == 0 ? xm[ROW] : yr[1 + ROW][I - 1]) : (I == VX - 1 ? xp[ROW] : yr[1 + ROW][I + 1]);
+  }
+  __device__ __forceinline__ T y(int d) const { return yr[1 + ROW + d][I]; }
+  __device__ __forceinline__ T z(int d) const { return d < 0 ? zm[ROW][I] : zp[ROW][I]; }
+  __device__ __forceinline__ T u() const { return T(0); }
+  __device__ __forceinline__ T k(int g) const { return kv[g][I]; }
+};
+
+// The VX points of row ROW of a task.
+template <int S, typename T, int VX, int ROW, int I>
+__device__ __forceinline__ void task_row(const T (*yr)[VX], const T (*zm)[VX], const T (*zp)[VX], const T* xm,
+                                         const T* xp, const T (*kv)[VX], const T* cst, T* r) {
+  if constexpr (I < VX) {
+    const TaskAcc<T, VX, ROW, I> acc{yr, zm, zp, xm, xp, kv};
+    r[I] = point_update<S, T>(acc, cst);
+    task_row<S, T, VX, ROW, I + 1>(yr, zm, zp, xm, xp, kv, cst, r);
+  }
+}
+
+// Coefficient grids 0 .. NC-1 of one row's VX columns: 16-byte read-only loads.
+template <typename T, int VX, int NC>
+__device__ __forceinline__ void load_coef(const T* kp, int64_t gstride, T (*kv)[VX]) {
+  using V16 = typename std::conditional<sizeof(T) == 4, float4, double2>::type;
+#pragma unroll
+  for (int q = 0; q < NC; ++q) {
+    const V16 k = __ldg(reinterpret_cast<const V16*>(kp + q * gstride));
+    if constexpr (sizeof(T) == 4) {
+      kv[q][0] = k.x; kv[q][1] = k.y; kv[q][2] = k.z; kv[q][3] = k.w;
+    } else {
+      kv[q][0] = k.x; kv[q][1] = k.y;
+    }
+  }
+}
+
+__device__ __forceinline__ void st_async_push(uint32_t addr, float v, uint32_t mbar) {
+  asm volatile("st.async.shared::cluster.mbarrier::complete_tx::bytes.f32 [%0], %1, [%2];" ::"r"(addr), "f"(v),
+               "r"(mbar)
+               : "memory");
+}
+__device__ __forceinline__ void st_async_push(uint32_t addr, double v, uint32_t mbar) {
+  asm volatile("st.async.shared::cluster.mbarrier::complete_tx::bytes.f64 [%0], %1, [%2];" ::"r"(addr), "d"(v),
+               "r"(mbar)
+               : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait_cluster(uint32_t m, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{ .reg .pred p; mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2; selp.u32 %0, 1, 0, "
+      "p; }"
+      : "=r"(ok)
+      : "r"(m), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Named barrier ID (1..15; 0 is __syncthreads) over n threads: wait for all, or arrive only.  The
+// id is an immediate, so the kernel reserves only the barriers it uses.
+template <int ID>
+__device__ __forceinline__ void nbar_sync(int n) { asm volatile("bar.sync %0, %1;" ::"n"(ID), "r"(n) : "memory"); }
+template <int ID>
+__device__ __forceinline__ void nbar_arrive(int n) { asm volatile("bar.arrive %0, %1;" ::"n"(ID), "r"(n) : "memory"); }
+// The block's barriers between its computing warps and its two movers: FULL(w) (inputs of step w
+// ready, ids 1-2 by step parity) and DONE(w) (step w computed, ids 3-4).  Alternating ids keep a
+// producer's arrival for step w+1 from counting towards step w.
+__device__ __forceinline__ void sync_full(int w, int n) {
+  if (w & 1) nbar_sync<2>(n);
+  else nbar_sync<1>(n);
+}
+__device__ __forceinline__ void arrive_full(int w, int n) {
+  if (w & 1) nbar_arrive<2>(n);
+  else nbar_arrive<1>(n);
+}
+__device__ __forceinline__ void sync_done(int w, int n) {
+  if (w & 1) nbar_sync<4>(n);
+  else nbar_sync<3>(n);
+}
+__device__ __forceinline__ void arrive_done(int w, int n) {
+  if (w & 1) nbar_arrive<4>(n);
+  else nbar_arrive<3>(n);
+}
+constexpr int kMovers = 64;  // the block's last two warps move data; the others compute
+
+// One tile (diamond (a, a - rho), this block's x slab) from staging to write-back.
+// Halo pushes a block receives per step: from its left neighbour if that one's slab is full (it
+// then pushes its last column), from its right neighbour if it has columns (its first column).
+__device__ __forceinline__ int halo_senders(int nx, int XW, int C, int rank) {
+  const int x0 = rank * XW - 1;
+  return ((C > 1 && rank > 0 && nx - (x0 - XW) >= XW) ? 1 : 0) + ((C > 1 && rank < C - 1 && nx - (x0 + XW) > 0) ? 1 : 0);
+}
+
+// gstep: wavefront steps the block has run in earlier tiles of this launch; the two halo
+// mbarriers (initialised once per launch) serve global steps of their parity, one phase each.
+template <int S, typename T, int G>
+__device__ __forceinline__ void mwd_async_tile(const MwdArgs& A, const int rho, const int a, int& gstep) {
+  static_assert(Traits<S>::R == 1 && !Traits<S>::ORDER2 && !Traits<S>::BOX, "radius-1 first-order stencils");
+  constexpr int R = 1;
+  constexpr int NC = Traits<S>::NCOEF;
+  constexpr int NCO = NC > 0 ? NC : 1;
+  constexpr int A16 = 16 / (int)sizeof(T);
+  constexpr int VX = A16;  // one 16-byte vector per task
+  constexpr int HM = A16;  // shared column of the slab's first column (R rounded up to 16 bytes)
+  using V16 = typename std::conditional<sizeof(T) == 4, float4, double2>::type;
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  T* sm = reinterpret_cast<T*>(smem_raw);
+  const int NZ = A.NZ, YW = A.YW, XT = A.XT, XW = A.XW, C = A.C, K = A.K;
+  const int L = A.lead;  // steps between a plane's staging and its first use
+  const int pe = YW * XT;
+  const int be = NZ * pe;
+  const int ring = be;
+  uint64_t* hb = reinterpret_cast<uint64_t*>(smem_raw + (((size_t)2 * be * sizeof(T) + 15) / 16) * 16);
+  int* lev_lo = reinterpret_cast<int*>(hb + 2);
+  int* lev_w = lev_lo + A.H;
+  int* lev_pp = lev_w + A.H;
+  int* row_mask = lev_pp + A.H + 1;
+
+  const int nx = (int)A.g.nx, ny = (int)A.g.ny, nz = (int)A.g.nz;
+  const int ldx = (int)A.g.ldx;
+  const int64_t gplane = A.g.sy * A.g.ldx;
+  const int rank = (C > 1) ? (int)cluster_ctarank() : 0;
+  const int dw = A.dw;
+  const int b = a - rho;
+  const int P0 = a * dw - rho * (dw / 2);
+  const int Y0 = P0 - R;
+  const int pc0 = rank * XW;  // padded column of slab column 0
+  const int x0 = pc0 - R;     // its interior column
+  const int vlo = max(0, -x0);
+  const int vhi = min(XW, nx - x0);
+  const bool active = vhi > vlo;
+  const int Hh = A.H / 2;
+  const int tb = max((rho - 1) * Hh + 1, 0);
+  const int te = min((rho + 1) * Hh - 1, A.T - 1);
+  if (tb > te) return;  // uniform over the cluster
+  const int nlev = te - tb + 1, smax = nlev - 1;
+  const int NT = blockDim.x, tid = threadIdx.x;
+  const int NTc = NT - kMovers;
+  const bool mover = tid >= NTc;
+  const int mtid = tid - NTc;
+  const int npush_in = halo_senders(nx, XW, C, rank);
+  const uint32_t hb0 = smem_addr(&hb[0]);
+  const int g0 = gstep;  // global step of this tile's step 0
+  const int W = nz + smax * K;  // wavefront steps (one plane per level and step)
+
+  if (tid == 0) {
+    int acc = 0;
+    for (int s = 0; s < nlev; ++s) {
+      const int t = tb + s;
+      const int lo = max(lev_lo_of(a, b, dw, R, t), 0);
+      const int hi = min(lev_hi_of(a, b, dw, R, t), ny);
+      lev_lo[s] = lo;
+      lev_w[s] = max(hi - lo, 0);
+      lev_pp[s] = acc;
+      acc += (max(hi - lo, 0) + 1) / 2;
+    }
+    lev_pp[nlev] = acc;
+  }
+  gstep += W;
+  for (int yy = tid; yy < YW; yy += NT) {
+    const int y = Y0 + yy;
+    int m = 0;
+    if (y >= 0 && y < ny && y >= P0 && y < P0 + dw) {
+      int cnt = 0, par = 0;
+      for (int s = 0; s < nlev; ++s) {
+        const int t = tb + s;
+        if (y >= lev_lo_of(a, b, dw, R, t) && y < lev_hi_of(a, b, dw, R, t)) {
+          ++cnt;
+          par = (t + 1) & 1;
+        }
+      }
+      m = (cnt >= 2) ? 3 : (cnt == 1 ? (1 << par) : 0);
+    }
+    row_mask[yy] = m;
+  }
+  __syncthreads();
+  // halo bytes one neighbour pushes in step w: one element per row of every level whose plane of
+  // step w lies in [0, nz)
+  auto halo_bytes = [&](int w) -> uint32_t {
+    uint32_t n = 0;
+    for (int s = 0; s < nlev; ++s) {
+      const int z = w - s * K;
+      if (z >= 0 && z < nz) n += (uint32_t)lev_w[s];
+    }
+    return n * (uint32_t)npush_in * (uint32_t)sizeof(T);
+  };
+  // arm the phases of steps 0 and 1 (the previous tile waited for every phase it used)
+  if (mtid == 0 && npush_in) {
+    mbar_expect_tx(&hb[g0 & 1], halo_bytes(0));
+    if (W > 1) mbar_expect_tx(&hb[(g0 + 1) & 1], halo_bytes(1));
+  }
+
+  // ---- movers: staging (both buffers, rows [ylo, yhi), 16-byte chunks [cb, ce)) and write-back
+  //      (rows of the projection, owned chunks); (row, chunk) spread over the 64 mover threads ----
+  const int ylo = max(Y0, -R), yhi = min(Y0 + YW, ny + R);
+  const int nrow = active ? max(yhi - ylo, 0) : 0;
+  const int cb = max(pc0 - HM, 0), ce = min(pc0 + XW + HM, ldx);
+  const int nch = active ? max((ce - cb) / A16, 0) : 0;
+  const int wy0 = max(P0, 0), wy1 = min(P0 + dw, ny);
+  const int wcend = min(pc0 + XW, ldx);
+  const int nchw = active ? max((wcend - pc0) / A16, 0) : 0;
+  const int s_rpp = nch > 0 ? max(1, kMovers / nch) : 1;  // rows per pass
+  const int s_r0 = nch > 0 ? (nch <= kMovers ? mtid / nch : 0) : 1 << 30;
+  const int s_c0 = nch > 0 ? (nch <= kMovers ? mtid % nch : mtid) : 0;
+  const int s_cs = nch <= kMovers ? (nch > 0 ? nch : 1) : kMovers;
+  const int w_rpp = nchw > 0 ? max(1, kMovers / nchw) : 1;
+  const int w_r0 = nchw > 0 ? (nchw <= kMovers ? mtid / nchw : 0) : 1 << 30;
+  const int w_c0 = nchw > 0 ? (nchw <= kMovers ? mtid % nchw : mtid) : 0;
+  const int w_cs = nchw <= kMovers ? (nchw > 0 ? nchw : 1) : kMovers;
+  const T* gb0 = static_cast<const T*>(A.buf0);
+  const T* gb1 = static_cast<const T*>(A.buf1);
+  T* go0 = static_cast<T*>(A.buf0);
+  T* go1 = static_cast<T*>(A.buf1);
+  auto stage = [&](int z) {  // movers: plane z of both buffers into its ring slot
+    if (z < -R || z >= nz + R || s_r0 >= s_rpp) return;
+    const int slot = (z + R) % NZ;
+    const int64_t zo = (int64_t)(z + R) * gplane;
+    for (int rr = s_r0; rr < 2 * nrow; rr += s_rpp) {
+      const int p = rr >= nrow;
+      const int y = ylo + rr - p * nrow;
+      const T* src = (p ? gb1 : gb0) + zo + (int64_t)(y + R) * ldx + cb;
+      T* dst = sm + p * be + slot * pe + (y - Y0) * XT + (cb - (pc0 - HM));
+      for (int ch = s_c0; ch < nch; ch += s_cs) cp_async16_cg(dst + ch * A16, src + ch * A16);
+    }
+  };
+  auto write_back = [&](int z) {  // movers: the masked rows of plane z, owned columns
+    if (z < 0 || z >= nz || w_r0 >= w_rpp) return;
+    const int slot = (z + R) % NZ;
+    const int64_t zo = (int64_t)(z + R) * gplane;
+    for (int yy = wy0 - Y0 + w_r0; yy < wy1 - Y0; yy += w_rpp) {
+      const int m = row_mask[yy];
+      const int64_t go = zo + (int64_t)(Y0 + yy + R) * ldx + pc0;
+      const T* src = sm + slot * pe + yy * XT + HM;
+      for (int ch = w_c0; ch < nchw; ch += w_cs) {
+        if (m & 1) *reinterpret_cast<V16*>(go0 + go + ch * A16) = *reinterpret_cast<const V16*>(src + ch * A16);
+        if (m & 2)
+          *reinterpret_cast<V16*>(go1 + go + ch * A16) = *reinterpret_cast<const V16*>(src + be + ch * A16);
+      }
+    }
+  };
+
+  // ---- computing threads: tasks (level s, row pair, 16-byte vector), owned for the tile, each
+  //      with a register window of planes z-1 and z of its two rows ----
+  int t_in[G], t_out[G], t_z[G], t_po[G], t_fl[G], t_par[G];
+  const T* t_k[G];
+  T t_zm[G][2][VX], t_zc[G][2][VX];
+  if (!mover) {
+    const int npairs = lev_pp[nlev];
+    const int nvec = XW / VX;
+#pragma unroll
+    for (int g = 0; g < G; ++g) {
+      const int id = tid + g * NTc;
+      const int pr = id / nvec, xl = (id - pr * nvec) * VX;
+      const bool valid = active && pr < npairs && xl + VX > vlo && xl < vhi;
+      int s = 0;
+      if (valid)
+        while (lev_pp[s + 1] <= pr) ++s;
+      const int y0 = valid ? lev_lo[s] + 2 * (pr - lev_pp[s]) : 0;
+      const int t = tb + s;
+      const int ro = (y0 - Y0) * XT + HM + xl;
+      t_in[g] = (t & 1) * be + ro;
+      t_out[g] = ((t & 1) ^ 1) * be + ro;
+      t_z[g] = -s * K;
+      t_po[g] = (((-s * K + R) % NZ + NZ) % NZ) * pe;
+      const int lo = max(0, vlo - xl), hi = min(VX, vhi - xl);
+      const bool row1 = valid && (y0 + 1 < lev_lo[s] + lev_w[s]);
+      // bits: 0 valid, 1 second row, 2 push left, 3 push right, 4 partial vector, 5 window
+      // loaded, 8.. lo, 12.. hi
+      t_fl[g] = (valid ? 1 : 0) | (row1 ? 2 : 0) | ((valid && C > 1 && rank > 0 && xl < R) ? 4 : 0) |
+                ((valid && C > 1 && rank < C - 1 && vhi == XW && xl + VX > XW - R) ? 8 : 0) |
+                ((lo != 0 || hi != VX) ? 16 : 0) | (lo << 8) | (hi << 12);
+      t_par[g] = (x0 + xl + y0 + t) & 1;
+      t_k[g] = NC ? static_cast<const T*>(A.coef) + (int64_t)(-s * K + R) * gplane + (int64_t)(y0 + R) * ldx +
+                        (pc0 + xl)
+                  : nullptr;
+    }
+  }
+  T cst[5];
+#pragma unroll
+  for (int i = 0; i < 5; ++i) cst[i] = sizeof(T) == 8 ? static_cast<T>(A.c[i]) : static_cast<T>(A.cf[i]);
+  const int64_t gstride = A.g.gstride;
+  const uint32_t sm_u32 = smem_addr(sm);
+  const uint32_t left_base = (C > 1 && rank > 0) ? map_to_rank(sm_u32, rank - 1) : 0u;
+  const uint32_t right_base = (C > 1 && rank < C - 1) ? map_to_rank(sm_u32, rank + 1) : 0u;
+  const uint32_t left_hb = (C > 1 && rank > 0) ? map_to_rank(hb0, rank - 1) : 0u;
+  const uint32_t right_hb = (C > 1 && rank < C - 1) ? map_to_rank(hb0, rank + 1) : 0u;
+
+  // ---- prologue: the planes of steps 0 .. L-1 requested (one group per step), those of steps 0
+  //      and 1 waited for ----
+  if (mover) {
+    for (int z = -R; z < 1 + R; ++z) stage(z);
+    cp_async_commit();
+    for (int j = 1; j < L; ++j) {
+      stage(j + R);
+      cp_async_commit();
+    }
+    cp_async_wait_pending(L - 2);
+  }
+  // all blocks' halo mbarriers are armed, and the first planes visible
+  __syncwarp();
+  cluster_barrier();
+
+  if (!mover) {
+    for (int w = 0; w < W; ++w) {
+      __syncwarp();  // the named barriers are warp-aligned instructions
+      if (w > 0) sync_full(w, NT);
+#pragma unroll
+      for (int g = 0; g < G; ++g) {
+        const int fl = t_fl[g];
+        const int z = t_z[g] + w;
+        const int po = t_po[g];
+        t_po[g] = (po + pe == ring) ? 0 : po + pe;  // the task's plane of step w+1
+        const T* kp = t_k[g];
+        if constexpr (NC > 0) t_k[g] += gplane;
+        if (!(fl & 1) || z < 0 || z >= nz) continue;
+        const T* Vb = sm + t_in[g];
+        const T* P = Vb + po;
+        const bool row1 = fl & 2;
+        if (!(fl & 32)) {  // first plane of the task: load the window (planes z-1, z)
+          const int pm = (po == 0 ? ring : po) - pe;
+          lds_vec<T, VX>(Vb + pm, t_zm[g][0]);
+          lds_vec<T, VX>(Vb + pm + XT, t_zm[g][1]);
+          lds_vec<T, VX>(P, t_zc[g][0]);
+          lds_vec<T, VX>(P + XT, t_zc[g][1]);
+          t_fl[g] |= 32;
+        }
+        const int pp = (po + pe == ring) ? 0 : po + pe;
+        T yr[4][VX], zp[2][VX], xm[2], xp[2];
+        lds_vec<T, VX>(P - XT, yr[0]);
+        // without a second row, row y0+2 may lie past the tile: read row y0+1 instead
+        lds_vec<T, VX>(P + (row1 ? 2 * XT : XT), yr[3]);
+        lds_vec<T, VX>(Vb + pp, zp[0]);
+        lds_vec<T, VX>(Vb + pp + XT, zp[1]);
+        xm[0] = P[-1];
+        xp[0] = P[VX];
+        xm[1] = P[XT - 1];
+        xp[1] = P[XT + VX];
+#pragma unroll
+        for (int i = 0; i < VX; ++i) {
+          yr[1][i] = t_zc[g][0][i];
+          yr[2][i] = t_zc[g][1][i];
+        }
+        T r0[VX], r1[VX];
+        T kv[NCO][VX];
+        // row by row, so that only one row's coefficients are live at a time
+        if constexpr (NC > 0) load_coef<T, VX, NC>(kp, gstride, kv);
+        task_row<S, T, VX, 0, 0>(yr, t_zm[g], zp, xm, xp, kv, cst, r0);
+        if constexpr (NC > 0) load_coef<T, VX, NC>(kp + ldx, gstride, kv);
+        task_row<S, T, VX, 1, 0>(yr, t_zm[g], zp, xm, xp, kv, cst, r1);
+        if constexpr (Traits<S>::RB) {
+          // red-black: only points with (x + y + z + t) even are updated (row y0+1 has the other
+          // colour); the others keep their value
+#pragma unroll
+          for (int i = 0; i < VX; ++i) {
+            const bool odd0 = (t_par[g] + i + z) & 1;
+            if (odd0) r0[i] = yr[1][i];
+            else r1[i] = yr[2][i];
+          }
+        }
+        T* Ub = sm + t_out[g] + po;
+        if (!(fl & 16)) {
+          sts_vec<T, VX>(Ub, r0);
+          if (row1) sts_vec<T, VX>(Ub + XT, r1);
+        } else {
+          const int lo = (fl >> 8) & 15, hi = (fl >> 12) & 15;
+#pragma unroll
+          for (int i = 0; i < VX; ++i)
+            if (i >= lo && i < hi) {
+              Ub[i] = r0[i];
+              if (row1) Ub[XT + i] = r1[i];
+            }
+        }
+        if (fl & 12) {  // x-halo pushes of this step (counted on the neighbour's halo mbarrier)
+          const uint32_t so = (uint32_t)(t_out[g] + po) * (uint32_t)sizeof(T);
+          if (fl & 4) {  // first column -> left neighbour's right halo column
+            const uint32_t oi = so + (uint32_t)(XW * (int)sizeof(T));
+            const uint32_t mb = left_hb + (uint32_t)(((g0 + w) & 1) * 8);
+            st_async_push(left_base + oi, r0[0], mb);
+            if (row1) st_async_push(left_base + oi + (uint32_t)(XT * (int)sizeof(T)), r1[0], mb);
+          }
+          if (fl & 8) {  // last column -> right neighbour's left halo column
+            const uint32_t oi = so + (uint32_t)((VX - 1) * (int)sizeof(T)) - (uint32_t)(XW * (int)sizeof(T));
+            const uint32_t mb = right_hb + (uint32_t)(((g0 + w) & 1) * 8);
+            st_async_push(right_base + oi, r0[VX - 1], mb);
+            if (row1) st_async_push(right_base + oi + (uint32_t)(XT * (int)sizeof(T)), r1[VX - 1], mb);
+          }
+        }
+        // slide the window one plane up
+#pragma unroll
+        for (int i = 0; i < VX; ++i) {
+          t_zm[g][0][i] = t_zc[g][0][i];
+          t_zm[g][1][i] = t_zc[g][1][i];
+          t_zc[g][0][i] = zp[0][i];
+          t_zc[g][1][i] = zp[1][i];
+        }
+      }
+      __syncwarp();
+      arrive_done(w, NT);
+    }
+  } else {
+    // movers, iteration `it` (overlapping the computation of step `it`): write back the planes
+    // the top level finished in step it-1, stage the planes of step it+L, wait for those of step
+    // it+2 and for the neighbours' halo bytes of step it, then release step it+1
+    for (int it = 0; it <= W; ++it) {
+      if (it > 0) {
+        __syncwarp();
+        sync_done(it - 1, NT);
+        write_back(it - 1 - smax * K);
+      }
+      if (it == W) break;
+      stage(it + L + R);
+      cp_async_commit();
+      cp_async_wait_pending(L - 2);
+      if (mtid < 32 && npush_in) {  // the first mover warp, all lanes together
+        const int gs = g0 + it;
+        const uint32_t mb = hb0 + (uint32_t)((gs & 1) * 8);
+        const uint32_t parity = (uint32_t)((gs >> 1) & 1);
+        if (!mbar_try_wait_cluster(mb, parity)) {
+          const uint64_t t0 = global_ns();
+          while (!mbar_try_wait_cluster(mb, parity)) {
+            if (global_ns() - t0 > kMbarWaitNs) {
+              atomicOr(A.err, GIRIH_ETIMEOUT);
+              break;
+            }
+          }
+        }
+        __syncwarp();
+        // every waiter has seen the phase of step it complete: arm the mbarrier for step it+2
+        if (mtid == 0 && it + 2 < W) mbar_expect_tx(&hb[gs & 1], halo_bytes(it + 2));
+      }
+      __syncwarp();
+      if (it + 1 < W) arrive_full(it + 1, NT);
+    }
+    cp_async_wait_group<0>();
+  }
+}
+
+// Persistent kernel: every cluster of a grid that fits the device at once takes diamonds from the
+// FIFO in row-major order and starts one once its two parents in the previous row have published
+// completion (the runtime of Sect. 4.2.3; same protocol as mwd_vec_kernel's persistent mode).  The
+// cluster barrier after a tile orders every block's write-back stores (release) before rank 0
+// publishes the flag.
+template <int S, typename T, int G>
+__global__ void __launch_bounds__(G == 1 ? 640 : (G == 2 ? 512 : 256), 1) mwd_async_kernel(const MwdArgs A) {
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  const int C = A.C;
+  const int rank = (C > 1) ? (int)cluster_ctarank() : 0;
+  const size_t ring_bytes = (((size_t)2 * A.NZ * A.YW * A.XT * sizeof(T) + 15) / 16) * 16;
+  int* slot = reinterpret_cast<int*>(smem_raw + ring_bytes + 16) + 3 * A.H + 1 + A.YW;
+  // the two halo mbarriers, initialised once per launch (the first cluster barrier below orders
+  // the initialisation before any neighbour's push)
+  if (threadIdx.x == 0 && halo_senders((int)A.g.nx, A.XW, C, rank) > 0) {
+    uint64_t* hb = reinterpret_cast<uint64_t*>(smem_raw + ring_bytes);
+    mbar_init(&hb[0], 1);
+    mbar_init(&hb[1], 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  int gstep = 0;
+  for (;;) {
+    if (rank == 0 && threadIdx.x == 0) {
+      const int it = atomicAdd(A.fifo, 1);
+      for (int r = 0; r < C; ++r) st_cluster_u32(map_to_rank(smem_addr(slot), (uint32_t)r), (uint32_t)it);
+    }
+    __syncwarp();
+    cluster_barrier();
+    const int it = *reinterpret_cast<volatile int*>(slot);
+    if (it >= A.n_items) break;
+    const int rho = A.items[2 * it], a = A.items[2 * it + 1];
+    if (rank == 0 && threadIdx.x == 0 && rho > 0) {
+      const int first = A.rows[3 * (rho - 1)], amin = A.rows[3 * (rho - 1) + 1], nd = A.rows[3 * (rho - 1) + 2];
+      const uint64_t t0 = global_ns();
+      const bool gave_up = *reinterpret_cast<volatile int*>(A.err) != 0;
+      for (int d = a - 1; d <= a && !gave_up; ++d) {
+        if (d < amin || d >= amin + nd) continue;
+        const int* f = A.flags + first + (d - amin);
+        int v;
+        for (;;) {
+          asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(f) : "memory");
+          if (v == A.epoch) break;
+          if (global_ns() - t0 > kMbarWaitNs) {
+            atomicOr(A.err, GIRIH_ETIMEOUT);
+            break;
+          }
+        }
+      }
+    }
+    __syncwarp();
+    cluster_barrier();
+    mwd_async_tile<S, T, G>(A, rho, a, gstep);
+    __syncwarp();
+    cluster_barrier();
+    if (rank == 0 && threadIdx.x == 0) {
+      asm volatile("fence.acq_rel.gpu;" ::: "memory");
+      asm volatile("st.relaxed.gpu.global.u32 [%0], %1;" ::"l"(A.flags + it), "r"(A.epoch) : "memory");
+    }
+  }
+}
+
+}  // namespace girih

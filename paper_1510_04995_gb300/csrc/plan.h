@@ -39,8 +39,10 @@ int cuda_fail(cudaError_t e, const char* where);
 // Validates a configuration for the plan's device and layout.  ptrs16: the buffers of the run
 // are 16-byte aligned (plan-time checks assume so); mv_out: the kernel's data path.
 int check_config(const Plan* p, const girih_config* c, int64_t* smem_out, int* xw_out, int* g_out,
-                 int* mv_out = nullptr, bool ptrs16 = true);
+                 int* mv_out = nullptr, bool ptrs16 = true, int* lead_out = nullptr);
 int run_sweep(Plan* p, int64_t T, void* u, void* u_prev, const void* coeffs, const double* c,
               const girih_config& cfg, cudaStream_t st);
 int64_t mwd_rows(int64_t T, int dw, int R);
+// x slab per block of the blocked kernel for a cluster of C blocks on data path mv
+int slab_width(const Plan* p, int C, int mv);
 }  // namespace girih

@@ -1,5 +1,5 @@
 // Point updates of the seven stencils (arXiv 1510.04995, Sect. 2.2, Listings 1-4, and the
-// 27-point box operator and red-black Gauss-Seidel of Sect. 7) and the small
+// 27-point box operator and red-black Gauss-Seidel of Sect. 8.4) and the small
 // device helpers the sweep kernels share.
 //
 // Every kernel of the library computes a lattice-site update (LUP) through exactly one of the

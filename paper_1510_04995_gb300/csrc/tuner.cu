@@ -138,6 +138,22 @@ std::vector<girih_config> candidates(Plan* p) {
             girih_config c{GIRIH_ALGO_MWD, dw, nf, C, th, v};
             if (check_config(p, &c, nullptr, nullptr, nullptr) == GIRIH_OK) out.push_back(c);
           }
+  // RELAXED_PERSISTENT: blocks sized to the tile's tasks (1, 2 or 4 per computing thread, whole
+  // warps) plus the two data-moving warps
+  if (async_stencil(p->stencil) && p->bulk_layout)
+    for (int dw = 2 * R; dw <= 64 * R; dw += 2 * R)
+      for (int C : {1, 2, 4, 8, 16}) {
+        const int64_t tasks = (int64_t)mwd_max_pairs(R, dw) * (slab_width(p, C, MV_ASYNC) / mwd_vx(p->stencil,
+                                                                                                   p->dtype, MV_ASYNC));
+        int last = 0;
+        for (int G : {1, 2, 4}) {
+          const int th = (int)std::max<int64_t>(32, (tasks + 32LL * G - 1) / (32LL * G) * 32) + kAsyncMovers;
+          if (th == last || th > async_max_threads(G)) continue;
+          last = th;
+          girih_config c{GIRIH_ALGO_MWD, dw, 1, C, th, GIRIH_RELAXED_PERSISTENT};
+          if (check_config(p, &c, nullptr, nullptr, nullptr) == GIRIH_OK) out.push_back(c);
+        }
+      }
   g_err_clear();
   return out;
 }

@@ -96,7 +96,8 @@ def test_sampled_points_against_oracle_cones(workload):
         assert abs(got - ref) <= 1e-12 * scale, ((i, j, k), got, ref)
 
 
-@pytest.mark.parametrize("variant", ["NAIVE", "FED", "FED_BULK", "FED_ELEM", "RELAXED", "FED_PERSISTENT"])
+@pytest.mark.parametrize("variant", ["NAIVE", "FED", "FED_BULK", "FED_ELEM", "RELAXED", "FED_PERSISTENT",
+                                     "RELAXED_PERSISTENT"])
 def test_blocked_repeatable_under_load(variant):
     """Repeated large sweeps in each data path, bit for bit against one naive sweep: a staging or
     synchronisation race shows up as a rare, localised difference, so several long runs with many
@@ -106,7 +107,8 @@ def test_blocked_repeatable_under_load(variant):
     ldx = 516
     p = girih.plan(stencil, nx, ny, nz, dtype=dtype, T=T, ldx=ldx)
     cfg = (girih.config(girih.NAIVE) if variant == "NAIVE" else
-           girih.config(girih.MWD, dw=8, nf=1, cluster=8, threads=512, variant=getattr(girih, variant)))
+           girih.config(girih.MWD, dw=8, nf=1, cluster=8, threads=352 if variant == "RELAXED_PERSISTENT" else 512,
+                        variant=getattr(girih, variant)))
     u, up, co, c = inputs.make_problem(stencil, nx, ny, nz, backend="torch", device="cuda", ldx=ldx)
     u, up = u.float().contiguous(), up.float().contiguous()
     nu, nup = u.clone(), up.clone()
@@ -117,3 +119,32 @@ def test_blocked_repeatable_under_load(variant):
         girih.status(p)
         torch.cuda.synchronize()
         assert torch.equal(bu, nu) and torch.equal(bup, nup), (variant, int((bu != nu).sum()))
+
+
+@pytest.mark.parametrize("workload,cfgkw", [
+    ("7pt_const_f32_512", dict(dw=8, nf=1, cluster=8, threads=352)),
+    ("7pt_const_f64_512", dict(dw=8, nf=1, cluster=16, threads=352)),
+    ("7pt_var_f32_480", dict(dw=8, nf=1, cluster=8, threads=320)),
+    ("7pt_rbgs_f32_512", dict(dw=12, nf=1, cluster=16, threads=416)),
+])
+def test_relaxed_persistent_full_size(workload, cfgkw):
+    """The neighbour-synchronised persistent kernel on the benchmark grids (full T), in cluster
+    and diamond shapes that hold one or two blocks per SM: bit for bit the naive sweep."""
+    import torch
+    import bench
+    stencil, dtype, nx, ny, nz, T = bench.WORKLOADS[workload]
+    a16 = 16 // (8 if dtype == "f64" else 4)
+    ldx = -(-(nx + 2) // a16) * a16
+    p = girih.plan(stencil, nx, ny, nz, dtype=dtype, T=T, ldx=ldx)
+    cfg = girih.config(girih.MWD, variant=girih.RELAXED_PERSISTENT, **cfgkw)
+    assert p.feasible(cfg), cfg
+    u, up, co, c = inputs.make_problem(stencil, nx, ny, nz, backend="torch", device="cuda", ldx=ldx)
+    tdt = torch.float64 if dtype == "f64" else torch.float32
+    u, up = u.to(tdt).contiguous(), up.to(tdt).contiguous()
+    co = co.to(tdt).contiguous() if co is not None else None
+    bu, bup = u.clone(), up.clone()
+    girih.run(p, bu, bup, co, c=c, cfg=cfg)
+    girih.status(p)
+    girih.run(p, u, up, co, c=c, cfg=girih.config(girih.NAIVE))
+    torch.cuda.synchronize()
+    assert torch.equal(bu, u) and torch.equal(bup, up), (workload, cfg)

@@ -27,6 +27,20 @@ def _p(t):
     return ctypes.c_void_p(t.data_ptr())
 
 
+BLOCKS = ("W1", "b1", "W2", "b2", "W3", "b3")
+
+
+def assert_blockwise_close(g, go, d, rtol=1e-4, what="gradient"):
+    """Element-by-element comparison per parameter block (W1, b1, W2, b2, W3, b3):
+    |g - g_o| <= rtol * max|g_o(block)| + 1e-6 * max|g_o|, so that a wrong small block (a bias
+    gradient next to the large W2 block) cannot hide inside a global norm."""
+    scale = float(np.max(np.abs(go)))
+    for name, gb, ob in zip(BLOCKS, mlp.unpack(np.asarray(g, dtype=np.float64), d), mlp.unpack(go, d)):
+        tol = rtol * float(np.max(np.abs(ob))) + 1e-6 * scale
+        err = np.abs(np.asarray(gb) - np.asarray(ob))
+        assert float(np.max(err)) <= tol, f"{what} block {name}: max error {np.max(err):.3e} > {tol:.3e}"
+
+
 def _rand(n, d, seed):
     rng = np.random.default_rng(seed)
     X = rng.uniform(-1, 1, size=(n, d))
@@ -57,7 +71,7 @@ def test_forward_and_gradient_match_oracle(n):
     yo, _ = mlp.forward(p, X)
     go = mlp.backward(p, X, t)
     assert np.max(np.abs(y - yo)) <= 1e-4 * max(1.0, np.max(np.abs(yo)))
-    assert np.linalg.norm(g - go) <= 1e-4 * np.linalg.norm(go) + 1e-7
+    assert_blockwise_close(g, go, D)
     assert abs(loss - mlp.loss(p, X, t)) <= 1e-4 * mlp.loss(p, X, t)
 
 
@@ -81,6 +95,25 @@ def test_sgd_and_adam_steps_match_oracle():
         po, mo, vo = mlp.adam_step(po, g, mo, vo, step, 1e-2)
     torch.cuda.synchronize()
     assert np.allclose(dp.double().cpu().numpy(), po, rtol=1e-5, atol=1e-6)
+    # SGD and Adam on a full parameter vector of the network, compared block by block
+    npar = mlp.n_params(D)
+    p = rng.normal(size=npar)
+    g = rng.normal(size=npar)
+    dp = _dev(p)
+    girih.check(L.girih_mlp_sgd(_p(dp), _p(_dev(g)), npar, ctypes.c_float(0.05), None))
+    torch.cuda.synchronize()
+    assert_blockwise_close(dp.double().cpu().numpy(), mlp.sgd_step(p, g, 0.05), D, rtol=1e-6, what="SGD step")
+    dp = _dev(p)
+    m = torch.zeros(npar, device="cuda")
+    v = torch.zeros(npar, device="cuda")
+    mo, vo, po = np.zeros(npar), np.zeros(npar), p.copy()
+    for step in range(1, 4):
+        g = rng.normal(size=npar)
+        girih.check(L.girih_mlp_adam(_p(dp), _p(_dev(g)), _p(m), _p(v), npar, step, ctypes.c_float(1e-2),
+                                     ctypes.c_float(0.9), ctypes.c_float(0.999), ctypes.c_float(1e-8), None))
+        po, mo, vo = mlp.adam_step(po, g, mo, vo, step, 1e-2)
+    torch.cuda.synchronize()
+    assert_blockwise_close(dp.double().cpu().numpy(), po, D, rtol=1e-5, what="Adam step")
 
 
 def test_gpu_training_reduces_loss_like_oracle():

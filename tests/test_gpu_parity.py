@@ -360,10 +360,112 @@ def test_persistent_schedule_reuse_and_rejects_unaligned():
     assert p.launch_count(bad) == 2  # one persistent launch + the exchange for odd T
 
 
+# (dw, cluster, threads): 1, 2 and 4 tasks per computing thread (the last two warps move data)
+ASYNC_CFGS = [(4, 1, 256), (8, 2, 224), (8, 2, 160), (8, 4, 128), (12, 8, 96), (6, 16, 96), (16, 2, 512)]
+
+
+@pytest.mark.parametrize("stencil", [0, 1, 6])
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+def test_relaxed_persistent(stencil, dtype):
+    """RELAXED_PERSISTENT (the persistent FIFO schedule with neighbour-only synchronisation: a block
+    waits per step for its own results and for the exact halo bytes its two neighbours pushed)
+    reorders tiles and synchronises differently, but never changes a point's arithmetic:
+    bit-identical to the naive sweep for clusters of 1 to 16 blocks, truncated and full diamond
+    rows, and thread counts that give 1, 2 or 4 tasks per computing thread."""
+    nx, ny, nz = SIZES[1]
+    ldx = _aligned_ldx(nx, 1, dtype)
+    for dw, cl, th in ASYNC_CFGS:
+        H = dw
+        for T in (1, H - 1, 2 * H + 3):
+            u, up, co, c = inputs.make_problem(stencil, nx, ny, nz, seed=17 + T + dw, ldx=ldx)
+            nu, nup = gpu_sweep(stencil, dtype, u, up, co, c, T, nx, ny, nz, girih.config(girih.NAIVE), ldx=ldx)
+            kw = dict(dw=dw, nf=1, cluster=cl, threads=th, variant=girih.RELAXED_PERSISTENT)
+            cfg = feasible_cfg(stencil, dtype, nx, ny, nz, kw, ldx=ldx)
+            assert cfg.variant == girih.RELAXED_PERSISTENT
+            pu, pup = gpu_sweep(stencil, dtype, u, up, co, c, T, nx, ny, nz, cfg, ldx=ldx)
+            assert np.array_equal(pu, nu) and np.array_equal(pup, nup), (dw, cl, T, cfg)
+
+
+@pytest.mark.parametrize("shape", [(1, 1, 1), (33, 1, 9), (5, 70, 3), (129, 7, 40), (2, 2, 2)])
+def test_relaxed_persistent_degenerate_shapes(shape):
+    nx, ny, nz = shape
+    for dtype in ("f32", "f64"):
+        ldx = _aligned_ldx(nx, 1, dtype)
+        for stencil in (0, 1, 6):
+            T = 7
+            u, up, co, c = inputs.make_problem(stencil, nx, ny, nz, seed=4, ldx=ldx)
+            nu, nup = gpu_sweep(stencil, dtype, u, up, co, c, T, nx, ny, nz, girih.config(girih.NAIVE), ldx=ldx)
+            for dw, cl in ((4, 2), (8, 4)):
+                cfg = feasible_cfg(stencil, dtype, nx, ny, nz,
+                                   dict(dw=dw, nf=1, cluster=cl, threads=256, variant=girih.RELAXED_PERSISTENT),
+                                   ldx=ldx)
+                pu, pup = gpu_sweep(stencil, dtype, u, up, co, c, T, nx, ny, nz, cfg, ldx=ldx)
+                assert np.array_equal(pu, nu) and np.array_equal(pup, nup), (shape, dtype, stencil, cfg)
+
+
+def test_relaxed_persistent_rejections():
+    """The variant exists for the radius-1 first-order stencils on the vector layout: other
+    stencils, unaligned layouts and unaligned coefficient grids are rejected with nothing enqueued."""
+    import torch
+    from gpu_util import to_dev
+    cfg = girih.config(girih.MWD, dw=8, nf=1, cluster=2, threads=256, variant=girih.RELAXED_PERSISTENT)
+    for stencil in (2, 3, 4, 5):
+        R = inputs.RADIUS[stencil]
+        nx, ny, nz = SIZES[R]
+        p = girih.plan(stencil, nx, ny, nz, dtype="f32", T=3, ldx=_aligned_ldx(nx, R, "f32"))
+        bad = girih.config(girih.MWD, dw=2 * R * 4, nf=1, cluster=2, threads=256, variant=girih.RELAXED_PERSISTENT)
+        assert not p.feasible(bad), stencil
+    nx, ny, nz = SIZES[1]
+    ldx = _aligned_ldx(nx, 1, "f32")
+    assert not girih.plan(0, nx, ny, nz, dtype="f32", T=3, ldx=ldx + 1).feasible(cfg)
+    p0 = girih.plan(0, nx, ny, nz, dtype="f32", T=3, ldx=ldx)
+    assert not p0.feasible(girih.config(girih.MWD, dw=8, nf=2, cluster=2, threads=256,
+                                        variant=girih.RELAXED_PERSISTENT))  # one plane per step
+    assert not p0.feasible(girih.config(girih.MWD, dw=4, nf=1, cluster=2, threads=64,
+                                        variant=girih.RELAXED_PERSISTENT))  # no computing warp
+    p = girih.plan(1, nx, ny, nz, dtype="f32", T=3, ldx=ldx)
+    assert p.feasible(cfg)
+    u, up, co, c = inputs.make_problem(1, nx, ny, nz, seed=2, ldx=ldx)
+    du, dup = to_dev(u, "f32"), to_dev(up, "f32")
+    big = torch.zeros(co.size + 1, dtype=torch.float32, device="cuda")
+    dco = big[1:].view(co.shape)  # 4 bytes past a 256-byte boundary
+    dco.copy_(to_dev(co, "f32"))
+    before = du.clone()
+    with pytest.raises(girih.GirihError):
+        girih.run(p, du, dup, dco, c=c, cfg=cfg)
+    torch.cuda.synchronize()
+    assert torch.equal(du, before)
+
+
+def test_persistent_schedule_on_fresh_plan_and_nonblocking_stream():
+    """The plan's completion flags are cleared on the sweep's own stream: a persistent sweep
+    launched on a non-blocking stream right after the plan is created (and after earlier plans
+    whose freed flag buffers the allocator may hand out again, still holding their epochs) is
+    ordered after that clear and equals the naive sweep bit for bit."""
+    import torch
+    from gpu_util import to_dev
+    stencil, dtype, nx, ny, nz, T = 0, "f32", 70, 45, 33, 9
+    ldx = _aligned_ldx(nx, 1, dtype)
+    u, up, co, c = inputs.make_problem(stencil, nx, ny, nz, seed=8, ldx=ldx)
+    nu, nup = gpu_sweep(stencil, dtype, u, up, co, c, T, nx, ny, nz, girih.config(girih.NAIVE), ldx=ldx)
+    cfg = girih.config(girih.MWD, dw=4, nf=1, cluster=2, threads=256, variant=girih.FED_PERSISTENT)
+    side = torch.cuda.Stream()  # torch's side streams do not synchronise with the legacy stream
+    for rep in range(4):
+        p = girih.plan(stencil, nx, ny, nz, dtype=dtype, T=T, ldx=ldx)
+        du, dup = to_dev(u, dtype), to_dev(up, dtype)
+        torch.cuda.synchronize()
+        with torch.cuda.stream(side):
+            girih.run(p, du, dup, None, c=c, cfg=cfg, stream=side)
+            girih.status(p, stream=side)
+        side.synchronize()
+        assert np.array_equal(du.cpu().numpy(), nu) and np.array_equal(dup.cpu().numpy(), nup), rep
+        del p
+
+
 @pytest.mark.parametrize("stencil", [5, 6])
 @pytest.mark.parametrize("dtype", ["f64", "f32"])
 def test_vector_only_stencils_paths_and_layouts(stencil, dtype):
-    """The 27-point box stencil and red-black Gauss-Seidel (Sect. 7): the box stencil's diagonal
+    """The 27-point box stencil and red-black Gauss-Seidel (Sect. 8.4): the box stencil's diagonal
     dependencies (edges and corners of the tile) and red-black's colour-masked half-sweeps are
     met by the same diamonds and wavefront.  The vector path (FED), the bulk-copy path
     (FED_BULK) and the persistent schedule agree with the naive sweep bit for bit, including

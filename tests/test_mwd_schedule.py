@@ -26,7 +26,7 @@ MODES = [(c, m) for c in CASES for m in ("element", "vec_f32", "bulk_f32")] + \
 
 @pytest.mark.parametrize("case", [c for c in CASES if c[0] == 1])
 def test_schedule_model_box_stencil(case):
-    """The 27-point box stencil's diagonal reads (Sect. 7: the tiles already cover edge and corner
+    """The 27-point box stencil's diagonal reads (Sect. 8.4: the tiles already cover edge and corner
     dependencies) find level t in every ring slot and halo column they touch."""
     for a16 in (4, 2):
         assert simulate(*case, vec=True, a16=a16, box=True)

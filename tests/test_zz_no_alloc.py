@@ -53,11 +53,16 @@ def test_static_backward_matches_workspace_backward_twice():
         girih.check(L.girih_mlp_backward_static(_p(dp), _p(dX), _p(dt), n, D, _p(g), _p(loss), None))
         torch.cuda.synchronize()
         gr, gs = g_ref.double().cpu().numpy(), g.double().cpu().numpy()
-        assert np.linalg.norm(gs - gr) <= 1e-4 * np.linalg.norm(gr), call
-        assert abs(float(loss) - float(l_ref)) <= 1e-4 * float(l_ref), call
-        # and both agree with the FP64 oracle at the network tests' tolerance
+        # the same kernels with a fixed-order reduction on a different workspace: identical bits
+        assert torch.equal(g, g_ref), call
+        assert torch.equal(loss, l_ref), call
+        # and, per parameter block and element by element, the FP64 oracle at the network tests'
+        # tolerance
         go = mlp.backward(p.astype(np.float64), X.astype(np.float64), t.astype(np.float64))
-        assert np.linalg.norm(gs - go) <= 1e-4 * np.linalg.norm(go), call
+        scale = float(np.max(np.abs(go)))
+        for name, gb, ob in zip(("W1", "b1", "W2", "b2", "W3", "b3"), mlp.unpack(gs, D), mlp.unpack(go, D)):
+            tol = 1e-4 * float(np.max(np.abs(ob))) + 1e-6 * scale
+            assert float(np.max(np.abs(gb - ob))) <= tol, (call, name)
 
 
 def test_static_backward_rejects_too_many_rows():
