@@ -10,6 +10,8 @@
 #include <string>
 #include <vector>
 
+#include <cudaTypedefs.h>
+
 #include "internal.h"
 #include "plan.h"
 
@@ -142,6 +144,9 @@ int check_config(const Plan* p, const girih_config* c, int64_t* smem_out, int* x
   const int lead = mv == MV_ASYNC ? mwd_async_lead(p->stencil, p->dtype, c->dw, c->nf, XW, c->threads, G, p->smem_optin)
                                   : kAsyncLeadMin;
   const MwdShape sh = mwd_shape(p->stencil, p->dtype, c->dw, c->nf, XW, mv, lead);
+  if (mv == MV_ASYNC && sh.XT > 256)
+    return fail(GIRIH_EINVAL, "RELAXED_PERSISTENT stages a slab of %d columns with its halo per tensor copy (at "
+                "most 256): use a larger cluster", sh.XT);
   if (sh.smem_bytes > p->smem_optin)
     return fail(GIRIH_EINVAL, "config needs %lld bytes of shared memory per block (device limit %lld)",
                 (long long)sh.smem_bytes, (long long)p->smem_optin);
@@ -185,6 +190,42 @@ static girih_config default_config(Plan* p) {
 
 static int launch_persistent(Plan* p, MwdArgs a, int64_t rows, const girih_config& cfg, int G, int mv,
                              int64_t smem, cudaStream_t st, cudaError_t* e_out);
+
+// 3D tensor maps of the two buffers for the RELAXED_PERSISTENT staging copies: the padded grid
+// (ldx x (ny+2R) x (nz+2R)), a box of one slab with its halo (XT columns) x YW rows x 1 plane;
+// elements outside the grid read as zeros.
+// The driver's tensor-map encoder, looked up through the runtime (the library does not link the
+// driver library, so that it loads on machines without a GPU driver).
+static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  if (!fn) {
+    void* f = nullptr;
+    cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(f);
+    cudaGetLastError();
+  }
+  return fn;
+}
+
+static int encode_plane_maps(const Plan* p, void* u, void* up, int XT, int YW, CUtensorMap* tm) {
+  const PFN_cuTensorMapEncodeTiled_v12000 encode = tensor_map_encoder();
+  if (!encode) return fail(GIRIH_ECUDA, "the driver's cuTensorMapEncodeTiled is not available");
+  const cuuint64_t dims[3] = {(cuuint64_t)p->ldx, (cuuint64_t)(p->ny + 2 * p->R), (cuuint64_t)(p->nz + 2 * p->R)};
+  const cuuint64_t strides[2] = {(cuuint64_t)p->ldx * p->elem, (cuuint64_t)(p->ny + 2 * p->R) * p->ldx * p->elem};
+  const cuuint32_t box[3] = {(cuuint32_t)XT, (cuuint32_t)YW, 1u};
+  const cuuint32_t estr[3] = {1u, 1u, 1u};
+  const CUtensorMapDataType dt = p->dtype == GIRIH_F64 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
+  void* bufs[2] = {u, up};
+  for (int i = 0; i < 2; ++i) {
+    const CUresult r = encode(&tm[i], dt, 3, bufs[i], dims, strides, box, estr,
+                                              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                                              CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return fail(GIRIH_ECUDA, "tensor map of buffer %d: CUresult %d", i, (int)r);
+  }
+  return GIRIH_OK;
+}
 
 int run_sweep(Plan* p, int64_t T, void* u, void* u_prev, const void* coeffs, const double* c,
               const girih_config& cfg, cudaStream_t st) {
@@ -239,6 +280,11 @@ int run_sweep(Plan* p, int64_t T, void* u, void* u_prev, const void* coeffs, con
     a.XT = sh.XT;
     a.err = p->err;
     a.lead = lead;
+    a.PE = sh.PE;
+    if (mv == MV_ASYNC) {
+      const int rc3 = encode_plane_maps(p, u, u_prev, sh.XT, sh.YW, a.tm);
+      if (rc3 != GIRIH_OK) return rc3;
+    }
     a.relaxed = (cfg.variant == GIRIH_RELAXED || cfg.variant == GIRIH_RELAXED_ELEM) ? 1 : 0;
     const int64_t rows = mwd_rows(T, cfg.dw, p->R);
     if (persistent_variant(cfg.variant)) {

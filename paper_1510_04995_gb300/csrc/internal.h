@@ -1,6 +1,7 @@
 // Internal interfaces between the C-ABI layer (api.cu, tuner.cu) and the kernel translation
 // units (naive.cu, mwd.cu, mlp.cu).  Not part of the public ABI.
 #pragma once
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -60,11 +61,16 @@ struct MwdArgs {
   int* flags;
   int* fifo;
   int32_t lead;  // RELAXED_PERSISTENT: steps between a plane's staging and its first use (3..8)
+  int32_t PE;    // RELAXED_PERSISTENT: elements per ring slot (YW * XT rounded up to 128 bytes)
+  // RELAXED_PERSISTENT: 3D tensor maps of buf0 and buf1 (padded grid, box XT x YW x 1) for the
+  // staging copies; the kernel takes MwdArgs as a __grid_constant__ parameter
+  alignas(64) CUtensorMap tm[2];
 };
 
 struct MwdShape {
   int32_t NZ, YW, XT;
   int64_t smem_bytes;
+  int32_t PE = 0;  // RELAXED_PERSISTENT: elements per ring slot
 };
 // Data paths of the blocked kernel: per-element staging (any layout); 16-byte vectors on a
 // shifted slab partition (rows of 16-byte multiples, 16-byte aligned buffers) moved by cp.async
@@ -83,7 +89,8 @@ inline bool async_stencil(int stencil) {
 #define GIRIH_ASYNC_LEAD_MAX 8
 #endif
 constexpr int kAsyncLeadMin = 3;
-constexpr int kAsyncMovers = 64;  // threads of the RELAXED_PERSISTENT block that move data
+constexpr int kAsyncMovers = 32;    // threads of the RELAXED_PERSISTENT block that move data
+constexpr int kAsyncLoadBars = 8;   // its staging mbarriers (the lead is at most 8)
 constexpr int kAsyncLeadMax = GIRIH_ASYNC_LEAD_MAX;
 // Largest block of the RELAXED_PERSISTENT kernel for G tasks per thread (its launch bound).
 inline int async_max_threads(int G) { return G == 1 ? 640 : (G == 2 ? 512 : 256); }

@@ -46,8 +46,10 @@ MwdShape mwd_shape(int stencil, int dtype, int dw, int nf, int XW, int mv, int l
     s.NZ = L + 2 * R + 1 + (H - 2) * K;
     s.YW = dw + 2 * R;
     s.XT = XW + 2 * ((R + a16 - 1) / a16 * a16);
-    const int64_t ring = 2LL * s.NZ * s.YW * s.XT * elem;
-    s.smem_bytes = (ring + 15) / 16 * 16 + 16 + (3LL * H + 1 + s.YW + 1) * 4;
+    const int per128 = 128 / elem;  // slots start on 128-byte boundaries (tensor copy destinations)
+    s.PE = (s.YW * s.XT + per128 - 1) / per128 * per128;
+    const int64_t ring = 2LL * s.NZ * s.PE * elem;
+    s.smem_bytes = (ring + 15) / 16 * 16 + 8LL * (2 + kAsyncLoadBars) + (3LL * H + 2) * 4;
     return s;
   }
   const bool bulk = mv == MV_BULK;

@@ -1,35 +1,39 @@
 // Wavefront-diamond sweep with neighbour-only synchronisation (variant RELAXED_PERSISTENT): the
 // tiling, wavefront and persistent FIFO schedule of the FED_PERSISTENT kernel (mwd_vec.cuh,
-// Sects. 4.2.1 and 4.2.3), with the per-step synchronisation reduced to what the data flow needs.
+// Sects. 4.2.1 and 4.2.3), with the per-step synchronisation reduced to what the data flow needs
+// and the data movement taken off the computing warps.
 //
-// A wavefront step of a tile needs, besides the block's own results of the previous step (a
-// block-local barrier), only the x-halo columns its two neighbours in the cluster computed in
-// that step.  Those arrive as asynchronous remote stores (st.async) that count their bytes on an
-// mbarrier of the receiving block, which waits for exactly that many bytes: the relaxed
-// synchronisation of Sect. 4.2.1 (a thread group member waits for its neighbour, not for the
-// whole group), here along x where the halo exchange goes both ways.  No cluster-wide barrier and
-// no release fence is taken per step, so nothing waits for the write-back stores or the staging
-// copies in flight to reach memory; a cluster barrier (with release) is taken once per tile.
+// Synchronisation.  A wavefront step of a tile needs, besides the block's own results of the
+// previous step, only the x-halo columns its two neighbours in the cluster computed in that step.
+// Those arrive as asynchronous remote stores (st.async) that count their bytes on a halo mbarrier
+// of the receiving block, which waits for exactly that many bytes: the relaxed synchronisation
+// of Sect. 4.2.1 (a thread group member waits for its neighbour, not for the whole group), here
+// along x where the halo exchange goes both ways.  No cluster-wide barrier and no release fence
+// is taken per step (a cluster barrier is taken once per tile).  One plane per level and step
+// (nf = 1): then a block can run at most one step ahead of a neighbour, and a push of step w+1
+// (planes w+1 - s*K of level s) never meets a value the receiver still reads in step w (level
+// s-1 reads its x neighbours at planes w - (s-1)*K = w + 1 - s*K + 1).
 //
-// Step w of a block (every thread):
-//   1. update its tasks (level s, row pair, one 16-byte vector; planes w*nf - s*K ...) from the
-//      shared ring;
-//   2. wait for its own staging copies of the planes step w+1 reads; block barrier (A);
-//   3. push the results of its edge tasks to the neighbours (st.async, the neighbour's halo
-//      mbarrier of step w); arm this block's halo mbarrier for step w+1;
-//   4. write back (16-byte loads and stores) the planes the top level finished in step w;
-//   5. stage (cp.async) the planes first read at step w + L into the ring;
-//   6. wait (bounded) until the neighbours' halo bytes of step w have arrived.
-// A block can therefore run at most one step ahead of a neighbour; pushes are issued after the
-// pusher's own reads of that step are done (barrier A), so a push never overwrites a value its
-// receiver still reads, and a plane's staging copy completes (step 2 of the step before it is
-// first read) before any neighbour can push into it.
+// Warp roles.  The computing warps own tasks (level s, row pair y0/y0+1, one 16-byte vector of
+// columns) for the whole tile; a task keeps planes z-1 and z of its two rows in registers and per
+// plane reads plane z+1 of its rows, rows y0-1 and y0+2 of plane z and the two x neighbours of
+// each row from shared memory, and writes two 16-byte vectors.  A value that no later level of
+// the tile overwrites (level t + 2 does not cover the row) is final: the task also stores it to
+// global memory, so there is no separate write-back pass and the halo is never written.  The last
+// warp stages planes with the bulk-copy (TMA) engine: one tensor copy per buffer and plane (a box
+// of YW rows x XT columns, the slab and its halo), completing on one of eight load mbarriers
+// (global step modulo 8), LEAD steps ahead of use.  Step w (named barriers FULL and DONE):
+//   computing warps:  wait FULL(w); update and store; proxy fence (results -> later bulk copies
+//     into the same slots); arrive DONE(w)
+//   mover, iteration w (overlapping the computing warps' step w):  wait DONE(w-1); stage the
+//     plane first read at step w+L; wait for the staging of step w+2 and for the neighbours'
+//     halo bytes of step w; arrive FULL(w+1).
+// Staging two steps ahead of need means a plane has landed before any neighbour (at most one
+// step ahead) can push into it.
 //
-// Staging lead L (A.lead, 3..8 steps): the host takes the deepest lead whose ring keeps as many
-// blocks per SM as the shallowest; at a few hundred nanoseconds per step a plane needs several
-// steps to arrive from HBM.  Ring depth: a slot is restaged (step 5) once its previous plane is
-// below every level's read window and its write-back (step 4 of an earlier step) is done:
-//     NZ = max(L nf + 2R, (L + 1) nf + R) + smax K,   K = R + nf, smax = H - 2.
+// Ring depth: a slot is restaged once its previous plane is below every level's read window in
+// the step being computed:  NZ = L + 2R + 1 + smax K,  K = R + 1, smax = H - 2,  L = lead (3..8).
+// Planes are padded to 128 bytes (the tensor copies' destination alignment).
 //
 // Radius-1 first-order stencils (7-point constant, 7-point variable, red-black Gauss-Seidel) on
 // rows of 16-byte multiples with 16-byte aligned buffers.  Every point goes through point_update
@@ -40,21 +44,6 @@
 #include "mwd_kernel.cuh"
 
 namespace girih {
-
-
-// Wait until at most n (0..7) of this thread's committed cp.async groups are still pending.
-__device__ __forceinline__ void cp_async_wait_pending(int n) {
-  switch (n) {
-    case 0: cp_async_wait_group<0>(); break;
-    case 1: cp_async_wait_group<1>(); break;
-    case 2: cp_async_wait_group<2>(); break;
-    case 3: cp_async_wait_group<3>(); break;
-    case 4: cp_async_wait_group<4>(); break;
-    case 5: cp_async_wait_group<5>(); break;
-    case 6: cp_async_wait_group<6>(); break;
-    default: cp_async_wait_group<7>(); break;
-  }
-}
 
 // Accessor of one point of a task: row ROW (0: y0, 1: y0+1) and column I of the vector (both
 // compile-time after unrolling, so every access is a register):
@@ -131,7 +120,7 @@ template <int ID>
 __device__ __forceinline__ void nbar_sync(int n) { asm volatile("bar.sync %0, %1;" ::"n"(ID), "r"(n) : "memory"); }
 template <int ID>
 __device__ __forceinline__ void nbar_arrive(int n) { asm volatile("bar.arrive %0, %1;" ::"n"(ID), "r"(n) : "memory"); }
-// The block's barriers between its computing warps and its two movers: FULL(w) (inputs of step w
+// The block's barriers between its computing warps and its mover warp: FULL(w) (inputs of step w
 // ready, ids 1-2 by step parity) and DONE(w) (step w computed, ids 3-4).  Alternating ids keep a
 // producer's arrival for step w+1 from counting towards step w.
 __device__ __forceinline__ void sync_full(int w, int n) {
@@ -150,9 +139,13 @@ __device__ __forceinline__ void arrive_done(int w, int n) {
   if (w & 1) nbar_arrive<4>(n);
   else nbar_arrive<3>(n);
 }
-constexpr int kMovers = 64;  // the block's last two warps move data; the others compute
+constexpr int kMovers = 32;  // the block's last warp moves data; the others compute
+constexpr int kLoadBars = 8;  // mbarriers of the staging copies, by global step modulo 8 (lead <= 8)
 
-// One tile (diamond (a, a - rho), this block's x slab) from staging to write-back.
+
+__device__ __forceinline__ void fence_proxy_async_shared() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+__device__ __forceinline__ void fence_proxy_async_global() { asm volatile("fence.proxy.async.global;" ::: "memory"); }
+
 // Halo pushes a block receives per step: from its left neighbour if that one's slab is full (it
 // then pushes its last column), from its right neighbour if it has columns (its first column).
 __device__ __forceinline__ int halo_senders(int nx, int XW, int C, int rank) {
@@ -160,8 +153,33 @@ __device__ __forceinline__ int halo_senders(int nx, int XW, int C, int rank) {
   return ((C > 1 && rank > 0 && nx - (x0 - XW) >= XW) ? 1 : 0) + ((C > 1 && rank < C - 1 && nx - (x0 + XW) > 0) ? 1 : 0);
 }
 
-// gstep: wavefront steps the block has run in earlier tiles of this launch; the two halo
-// mbarriers (initialised once per launch) serve global steps of their parity, one phase each.
+// Tensor copy of box (x, y, z) of a 3D tensor map into shared memory, completing on mbar.  x may
+// be negative or past the end (filled with zeros); x * element size is a multiple of 16 bytes.
+__device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* tm, int x, int y, int z, uint64_t* mbar) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], "
+      "[%5];" ::"r"(smem_addr(dst)),
+      "l"(reinterpret_cast<uint64_t>(tm)), "r"(x), "r"(y), "r"(z), "r"(smem_addr(mbar))
+      : "memory");
+}
+
+// Bounded wait of all lanes of a warp on an mbarrier phase; a timeout sets the error word.
+__device__ __forceinline__ void warp_wait_phase(uint32_t mb, uint32_t parity, int* err) {
+  if (!mbar_try_wait_cluster(mb, parity)) {
+    const uint64_t t0 = global_ns();
+    while (!mbar_try_wait_cluster(mb, parity)) {
+      if (global_ns() - t0 > kMbarWaitNs) {
+        atomicOr(err, GIRIH_ETIMEOUT);
+        break;
+      }
+    }
+  }
+  __syncwarp();
+}
+
+// One tile (diamond (a, a - rho), this block's x slab) from staging to write-back.  gstep: wavefront
+// steps the block has run in earlier tiles of this launch; the halo and load mbarriers serve
+// global steps in turn (halo: by parity, loads: modulo kLoadBars), one phase per step.
 template <int S, typename T, int G>
 __device__ __forceinline__ void mwd_async_tile(const MwdArgs& A, const int rho, const int a, int& gstep) {
   static_assert(Traits<S>::R == 1 && !Traits<S>::ORDER2 && !Traits<S>::BOX, "radius-1 first-order stencils");
@@ -171,19 +189,18 @@ __device__ __forceinline__ void mwd_async_tile(const MwdArgs& A, const int rho, 
   constexpr int A16 = 16 / (int)sizeof(T);
   constexpr int VX = A16;  // one 16-byte vector per task
   constexpr int HM = A16;  // shared column of the slab's first column (R rounded up to 16 bytes)
-  using V16 = typename std::conditional<sizeof(T) == 4, float4, double2>::type;
   extern __shared__ __align__(128) unsigned char smem_raw[];
   T* sm = reinterpret_cast<T*>(smem_raw);
   const int NZ = A.NZ, YW = A.YW, XT = A.XT, XW = A.XW, C = A.C, K = A.K;
   const int L = A.lead;  // steps between a plane's staging and its first use
-  const int pe = YW * XT;
+  const int pe = A.PE;  // elements per plane slot: YW * XT rounded up to 128 bytes
   const int be = NZ * pe;
   const int ring = be;
   uint64_t* hb = reinterpret_cast<uint64_t*>(smem_raw + (((size_t)2 * be * sizeof(T) + 15) / 16) * 16);
-  int* lev_lo = reinterpret_cast<int*>(hb + 2);
+  uint64_t* lb = hb + 2;
+  int* lev_lo = reinterpret_cast<int*>(lb + kLoadBars);
   int* lev_w = lev_lo + A.H;
   int* lev_pp = lev_w + A.H;
-  int* row_mask = lev_pp + A.H + 1;
 
   const int nx = (int)A.g.nx, ny = (int)A.g.ny, nz = (int)A.g.nz;
   const int ldx = (int)A.g.ldx;
@@ -206,11 +223,13 @@ __device__ __forceinline__ void mwd_async_tile(const MwdArgs& A, const int rho, 
   const int NT = blockDim.x, tid = threadIdx.x;
   const int NTc = NT - kMovers;
   const bool mover = tid >= NTc;
-  const int mtid = tid - NTc;
+  const int lane = tid & 31;
   const int npush_in = halo_senders(nx, XW, C, rank);
   const uint32_t hb0 = smem_addr(&hb[0]);
-  const int g0 = gstep;  // global step of this tile's step 0
+  const uint32_t lb0 = smem_addr(&lb[0]);
+  const int g0 = gstep;         // global step of this tile's step 0
   const int W = nz + smax * K;  // wavefront steps (one plane per level and step)
+  gstep += W;
 
   if (tid == 0) {
     int acc = 0;
@@ -225,23 +244,6 @@ __device__ __forceinline__ void mwd_async_tile(const MwdArgs& A, const int rho, 
     }
     lev_pp[nlev] = acc;
   }
-  gstep += W;
-  for (int yy = tid; yy < YW; yy += NT) {
-    const int y = Y0 + yy;
-    int m = 0;
-    if (y >= 0 && y < ny && y >= P0 && y < P0 + dw) {
-      int cnt = 0, par = 0;
-      for (int s = 0; s < nlev; ++s) {
-        const int t = tb + s;
-        if (y >= lev_lo_of(a, b, dw, R, t) && y < lev_hi_of(a, b, dw, R, t)) {
-          ++cnt;
-          par = (t + 1) & 1;
-        }
-      }
-      m = (cnt >= 2) ? 3 : (cnt == 1 ? (1 << par) : 0);
-    }
-    row_mask[yy] = m;
-  }
   __syncthreads();
   // halo bytes one neighbour pushes in step w: one element per row of every level whose plane of
   // step w lies in [0, nz)
@@ -253,65 +255,37 @@ __device__ __forceinline__ void mwd_async_tile(const MwdArgs& A, const int rho, 
     }
     return n * (uint32_t)npush_in * (uint32_t)sizeof(T);
   };
-  // arm the phases of steps 0 and 1 (the previous tile waited for every phase it used)
-  if (mtid == 0 && npush_in) {
-    mbar_expect_tx(&hb[g0 & 1], halo_bytes(0));
-    if (W > 1) mbar_expect_tx(&hb[(g0 + 1) & 1], halo_bytes(1));
-  }
 
-  // ---- movers: staging (both buffers, rows [ylo, yhi), 16-byte chunks [cb, ce)) and write-back
-  //      (rows of the projection, owned chunks); (row, chunk) spread over the 64 mover threads ----
-  const int ylo = max(Y0, -R), yhi = min(Y0 + YW, ny + R);
-  const int nrow = active ? max(yhi - ylo, 0) : 0;
-  const int cb = max(pc0 - HM, 0), ce = min(pc0 + XW + HM, ldx);
-  const int nch = active ? max((ce - cb) / A16, 0) : 0;
-  const int wy0 = max(P0, 0), wy1 = min(P0 + dw, ny);
-  const int wcend = min(pc0 + XW, ldx);
-  const int nchw = active ? max((wcend - pc0) / A16, 0) : 0;
-  const int s_rpp = nch > 0 ? max(1, kMovers / nch) : 1;  // rows per pass
-  const int s_r0 = nch > 0 ? (nch <= kMovers ? mtid / nch : 0) : 1 << 30;
-  const int s_c0 = nch > 0 ? (nch <= kMovers ? mtid % nch : mtid) : 0;
-  const int s_cs = nch <= kMovers ? (nch > 0 ? nch : 1) : kMovers;
-  const int w_rpp = nchw > 0 ? max(1, kMovers / nchw) : 1;
-  const int w_r0 = nchw > 0 ? (nchw <= kMovers ? mtid / nchw : 0) : 1 << 30;
-  const int w_c0 = nchw > 0 ? (nchw <= kMovers ? mtid % nchw : mtid) : 0;
-  const int w_cs = nchw <= kMovers ? (nchw > 0 ? nchw : 1) : kMovers;
-  const T* gb0 = static_cast<const T*>(A.buf0);
-  const T* gb1 = static_cast<const T*>(A.buf1);
-  T* go0 = static_cast<T*>(A.buf0);
-  T* go1 = static_cast<T*>(A.buf1);
-  auto stage = [&](int z) {  // movers: plane z of both buffers into its ring slot
-    if (z < -R || z >= nz + R || s_r0 >= s_rpp) return;
-    const int slot = (z + R) % NZ;
-    const int64_t zo = (int64_t)(z + R) * gplane;
-    for (int rr = s_r0; rr < 2 * nrow; rr += s_rpp) {
-      const int p = rr >= nrow;
-      const int y = ylo + rr - p * nrow;
-      const T* src = (p ? gb1 : gb0) + zo + (int64_t)(y + R) * ldx + cb;
-      T* dst = sm + p * be + slot * pe + (y - Y0) * XT + (cb - (pc0 - HM));
-      for (int ch = s_c0; ch < nch; ch += s_cs) cp_async16_cg(dst + ch * A16, src + ch * A16);
-    }
-  };
-  auto write_back = [&](int z) {  // movers: the masked rows of plane z, owned columns
-    if (z < 0 || z >= nz || w_r0 >= w_rpp) return;
-    const int slot = (z + R) % NZ;
-    const int64_t zo = (int64_t)(z + R) * gplane;
-    for (int yy = wy0 - Y0 + w_r0; yy < wy1 - Y0; yy += w_rpp) {
-      const int m = row_mask[yy];
-      const int64_t go = zo + (int64_t)(Y0 + yy + R) * ldx + pc0;
-      const T* src = sm + slot * pe + yy * XT + HM;
-      for (int ch = w_c0; ch < nchw; ch += w_cs) {
-        if (m & 1) *reinterpret_cast<V16*>(go0 + go + ch * A16) = *reinterpret_cast<const V16*>(src + ch * A16);
-        if (m & 2)
-          *reinterpret_cast<V16*>(go1 + go + ch * A16) = *reinterpret_cast<const V16*>(src + be + ch * A16);
+  // ---- mover: the staging copies of tile step j (planes -R .. R for step 0, plane j + R for step
+  //      j >= 1: the planes level 0 newly reads), both buffers, completing on load mbarrier
+  //      (g0 + j) mod kLoadBars ----
+  const uint32_t box_bytes = (uint32_t)(YW * XT * (int)sizeof(T));
+  auto stage_step = [&](int j) {
+    const int zlo = j == 0 ? -R : j + R, zhi = j + R;
+    int np = 0;
+    for (int z = zlo; z <= zhi; ++z) np += (z >= -R && z < nz + R && active) ? 1 : 0;
+    uint64_t* m = &lb[(g0 + j) % kLoadBars];
+    if (lane == 0) {
+      mbar_expect_tx(m, (uint32_t)np * 2u * box_bytes);
+      for (int z = zlo; z <= zhi; ++z) {
+        if (z < -R || z >= nz + R || !active) continue;
+        const int slot = (z + R) % NZ;
+        tma_load_3d(sm + slot * pe, &A.tm[0], pc0 - HM, Y0 + R, z + R, m);
+        tma_load_3d(sm + be + slot * pe, &A.tm[1], pc0 - HM, Y0 + R, z + R, m);
       }
     }
+    __syncwarp();
+  };
+  auto wait_step = [&](int j) {  // all lanes: the staging of tile step j has landed
+    const int gs = g0 + j;
+    warp_wait_phase(lb0 + (uint32_t)((gs % kLoadBars) * 8), (uint32_t)((gs / kLoadBars) & 1), A.err);
   };
 
   // ---- computing threads: tasks (level s, row pair, 16-byte vector), owned for the tile, each
   //      with a register window of planes z-1 and z of its two rows ----
   int t_in[G], t_out[G], t_z[G], t_po[G], t_fl[G], t_par[G];
   const T* t_k[G];
+  T* t_g[G];
   T t_zm[G][2][VX], t_zc[G][2][VX];
   if (!mover) {
     const int npairs = lev_pp[nlev];
@@ -333,11 +307,18 @@ __device__ __forceinline__ void mwd_async_tile(const MwdArgs& A, const int rho, 
       t_po[g] = (((-s * K + R) % NZ + NZ) % NZ) * pe;
       const int lo = max(0, vlo - xl), hi = min(VX, vhi - xl);
       const bool row1 = valid && (y0 + 1 < lev_lo[s] + lev_w[s]);
+      // a row's value of level t+1 is final in the tile unless level t+2 also updates the row
+      auto covers = [&](int y, int tt) {
+        return tt <= te && y >= max(lev_lo_of(a, b, dw, R, tt), 0) && y < min(lev_hi_of(a, b, dw, R, tt), ny);
+      };
+      const bool fin0 = valid && !covers(y0, t + 2), fin1 = row1 && !covers(y0 + 1, t + 2);
       // bits: 0 valid, 1 second row, 2 push left, 3 push right, 4 partial vector, 5 window
-      // loaded, 8.. lo, 12.. hi
+      // loaded, 6 row y0 final, 7 row y0+1 final, 8.. lo, 12.. hi
       t_fl[g] = (valid ? 1 : 0) | (row1 ? 2 : 0) | ((valid && C > 1 && rank > 0 && xl < R) ? 4 : 0) |
                 ((valid && C > 1 && rank < C - 1 && vhi == XW && xl + VX > XW - R) ? 8 : 0) |
-                ((lo != 0 || hi != VX) ? 16 : 0) | (lo << 8) | (hi << 12);
+                ((lo != 0 || hi != VX) ? 16 : 0) | (fin0 ? 64 : 0) | (fin1 ? 128 : 0) | (lo << 8) | (hi << 12);
+      t_g[g] = static_cast<T*>(((t + 1) & 1) ? A.buf1 : A.buf0) + (int64_t)(-s * K + R) * gplane +
+               (int64_t)(y0 + R) * ldx + (pc0 + xl);
       t_par[g] = (x0 + xl + y0 + t) & 1;
       t_k[g] = NC ? static_cast<const T*>(A.coef) + (int64_t)(-s * K + R) * gplane + (int64_t)(y0 + R) * ldx +
                         (pc0 + xl)
@@ -354,16 +335,17 @@ __device__ __forceinline__ void mwd_async_tile(const MwdArgs& A, const int rho, 
   const uint32_t left_hb = (C > 1 && rank > 0) ? map_to_rank(hb0, rank - 1) : 0u;
   const uint32_t right_hb = (C > 1 && rank < C - 1) ? map_to_rank(hb0, rank + 1) : 0u;
 
-  // ---- prologue: the planes of steps 0 .. L-1 requested (one group per step), those of steps 0
-  //      and 1 waited for ----
+  // ---- prologue (mover): arm the halo phases of steps 0 and 1 (the previous tile waited for
+  //      every phase it used), request the planes of steps 0 .. L-1, wait for steps 0 and 1 ----
   if (mover) {
-    for (int z = -R; z < 1 + R; ++z) stage(z);
-    cp_async_commit();
-    for (int j = 1; j < L; ++j) {
-      stage(j + R);
-      cp_async_commit();
+    if (lane == 0 && npush_in) {
+      mbar_expect_tx(&hb[g0 & 1], halo_bytes(0));
+      if (W > 1) mbar_expect_tx(&hb[(g0 + 1) & 1], halo_bytes(1));
     }
-    cp_async_wait_pending(L - 2);
+    fence_proxy_async_global();  // global data acquired before this tile -> bulk loads
+    for (int j = 0; j < L && j < W; ++j) stage_step(j);
+    wait_step(0);
+    if (W > 1) wait_step(1);
   }
   // all blocks' halo mbarriers are armed, and the first planes visible
   __syncwarp();
@@ -381,6 +363,8 @@ __device__ __forceinline__ void mwd_async_tile(const MwdArgs& A, const int rho, 
         t_po[g] = (po + pe == ring) ? 0 : po + pe;  // the task's plane of step w+1
         const T* kp = t_k[g];
         if constexpr (NC > 0) t_k[g] += gplane;
+        T* gp = t_g[g];
+        t_g[g] += gplane;
         if (!(fl & 1) || z < 0 || z >= nz) continue;
         const T* Vb = sm + t_in[g];
         const T* P = Vb + po;
@@ -430,6 +414,8 @@ __device__ __forceinline__ void mwd_async_tile(const MwdArgs& A, const int rho, 
         if (!(fl & 16)) {
           sts_vec<T, VX>(Ub, r0);
           if (row1) sts_vec<T, VX>(Ub + XT, r1);
+          if (fl & 64) sts_vec<T, VX>(gp, r0);  // final values go to global memory as well
+          if (fl & 128) sts_vec<T, VX>(gp + ldx, r1);
         } else {
           const int lo = (fl >> 8) & 15, hi = (fl >> 12) & 15;
 #pragma unroll
@@ -437,6 +423,8 @@ __device__ __forceinline__ void mwd_async_tile(const MwdArgs& A, const int rho, 
             if (i >= lo && i < hi) {
               Ub[i] = r0[i];
               if (row1) Ub[XT + i] = r1[i];
+              if (fl & 64) gp[i] = r0[i];
+              if (fl & 128) gp[ldx + i] = r1[i];
             }
         }
         if (fl & 12) {  // x-halo pushes of this step (counted on the neighbour's halo mbarrier)
@@ -463,65 +451,50 @@ __device__ __forceinline__ void mwd_async_tile(const MwdArgs& A, const int rho, 
           t_zc[g][1][i] = zp[1][i];
         }
       }
+      fence_proxy_async_shared();  // shared-memory results ordered before later bulk copies into the slots
       __syncwarp();
       arrive_done(w, NT);
     }
   } else {
-    // movers, iteration `it` (overlapping the computation of step `it`): write back the planes
-    // the top level finished in step it-1, stage the planes of step it+L, wait for those of step
-    // it+2 and for the neighbours' halo bytes of step it, then release step it+1
-    for (int it = 0; it <= W; ++it) {
+    for (int it = 0; it < W; ++it) {
       if (it > 0) {
         __syncwarp();
         sync_done(it - 1, NT);
-        write_back(it - 1 - smax * K);
       }
-      if (it == W) break;
-      stage(it + L + R);
-      cp_async_commit();
-      cp_async_wait_pending(L - 2);
-      if (mtid < 32 && npush_in) {  // the first mover warp, all lanes together
+      if (it + L < W) stage_step(it + L);
+      if (it + 2 < W) wait_step(it + 2);
+      if (npush_in) {
         const int gs = g0 + it;
-        const uint32_t mb = hb0 + (uint32_t)((gs & 1) * 8);
-        const uint32_t parity = (uint32_t)((gs >> 1) & 1);
-        if (!mbar_try_wait_cluster(mb, parity)) {
-          const uint64_t t0 = global_ns();
-          while (!mbar_try_wait_cluster(mb, parity)) {
-            if (global_ns() - t0 > kMbarWaitNs) {
-              atomicOr(A.err, GIRIH_ETIMEOUT);
-              break;
-            }
-          }
-        }
-        __syncwarp();
-        // every waiter has seen the phase of step it complete: arm the mbarrier for step it+2
-        if (mtid == 0 && it + 2 < W) mbar_expect_tx(&hb[gs & 1], halo_bytes(it + 2));
+        warp_wait_phase(hb0 + (uint32_t)((gs & 1) * 8), (uint32_t)((gs >> 1) & 1), A.err);
+        // every lane has seen the phase of step it complete: arm the mbarrier for step it+2
+        if (lane == 0 && it + 2 < W) mbar_expect_tx(&hb[gs & 1], halo_bytes(it + 2));
       }
       __syncwarp();
       if (it + 1 < W) arrive_full(it + 1, NT);
     }
-    cp_async_wait_group<0>();
+    __syncwarp();
+    if (W > 0) sync_done(W - 1, NT);
   }
 }
 
 // Persistent kernel: every cluster of a grid that fits the device at once takes diamonds from the
 // FIFO in row-major order and starts one once its two parents in the previous row have published
 // completion (the runtime of Sect. 4.2.3; same protocol as mwd_vec_kernel's persistent mode).  The
-// cluster barrier after a tile orders every block's write-back stores (release) before rank 0
-// publishes the flag.
+// cluster barrier after a tile orders every block's stores of final values (release) before rank
+// 0 publishes the flag.
 template <int S, typename T, int G>
-__global__ void __launch_bounds__(G == 1 ? 640 : (G == 2 ? 512 : 256), 1) mwd_async_kernel(const MwdArgs A) {
+__global__ void __launch_bounds__(G == 1 ? 640 : (G == 2 ? 512 : 256), 1)
+    mwd_async_kernel(const __grid_constant__ MwdArgs A) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
   const int C = A.C;
   const int rank = (C > 1) ? (int)cluster_ctarank() : 0;
-  const size_t ring_bytes = (((size_t)2 * A.NZ * A.YW * A.XT * sizeof(T) + 15) / 16) * 16;
-  int* slot = reinterpret_cast<int*>(smem_raw + ring_bytes + 16) + 3 * A.H + 1 + A.YW;
-  // the two halo mbarriers, initialised once per launch (the first cluster barrier below orders
-  // the initialisation before any neighbour's push)
-  if (threadIdx.x == 0 && halo_senders((int)A.g.nx, A.XW, C, rank) > 0) {
-    uint64_t* hb = reinterpret_cast<uint64_t*>(smem_raw + ring_bytes);
-    mbar_init(&hb[0], 1);
-    mbar_init(&hb[1], 1);
+  const size_t ring_bytes = (((size_t)2 * A.NZ * A.PE * sizeof(T) + 15) / 16) * 16;
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem_raw + ring_bytes);
+  int* slot = reinterpret_cast<int*>(bars + 2 + kLoadBars) + 3 * A.H + 1;
+  // the halo and load mbarriers, initialised once per launch (the first cluster barrier below
+  // orders the initialisation before any neighbour's push or bulk copy)
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < 2 + kLoadBars; ++i) mbar_init(&bars[i], 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   int gstep = 0;

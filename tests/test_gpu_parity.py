@@ -421,8 +421,8 @@ def test_relaxed_persistent_rejections():
     p0 = girih.plan(0, nx, ny, nz, dtype="f32", T=3, ldx=ldx)
     assert not p0.feasible(girih.config(girih.MWD, dw=8, nf=2, cluster=2, threads=256,
                                         variant=girih.RELAXED_PERSISTENT))  # one plane per step
-    assert not p0.feasible(girih.config(girih.MWD, dw=4, nf=1, cluster=2, threads=64,
-                                        variant=girih.RELAXED_PERSISTENT))  # no computing warp
+    assert not p0.feasible(girih.config(girih.MWD, dw=16, nf=1, cluster=2, threads=64,
+                                        variant=girih.RELAXED_PERSISTENT))  # more tasks than 4 per thread
     p = girih.plan(1, nx, ny, nz, dtype="f32", T=3, ldx=ldx)
     assert p.feasible(cfg)
     u, up, co, c = inputs.make_problem(1, nx, ny, nz, seed=2, ldx=ldx)
