@@ -129,8 +129,8 @@ int check_config(const Plan* p, const girih_config* c, int64_t* smem_out, int* x
     return fail(GIRIH_EINVAL, "dw=%d with a %d-wide slab has %d row pairs x %d vectors: more tasks than the %d "
                 "computing threads of a %d-thread block hold (blocks of at most %d, %d, %d threads for 1, 2, 4 tasks "
                 "per thread)", c->dw, XW, mwd_max_pairs(R, c->dw), XW / mwd_vx(p->stencil, p->dtype, mv),
-                c->threads - kAsyncMovers, c->threads, async_max_threads(1), async_max_threads(2),
-                async_max_threads(4));
+                c->threads - kAsyncMovers, c->threads, async_max_threads(1, ncoef_of(p->stencil) > 0), async_max_threads(2, ncoef_of(p->stencil) > 0),
+                async_max_threads(4, ncoef_of(p->stencil) > 0));
   if (G == 0)
     return fail(GIRIH_EINVAL, "dw=%d with a %d-wide slab has %d row pairs x %d column groups: no groups-per-thread "
                 "count fits %d threads within the kernel's launch bound (%d threads for one group per thread)",

@@ -92,8 +92,11 @@ constexpr int kAsyncLeadMin = 3;
 constexpr int kAsyncMovers = 32;    // threads of the RELAXED_PERSISTENT block that move data
 constexpr int kAsyncLoadBars = 8;   // its staging mbarriers (the lead is at most 8)
 constexpr int kAsyncLeadMax = GIRIH_ASYNC_LEAD_MAX;
-// Largest block of the RELAXED_PERSISTENT kernel for G tasks per thread (its launch bound).
-inline int async_max_threads(int G) { return G == 1 ? 640 : (G == 2 ? 512 : 256); }
+// Largest block of the RELAXED_PERSISTENT kernel for G tasks per thread (its launch bound); the
+// variable-coefficient stencils hold a prefetched plane of coefficients per task in registers.
+constexpr int async_max_threads(int G, bool coef) {
+  return coef ? (G == 1 ? 512 : (G == 2 ? 288 : 160)) : (G == 1 ? 640 : (G == 2 ? 512 : 256));
+}
 inline bool mv_shifted(int mv) { return mv != MV_ELEM; }
 MwdShape mwd_shape(int stencil, int dtype, int dw, int nf, int XW, int mv, int lead = kAsyncLeadMin);
 // RELAXED_PERSISTENT: the staging lead for a configuration (see kAsyncLeadMax) and its shape.

@@ -112,7 +112,7 @@ int mwd_pairs_per_thread(int stencil, int dtype, int dw, int XW, int threads, in
   const int64_t ng = (int64_t)mwd_max_pairs(R, dw) * (XW / vx);
   if (mv == MV_ASYNC) {  // the block's last two warps move data; the others compute
     for (int G : {1, 2, 4})
-      if (threads <= async_max_threads(G) && ng <= (int64_t)G * (threads - kAsyncMovers)) return G;
+      if (threads <= async_max_threads(G, ncoef_of(stencil) > 0) && ng <= (int64_t)G * (threads - kAsyncMovers)) return G;
     return 0;
   }
   const int ct = threads;

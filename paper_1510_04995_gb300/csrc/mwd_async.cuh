@@ -78,6 +78,34 @@ __device__ __forceinline__ void task_row(const T (*yr)[VX], const T (*zm)[VX], c
   }
 }
 
+// As TaskAcc, with the coefficients of both rows: kv[g][ROW][i].
+template <typename T, int VX, int ROW, int I>
+struct TaskAcc2 {
+  const T (*yr)[VX];
+  const T (*zm)[VX];
+  const T (*zp)[VX];
+  const T* xm;
+  const T* xp;
+  const T (*kv)[2][VX];
+  __device__ __forceinline__ T c() const { return yr[1 + ROW][I]; }
+  __device__ __forceinline__ T x(int d) const {
+    return d < 0 ? (I == 0 ? xm[ROW] : yr[1 + ROW][I - 1]) : (I == VX - 1 ? xp[ROW] : yr[1 + ROW][I + 1]);
+  }
+  __device__ __forceinline__ T y(int d) const { return yr[1 + ROW + d][I]; }
+  __device__ __forceinline__ T z(int d) const { return d < 0 ? zm[ROW][I] : zp[ROW][I]; }
+  __device__ __forceinline__ T u() const { return T(0); }
+  __device__ __forceinline__ T k(int g) const { return kv[g][ROW][I]; }
+};
+template <int S, typename T, int VX, int ROW, int I>
+__device__ __forceinline__ void task_row2(const T (*yr)[VX], const T (*zm)[VX], const T (*zp)[VX], const T* xm,
+                                          const T* xp, const T (*kv)[2][VX], const T* cst, T* r) {
+  if constexpr (I < VX) {
+    const TaskAcc2<T, VX, ROW, I> acc{yr, zm, zp, xm, xp, kv};
+    r[I] = point_update<S, T>(acc, cst);
+    task_row2<S, T, VX, ROW, I + 1>(yr, zm, zp, xm, xp, kv, cst, r);
+  }
+}
+
 // Coefficient grids 0 .. NC-1 of one row's VX columns: 16-byte read-only loads.
 template <typename T, int VX, int NC>
 __device__ __forceinline__ void load_coef(const T* kp, int64_t gstride, T (*kv)[VX]) {
@@ -91,6 +119,23 @@ __device__ __forceinline__ void load_coef(const T* kp, int64_t gstride, T (*kv)[
       kv[q][0] = k.x; kv[q][1] = k.y;
     }
   }
+}
+
+// Coefficient grids 0 .. NC-1 of two rows (row y0 at kp, row y0+1 at kp + ldx): kv[g][row][i].
+template <typename T, int VX, int NC>
+__device__ __forceinline__ void load_coef_pair(const T* kp, int64_t gstride, int ldx, T (*kv)[2][VX]) {
+  using V16 = typename std::conditional<sizeof(T) == 4, float4, double2>::type;
+#pragma unroll
+  for (int q = 0; q < NC; ++q)
+#pragma unroll
+    for (int r = 0; r < 2; ++r) {
+      const V16 k = __ldg(reinterpret_cast<const V16*>(kp + q * gstride + r * ldx));
+      if constexpr (sizeof(T) == 4) {
+        kv[q][r][0] = k.x; kv[q][r][1] = k.y; kv[q][r][2] = k.z; kv[q][r][3] = k.w;
+      } else {
+        kv[q][r][0] = k.x; kv[q][r][1] = k.y;
+      }
+    }
 }
 
 __device__ __forceinline__ void st_async_push(uint32_t addr, float v, uint32_t mbar) {
@@ -287,6 +332,9 @@ __device__ __forceinline__ void mwd_async_tile(const MwdArgs& A, const int rho, 
   const T* t_k[G];
   T* t_g[G];
   T t_zm[G][2][VX], t_zc[G][2][VX];
+  // coefficient grids of the task's plane, loaded one step ahead (variable-coefficient stencils):
+  // the read-only loads of plane z+1 are in flight while the block synchronises and computes
+  T t_kn[G][NC > 0 ? NC : 1][NC > 0 ? 2 : 1][VX];
   if (!mover) {
     const int npairs = lev_pp[nlev];
     const int nvec = XW / VX;
@@ -394,12 +442,18 @@ __device__ __forceinline__ void mwd_async_tile(const MwdArgs& A, const int rho, 
           yr[2][i] = t_zc[g][1][i];
         }
         T r0[VX], r1[VX];
-        T kv[NCO][VX];
-        // row by row, so that only one row's coefficients are live at a time
-        if constexpr (NC > 0) load_coef<T, VX, NC>(kp, gstride, kv);
-        task_row<S, T, VX, 0, 0>(yr, t_zm[g], zp, xm, xp, kv, cst, r0);
-        if constexpr (NC > 0) load_coef<T, VX, NC>(kp + ldx, gstride, kv);
-        task_row<S, T, VX, 1, 0>(yr, t_zm[g], zp, xm, xp, kv, cst, r1);
+        if constexpr (NC > 0) {
+          if (!(fl & 32)) load_coef_pair<T, VX, NC>(kp, gstride, ldx, t_kn[g]);  // first plane: not prefetched
+          task_row2<S, T, VX, 0, 0>(yr, t_zm[g], zp, xm, xp, t_kn[g], cst, r0);
+          task_row2<S, T, VX, 1, 0>(yr, t_zm[g], zp, xm, xp, t_kn[g], cst, r1);
+          // prefetch the next plane's coefficients: consumed in the next step, so the loads are in
+          // flight while the block finishes this step and synchronises
+          if (z + 1 < nz) load_coef_pair<T, VX, NC>(kp + gplane, gstride, ldx, t_kn[g]);
+        } else {
+          T kv[1][VX];
+          task_row<S, T, VX, 0, 0>(yr, t_zm[g], zp, xm, xp, kv, cst, r0);
+          task_row<S, T, VX, 1, 0>(yr, t_zm[g], zp, xm, xp, kv, cst, r1);
+        }
         if constexpr (Traits<S>::RB) {
           // red-black: only points with (x + y + z + t) even are updated (row y0+1 has the other
           // colour); the others keep their value
@@ -483,7 +537,7 @@ __device__ __forceinline__ void mwd_async_tile(const MwdArgs& A, const int rho, 
 // cluster barrier after a tile orders every block's stores of final values (release) before rank
 // 0 publishes the flag.
 template <int S, typename T, int G>
-__global__ void __launch_bounds__(G == 1 ? 640 : (G == 2 ? 512 : 256), 1)
+__global__ void __launch_bounds__(async_max_threads(G, Traits<S>::NCOEF > 0), 1)
     mwd_async_kernel(const __grid_constant__ MwdArgs A) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
   const int C = A.C;
@@ -496,6 +550,10 @@ __global__ void __launch_bounds__(G == 1 ? 640 : (G == 2 ? 512 : 256), 1)
   if (threadIdx.x == 0) {
     for (int i = 0; i < 2 + kLoadBars; ++i) mbar_init(&bars[i], 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (threadIdx.x == blockDim.x - 1) {  // the mover's tensor-map descriptors, fetched once
+    asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&A.tm[0])) : "memory");
+    asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&A.tm[1])) : "memory");
   }
   int gstep = 0;
   for (;;) {

@@ -148,7 +148,7 @@ std::vector<girih_config> candidates(Plan* p) {
         int last = 0;
         for (int G : {1, 2, 4}) {
           const int th = (int)std::max<int64_t>(32, (tasks + 32LL * G - 1) / (32LL * G) * 32) + kAsyncMovers;
-          if (th == last || th > async_max_threads(G)) continue;
+          if (th == last || th > async_max_threads(G, ncoef_of(p->stencil) > 0)) continue;
           last = th;
           girih_config c{GIRIH_ALGO_MWD, dw, 1, C, th, GIRIH_RELAXED_PERSISTENT};
           if (check_config(p, &c, nullptr, nullptr, nullptr) == GIRIH_OK) out.push_back(c);

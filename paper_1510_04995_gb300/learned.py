@@ -26,8 +26,8 @@ import time
 
 import numpy as np
 
-from . import (F32, F64, FED, FED_BULK, MLP_FEATURES, MWD, NAIVE, RELAXED, Config, TuneRow, check,
-               config, config_array, lib, plan)
+from . import (F32, F64, FED, FED_BULK, MLP_FEATURES, MWD, NAIVE, RADIUS, RELAXED, RELAXED_PERSISTENT, Config,
+               TuneRow, check, config, config_array, lib, model_code_balance, plan)
 
 # The 12 non-cubic grids of the learned-tuner sweep (nx, ny, nz), and the held-out ones (#3, #7, #10).
 GRIDS = [(128, 256, 512), (256, 128, 512), (192, 384, 512), (256, 512, 512), (384, 256, 512),
@@ -42,11 +42,24 @@ def _dt(d):
     return {"f64": F64, "f32": F32, F64: F64, F32: F32}[d]
 
 
+def aligned_ldx(stencil, nx, dtype) -> int:
+    """The leading dimension the experiment uses: nx + 2R rounded up to 16 bytes (the layout the
+    vector, bulk-copy and neighbour-synchronised paths of the blocked sweep take)."""
+    a16 = 16 // (8 if _dt(dtype) == F64 else 4)
+    return -(-(nx + 2 * RADIUS[stencil]) // a16) * a16
+
+
+def problem_plan(stencil, dtype, nx, ny, nz, T):
+    return plan(stencil, nx, ny, nz, dtype=dtype, T=T, ldx=aligned_ldx(stencil, nx, dtype))
+
+
 def space(p) -> list:
     """The experiment's search space for a plan: the naive sweep and the feasible blocked sweeps
     with diamond widths 2R, 4R, 8R, 16R, wavefront widths 1 and 2, clusters 1, 4, 8, 16, 256 or
     512 threads, and the FED / FED_BULK data paths (RELAXED where the cluster has more than one
-    block, with 512 threads)."""
+    block, with 512 threads); plus the neighbour-synchronised persistent sweep (RELAXED_PERSISTENT)
+    for the same diamond widths and clusters 4, 8, 16, in the block sizes the tuner enumerates for
+    it (the tile's tasks at 1, 2 or 4 per computing thread)."""
     R = p.R
     out = [config(NAIVE, 0, 1, 1, 256, FED)]
     for dw in (2 * R, 4 * R, 8 * R, 16 * R):
@@ -58,6 +71,13 @@ def space(p) -> list:
                         c = config(MWD, dw, nf, cl, th, v)
                         if p.feasible(c):
                             out.append(c)
+    n = ctypes.c_int32()
+    check(lib().girih_tune_candidates(p.handle, None, 0, ctypes.byref(n)))
+    if n.value:
+        arr = (Config * n.value)()
+        check(lib().girih_tune_candidates(p.handle, arr, n.value, ctypes.byref(n)))
+        out += [c for c in arr if c.variant == RELAXED_PERSISTENT and c.dw in (2 * R, 4 * R, 8 * R, 16 * R)
+                and c.cluster in (4, 8, 16)]
     return out
 
 
@@ -65,7 +85,7 @@ def collect(db_path: str, problems, T: int = 16, tol: float = 0.05, max_steps: i
             log=print):
     """Exhaustively tune every (stencil, dtype, nx, ny, nz) problem over space(); rows go to db_path."""
     for (stencil, dtype, nx, ny, nz) in problems:
-        p = plan(stencil, nx, ny, nz, dtype=dtype, T=T)
+        p = problem_plan(stencil, dtype, nx, ny, nz, T)
         best = TuneRow()
         nm = ctypes.c_int32()
         arr, n = config_array(space(p))
@@ -190,6 +210,65 @@ def evaluate(rows, scores: np.ndarray, k: int):
     return out
 
 
+# domain-sized streams N_D of the code-balance model (Eq. 5) and spatial minimum elements per LUP
+_ND = {0: 2, 1: 9, 2: 2, 3: 15, 4: 3, 5: 2, 6: 2}
+_SPATIAL = {0: 2, 1: 9, 2: 3, 3: 16, 4: 4, 5: 2, 6: 2}
+
+
+def model_bytes(r) -> float:
+    """Bytes per LUP a candidate moves by the paper's models: the spatial minimum for the naive
+    sweep, Eq. 5's code balance B_C for a blocked one."""
+    s = int(r["stencil"])
+    elem = 8 if int(r["dtype"]) == F64 else 4
+    if int(r["algo"]) == NAIVE:
+        return float(_SPATIAL[s] * elem)
+    return model_code_balance(int(r["dw"]), RADIUS[s], _ND[s], elem)
+
+
+def baselines(rows, scores: np.ndarray, k: int, draws: int = 2000, seed: int = 7):
+    """The network's top k against the methods without it, per problem: the naive sweep alone
+    ("always naive"), the k candidates the code-balance model ranks cheapest (ties kept in the
+    tuner's order), and k candidates drawn at random (mean over `draws` seeded draws of the best
+    of k).  Each method: fraction of the exhaustive best and fraction of the exhaustive tuning
+    time spent measuring its candidates."""
+    rng = np.random.default_rng(seed)
+    out = []
+    keys = [problem_key(r) for r in rows]
+    for key in sorted(set(keys)):
+        idx = [i for i, kk in enumerate(keys) if kk == key]
+        g = np.array([rows[i]["glups"] for i in idx])
+        cost = np.array([rows[i]["tune_seconds"] for i in idx])
+        best, total = g.max(), cost.sum()
+        net = np.argsort(-scores[idx], kind="stable")[:k]
+        mb = np.array([model_bytes(rows[i]) for i in idx])
+        mod = np.argsort(mb, kind="stable")[:k]
+        naive = [j for j, i in enumerate(idx) if int(rows[i]["algo"]) == NAIVE]
+        kk = min(k, len(idx))
+        rnd = [rng.choice(len(idx), kk, replace=False) for _ in range(draws)]
+        out.append({"problem": key, "candidates": len(idx),
+                    "network": {"ratio": float(g[net].max() / best), "cost_fraction": float(cost[net].sum() / total)},
+                    "model_top_k": {"ratio": float(g[mod].max() / best), "cost_fraction": float(cost[mod].sum() / total)},
+                    "always_naive": ({"ratio": float(g[naive].max() / best),
+                                      "cost_fraction": float(cost[naive].sum() / total)} if naive else None),
+                    "random_k": {"ratio": float(np.mean([g[c].max() for c in rnd]) / best),
+                                 "cost_fraction": float(np.mean([cost[c].sum() for c in rnd]) / total)}})
+    return out
+
+
+def summarize(res):
+    """Worst and mean fraction of the exhaustive best, and the total measurement-time fraction, per
+    method of baselines()."""
+    out = {}
+    for m in ("network", "model_top_k", "always_naive", "random_k"):
+        vals = [r[m] for r in res if r.get(m)]
+        if not vals:
+            continue
+        out[m] = {"worst_ratio": min(v["ratio"] for v in vals), "mean_ratio": float(np.mean([v["ratio"] for v in vals])),
+                  "problems_at_95pct": sum(v["ratio"] >= 0.95 for v in vals), "problems": len(vals),
+                  "mean_cost_fraction": float(np.mean([v["cost_fraction"] for v in vals]))}
+    return out
+
+
 def tune(p, params: np.ndarray, k: int = 5, tol: float = 0.05, max_steps: int = 32):
     """Live learned tuning of a plan: returns (TuneRow, measured count, seconds)."""
     import torch
@@ -234,7 +313,7 @@ def experiment(out_dir: str, stencils=(0, 1, 2, 3), dtypes=("f64", "f32"), grids
     base = []
     for key in sorted({problem_key(r) for r in test_rows}):
         s, d, nx, ny, nz = key
-        p = plan(s, nx, ny, nz, dtype=d, T=T)
+        p = problem_plan(s, d, nx, ny, nz, T)
         dflt = p.config.as_dict()
         rs = [r for r in test_rows if problem_key(r) == key]
         best = max(r["glups"] for r in rs)
@@ -246,15 +325,23 @@ def experiment(out_dir: str, stencils=(0, 1, 2, 3), dtypes=("f64", "f32"), grids
         for key in sorted({problem_key(r) for r in test_rows}):
             s, d, nx, ny, nz = key
             rs = [r for r in test_rows if problem_key(r) == key]
-            p = plan(s, nx, ny, nz, dtype=d, T=T)
+            p = problem_plan(s, d, nx, ny, nz, T)
             row, nm, secs = tune(p, params, k=k, tol=tol, max_steps=max_steps)
             exh_secs = sum(r["tune_seconds"] for r in rs)
             live_res.append({"problem": key, "learned_glups": row.glups, "measured": nm, "seconds": secs,
                              "exhaustive_best": max(r["glups"] for r in rs), "exhaustive_seconds": exh_secs})
             p.close()
+    test_scores = predict(params, features(test_rows)) if test_rows else np.zeros(0)
+    cmp_all = baselines(test_rows, test_scores, k) if test_rows else []
+    # the blocked sub-space alone (the winner varies with the problem there): the network ranks
+    # only the blocked candidates
+    bl = [i for i, r in enumerate(test_rows) if int(r["algo"]) == MWD]
+    blocked_rows = [test_rows[i] for i in bl]
+    cmp_blocked = baselines(blocked_rows, test_scores[bl], k) if bl else []
     report = {"train_problems": len({problem_key(r) for r in train_rows}), "train_rows": len(train_rows),
               "train_seconds": train_s, "loss_history": hist, "k": k, "offline": res, "default": base,
-              "live": live_res}
+              "live": live_res, "baselines": cmp_all, "baselines_summary": summarize(cmp_all),
+              "blocked_only": cmp_blocked, "blocked_only_summary": summarize(cmp_blocked)}
     with open(os.path.join(out_dir, "report.json"), "w") as f:
         json.dump(report, f, indent=1)
     return report
@@ -281,7 +368,7 @@ def unseen(out_dir: str, params_path: str, stencils=(4, 5, 6), dtypes=("f64", "f
     for key in sorted({problem_key(r) for r in rows}):
         s, d, nx, ny, nz = key
         rs = [r for r in rows if problem_key(r) == key]
-        p = plan(s, nx, ny, nz, dtype=d, T=T)
+        p = problem_plan(s, d, nx, ny, nz, T)
         row, nm, secs = tune(p, params, k=k, tol=tol, max_steps=max_steps)
         live_res.append({"problem": key, "learned_glups": row.glups, "learned_config": row.cfg.as_dict(),
                          "measured": nm, "seconds": secs, "exhaustive_best": max(r["glups"] for r in rs),
@@ -321,4 +408,4 @@ if __name__ == "__main__":
     rep = experiment(a.out_dir, tuple(int(s) for s in a.stencils.split(",")), tuple(a.dtypes.split(",")), gl, a.T,
                      a.tol, a.max_steps, a.k, a.epochs, not a.no_live)
     print(json.dumps({k: rep[k] for k in ("train_problems", "train_rows", "train_seconds", "offline", "default",
-                                          "live")}, indent=1))
+                                          "live", "baselines_summary", "blocked_only_summary")}, indent=1))
