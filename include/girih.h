@@ -97,7 +97,16 @@ typedef enum { GIRIH_ALGO_NAIVE = 0, GIRIH_ALGO_MWD = 1 } girih_algo;
  *              shared memory asynchronously (st.async, counted on an mbarrier).  Radius-1
  *              first-order stencils (7PT_CONST, 7PT_VAR, 7PT_RBGS) on the vector path's
  *              layout (16-byte rows, 16-byte aligned buffers and coefficient grids); EINVAL
- *              otherwise.  Buffers and bounded waits as FED_PERSISTENT.                    */
+ *              otherwise.  Buffers and bounded waits as FED_PERSISTENT.
+ *   OVERLAP_PERSISTENT -- RELAXED_PERSISTENT's schedule, blocks and data movement with no
+ *              exchange between the blocks of a cluster inside a wavefront step: each block
+ *              stages its x slab plus (H-1)R columns per side (rounded up to 16 bytes) and
+ *              updates level s of the diamond over its slab widened by (H-2-s)R columns per
+ *              side, repeating the neighbours' edge columns instead of receiving them (the
+ *              results stay bit-identical).  Before storing final values a block checks that
+ *              both neighbours have staged the planes concerned (progress words in shared
+ *              memory at cluster scope; a bounded wait).  Same stencils,
+ *              layout, alignment and EINVAL rules as RELAXED_PERSISTENT.                   */
 typedef enum {
   GIRIH_FED = 0,
   GIRIH_RELAXED = 1,
@@ -105,7 +114,8 @@ typedef enum {
   GIRIH_FED_ELEM = 3,
   GIRIH_RELAXED_ELEM = 4,
   GIRIH_FED_PERSISTENT = 5,
-  GIRIH_RELAXED_PERSISTENT = 6
+  GIRIH_RELAXED_PERSISTENT = 6,
+  GIRIH_OVERLAP_PERSISTENT = 7
 } girih_variant;
 
 #define GIRIH_OK 0

@@ -21,7 +21,8 @@ HEADER = os.path.join(os.path.dirname(HERE), "include", "girih.h")
 S7C, S7V, S25C, S25V, S25CG, S27B, S7RB = 0, 1, 2, 3, 4, 5, 6
 F64, F32 = 0, 1
 NAIVE, MWD = 0, 1
-FED, RELAXED, FED_BULK, FED_ELEM, RELAXED_ELEM, FED_PERSISTENT, RELAXED_PERSISTENT = 0, 1, 2, 3, 4, 5, 6
+FED, RELAXED, FED_BULK, FED_ELEM, RELAXED_ELEM, FED_PERSISTENT, RELAXED_PERSISTENT, OVERLAP_PERSISTENT = (
+    0, 1, 2, 3, 4, 5, 6, 7)
 RADIUS = {0: 1, 1: 1, 2: 4, 3: 4, 4: 4, 5: 1, 6: 1}
 NCOEF = {0: 0, 1: 7, 2: 0, 3: 13, 4: 1, 5: 0, 6: 0}
 STATUS = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "EKERNEL", 5: "ETIMEOUT", 6: "ENOTIMPL"}

@@ -78,10 +78,18 @@ static int mwd_path(const Plan* p, const girih_config* c, bool ptrs16) {
   const int64_t plane = (p->ny + 2 * p->R) * p->ldx;
   const bool vec = p->bulk_layout && ptrs16 && plane < (1LL << 30);
   if (c->variant == GIRIH_RELAXED_PERSISTENT) return vec ? MV_ASYNC : MV_ELEM;
+  if (c->variant == GIRIH_OVERLAP_PERSISTENT) return vec ? MV_OVL : MV_ELEM;
   return vec ? MV_VEC : MV_ELEM;
 }
 
-static bool persistent_variant(int v) { return v == GIRIH_FED_PERSISTENT || v == GIRIH_RELAXED_PERSISTENT; }
+static bool persistent_variant(int v) {
+  return v == GIRIH_FED_PERSISTENT || v == GIRIH_RELAXED_PERSISTENT || v == GIRIH_OVERLAP_PERSISTENT;
+}
+// variants of the warp-specialised kernels (radius-1 first-order stencils, tensor-map staging)
+static bool tma_variant(int v) { return v == GIRIH_RELAXED_PERSISTENT || v == GIRIH_OVERLAP_PERSISTENT; }
+static const char* variant_name(int v) {
+  return v == GIRIH_OVERLAP_PERSISTENT ? "OVERLAP_PERSISTENT" : "RELAXED_PERSISTENT";
+}
 
 int check_config(const Plan* p, const girih_config* c, int64_t* smem_out, int* xw_out, int* g_out, int* mv_out,
                  bool ptrs16, int* lead_out) {
@@ -91,19 +99,20 @@ int check_config(const Plan* p, const girih_config* c, int64_t* smem_out, int* x
     return GIRIH_OK;
   }
   if (c->algo != GIRIH_ALGO_MWD) return fail(GIRIH_EINVAL, "unknown algo %d", c->algo);
-  if (c->variant < GIRIH_FED || c->variant > GIRIH_RELAXED_PERSISTENT)
+  if (c->variant < GIRIH_FED || c->variant > GIRIH_OVERLAP_PERSISTENT)
     return fail(GIRIH_EINVAL, "unknown variant %d", c->variant);
   if (c->variant == GIRIH_FED_PERSISTENT && mwd_path(p, c, ptrs16) != MV_VEC)
     return fail(GIRIH_EINVAL, "FED_PERSISTENT needs rows of 16-byte multiples and 16-byte aligned buffers");
-  if (c->variant == GIRIH_RELAXED_PERSISTENT) {
+  if (tma_variant(c->variant)) {
+    const char* vn = variant_name(c->variant);
     if (!async_stencil(p->stencil))
-      return fail(GIRIH_EINVAL, "RELAXED_PERSISTENT is built for the radius-1 first-order stencils (7-point "
-                  "constant, 7-point variable, red-black Gauss-Seidel)");
-    if (mwd_path(p, c, ptrs16) != MV_ASYNC)
-      return fail(GIRIH_EINVAL, "RELAXED_PERSISTENT needs rows of 16-byte multiples and 16-byte aligned buffers");
-    if (c->nf != 1) return fail(GIRIH_EINVAL, "RELAXED_PERSISTENT advances one plane per level and step (nf = 1)");
+      return fail(GIRIH_EINVAL, "%s is built for the radius-1 first-order stencils (7-point constant, 7-point "
+                  "variable, red-black Gauss-Seidel)", vn);
+    if (!mv_tma(mwd_path(p, c, ptrs16)))
+      return fail(GIRIH_EINVAL, "%s needs rows of 16-byte multiples and 16-byte aligned buffers", vn);
+    if (c->nf != 1) return fail(GIRIH_EINVAL, "%s advances one plane per level and step (nf = 1)", vn);
     if (c->threads <= kAsyncMovers)
-      return fail(GIRIH_EINVAL, "RELAXED_PERSISTENT needs more than %d threads (two warps move data)", kAsyncMovers);
+      return fail(GIRIH_EINVAL, "%s needs more than %d threads (one warp moves data)", vn, kAsyncMovers);
   }
   if (vec_only(p->stencil) && mwd_path(p, c, ptrs16) == MV_ELEM)
     return fail(GIRIH_EINVAL, "the blocked sweep of the box and red-black stencils needs the vector path: rows of "
@@ -125,6 +134,12 @@ int check_config(const Plan* p, const girih_config* c, int64_t* smem_out, int* x
   const int XW = slab_width(p, c->cluster, mv);
   const int cthreads = c->threads;
   const int G = mwd_pairs_per_thread(p->stencil, p->dtype, c->dw, XW, c->threads, mv);
+  if (G == 0 && mv == MV_OVL)
+    return fail(GIRIH_EINVAL, "dw=%d with a %d-wide slab has %lld tasks on its widened levels: more than the %d "
+                "computing threads of a %d-thread block hold at 1, 2 or 4 per thread (blocks of at most %d, %d, %d "
+                "threads)", c->dw, XW, (long long)mwd_ovl_tasks(R, c->dw, XW, mwd_vx(p->stencil, p->dtype, mv)),
+                c->threads - kAsyncMovers, c->threads, async_max_threads(1, ncoef_of(p->stencil) > 0),
+                async_max_threads(2, ncoef_of(p->stencil) > 0), async_max_threads(4, ncoef_of(p->stencil) > 0));
   if (G == 0 && mv == MV_ASYNC)
     return fail(GIRIH_EINVAL, "dw=%d with a %d-wide slab has %d row pairs x %d vectors: more tasks than the %d "
                 "computing threads of a %d-thread block hold (blocks of at most %d, %d, %d threads for 1, 2, 4 tasks "
@@ -141,12 +156,12 @@ int check_config(const Plan* p, const girih_config* c, int64_t* smem_out, int* x
     return fail(GIRIH_EINVAL, "25-point FP64 tiles allow at most 2 row pairs per thread (registers)");
   if (p->ny > (1 << 28) || p->nx > (1 << 28) || p->nz > (1 << 28))
     return fail(GIRIH_EINVAL, "grid too large for the blocked kernel");
-  const int lead = mv == MV_ASYNC ? mwd_async_lead(p->stencil, p->dtype, c->dw, c->nf, XW, c->threads, G, p->smem_optin)
-                                  : kAsyncLeadMin;
+  const int lead = mv_tma(mv) ? mwd_async_lead(p->stencil, p->dtype, c->dw, c->nf, XW, c->threads, G, p->smem_optin, mv)
+                               : kAsyncLeadMin;
   const MwdShape sh = mwd_shape(p->stencil, p->dtype, c->dw, c->nf, XW, mv, lead);
-  if (mv == MV_ASYNC && sh.XT > 256)
-    return fail(GIRIH_EINVAL, "RELAXED_PERSISTENT stages a slab of %d columns with its halo per tensor copy (at "
-                "most 256): use a larger cluster", sh.XT);
+  if (mv_tma(mv) && sh.XT > 256)
+    return fail(GIRIH_EINVAL, "%s stages a slab of %d columns with its halo per tensor copy (at "
+                "most 256): use a larger cluster", variant_name(c->variant), sh.XT);
   if (sh.smem_bytes > p->smem_optin)
     return fail(GIRIH_EINVAL, "config needs %lld bytes of shared memory per block (device limit %lld)",
                 (long long)sh.smem_bytes, (long long)p->smem_optin);
@@ -281,7 +296,8 @@ int run_sweep(Plan* p, int64_t T, void* u, void* u_prev, const void* coeffs, con
     a.err = p->err;
     a.lead = lead;
     a.PE = sh.PE;
-    if (mv == MV_ASYNC) {
+    a.HMO = sh.HM;
+    if (mv_tma(mv)) {
       const int rc3 = encode_plane_maps(p, u, u_prev, sh.XT, sh.YW, a.tm);
       if (rc3 != GIRIH_OK) return rc3;
     }
@@ -420,9 +436,9 @@ int validate_run(Plan* p, void* u, void* u_prev, const void* coeffs, const girih
     if ((*cfg)->variant == GIRIH_FED_BULK &&
         ((reinterpret_cast<uintptr_t>(u) | reinterpret_cast<uintptr_t>(u_prev)) & 15) != 0)
       return fail(GIRIH_EINVAL, "FED_BULK needs 16-byte aligned buffers");
-    if ((*cfg)->variant == GIRIH_RELAXED_PERSISTENT && nc > 0 && (reinterpret_cast<uintptr_t>(coeffs) & 15) != 0)
-      return fail(GIRIH_EINVAL, "RELAXED_PERSISTENT reads coefficient grids in 16-byte vectors: coeffs must be "
-                  "16-byte aligned");
+    if (tma_variant((*cfg)->variant) && nc > 0 && (reinterpret_cast<uintptr_t>(coeffs) & 15) != 0)
+      return fail(GIRIH_EINVAL, "%s reads coefficient grids in 16-byte vectors: coeffs must be 16-byte aligned",
+                  variant_name((*cfg)->variant));
   } else if ((*cfg)->algo != GIRIH_ALGO_NAIVE) {
     return fail(GIRIH_EINVAL, "unknown algo %d", (*cfg)->algo);
   }

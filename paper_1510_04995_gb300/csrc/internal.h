@@ -62,6 +62,7 @@ struct MwdArgs {
   int* fifo;
   int32_t lead;  // RELAXED_PERSISTENT: steps between a plane's staging and its first use (3..8)
   int32_t PE;    // RELAXED_PERSISTENT: elements per ring slot (YW * XT rounded up to 128 bytes)
+  int32_t HMO;   // OVERLAP_PERSISTENT: staged columns on each side of the slab
   // RELAXED_PERSISTENT: 3D tensor maps of buf0 and buf1 (padded grid, box XT x YW x 1) for the
   // staging copies; the kernel takes MwdArgs as a __grid_constant__ parameter
   alignas(64) CUtensorMap tm[2];
@@ -71,6 +72,7 @@ struct MwdShape {
   int32_t NZ, YW, XT;
   int64_t smem_bytes;
   int32_t PE = 0;  // RELAXED_PERSISTENT: elements per ring slot
+  int32_t HM = 0;  // OVERLAP_PERSISTENT: staged columns on each side of the slab
 };
 // Data paths of the blocked kernel: per-element staging (any layout); 16-byte vectors on a
 // shifted slab partition (rows of 16-byte multiples, 16-byte aligned buffers) moved by cp.async
@@ -78,7 +80,16 @@ struct MwdShape {
 // (FED_BULK).
 // MV_ASYNC: the vector path's partition and data movement with neighbour-only synchronisation
 // and the persistent schedule (RELAXED_PERSISTENT, mwd_async.cuh; radius-1 first-order stencils).
-enum { MV_ELEM = 0, MV_VEC = 1, MV_BULK = 2, MV_ASYNC = 3 };
+// MV_OVL: the same blocks on x slabs widened by the halo every level needs, with no exchange
+// between blocks inside a step (OVERLAP_PERSISTENT, mwd_overlap.cuh).
+enum { MV_ELEM = 0, MV_VEC = 1, MV_BULK = 2, MV_ASYNC = 3, MV_OVL = 4 };
+inline bool mv_tma(int mv) { return mv == MV_ASYNC || mv == MV_OVL; }
+// OVERLAP_PERSISTENT: staged columns on each side of a slab, (H - 1) R rounded up to 16 bytes
+// (the bottom level of an unclipped diamond reads (smax + 1) R = (H - 1) R columns beyond it).
+inline int ovl_margin(int H, int R, int a16) { return ((H - 1) * R + a16 - 1) / a16 * a16; }
+// Its tasks (row pair x 16-byte vector over the widened level ranges) for an unclipped diamond on
+// an interior slab of XW columns.
+int64_t mwd_ovl_tasks(int R, int dw, int XW, int vx);
 // stencils the RELAXED_PERSISTENT kernel is built for
 inline bool async_stencil(int stencil) {
   return stencil == GIRIH_7PT_CONST || stencil == GIRIH_7PT_VAR || stencil == GIRIH_7PT_RBGS;
@@ -100,7 +111,8 @@ constexpr int async_max_threads(int G, bool coef) {
 inline bool mv_shifted(int mv) { return mv != MV_ELEM; }
 MwdShape mwd_shape(int stencil, int dtype, int dw, int nf, int XW, int mv, int lead = kAsyncLeadMin);
 // RELAXED_PERSISTENT: the staging lead for a configuration (see kAsyncLeadMax) and its shape.
-int mwd_async_lead(int stencil, int dtype, int dw, int nf, int XW, int threads, int G, int64_t smem_optin);
+int mwd_async_lead(int stencil, int dtype, int dw, int nf, int XW, int threads, int G, int64_t smem_optin,
+                   int mv = MV_ASYNC);
 // Launch one diamond row: ndiam tiles, each a cluster of a.C blocks of `threads` threads.
 // G = groups per thread (1, 2, 4 or 8), from mwd_pairs_per_thread; mv = data path.
 cudaError_t launch_mwd_row(int stencil, int dtype, const MwdArgs& a, int ndiam, int threads, int G, int mv,

@@ -16,9 +16,11 @@ void* mwd_vec_kernel_box(int dtype, int G, bool tma);
 void* mwd_vec_kernel_rb(int dtype, int G, bool tma);
 
 void* mwd_async_kernel_ptr(int stencil, int dtype, int G);
+void* mwd_ovl_kernel_ptr(int stencil, int dtype, int G);
 
 static void* pick(int stencil, int dtype, int G, int mv) {
   if (mv == MV_ASYNC) return mwd_async_kernel_ptr(stencil, dtype, G);
+  if (mv == MV_OVL) return mwd_ovl_kernel_ptr(stencil, dtype, G);
   if (mv_shifted(mv)) {
     const bool tma = mv == MV_BULK;
     if (stencil == GIRIH_25PT_CGRID) return mwd_vec_kernel_cg(dtype, G, tma);
@@ -37,6 +39,20 @@ MwdShape mwd_shape(int stencil, int dtype, int dw, int nf, int XW, int mv, int l
   const int elem = dtype == GIRIH_F64 ? 8 : 4;
   const int a16 = 16 / elem;
   MwdShape s;
+  if (mv == MV_OVL) {
+    // the MV_ASYNC ring on widened slabs; load mbarriers, progress words (2) and item slot,
+    // level tables (5H+2)
+    const int L = lead;
+    s.HM = ovl_margin(H, R, a16);
+    s.NZ = L + 2 * R + 1 + (H - 2) * K;
+    s.YW = dw + 2 * R;
+    s.XT = XW + 2 * s.HM;
+    const int per128 = 128 / elem;
+    s.PE = (s.YW * s.XT + per128 - 1) / per128 * per128;
+    const int64_t ring = 2LL * s.NZ * s.PE * elem;
+    s.smem_bytes = (ring + 15) / 16 * 16 + 8LL * kAsyncLoadBars + 16 + (5LL * H + 2) * 4;
+    return s;
+  }
   if (mv == MV_ASYNC) {
     // ring (one plane per level and step): a slot is restaged, L steps ahead and while the
     // computing warps run the current step, once its plane is below every level's read window and
@@ -73,10 +89,11 @@ MwdShape mwd_shape(int stencil, int dtype, int dw, int nf, int XW, int mv, int l
   return s;
 }
 
-int mwd_async_lead(int stencil, int dtype, int dw, int nf, int XW, int threads, int G, int64_t smem_optin) {
-  const void* k = mwd_async_kernel_ptr(stencil, dtype, G);
+int mwd_async_lead(int stencil, int dtype, int dw, int nf, int XW, int threads, int G, int64_t smem_optin,
+                   int mv) {
+  const void* k = pick(stencil, dtype, G, mv);
   auto per_sm = [&](int L) {
-    const MwdShape sh = mwd_shape(stencil, dtype, dw, nf, XW, MV_ASYNC, L);
+    const MwdShape sh = mwd_shape(stencil, dtype, dw, nf, XW, mv, L);
     if (sh.smem_bytes > smem_optin) return 0;
     if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh.smem_bytes) != cudaSuccess) {
       cudaGetLastError();
@@ -96,6 +113,17 @@ int mwd_async_lead(int stencil, int dtype, int dw, int nf, int XW, int threads, 
   return kAsyncLeadMin;
 }
 
+int64_t mwd_ovl_tasks(int R, int dw, int XW, int vx) {
+  const int H = dw / R, hm = ovl_margin(H, R, vx), smax = H - 2;
+  int64_t n = 0;
+  for (int k = 1; k < H; ++k) {  // level s = k - 1
+    const int e = (smax - (k - 1)) * R;
+    const int nv = (hm + XW + e + vx - 1) / vx - (hm - e) / vx;
+    n += (int64_t)R * (k < H - k ? k : H - k) * nv;
+  }
+  return n;
+}
+
 // Row pairs of the widest (unclipped) diamond: levels k = 1..H-1 have 2R*min(k, H-k) rows.
 int mwd_max_pairs(int R, int dw) {
   const int H = dw / R;
@@ -110,6 +138,12 @@ int mwd_pairs_per_thread(int stencil, int dtype, int dw, int XW, int threads, in
   const int R = radius_of(stencil);
   const int vx = mwd_vx(stencil, dtype, mv), lbf = mwd_lbf(stencil, dtype, mv);
   const int64_t ng = (int64_t)mwd_max_pairs(R, dw) * (XW / vx);
+  if (mv == MV_OVL) {  // the block's last warp moves data; the others compute
+    const int64_t nt = mwd_ovl_tasks(R, dw, XW, vx);
+    for (int G : {1, 2, 4})
+      if (threads <= async_max_threads(G, ncoef_of(stencil) > 0) && nt <= (int64_t)G * (threads - kAsyncMovers)) return G;
+    return 0;
+  }
   if (mv == MV_ASYNC) {  // the block's last two warps move data; the others compute
     for (int G : {1, 2, 4})
       if (threads <= async_max_threads(G, ncoef_of(stencil) > 0) && ng <= (int64_t)G * (threads - kAsyncMovers)) return G;

@@ -1,0 +1,418 @@
+// Wavefront-diamond sweep on overlapped x slabs (variant OVERLAP_PERSISTENT): the tiling,
+// wavefront, persistent FIFO schedule and warp roles of RELAXED_PERSISTENT (mwd_async.cuh), with
+// the per-step halo exchange between the blocks of a cluster replaced by redundant computation.
+//
+// Slabs.  A tile of H-1 levels (smax = H-2) has its blocks split x into slabs as before, but a
+// block stages its slab plus HM >= (smax+1) R columns on each side (rounded up to 16 bytes) and
+// updates level s over its slab widened by (smax - s) R columns per side: level s reads level s-1
+// only inside the columns level s-1 updated, and the top level covers exactly the slab.  The
+// widened columns repeat work a neighbour does for its own slab (bit for bit the same, since every
+// point goes through point_update); nothing crosses between blocks inside a step, so a wavefront
+// step waits for the block's own results only.  The redundant columns cost (sum over levels of
+// 2 (smax - s) R rounded to vectors) / slab width extra updates: about 13 % for FP32 diamonds of
+// width 8 on 68-column slabs, 2-5 % for FP64 diamonds of width 4.
+//
+// The one cross-block hazard left is write-after-read: a block stores the final values of its own
+// slab to global memory in place, while a neighbour reads those columns, as its widened halo,
+// through its staging copies of the same planes.  Each block therefore publishes to its two
+// neighbours how many of its wavefront steps have landed in shared memory (a progress word in the
+// neighbour's shared memory, stored once the staging copies are seen complete), and before step w
+// the mover checks
+// that both neighbours have staged every plane the block stores final values to in step w.  Final
+// values appear only from the first level that level s+2 no longer covers (sf), so the check needs
+// the neighbours' staging of step w - sf K - R: with the staging lead L the blocks may drift apart
+// by L + sf K steps before one waits, and the check is off the critical path in practice.  A block
+// that is ahead waits for one that is behind, never the reverse, so the cluster cannot deadlock.
+//
+// Tasks (level s, row pair, 16-byte vector) run over the level's widened vector range, pair-major;
+// consecutive lanes hold consecutive vectors of a pair, so a task takes its x neighbours from the
+// neighbouring lanes (shuffles) and reads shared memory only at the ends of a pair's run and of
+// the warp.  Partial vectors occur only at the grid's x boundary.
+#pragma once
+#include "mwd_async.cuh"
+
+namespace girih {
+
+// Publish the block's staging progress `count` (wavefront steps landed, counted over the launch)
+// to the progress word `slot` (0: written by the left neighbour, 1: by the right one) of block
+// `rank` of the cluster.  A relaxed store with no fence: the mover issues it only after its
+// acquiring wait on the load mbarrier has seen the staging copies complete, so the copies' reads
+// of global memory are done before the count can be observed, and the neighbour stores to those
+// columns only after observing it (a release fence here would wait for the block's outstanding
+// global stores of final values on every step).
+__device__ __forceinline__ void publish_progress(uint32_t prog_base, int rank, int slot, uint32_t count) {
+  st_cluster_u32(map_to_rank(prog_base + 4u * (uint32_t)slot, (uint32_t)rank), count);
+}
+
+// One tile (diamond (a, a - rho), this block's widened x slab) from staging to write-back.
+// gstep: wavefront steps the block has run in earlier tiles of this launch (the load mbarriers
+// serve global steps modulo kLoadBars; progress words count global steps).
+template <int S, typename T, int G>
+__device__ __forceinline__ void mwd_ovl_tile(const MwdArgs& A, const int rho, const int a, int& gstep) {
+  static_assert(Traits<S>::R == 1 && !Traits<S>::ORDER2 && !Traits<S>::BOX, "radius-1 first-order stencils");
+  constexpr int R = 1;
+  constexpr int NC = Traits<S>::NCOEF;
+  constexpr int VX = 16 / (int)sizeof(T);  // one 16-byte vector per task
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  T* sm = reinterpret_cast<T*>(smem_raw);
+  const int NZ = A.NZ, YW = A.YW, XT = A.XT, XW = A.XW, C = A.C, K = A.K;
+  const int HM = A.HMO;  // staged columns on each side of the slab (a multiple of VX)
+  const int L = A.lead;
+  const int pe = A.PE;
+  const int be = NZ * pe;
+  const int ring = be;
+  uint64_t* lb = reinterpret_cast<uint64_t*>(smem_raw + (((size_t)2 * be * sizeof(T) + 15) / 16) * 16);
+  int* prog = reinterpret_cast<int*>(lb + kLoadBars);  // [0] left neighbour's progress, [1] right's
+  int* lev_lo = prog + 4;
+  int* lev_w = lev_lo + A.H;
+  int* lev_f = lev_w + A.H;   // first vector of the level's widened range (shared-memory column / VX)
+  int* lev_nv = lev_f + A.H;  // vectors in that range
+  int* lev_tp = lev_nv + A.H;  // tasks of the levels below (H + 1 entries)
+  int* tile_sf = lev_tp + A.H + 1;  // first level with final values
+
+  const int nx = (int)A.g.nx, ny = (int)A.g.ny, nz = (int)A.g.nz;
+  const int ldx = (int)A.g.ldx;
+  const int64_t gplane = A.g.sy * A.g.ldx;
+  const int rank = (C > 1) ? (int)cluster_ctarank() : 0;
+  const int dw = A.dw;
+  const int b = a - rho;
+  const int P0 = a * dw - rho * (dw / 2);
+  const int Y0 = P0 - R;
+  const int pc0 = rank * XW;      // padded column of the slab's first column
+  const int sc0 = pc0 - HM;       // padded column of shared column 0
+  const int cl = R - sc0;         // shared column of interior x = 0
+  const int ch = nx + R - sc0;    // of interior x = nx (exclusive end)
+  const int Hh = A.H / 2;
+  const int tb = max((rho - 1) * Hh + 1, 0);
+  const int te = min((rho + 1) * Hh - 1, A.T - 1);
+  if (tb > te) return;  // uniform over the cluster
+  const int nlev = te - tb + 1, smax = nlev - 1;
+  const int NT = blockDim.x, tid = threadIdx.x;
+  const int NTc = NT - kMovers;
+  const bool mover = tid >= NTc;
+  const int lane = tid & 31;
+  const uint32_t lb0 = smem_addr(&lb[0]);
+  const int g0 = gstep;
+  const int W = nz + smax * K;
+  gstep += W;
+
+  // a row's value of level t+1 is final in the tile unless level t+2 also updates the row
+  auto covers = [&](int y, int tt) {
+    return tt <= te && y >= max(lev_lo_of(a, b, dw, R, tt), 0) && y < min(lev_hi_of(a, b, dw, R, tt), ny);
+  };
+  if (tid == 0) {
+    int acc = 0, sf = nlev;
+    for (int s = 0; s < nlev; ++s) {
+      const int t = tb + s;
+      const int lo = max(lev_lo_of(a, b, dw, R, t), 0);
+      const int hi = min(lev_hi_of(a, b, dw, R, t), ny);
+      const int e = (smax - s) * R;
+      const int c0 = max(HM - e, cl), c1 = min(HM + XW + e, ch);
+      const int f = c0 / VX, nv = c1 > c0 ? (c1 + VX - 1) / VX - f : 0;
+      const int w = max(hi - lo, 0);
+      lev_lo[s] = lo;
+      lev_w[s] = w;
+      lev_f[s] = f;
+      lev_nv[s] = nv;
+      lev_tp[s] = acc;
+      acc += (w + 1) / 2 * nv;
+      if (sf == nlev && w > 0 && (!covers(lo, t + 2) || !covers(hi - 1, t + 2))) sf = s;
+    }
+    lev_tp[nlev] = acc;
+    *tile_sf = sf;
+  }
+  __syncthreads();
+  const int sf = *tile_sf;
+
+  // ---- mover: staging copies of tile step j (planes -R .. R for step 0, plane j + R for step
+  //      j >= 1), both buffers, completing on load mbarrier (g0 + j) mod kLoadBars ----
+  const uint32_t box_bytes = (uint32_t)(YW * XT * (int)sizeof(T));
+  auto stage_step = [&](int j) {
+    const int zlo = j == 0 ? -R : j + R, zhi = j + R;
+    int np = 0;
+    for (int z = zlo; z <= zhi; ++z) np += (z >= -R && z < nz + R) ? 1 : 0;
+    uint64_t* m = &lb[(g0 + j) % kLoadBars];
+    if (lane == 0) {
+      mbar_expect_tx(m, (uint32_t)np * 2u * box_bytes);
+      for (int z = zlo; z <= zhi; ++z) {
+        if (z < -R || z >= nz + R) continue;
+        const int slot = (z + R) % NZ;
+        tma_load_3d(sm + slot * pe, &A.tm[0], sc0, Y0 + R, z + R, m);
+        tma_load_3d(sm + be + slot * pe, &A.tm[1], sc0, Y0 + R, z + R, m);
+      }
+    }
+    __syncwarp();
+  };
+  auto wait_step = [&](int j) {
+    const int gs = g0 + j;
+    warp_wait_phase(lb0 + (uint32_t)((gs % kLoadBars) * 8), (uint32_t)((gs / kLoadBars) & 1), A.err);
+  };
+  const bool has_l = C > 1 && rank > 0, has_r = C > 1 && rank < C - 1;
+  const uint32_t prog_base = smem_addr(prog);
+  // the staging of tile steps 0 .. j has landed: tell the neighbours (their slot 1 / slot 0)
+  auto publish = [&](int j) {
+    if (lane == 0) {
+      if (has_l) publish_progress(prog_base, rank - 1, 1, (uint32_t)(g0 + j + 1));
+      if (has_r) publish_progress(prog_base, rank + 1, 0, (uint32_t)(g0 + j + 1));
+    }
+    __syncwarp();
+  };
+  // step w stores final values to planes up to w - sf K; a neighbour stages plane z in its tile
+  // step max(z - R, 0): wait until both neighbours have landed that step
+  auto check_neighbours = [&](int w) {
+    const int j = max(w - sf * K - R, 0);
+    if ((has_l || has_r) && sf < nlev) wait_counts(prog, has_l, has_r, (uint32_t)(g0 + j + 1), kMbarWaitNs, A.err);
+    __syncwarp();
+  };
+
+  // ---- computing threads: tasks over the widened level ranges, G per thread ----
+  int t_in[G], t_out[G], t_z[G], t_po[G], t_fl[G], t_par[G];
+  const T* t_k[G];
+  T* t_g[G];
+  T t_zm[G][2][VX], t_zc[G][2][VX];
+  T t_kn[G][NC > 0 ? NC : 1][NC > 0 ? 2 : 1][VX];
+  if (!mover) {
+    const int ntask = lev_tp[nlev];
+#pragma unroll
+    for (int g = 0; g < G; ++g) {
+      const int id = tid + g * NTc;
+      const bool valid = id < ntask;
+      int s = 0, pr = 0, xv = 0, loc = 0, nv = 1;
+      if (valid) {
+        while (lev_tp[s + 1] <= id) ++s;
+        nv = lev_nv[s];
+        loc = id - lev_tp[s];
+        pr = loc / nv;
+        xv = lev_f[s] + (loc - pr * nv);
+      }
+      const int xl = xv * VX;  // shared column of the vector
+      const int y0 = valid ? lev_lo[s] + 2 * pr : 0;
+      const int t = tb + s;
+      const int ro = (y0 - Y0) * XT + xl;
+      // tasks without work read a fixed cell inside the slot (the warp loads and shuffles as a
+      // whole while any of its lanes has work)
+      t_in[g] = valid ? (t & 1) * be + ro : XT + VX;
+      t_out[g] = valid ? ((t & 1) ^ 1) * be + ro : XT + VX;
+      t_z[g] = -s * K;
+      t_po[g] = (((-s * K + R) % NZ + NZ) % NZ) * pe;
+      const int lo = max(0, cl - xl), hi = min(VX, ch - xl);
+      const bool row1 = valid && (y0 + 1 < lev_lo[s] + lev_w[s]);
+      const bool own = xl >= HM && xl < HM + XW;  // the vector is in the block's own slab
+      const bool fin0 = valid && own && !covers(y0, t + 2), fin1 = row1 && own && !covers(y0 + 1, t + 2);
+      const int xr = loc - pr * nv;  // position of the vector in its pair's run
+      const bool own_l = xr == 0 || lane == 0;
+      const bool own_r = xr == nv - 1 || lane == 31;
+      // bits: 0 valid, 1 second row, 4 partial vector, 5 window loaded, 6 row y0 final, 7 row
+      // y0+1 final, 8.. lo, 12.. hi, 16 left neighbour from shared memory, 17 right neighbour
+      // from shared memory
+      t_fl[g] = (valid ? 1 : 0) | (row1 ? 2 : 0) | ((lo != 0 || hi != VX) ? 16 : 0) | (fin0 ? 64 : 0) |
+                (fin1 ? 128 : 0) | (lo << 8) | (hi << 12) | (own_l ? (1 << 16) : 0) | (own_r ? (1 << 17) : 0);
+      t_g[g] = static_cast<T*>(((t + 1) & 1) ? A.buf1 : A.buf0) + (int64_t)(-s * K + R) * gplane +
+               (int64_t)(y0 + R) * ldx + (sc0 + xl);
+      t_par[g] = (sc0 - R + xl + y0 + t) & 1;
+      t_k[g] = NC ? static_cast<const T*>(A.coef) + (int64_t)(-s * K + R) * gplane + (int64_t)(y0 + R) * ldx +
+                        (sc0 + xl)
+                  : nullptr;
+    }
+  }
+  T cst[5];
+#pragma unroll
+  for (int i = 0; i < 5; ++i) cst[i] = sizeof(T) == 8 ? static_cast<T>(A.c[i]) : static_cast<T>(A.cf[i]);
+  const int64_t gstride = A.g.gstride;
+
+  // ---- prologue (mover): request the planes of steps 0 .. L-1, wait for steps 0 and 1, publish ----
+  if (mover) {
+    fence_proxy_async_global();  // global data acquired before this tile -> bulk loads
+    for (int j = 0; j < L && j < W; ++j) stage_step(j);
+    wait_step(0);
+    if (W > 1) wait_step(1);
+    publish(W > 1 ? 1 : 0);
+    check_neighbours(0);
+  }
+  __syncwarp();
+  __syncthreads();
+
+  if (!mover) {
+    for (int w = 0; w < W; ++w) {
+      __syncwarp();  // the named barriers are warp-aligned instructions
+      if (w > 0) sync_full(w, NT);
+#pragma unroll
+      for (int g = 0; g < G; ++g) {
+        const int fl = t_fl[g];
+        const int z = t_z[g] + w;
+        const int po = t_po[g];
+        t_po[g] = (po + pe == ring) ? 0 : po + pe;  // the task's plane of step w+1
+        const T* kp = t_k[g];
+        if constexpr (NC > 0) t_k[g] += gplane;
+        T* gp = t_g[g];
+        t_g[g] += gplane;
+        const bool live = (fl & 1) && z >= 0 && z < nz;
+        if (!__any_sync(0xffffffffu, live)) continue;
+        const T* Vb = sm + t_in[g];
+        const T* P = Vb + po;
+        const bool row1 = fl & 2;
+        if (live && !(fl & 32)) {  // first plane of the task: load the window (planes z-1, z)
+          const int pm = (po == 0 ? ring : po) - pe;
+          lds_vec<T, VX>(Vb + pm, t_zm[g][0]);
+          lds_vec<T, VX>(Vb + pm + XT, t_zm[g][1]);
+          lds_vec<T, VX>(P, t_zc[g][0]);
+          lds_vec<T, VX>(P + XT, t_zc[g][1]);
+          t_fl[g] |= 32;
+        }
+        const int pp = (po + pe == ring) ? 0 : po + pe;
+        T yr[4][VX], zp[2][VX], xm[2], xp[2];
+        lds_vec<T, VX>(P - XT, yr[0]);
+        // without a second row, row y0+2 may lie past the tile: read row y0+1 instead
+        lds_vec<T, VX>(P + (row1 ? 2 * XT : XT), yr[3]);
+        lds_vec<T, VX>(Vb + pp, zp[0]);
+        lds_vec<T, VX>(Vb + pp + XT, zp[1]);
+#pragma unroll
+        for (int i = 0; i < VX; ++i) {
+          yr[1][i] = t_zc[g][0][i];
+          yr[2][i] = t_zc[g][1][i];
+        }
+#pragma unroll
+        for (int r = 0; r < 2; ++r) {
+          const T l = __shfl_up_sync(0xffffffffu, yr[1 + r][VX - 1], 1);
+          const T q = __shfl_down_sync(0xffffffffu, yr[1 + r][0], 1);
+          xm[r] = (fl & (1 << 16)) ? P[r * XT - 1] : l;
+          xp[r] = (fl & (1 << 17)) ? P[r * XT + VX] : q;
+        }
+        if (!live) continue;
+        T r0[VX], r1[VX];
+        if constexpr (NC > 0) {
+          if (!(fl & 32)) load_coef_pair<T, VX, NC>(kp, gstride, ldx, t_kn[g]);  // first plane: not prefetched
+          task_row2<S, T, VX, 0, 0>(yr, t_zm[g], zp, xm, xp, t_kn[g], cst, r0);
+          task_row2<S, T, VX, 1, 0>(yr, t_zm[g], zp, xm, xp, t_kn[g], cst, r1);
+          // prefetch the next plane's coefficients: consumed in the next step
+          if (z + 1 < nz) load_coef_pair<T, VX, NC>(kp + gplane, gstride, ldx, t_kn[g]);
+        } else {
+          T kv[1][VX];
+          task_row<S, T, VX, 0, 0>(yr, t_zm[g], zp, xm, xp, kv, cst, r0);
+          task_row<S, T, VX, 1, 0>(yr, t_zm[g], zp, xm, xp, kv, cst, r1);
+        }
+        if constexpr (Traits<S>::RB) {
+          // red-black: only points with (x + y + z + t) even are updated (row y0+1 has the other
+          // colour); the others keep their value
+#pragma unroll
+          for (int i = 0; i < VX; ++i) {
+            const bool odd0 = (t_par[g] + i + z) & 1;
+            if (odd0) r0[i] = yr[1][i];
+            else r1[i] = yr[2][i];
+          }
+        }
+        T* Ub = sm + t_out[g] + po;
+        if (!(fl & 16)) {
+          sts_vec<T, VX>(Ub, r0);
+          if (row1) sts_vec<T, VX>(Ub + XT, r1);
+          if (fl & 64) sts_vec<T, VX>(gp, r0);  // final values of the own slab go to global memory
+          if (fl & 128) sts_vec<T, VX>(gp + ldx, r1);
+        } else {
+          const int lo = (fl >> 8) & 15, hi = (fl >> 12) & 15;
+#pragma unroll
+          for (int i = 0; i < VX; ++i)
+            if (i >= lo && i < hi) {
+              Ub[i] = r0[i];
+              if (row1) Ub[XT + i] = r1[i];
+              if (fl & 64) gp[i] = r0[i];
+              if (fl & 128) gp[ldx + i] = r1[i];
+            }
+        }
+        // slide the window one plane up
+#pragma unroll
+        for (int i = 0; i < VX; ++i) {
+          t_zm[g][0][i] = t_zc[g][0][i];
+          t_zm[g][1][i] = t_zc[g][1][i];
+          t_zc[g][0][i] = zp[0][i];
+          t_zc[g][1][i] = zp[1][i];
+        }
+      }
+      fence_proxy_async_shared();  // shared-memory results ordered before later bulk copies into the slots
+      __syncwarp();
+      arrive_done(w, NT);
+    }
+  } else {
+    for (int it = 0; it < W; ++it) {
+      if (it > 0) {
+        __syncwarp();
+        sync_done(it - 1, NT);
+      }
+      if (it + L < W) stage_step(it + L);
+      if (it + 2 < W) {
+        wait_step(it + 2);
+        publish(it + 2);
+      }
+      if (it + 1 < W) check_neighbours(it + 1);
+      __syncwarp();
+      if (it + 1 < W) arrive_full(it + 1, NT);
+    }
+    __syncwarp();
+    if (W > 0) sync_done(W - 1, NT);
+  }
+}
+
+// Persistent kernel: clusters take diamonds from the FIFO as in mwd_async_kernel (Sect. 4.2.3).
+template <int S, typename T, int G>
+__global__ void __launch_bounds__(async_max_threads(G, Traits<S>::NCOEF > 0), 1)
+    mwd_ovl_kernel(const __grid_constant__ MwdArgs A) {
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  const int C = A.C;
+  const int rank = (C > 1) ? (int)cluster_ctarank() : 0;
+  const size_t ring_bytes = (((size_t)2 * A.NZ * A.PE * sizeof(T) + 15) / 16) * 16;
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem_raw + ring_bytes);
+  int* prog = reinterpret_cast<int*>(bars + kLoadBars);
+  int* slot = prog + 2;
+  // load mbarriers initialised and progress words cleared once per launch (the first cluster
+  // barrier below orders both before any neighbour's write and any bulk copy)
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < kLoadBars; ++i) mbar_init(&bars[i], 1);
+    prog[0] = 0;
+    prog[1] = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (threadIdx.x == blockDim.x - 1) {  // the mover's tensor-map descriptors, fetched once
+    asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&A.tm[0])) : "memory");
+    asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&A.tm[1])) : "memory");
+  }
+  int gstep = 0;
+  for (;;) {
+    if (rank == 0 && threadIdx.x == 0) {
+      const int it = atomicAdd(A.fifo, 1);
+      for (int r = 0; r < C; ++r) st_cluster_u32(map_to_rank(smem_addr(slot), (uint32_t)r), (uint32_t)it);
+    }
+    __syncwarp();
+    cluster_barrier();
+    const int it = *reinterpret_cast<volatile int*>(slot);
+    if (it >= A.n_items) break;
+    const int rho = A.items[2 * it], a = A.items[2 * it + 1];
+    if (rank == 0 && threadIdx.x == 0 && rho > 0) {
+      const int first = A.rows[3 * (rho - 1)], amin = A.rows[3 * (rho - 1) + 1], nd = A.rows[3 * (rho - 1) + 2];
+      const uint64_t t0 = global_ns();
+      const bool gave_up = *reinterpret_cast<volatile int*>(A.err) != 0;
+      for (int d = a - 1; d <= a && !gave_up; ++d) {
+        if (d < amin || d >= amin + nd) continue;
+        const int* f = A.flags + first + (d - amin);
+        int v;
+        for (;;) {
+          asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(f) : "memory");
+          if (v == A.epoch) break;
+          if (global_ns() - t0 > kMbarWaitNs) {
+            atomicOr(A.err, GIRIH_ETIMEOUT);
+            break;
+          }
+        }
+      }
+    }
+    __syncwarp();
+    cluster_barrier();
+    mwd_ovl_tile<S, T, G>(A, rho, a, gstep);
+    __syncwarp();
+    cluster_barrier();
+    if (rank == 0 && threadIdx.x == 0) {
+      asm volatile("fence.acq_rel.gpu;" ::: "memory");
+      asm volatile("st.relaxed.gpu.global.u32 [%0], %1;" ::"l"(A.flags + it), "r"(A.epoch) : "memory");
+    }
+  }
+}
+
+}  // namespace girih

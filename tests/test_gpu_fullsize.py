@@ -97,7 +97,7 @@ def test_sampled_points_against_oracle_cones(workload):
 
 
 @pytest.mark.parametrize("variant", ["NAIVE", "FED", "FED_BULK", "FED_ELEM", "RELAXED", "FED_PERSISTENT",
-                                     "RELAXED_PERSISTENT"])
+                                     "RELAXED_PERSISTENT", "OVERLAP_PERSISTENT"])
 def test_blocked_repeatable_under_load(variant):
     """Repeated large sweeps in each data path, bit for bit against one naive sweep: a staging or
     synchronisation race shows up as a rare, localised difference, so several long runs with many
@@ -107,8 +107,8 @@ def test_blocked_repeatable_under_load(variant):
     ldx = 516
     p = girih.plan(stencil, nx, ny, nz, dtype=dtype, T=T, ldx=ldx)
     cfg = (girih.config(girih.NAIVE) if variant == "NAIVE" else
-           girih.config(girih.MWD, dw=8, nf=1, cluster=8, threads=352 if variant == "RELAXED_PERSISTENT" else 512,
-                        variant=getattr(girih, variant)))
+           girih.config(girih.MWD, dw=8, nf=1, cluster=8, threads=352 if variant.endswith("_PERSISTENT") and
+                        variant != "FED_PERSISTENT" else 512, variant=getattr(girih, variant)))
     u, up, co, c = inputs.make_problem(stencil, nx, ny, nz, backend="torch", device="cuda", ldx=ldx)
     u, up = u.float().contiguous(), up.float().contiguous()
     nu, nup = u.clone(), up.clone()
@@ -122,21 +122,26 @@ def test_blocked_repeatable_under_load(variant):
 
 
 @pytest.mark.parametrize("workload,cfgkw", [
-    ("7pt_const_f32_512", dict(dw=8, nf=1, cluster=8, threads=352)),
-    ("7pt_const_f64_512", dict(dw=8, nf=1, cluster=16, threads=352)),
-    ("7pt_var_f32_480", dict(dw=8, nf=1, cluster=8, threads=320)),
-    ("7pt_rbgs_f32_512", dict(dw=12, nf=1, cluster=16, threads=416)),
+    ("7pt_const_f32_512", dict(dw=8, nf=1, cluster=8, threads=352, variant=6)),
+    ("7pt_const_f64_512", dict(dw=8, nf=1, cluster=16, threads=352, variant=6)),
+    ("7pt_var_f32_480", dict(dw=8, nf=1, cluster=8, threads=320, variant=6)),
+    ("7pt_rbgs_f32_512", dict(dw=12, nf=1, cluster=16, threads=416, variant=6)),
+    ("7pt_const_f32_512", dict(dw=8, nf=1, cluster=8, threads=352, variant=7)),
+    ("7pt_const_f64_512", dict(dw=4, nf=1, cluster=8, threads=192, variant=7)),
+    ("7pt_var_f32_480", dict(dw=6, nf=1, cluster=8, threads=192, variant=7)),
+    ("7pt_rbgs_f32_512", dict(dw=12, nf=1, cluster=16, threads=480, variant=7)),
 ])
-def test_relaxed_persistent_full_size(workload, cfgkw):
-    """The neighbour-synchronised persistent kernel on the benchmark grids (full T), in cluster
-    and diamond shapes that hold one or two blocks per SM: bit for bit the naive sweep."""
+def test_persistent_tma_kernels_full_size(workload, cfgkw):
+    """The warp-specialised persistent kernels (RELAXED_PERSISTENT = 6, OVERLAP_PERSISTENT = 7) on
+    the benchmark grids (full T), in cluster and diamond shapes that hold one or two blocks per
+    SM: bit for bit the naive sweep."""
     import torch
     import bench
     stencil, dtype, nx, ny, nz, T = bench.WORKLOADS[workload]
     a16 = 16 // (8 if dtype == "f64" else 4)
     ldx = -(-(nx + 2) // a16) * a16
     p = girih.plan(stencil, nx, ny, nz, dtype=dtype, T=T, ldx=ldx)
-    cfg = girih.config(girih.MWD, variant=girih.RELAXED_PERSISTENT, **cfgkw)
+    cfg = girih.config(girih.MWD, **cfgkw)
     assert p.feasible(cfg), cfg
     u, up, co, c = inputs.make_problem(stencil, nx, ny, nz, backend="torch", device="cuda", ldx=ldx)
     tdt = torch.float64 if dtype == "f64" else torch.float32

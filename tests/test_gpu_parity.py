@@ -437,6 +437,75 @@ def test_relaxed_persistent_rejections():
     assert torch.equal(du, before)
 
 
+# (dw, cluster, threads) on the 70-wide grid: 1, 2 and 4 tasks per computing thread, clusters of 1
+# to 16 blocks (slabs of 72 down to 6 columns, widened by up to 16 columns per side), one-level
+# diamonds (dw = 2)
+OVL_CFGS = [(4, 1, 256), (8, 2, 288), (8, 2, 160), (8, 4, 96), (12, 8, 224), (6, 16, 96), (16, 8, 512), (2, 4, 64)]
+
+
+@pytest.mark.parametrize("stencil", [0, 1, 6])
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+def test_overlap_persistent(stencil, dtype):
+    """OVERLAP_PERSISTENT (blocks update their x slab widened by the halo each level needs and
+    repeat the neighbours' edge columns instead of exchanging them; final values wait only for
+    the neighbours' staging progress) never changes a point's arithmetic: bit-identical to the
+    naive sweep over cluster sizes, diamond widths, block sizes, truncated and full diamond rows."""
+    nx, ny, nz = SIZES[1]
+    ldx = _aligned_ldx(nx, 1, dtype)
+    for dw, cl, th in OVL_CFGS:
+        H = dw
+        for T in (1, H - 1, 2 * H + 3):
+            if T < 1:
+                continue
+            u, up, co, c = inputs.make_problem(stencil, nx, ny, nz, seed=29 + T + dw, ldx=ldx)
+            nu, nup = gpu_sweep(stencil, dtype, u, up, co, c, T, nx, ny, nz, girih.config(girih.NAIVE), ldx=ldx)
+            kw = dict(dw=dw, nf=1, cluster=cl, threads=th, variant=girih.OVERLAP_PERSISTENT)
+            if dw == 16 and dtype == "f64":
+                kw["dw"] = 12  # the FP64 ring of a 16-wide diamond exceeds the block's shared memory
+            cfg = feasible_cfg(stencil, dtype, nx, ny, nz, kw, ldx=ldx)
+            assert cfg.variant == girih.OVERLAP_PERSISTENT
+            pu, pup = gpu_sweep(stencil, dtype, u, up, co, c, T, nx, ny, nz, cfg, ldx=ldx)
+            assert np.array_equal(pu, nu) and np.array_equal(pup, nup), (dw, cl, T, cfg)
+
+
+@pytest.mark.parametrize("shape", [(1, 1, 1), (33, 1, 9), (5, 70, 3), (129, 7, 40), (2, 2, 2), (300, 9, 5)])
+def test_overlap_persistent_degenerate_shapes(shape):
+    """Slabs narrower than their widening, blocks with no columns, one-row and one-plane grids."""
+    nx, ny, nz = shape
+    for dtype in ("f32", "f64"):
+        ldx = _aligned_ldx(nx, 1, dtype)
+        for stencil in (0, 1, 6):
+            T = 7
+            u, up, co, c = inputs.make_problem(stencil, nx, ny, nz, seed=6, ldx=ldx)
+            nu, nup = gpu_sweep(stencil, dtype, u, up, co, c, T, nx, ny, nz, girih.config(girih.NAIVE), ldx=ldx)
+            for dw, cl in ((4, 2), (8, 4), (6, 16)):
+                cfg = feasible_cfg(stencil, dtype, nx, ny, nz,
+                                   dict(dw=dw, nf=1, cluster=cl, threads=256, variant=girih.OVERLAP_PERSISTENT),
+                                   ldx=ldx)
+                pu, pup = gpu_sweep(stencil, dtype, u, up, co, c, T, nx, ny, nz, cfg, ldx=ldx)
+                assert np.array_equal(pu, nu) and np.array_equal(pup, nup), (shape, dtype, stencil, cfg)
+
+
+def test_overlap_persistent_rejections():
+    """Same domain as RELAXED_PERSISTENT: other stencils, unaligned layouts, nf > 1 and blocks too
+    small for the widened tile are rejected."""
+    nx, ny, nz = SIZES[1]
+    for stencil in (2, 3, 4, 5):
+        R = inputs.RADIUS[stencil]
+        p = girih.plan(stencil, *SIZES[R], dtype="f32", T=3, ldx=_aligned_ldx(SIZES[R][0], R, "f32"))
+        assert not p.feasible(girih.config(girih.MWD, dw=8 * R, nf=1, cluster=2, threads=256,
+                                           variant=girih.OVERLAP_PERSISTENT)), stencil
+    ldx = _aligned_ldx(nx, 1, "f32")
+    cfg = girih.config(girih.MWD, dw=8, nf=1, cluster=2, threads=256, variant=girih.OVERLAP_PERSISTENT)
+    assert not girih.plan(0, nx, ny, nz, dtype="f32", T=3, ldx=ldx + 1).feasible(cfg)
+    p0 = girih.plan(0, nx, ny, nz, dtype="f32", T=3, ldx=ldx)
+    assert p0.feasible(cfg)
+    assert not p0.feasible(girih.config(girih.MWD, dw=8, nf=2, cluster=2, threads=256,
+                                        variant=girih.OVERLAP_PERSISTENT))
+    assert not p0.feasible(girih.config(girih.MWD, dw=16, nf=1, cluster=2, threads=64,
+                                        variant=girih.OVERLAP_PERSISTENT))  # 848 tasks > 4 x 32
+
+
 def test_persistent_schedule_on_fresh_plan_and_nonblocking_stream():
     """The plan's completion flags are cleared on the sweep's own stream: a persistent sweep
     launched on a non-blocking stream right after the plan is created (and after earlier plans
