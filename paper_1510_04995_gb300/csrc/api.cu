@@ -111,8 +111,9 @@ int check_config(const Plan* p, const girih_config* c, int64_t* smem_out, int* x
     if (!mv_tma(mwd_path(p, c, ptrs16)))
       return fail(GIRIH_EINVAL, "%s needs rows of 16-byte multiples and 16-byte aligned buffers", vn);
     if (c->nf != 1) return fail(GIRIH_EINVAL, "%s advances one plane per level and step (nf = 1)", vn);
-    if (c->threads <= kAsyncMovers)
-      return fail(GIRIH_EINVAL, "%s needs more than %d threads (one warp moves data)", vn, kAsyncMovers);
+    const int movers = c->variant == GIRIH_OVERLAP_PERSISTENT ? kOvlMovers : kAsyncMovers;
+    if (c->threads <= movers)
+      return fail(GIRIH_EINVAL, "%s needs more than %d threads (%d warp(s) move data)", vn, movers, movers / 32);
   }
   if (vec_only(p->stencil) && mwd_path(p, c, ptrs16) == MV_ELEM)
     return fail(GIRIH_EINVAL, "the blocked sweep of the box and red-black stencils needs the vector path: rows of "
@@ -138,7 +139,7 @@ int check_config(const Plan* p, const girih_config* c, int64_t* smem_out, int* x
     return fail(GIRIH_EINVAL, "dw=%d with a %d-wide slab has %lld tasks on its widened levels: more than the %d "
                 "computing threads of a %d-thread block hold at 1, 2 or 4 per thread (blocks of at most %d, %d, %d "
                 "threads)", c->dw, XW, (long long)mwd_ovl_tasks(R, c->dw, XW, mwd_vx(p->stencil, p->dtype, mv)),
-                c->threads - kAsyncMovers, c->threads, async_max_threads(1, ncoef_of(p->stencil) > 0),
+                c->threads - kOvlMovers, c->threads, async_max_threads(1, ncoef_of(p->stencil) > 0),
                 async_max_threads(2, ncoef_of(p->stencil) > 0), async_max_threads(4, ncoef_of(p->stencil) > 0));
   if (G == 0 && mv == MV_ASYNC)
     return fail(GIRIH_EINVAL, "dw=%d with a %d-wide slab has %d row pairs x %d vectors: more tasks than the %d "

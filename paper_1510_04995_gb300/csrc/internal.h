@@ -101,6 +101,7 @@ inline bool async_stencil(int stencil) {
 #endif
 constexpr int kAsyncLeadMin = 3;
 constexpr int kAsyncMovers = 32;    // threads of the RELAXED_PERSISTENT block that move data
+constexpr int kOvlMovers = 64;      // of the OVERLAP_PERSISTENT block (a staging and a waiting warp)
 constexpr int kAsyncLoadBars = 8;   // its staging mbarriers (the lead is at most 8)
 constexpr int kAsyncLeadMax = GIRIH_ASYNC_LEAD_MAX;
 // Largest block of the RELAXED_PERSISTENT kernel for G tasks per thread (its launch bound); the

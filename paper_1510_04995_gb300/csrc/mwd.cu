@@ -138,10 +138,10 @@ int mwd_pairs_per_thread(int stencil, int dtype, int dw, int XW, int threads, in
   const int R = radius_of(stencil);
   const int vx = mwd_vx(stencil, dtype, mv), lbf = mwd_lbf(stencil, dtype, mv);
   const int64_t ng = (int64_t)mwd_max_pairs(R, dw) * (XW / vx);
-  if (mv == MV_OVL) {  // the block's last warp moves data; the others compute
+  if (mv == MV_OVL) {  // the block's last two warps move data; the others compute
     const int64_t nt = mwd_ovl_tasks(R, dw, XW, vx);
     for (int G : {1, 2, 4})
-      if (threads <= async_max_threads(G, ncoef_of(stencil) > 0) && nt <= (int64_t)G * (threads - kAsyncMovers)) return G;
+      if (threads <= async_max_threads(G, ncoef_of(stencil) > 0) && nt <= (int64_t)G * (threads - kOvlMovers)) return G;
     return 0;
   }
   if (mv == MV_ASYNC) {  // the block's last two warps move data; the others compute

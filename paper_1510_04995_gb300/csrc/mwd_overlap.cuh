@@ -24,6 +24,13 @@
 // by L + sf K steps before one waits, and the check is off the critical path in practice.  A block
 // that is ahead waits for one that is behind, never the reverse, so the cluster cannot deadlock.
 //
+// Warp roles: the computing warps, then a staging warp (issues the tensor copies of step w+L once
+// step w-1 is done) and a waiting warp (waits for the copies of step w+2 to land, publishes,
+// checks the neighbours, then releases step w+1), so that neither the copies' issue latency nor
+// the progress exchange sits between two steps of the computing warps.  Barriers: FULL(w) (ids
+// 1-2): computing warps and the waiting warp wait, the staging warp arrives once it has seen
+// step w-2 done; DONE(w) (ids 3-4): computing warps arrive, the staging warp waits.
+//
 // Tasks (level s, row pair, 16-byte vector) run over the level's widened vector range, pair-major;
 // consecutive lanes hold consecutive vectors of a pair, so a task takes its x neighbours from the
 // neighbouring lanes (shuffles) and reads shared memory only at the ends of a pair's run and of
@@ -33,15 +40,28 @@
 
 namespace girih {
 
-// Publish the block's staging progress `count` (wavefront steps landed, counted over the launch)
-// to the progress word `slot` (0: written by the left neighbour, 1: by the right one) of block
-// `rank` of the cluster.  A relaxed store with no fence: the mover issues it only after its
-// acquiring wait on the load mbarrier has seen the staging copies complete, so the copies' reads
-// of global memory are done before the count can be observed, and the neighbour stores to those
-// columns only after observing it (a release fence here would wait for the block's outstanding
-// global stores of final values on every step).
-__device__ __forceinline__ void publish_progress(uint32_t prog_base, int rank, int slot, uint32_t count) {
-  st_cluster_u32(map_to_rank(prog_base + 4u * (uint32_t)slot, (uint32_t)rank), count);
+__device__ __forceinline__ uint32_t ld_relaxed_cluster_u32(const int* p) {
+  uint32_t v;
+  asm volatile("ld.relaxed.cluster.shared::cta.u32 %0, [%1];" : "=r"(v) : "r"(smem_addr(p)) : "memory");
+  return v;
+}
+// Bounded wait of a warp until the progress words of the block's existing x neighbours reach
+// `need`; a timeout sets GIRIH_ETIMEOUT.  The stores of final values that this wait guards are made
+// after it in program order and after a block barrier, and no store is performed speculatively.
+__device__ __forceinline__ void wait_progress(const int* prog, bool left, bool right, uint32_t need, int* err) {
+  auto behind = [&]() {
+    return (left && ld_relaxed_cluster_u32(&prog[0]) < need) || (right && ld_relaxed_cluster_u32(&prog[1]) < need);
+  };
+  if (behind()) {
+    const uint64_t t0 = global_ns();
+    while (behind()) {
+      if (global_ns() - t0 > kMbarWaitNs) {
+        atomicOr(err, GIRIH_ETIMEOUT);
+        break;
+      }
+    }
+  }
+  __syncwarp();
 }
 
 // One tile (diamond (a, a - rho), this block's widened x slab) from staging to write-back.
@@ -88,8 +108,10 @@ __device__ __forceinline__ void mwd_ovl_tile(const MwdArgs& A, const int rho, co
   if (tb > te) return;  // uniform over the cluster
   const int nlev = te - tb + 1, smax = nlev - 1;
   const int NT = blockDim.x, tid = threadIdx.x;
-  const int NTc = NT - kMovers;
+  const int NTc = NT - kOvlMovers;
   const bool mover = tid >= NTc;
+  const bool stager = mover && tid < NTc + 32;
+  const int NF = NTc + kOvlMovers, ND = NTc + 32;  // threads of the FULL and DONE barriers
   const int lane = tid & 31;
   const uint32_t lb0 = smem_addr(&lb[0]);
   const int g0 = gstep;
@@ -127,41 +149,56 @@ __device__ __forceinline__ void mwd_ovl_tile(const MwdArgs& A, const int rho, co
   // ---- mover: staging copies of tile step j (planes -R .. R for step 0, plane j + R for step
   //      j >= 1), both buffers, completing on load mbarrier (g0 + j) mod kLoadBars ----
   const uint32_t box_bytes = (uint32_t)(YW * XT * (int)sizeof(T));
+  // planes are staged in increasing z from -R, so the ring slot of the next one ((z + R) mod NZ)
+  // advances by one per plane (kept by the staging lane)
+  int next_slot = 0;
   auto stage_step = [&](int j) {
-    const int zlo = j == 0 ? -R : j + R, zhi = j + R;
-    int np = 0;
-    for (int z = zlo; z <= zhi; ++z) np += (z >= -R && z < nz + R) ? 1 : 0;
-    uint64_t* m = &lb[(g0 + j) % kLoadBars];
+    const int z0 = j == 0 ? -R : j + R, z1 = min(j + R, nz + R - 1);
     if (lane == 0) {
-      mbar_expect_tx(m, (uint32_t)np * 2u * box_bytes);
-      for (int z = zlo; z <= zhi; ++z) {
-        if (z < -R || z >= nz + R) continue;
-        const int slot = (z + R) % NZ;
-        tma_load_3d(sm + slot * pe, &A.tm[0], sc0, Y0 + R, z + R, m);
-        tma_load_3d(sm + be + slot * pe, &A.tm[1], sc0, Y0 + R, z + R, m);
+      uint64_t* m = &lb[(g0 + j) & (kLoadBars - 1)];
+      mbar_expect_tx(m, (uint32_t)(z1 >= z0 ? z1 - z0 + 1 : 0) * 2u * box_bytes);
+      for (int z = z0; z <= z1; ++z) {
+        tma_load_3d(sm + next_slot * pe, &A.tm[0], sc0, Y0 + R, z + R, m);
+        tma_load_3d(sm + be + next_slot * pe, &A.tm[1], sc0, Y0 + R, z + R, m);
+        next_slot = next_slot + 1 == NZ ? 0 : next_slot + 1;
       }
     }
     __syncwarp();
   };
   auto wait_step = [&](int j) {
     const int gs = g0 + j;
-    warp_wait_phase(lb0 + (uint32_t)((gs % kLoadBars) * 8), (uint32_t)((gs / kLoadBars) & 1), A.err);
+    warp_wait_phase(lb0 + (uint32_t)((gs & (kLoadBars - 1)) * 8), (uint32_t)((gs / kLoadBars) & 1), A.err);
   };
   const bool has_l = C > 1 && rank > 0, has_r = C > 1 && rank < C - 1;
   const uint32_t prog_base = smem_addr(prog);
-  // the staging of tile steps 0 .. j has landed: tell the neighbours (their slot 1 / slot 0)
+  // the neighbours' progress words this block writes: slot 1 of the left one, slot 0 of the right
+  const uint32_t pub_l = has_l ? map_to_rank(prog_base + 4u, (uint32_t)(rank - 1)) : 0u;
+  const uint32_t pub_r = has_r ? map_to_rank(prog_base, (uint32_t)(rank + 1)) : 0u;
+  // the staging of tile steps 0 .. j has landed: tell the neighbours (a count of steps over the
+  // launch).  A relaxed store with no fence: it is issued only after the acquiring wait on the
+  // load mbarrier has seen the staging copies complete, so their reads of global memory are done
+  // before the count can be observed, and a neighbour stores to those columns only after
+  // observing it (a release fence here would wait for the block's outstanding global stores of
+  // final values on every step).
   auto publish = [&](int j) {
     if (lane == 0) {
-      if (has_l) publish_progress(prog_base, rank - 1, 1, (uint32_t)(g0 + j + 1));
-      if (has_r) publish_progress(prog_base, rank + 1, 0, (uint32_t)(g0 + j + 1));
+      if (has_l) st_cluster_u32(pub_l, (uint32_t)(g0 + j + 1));
+      if (has_r) st_cluster_u32(pub_r, (uint32_t)(g0 + j + 1));
     }
     __syncwarp();
   };
   // step w stores final values to planes up to w - sf K; a neighbour stages plane z in its tile
-  // step max(z - R, 0): wait until both neighbours have landed that step
+  // step max(z - R, 0): wait until both neighbours have landed that step.  The counts last read
+  // are kept, so shared memory is polled only when they do not already suffice.
+  uint32_t seen_l = 0, seen_r = 0;
   auto check_neighbours = [&](int w) {
-    const int j = max(w - sf * K - R, 0);
-    if ((has_l || has_r) && sf < nlev) wait_counts(prog, has_l, has_r, (uint32_t)(g0 + j + 1), kMbarWaitNs, A.err);
+    if (!(has_l || has_r) || sf >= nlev) return;
+    const uint32_t need = (uint32_t)(g0 + max(w - sf * K - R, 0) + 1);
+    if ((has_l && seen_l < need) || (has_r && seen_r < need)) {
+      wait_progress(prog, has_l, has_r, need, A.err);
+      seen_l = ld_relaxed_cluster_u32(&prog[0]);
+      seen_r = ld_relaxed_cluster_u32(&prog[1]);
+    }
     __syncwarp();
   };
 
@@ -220,10 +257,12 @@ __device__ __forceinline__ void mwd_ovl_tile(const MwdArgs& A, const int rho, co
   for (int i = 0; i < 5; ++i) cst[i] = sizeof(T) == 8 ? static_cast<T>(A.c[i]) : static_cast<T>(A.cf[i]);
   const int64_t gstride = A.g.gstride;
 
-  // ---- prologue (mover): request the planes of steps 0 .. L-1, wait for steps 0 and 1, publish ----
-  if (mover) {
+  // ---- prologue: the staging warp requests the planes of steps 0 .. L-1; the waiting warp waits
+  //      for steps 0 and 1, publishes and checks the neighbours for step 0 ----
+  if (stager) {
     fence_proxy_async_global();  // global data acquired before this tile -> bulk loads
     for (int j = 0; j < L && j < W; ++j) stage_step(j);
+  } else if (mover) {
     wait_step(0);
     if (W > 1) wait_step(1);
     publish(W > 1 ? 1 : 0);
@@ -235,7 +274,7 @@ __device__ __forceinline__ void mwd_ovl_tile(const MwdArgs& A, const int rho, co
   if (!mover) {
     for (int w = 0; w < W; ++w) {
       __syncwarp();  // the named barriers are warp-aligned instructions
-      if (w > 0) sync_full(w, NT);
+      if (w > 0) sync_full(w, NF);
 #pragma unroll
       for (int g = 0; g < G; ++g) {
         const int fl = t_fl[g];
@@ -329,25 +368,36 @@ __device__ __forceinline__ void mwd_ovl_tile(const MwdArgs& A, const int rho, co
       }
       fence_proxy_async_shared();  // shared-memory results ordered before later bulk copies into the slots
       __syncwarp();
-      arrive_done(w, NT);
+      arrive_done(w, ND);
     }
-  } else {
+  } else if (stager) {
+    // iteration it: step it-1 is done, so the slots of the planes first read at step it+L are
+    // free (ring depth); arriving at FULL(it+1) here keeps the computing warps from running two
+    // steps ahead of this warp's DONE waits
     for (int it = 0; it < W; ++it) {
       if (it > 0) {
         __syncwarp();
-        sync_done(it - 1, NT);
+        sync_done(it - 1, ND);
       }
+      __syncwarp();
+      if (it + 1 < W) arrive_full(it + 1, NF);
       if (it + L < W) stage_step(it + L);
+    }
+    __syncwarp();
+    if (W > 0) sync_done(W - 1, ND);
+  } else {
+    // iteration it (overlapping the computing warps' step it): the staging of step it+2 has
+    // landed (a plane is in place two steps before use), published; the neighbours have staged
+    // what step it+1 stores final values over; then FULL(it+1)
+    for (int it = 0; it + 1 < W; ++it) {
       if (it + 2 < W) {
         wait_step(it + 2);
         publish(it + 2);
       }
-      if (it + 1 < W) check_neighbours(it + 1);
+      check_neighbours(it + 1);
       __syncwarp();
-      if (it + 1 < W) arrive_full(it + 1, NT);
+      sync_full(it + 1, NF);
     }
-    __syncwarp();
-    if (W > 0) sync_done(W - 1, NT);
   }
 }
 

@@ -161,7 +161,7 @@ std::vector<girih_config> candidates(Plan* p) {
         const int64_t tasks = mwd_ovl_tasks(R, dw, slab_width(p, C, MV_OVL), mwd_vx(p->stencil, p->dtype, MV_OVL));
         int last = 0;
         for (int G : {1, 2, 4}) {
-          const int th = (int)std::max<int64_t>(32, (tasks + 32LL * G - 1) / (32LL * G) * 32) + kAsyncMovers;
+          const int th = (int)std::max<int64_t>(32, (tasks + 32LL * G - 1) / (32LL * G) * 32) + kOvlMovers;
           if (th == last || th > async_max_threads(G, ncoef_of(p->stencil) > 0)) continue;
           last = th;
           girih_config c{GIRIH_ALGO_MWD, dw, 1, C, th, GIRIH_OVERLAP_PERSISTENT};
