@@ -1,16 +1,21 @@
 """Benchmark of the temporally blocked stencil sweep on GB300.
 
 One "step" is one complete sweep: girih_run advancing the whole grid by T time steps with the
-blocked (wavefront-diamond) kernel.  Default workload: 7-point constant-coefficient stencil,
-FP64, 512^3 interior, T = 64 (the blocked-vs-naive configuration).  Prints ONE JSON line.
+configuration the tuner chose for the workload (naive or wavefront-diamond blocked).  Default
+workload: 7-point constant-coefficient stencil, FP64, 512^3 interior, T = 64 (the blocked-vs-naive
+configuration).  Prints ONE JSON line.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME] [--impl reference]
 
-value     GLUP/s of the blocked sweep (giga lattice-site updates per second, all ranks), inputs
-          resident in HBM; each grid (1 GiB per buffer at FP64 512^3) is larger than L2.
+value     GLUP/s of the configuration the exhaustive tuner recorded as fastest for the workload
+          (tuned_configs.json: the naive sweep or a blocked one), inputs resident in HBM; each grid
+          (1 GiB per buffer at FP64 512^3) is larger than L2.
 naive     the naive GPU sweep (one pass per time step) on the same workload, same timing.
+blocked   the fastest wavefront-diamond configuration the tuner recorded, timed the same way, with
+          its own roofline (FP64: the DP pipe; FP32: HBM at the Eq. 5 code balance) and DRAM traffic.
 e2e       same metric through girih_run_host: pinned host buffers copied in and out every step.
-roofline  the blocked kernel's achieved rate against its bound (FP64: the DP pipe; FP32: HBM).
+roofline  the roofline of the kernel that `value` times (FP64: the DP pipe, peak = the FMA rate
+          measured on this GPU; FP32: HBM, peak = the measured copy bandwidth).
 cpu_baseline  the FP64 oracle (plain C loops, OpenMP over z) on this host's cores, on a bounded
           sample of the same grid (fewer time steps).
 --impl reference  times only that oracle, per step on a bounded sample, as the reference arm.
@@ -55,22 +60,23 @@ STENCIL_NAME = {0: "7-point constant", 1: "7-point variable", 2: "25-point const
 INSTR_PER_LUP = {0: 7, 1: 7, 2: 28, 3: 28, 4: 28, 5: 27, 6: 7}
 # DRAM bytes per LUP measured by ncu (dram__bytes_read.sum + dram__bytes_write.sum of one launch
 # / LUPs of that launch) for a kernel on a smaller grid of the same workload, with the summary it
-# comes from; the roofline's "traffic" scales it to one launch of the benchmark grid
+# comes from; the roofline's "traffic" scales it to one launch of the benchmark grid.  Keys:
+# (kernel, stencil, dtype) with kernel ("naive",) or ("mwd", variant, dw, cluster, threads)
 MEASURED_BYTES_PER_LUP = {
-    ("naive", 0, "f64"): (15.69, "profiles/naive_7pt_const_f64_512x384x256.md"),
-    ("naive", 0, "f32"): (7.27, "profiles/naive_7pt_const_f32_512x384x256.md"),
-    ("naive", 1, "f64"): (72.81, "profiles/naive_7pt_var_f64_480x384x192.md"),
-    ("naive", 1, "f32"): (36.45, "profiles/naive_7pt_var_f32_480x384x256.md"),
-    ("naive", 2, "f64"): (24.05, "profiles/naive_25pt_const_f64_384x384x192.md"),
-    ("naive", 2, "f32"): (11.66, "profiles/naive_25pt_const_f32_384x384x256.md"),
-    ("naive", 3, "f64"): (132.06, "profiles/naive_25pt_var_f64_384x384x128.md"),
-    ("naive", 3, "f32"): (65.91, "profiles/naive_25pt_var_f32_384x384x192.md"),
-    ("naive", 4, "f64"): (32.35, "profiles/naive_25pt_cgrid_f64_384x384x192.md"),
-    ("naive", 4, "f32"): (16.12, "profiles/naive_25pt_cgrid_f32_384x384x256.md"),
-    ("naive", 5, "f64"): (15.33, "profiles/naive_27pt_box_f64_512x384x256.md"),
-    ("naive", 5, "f32"): (7.26, "profiles/naive_27pt_box_f32_512x384x256.md"),
-    ("naive", 6, "f64"): (15.7, "profiles/naive_7pt_rbgs_f64_512x384x256.md"),
-    ("naive", 6, "f32"): (7.29, "profiles/naive_7pt_rbgs_f32_512x384x256.md"),
+    (("naive",), 0, "f64"): (15.69, "profiles/naive_7pt_const_f64_512x384x256.md"),
+    (("naive",), 0, "f32"): (7.27, "profiles/naive_7pt_const_f32_512x384x256.md"),
+    (("naive",), 1, "f64"): (72.81, "profiles/naive_7pt_var_f64_480x384x192.md"),
+    (("naive",), 1, "f32"): (36.45, "profiles/naive_7pt_var_f32_480x384x256.md"),
+    (("naive",), 2, "f64"): (24.05, "profiles/naive_25pt_const_f64_384x384x192.md"),
+    (("naive",), 2, "f32"): (11.66, "profiles/naive_25pt_const_f32_384x384x256.md"),
+    (("naive",), 3, "f64"): (132.06, "profiles/naive_25pt_var_f64_384x384x128.md"),
+    (("naive",), 3, "f32"): (65.91, "profiles/naive_25pt_var_f32_384x384x192.md"),
+    (("naive",), 4, "f64"): (32.35, "profiles/naive_25pt_cgrid_f64_384x384x192.md"),
+    (("naive",), 4, "f32"): (16.12, "profiles/naive_25pt_cgrid_f32_384x384x256.md"),
+    (("naive",), 5, "f64"): (15.33, "profiles/naive_27pt_box_f64_512x384x256.md"),
+    (("naive",), 5, "f32"): (7.26, "profiles/naive_27pt_box_f32_512x384x256.md"),
+    (("naive",), 6, "f64"): (15.7, "profiles/naive_7pt_rbgs_f64_512x384x256.md"),
+    (("naive",), 6, "f32"): (7.29, "profiles/naive_7pt_rbgs_f32_512x384x256.md"),
 }
 # domain-sized streams N_D of the code-balance model and the spatial minimum bytes per LUP (in elements)
 ND = {0: 2, 1: 9, 2: 2, 3: 15, 4: 3, 5: 2, 6: 2}
@@ -366,6 +372,49 @@ def main():
     peaks, src = _peaks()
     # spatial-blocking roofline: HBM bandwidth / minimal bytes per LUP (u in, u out; coefficients in)
     spatial = float(peaks["hbm_gbs"]) / (SPATIAL_ELEMS[stencil] * elem)
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    fma = None
+    if dtype == "f64":
+        # the DP pipe's rate on this GPU, measured now (8 independent FMA chains per thread over
+        # every SM), next to the nominal SMs x 2 DFMA/clk x maximum SM clock
+        rate, secs = girih.measure_fma_rate("f64", stream)
+        fma = {"measured": rate, "seconds": secs, "sms": sms,
+               "nominal": sms * 2 * float(peaks.get("sm_max_mhz", 2070.0)) * 1e6}
+
+    def roofline(config, glups_per_gpu):
+        """Roofline of one configuration's kernel: FP64 against the DP pipe (explicitly rounded
+        ops per LUP x LUP/s vs the measured FMA rate), FP32 against HBM (algorithmic bytes = Eq. 5
+        code balance for a blocked sweep, the spatial minimum for the naive one, x LUP/s)."""
+        mwd = config.algo == girih.MWD
+        key = (("mwd", config.variant, config.dw, config.cluster, config.threads) if mwd else ("naive",),
+               stencil, dtype)
+        meas = MEASURED_BYTES_PER_LUP.get(key)
+        n_launch = p.launch_count(config)
+        # one launch of the naive sweep is one time step over the grid; of a blocked sweep, one
+        # diamond row (the persistent variants: the whole sweep)
+        lpl = nx * ny * nz if not mwd else lups / max(n_launch, 1)
+        per_s = glups_per_gpu * 1e9
+        if dtype == "f64":
+            achieved = per_s * INSTR_PER_LUP[stencil]
+            r = {"bound": "alu", "achieved": achieved * 1e-12, "peak": fma["measured"] * 1e-12, "unit": "Tinst/s",
+                 "frac": achieved / fma["measured"],
+                 "note": f"FP64 instructions/s ({INSTR_PER_LUP[stencil]} explicitly rounded ops per LUP) vs the "
+                         f"FMA rate measured on this GPU ({sms} SMs; nominal {sms} x 2 DFMA/clk x max clock = "
+                         f"{fma['nominal'] * 1e-12:.3f} T/s); HBM is not the bound"}
+        else:
+            bc = (girih.model_code_balance(config.dw, inputs.RADIUS[stencil], ND[stencil], elem) if mwd
+                  else SPATIAL_ELEMS[stencil] * elem)
+            achieved = per_s * bc
+            r = {"bound": "hbm", "achieved": achieved * 1e-9, "peak": float(peaks["hbm_gbs"]), "unit": "GB/s",
+                 "frac": achieved * 1e-9 / float(peaks["hbm_gbs"]),
+                 "note": f"algorithmic bytes = {'Eq. 5 code balance' if mwd else 'spatial minimum'} {bc:.2f} B/LUP"
+                         f" x LUPs ({src} HBM peak)"}
+        r["traffic"] = meas[0] * lpl if meas else None
+        r["lups_per_launch"] = lpl
+        if meas:
+            r["traffic_source"] = f"{meas[1]}: {meas[0]} DRAM bytes/LUP x {lpl:.4g} LUPs per launch"
+        return r
+
     blocked = None
     if blocked_cfg is not None:
         if blocked_cfg.as_dict() == cfg.as_dict():
@@ -374,36 +423,12 @@ def main():
             bms = timed(blocked_cfg, max(1, args.steps // 2), 1)
             bg = whole_job_glups(lups, max(1, args.steps // 2), ws, bms)
         blocked = {"glups": bg, "config": blocked_cfg.as_dict(), "vs_naive": (bg / naive) if naive else None,
-                   "frac_spatial_roofline": bg / ws / spatial}
+                   "frac_spatial_roofline": bg / ws / spatial, "roofline": roofline(blocked_cfg, bg / ws)}
 
-    # roofline of the dominant kernel (every launch of the timed region is the blocked kernel,
-    # except the exchange kernel for odd T, which the default workloads do not have)
+    # roofline of the dominant kernel: every launch of the timed region is the chosen
+    # configuration's kernel (plus the exchange kernel for odd T, which no workload here has)
     launches = p.launch_count(cfg)
-    per_gpu = lups * args.steps / (ms * 1e-3)
-    algo_name = "mwd" if cfg.algo == girih.MWD else "naive"
-    meas = MEASURED_BYTES_PER_LUP.get((algo_name, stencil, dtype))
-    # one launch of the naive sweep is one time step over the grid; of the blocked sweep, one
-    # diamond row (the sweep's LUPs over its launches, on average)
-    lups_per_launch = nx * ny * nz if cfg.algo == girih.NAIVE else lups / max(launches, 1)
-    traffic = meas[0] * lups_per_launch if meas else None
-    if dtype == "f64":
-        # FP64 pipe: 152 SMs x 2 DFMA per clock (1.25 TFLOP/s nominal) at the maximum SM clock
-        peak_inst = 152 * 2 * float(peaks.get("sm_max_mhz", 2070.0)) * 1e6
-        achieved = per_gpu * INSTR_PER_LUP[stencil]
-        roof = {"bound": "alu", "achieved": achieved * 1e-12, "peak": peak_inst * 1e-12,
-                "unit": "Tinst/s", "frac": achieved / peak_inst, "traffic": traffic,
-                "note": "FP64 instructions/s (one per explicitly rounded op, 7 or 28 per LUP) vs 152 SMs x 2 DFMA/clk "
-                        f"x max SM clock ({src} peaks file clock); HBM is not the bound"}
-    else:
-        bc = (girih.model_code_balance(cfg.dw, inputs.RADIUS[stencil], ND[stencil], elem)
-              if cfg.algo == girih.MWD else SPATIAL_ELEMS[stencil] * elem)
-        achieved = per_gpu * bc
-        roof = {"bound": "hbm", "achieved": achieved * 1e-9, "peak": float(peaks["hbm_gbs"]), "unit": "GB/s",
-                "frac": achieved * 1e-9 / float(peaks["hbm_gbs"]), "traffic": traffic,
-                "note": f"algorithmic bytes = model code balance {bc:.2f} B/LUP x LUPs ({src} HBM peak)"}
-
-    if meas:
-        roof["traffic_source"] = f"{meas[1]}: {meas[0]} DRAM bytes/LUP x {lups_per_launch:.4g} LUPs per launch"
+    roof = roofline(cfg, value / ws)
 
     e2e = None
     if not args.no_e2e:

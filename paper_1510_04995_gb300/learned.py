@@ -26,8 +26,8 @@ import time
 
 import numpy as np
 
-from . import (F32, F64, FED, FED_BULK, MLP_FEATURES, MWD, NAIVE, RADIUS, RELAXED, RELAXED_PERSISTENT, Config,
-               TuneRow, check, config, config_array, lib, model_code_balance, plan)
+from . import (F32, F64, FED, FED_BULK, MLP_FEATURES, MWD, NAIVE, OVERLAP_PERSISTENT, RADIUS, RELAXED,
+               RELAXED_PERSISTENT, Config, TuneRow, check, config, config_array, lib, model_code_balance, plan)
 
 # The 12 non-cubic grids of the learned-tuner sweep (nx, ny, nz), and the held-out ones (#3, #7, #10).
 GRIDS = [(128, 256, 512), (256, 128, 512), (192, 384, 512), (256, 512, 512), (384, 256, 512),
@@ -57,9 +57,10 @@ def space(p) -> list:
     """The experiment's search space for a plan: the naive sweep and the feasible blocked sweeps
     with diamond widths 2R, 4R, 8R, 16R, wavefront widths 1 and 2, clusters 1, 4, 8, 16, 256 or
     512 threads, and the FED / FED_BULK data paths (RELAXED where the cluster has more than one
-    block, with 512 threads); plus the neighbour-synchronised persistent sweep (RELAXED_PERSISTENT)
-    for the same diamond widths and clusters 4, 8, 16, in the block sizes the tuner enumerates for
-    it (the tile's tasks at 1, 2 or 4 per computing thread)."""
+    block, with 512 threads); plus the neighbour-synchronised and overlapped-slab persistent
+    sweeps (RELAXED_PERSISTENT, OVERLAP_PERSISTENT) for the same diamond widths and clusters 4, 8,
+    16, in the block sizes the tuner enumerates for them (the tile's tasks at 1, 2 or 4 per
+    computing thread)."""
     R = p.R
     out = [config(NAIVE, 0, 1, 1, 256, FED)]
     for dw in (2 * R, 4 * R, 8 * R, 16 * R):
@@ -76,8 +77,8 @@ def space(p) -> list:
     if n.value:
         arr = (Config * n.value)()
         check(lib().girih_tune_candidates(p.handle, arr, n.value, ctypes.byref(n)))
-        out += [c for c in arr if c.variant == RELAXED_PERSISTENT and c.dw in (2 * R, 4 * R, 8 * R, 16 * R)
-                and c.cluster in (4, 8, 16)]
+        out += [c for c in arr if c.variant in (RELAXED_PERSISTENT, OVERLAP_PERSISTENT)
+                and c.dw in (2 * R, 4 * R, 8 * R, 16 * R) and c.cluster in (4, 8, 16)]
     return out
 
 
