@@ -207,6 +207,14 @@ __device__ __forceinline__ void mwd_ovl_tile(const MwdArgs& A, const int rho, co
   const T* t_k[G];
   T* t_g[G];
   T t_zm[G][2][VX], t_zc[G][2][VX];
+  // rows y0-1 and y0+2 of the task's plane and, at the ends of a run, the x neighbours from
+  // shared memory.  With PRE they are loaded at the end of the previous step (that plane of
+  // level t was completed by level s-1 two steps before it is used), so that after the step's
+  // barrier only the plane z+1 rows are loaded before the arithmetic: 7-point constant FP32
+  // 645 -> 667 GLUP/s; the red-black sweep lost 3 % and the variable-coefficient one, whose
+  // prefetched coefficients already fill the registers, 23 %, so they load after the barrier.
+  constexpr bool PRE = S == 0;
+  T t_yh[G][2][VX], t_xs[G][4];
   T t_kn[G][NC > 0 ? NC : 1][NC > 0 ? 2 : 1][VX];
   if (!mover) {
     const int ntask = lev_tp[nlev];
@@ -290,32 +298,47 @@ __device__ __forceinline__ void mwd_ovl_tile(const MwdArgs& A, const int rho, co
         const T* Vb = sm + t_in[g];
         const T* P = Vb + po;
         const bool row1 = fl & 2;
+        // rows y0-1, y0+2 (without a second row, row y0+2 may lie past the tile: row y0+1 is
+        // read instead) and the shared-memory x neighbours of the plane at Q
+        auto load_side = [&](const T* Q) {
+          lds_vec<T, VX>(Q - XT, t_yh[g][0]);
+          lds_vec<T, VX>(Q + (row1 ? 2 * XT : XT), t_yh[g][1]);
+          if (fl & (1 << 16)) {
+            t_xs[g][0] = Q[-1];
+            t_xs[g][1] = Q[XT - 1];
+          }
+          if (fl & (1 << 17)) {
+            t_xs[g][2] = Q[VX];
+            t_xs[g][3] = Q[XT + VX];
+          }
+        };
         if (live && !(fl & 32)) {  // first plane of the task: load the window (planes z-1, z)
           const int pm = (po == 0 ? ring : po) - pe;
           lds_vec<T, VX>(Vb + pm, t_zm[g][0]);
           lds_vec<T, VX>(Vb + pm + XT, t_zm[g][1]);
           lds_vec<T, VX>(P, t_zc[g][0]);
           lds_vec<T, VX>(P + XT, t_zc[g][1]);
+          if (PRE) load_side(P);
           t_fl[g] |= 32;
         }
         const int pp = (po + pe == ring) ? 0 : po + pe;
+        if (!PRE) load_side(P);
         T yr[4][VX], zp[2][VX], xm[2], xp[2];
-        lds_vec<T, VX>(P - XT, yr[0]);
-        // without a second row, row y0+2 may lie past the tile: read row y0+1 instead
-        lds_vec<T, VX>(P + (row1 ? 2 * XT : XT), yr[3]);
         lds_vec<T, VX>(Vb + pp, zp[0]);
         lds_vec<T, VX>(Vb + pp + XT, zp[1]);
 #pragma unroll
         for (int i = 0; i < VX; ++i) {
+          yr[0][i] = t_yh[g][0][i];
           yr[1][i] = t_zc[g][0][i];
           yr[2][i] = t_zc[g][1][i];
+          yr[3][i] = t_yh[g][1][i];
         }
 #pragma unroll
         for (int r = 0; r < 2; ++r) {
           const T l = __shfl_up_sync(0xffffffffu, yr[1 + r][VX - 1], 1);
           const T q = __shfl_down_sync(0xffffffffu, yr[1 + r][0], 1);
-          xm[r] = (fl & (1 << 16)) ? P[r * XT - 1] : l;
-          xp[r] = (fl & (1 << 17)) ? P[r * XT + VX] : q;
+          xm[r] = (fl & (1 << 16)) ? t_xs[g][r] : l;
+          xp[r] = (fl & (1 << 17)) ? t_xs[g][2 + r] : q;
         }
         if (!live) continue;
         T r0[VX], r1[VX];
@@ -365,6 +388,7 @@ __device__ __forceinline__ void mwd_ovl_tile(const MwdArgs& A, const int rho, co
           t_zc[g][0][i] = zp[0][i];
           t_zc[g][1][i] = zp[1][i];
         }
+        if (PRE && z + 1 < nz) load_side(Vb + pp);  // the next plane's rows y0-1, y0+2 and x neighbours
       }
       fence_proxy_async_shared();  // shared-memory results ordered before later bulk copies into the slots
       __syncwarp();
