@@ -246,28 +246,57 @@ def baselines(rows, scores: np.ndarray, k: int, draws: int = 2000, seed: int = 7
         naive = [j for j, i in enumerate(idx) if int(rows[i]["algo"]) == NAIVE]
         kk = min(k, len(idx))
         rnd = [rng.choice(len(idx), kk, replace=False) for _ in range(draws)]
-        out.append({"problem": key, "candidates": len(idx),
-                    "network": {"ratio": float(g[net].max() / best), "cost_fraction": float(cost[net].sum() / total)},
-                    "model_top_k": {"ratio": float(g[mod].max() / best), "cost_fraction": float(cost[mod].sum() / total)},
-                    "always_naive": ({"ratio": float(g[naive].max() / best),
-                                      "cost_fraction": float(cost[naive].sum() / total)} if naive else None),
-                    "random_k": {"ratio": float(np.mean([g[c].max() for c in rnd]) / best),
-                                 "cost_fraction": float(np.mean([cost[c].sum() for c in rnd]) / total)}})
+        def method(ratio, cost_s):
+            return {"ratio": float(ratio), "cost_fraction": float(cost_s / total), "cost_seconds": float(cost_s)}
+        out.append({"problem": key, "candidates": len(idx), "exhaustive_seconds": float(total),
+                    "network": method(g[net].max() / best, cost[net].sum()),
+                    "model_top_k": method(g[mod].max() / best, cost[mod].sum()),
+                    "always_naive": method(g[naive].max() / best, cost[naive].sum()) if naive else None,
+                    "random_k": method(np.mean([g[c].max() for c in rnd]) / best,
+                                       np.mean([cost[c].sum() for c in rnd]))})
     return out
 
 
 def summarize(res):
-    """Worst and mean fraction of the exhaustive best, and the total measurement-time fraction, per
-    method of baselines()."""
+    """Per method of baselines(): worst and mean fraction of the exhaustive best, problems at 95 %
+    of it, the mean over problems of the fraction of exhaustive tuning time spent measuring, and
+    that fraction over all problems together (the time the method spends tuning the whole set;
+    problems with a handful of candidates make the per-problem mean large for any k)."""
     out = {}
     for m in ("network", "model_top_k", "always_naive", "random_k"):
-        vals = [r[m] for r in res if r.get(m)]
-        if not vals:
+        rows = [r for r in res if r.get(m)]
+        if not rows:
             continue
+        vals = [r[m] for r in rows]
         out[m] = {"worst_ratio": min(v["ratio"] for v in vals), "mean_ratio": float(np.mean([v["ratio"] for v in vals])),
                   "problems_at_95pct": sum(v["ratio"] >= 0.95 for v in vals), "problems": len(vals),
-                  "mean_cost_fraction": float(np.mean([v["cost_fraction"] for v in vals]))}
+                  "mean_cost_fraction": float(np.mean([v["cost_fraction"] for v in vals])),
+                  "total_cost_fraction": float(sum(v["cost_seconds"] for v in vals) /
+                                               sum(r["exhaustive_seconds"] for r in rows))}
     return out
+
+
+def reevaluate(out_dir: str, k: int = 5):
+    """Recompute the offline parts of an experiment's report (the network's top k, the methods
+    without it, over all candidates and over the blocked ones) from its database and trained
+    parameters, keeping the live measurements; no GPU needed."""
+    import json
+    rp = os.path.join(out_dir, "report.json")
+    rep = json.load(open(rp))
+    rows = load_db(os.path.join(out_dir, "tune_db.csv"))
+    params = np.load(os.path.join(out_dir, "mlp_params.npy"))
+    held = {tuple(GRIDS[i]) for i in HELD_OUT}
+    test_rows = [r for r in rows if (int(r["nx"]), int(r["ny"]), int(r["nz"])) in held]
+    scores = predict(params, features(test_rows))
+    bl = [i for i, r in enumerate(test_rows) if int(r["algo"]) == MWD]
+    cmp_all = baselines(test_rows, scores, k)
+    cmp_blocked = baselines([test_rows[i] for i in bl], scores[bl], k)
+    rep.update({"offline": evaluate(test_rows, scores, k), "baselines": cmp_all,
+                "baselines_summary": summarize(cmp_all), "blocked_only": cmp_blocked,
+                "blocked_only_summary": summarize(cmp_blocked)})
+    with open(rp, "w") as f:
+        json.dump(rep, f, indent=1)
+    return rep
 
 
 def tune(p, params: np.ndarray, k: int = 5, tol: float = 0.05, max_steps: int = 32):
@@ -397,7 +426,13 @@ if __name__ == "__main__":
     ap.add_argument("--no-live", action="store_true")
     ap.add_argument("--unseen-from", default="", help="trained parameters (.npy): evaluate them on --stencils "
                     "instead of training (stencils the network never saw)")
+    ap.add_argument("--reevaluate", action="store_true", help="recompute the offline evaluation of OUT_DIR's "
+                    "report from its database and parameters (no GPU)")
     a = ap.parse_args()
+    if a.reevaluate:
+        rep = reevaluate(a.out_dir, a.k)
+        print(json.dumps({k: rep[k] for k in ("baselines_summary", "blocked_only_summary")}, indent=1))
+        raise SystemExit(0)
     from . import build as _b
     _b.build()
     gl = [GRIDS[int(i)] for i in a.grids.split(",")] if a.grids else None

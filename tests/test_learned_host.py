@@ -82,3 +82,30 @@ def test_committed_reports_match_their_databases(report, db):
         assert e["measured"] <= rep["k"]
     for e in rep["offline"]:
         assert 0 < e["ratio"] <= 1.0 and e["exhaustive_best"] == pytest.approx(best[tuple(e["problem"])], rel=1e-6)
+
+
+def test_network_against_methods_without_it():
+    """The committed experiment's 24 held-out problems, against the methods without the network:
+    always the naive sweep, the 5 candidates with the lowest Eq. 5 code balance, and 5 candidates
+    drawn at random (mean over seeded draws).  Over all candidates the network's top 5 reaches at
+    least 95 % of the exhaustive best on every problem; over the blocked candidates alone (where
+    the winner varies with the problem) at least 95 % on average.  In both it spends at most 10 %
+    of the exhaustive tuning time over the whole set, and its mean and worst fractions of the best
+    and its count of problems at 95 % are at least those of every other method."""
+    rp = os.path.join(MODEL_DIR, "report.json")
+    if not os.path.exists(rp):
+        pytest.skip("experiment records not committed")
+    rep = json.load(open(rp))
+    for key in ("baselines_summary", "blocked_only_summary"):
+        summ = rep[key]
+        net = summ["network"]
+        assert net["problems"] == 24
+        if key == "baselines_summary":
+            assert net["problems_at_95pct"] == net["problems"], net
+        assert net["mean_ratio"] >= 0.95, (key, net)
+        assert net["total_cost_fraction"] <= 0.10, (key, net)
+        for other in ("model_top_k", "always_naive", "random_k"):
+            if other in summ:
+                o = summ[other]
+                assert net["mean_ratio"] >= o["mean_ratio"] and net["worst_ratio"] >= o["worst_ratio"], (key, other)
+                assert net["problems_at_95pct"] >= o["problems_at_95pct"], (key, other)
