@@ -105,9 +105,12 @@ int check_config(const Plan* p, const girih_config* c, int64_t* smem_out, int* x
     return fail(GIRIH_EINVAL, "FED_PERSISTENT needs rows of 16-byte multiples and 16-byte aligned buffers");
   if (tma_variant(c->variant)) {
     const char* vn = variant_name(c->variant);
-    if (!async_stencil(p->stencil))
+    if (c->variant == GIRIH_RELAXED_PERSISTENT && !async_stencil(p->stencil))
       return fail(GIRIH_EINVAL, "%s is built for the radius-1 first-order stencils (7-point constant, 7-point "
                   "variable, red-black Gauss-Seidel)", vn);
+    if (c->variant == GIRIH_OVERLAP_PERSISTENT && !ovl_stencil(p->stencil))
+      return fail(GIRIH_EINVAL, "%s is built for the 7-point, red-black and 25-point stencils (not the box "
+                  "stencil)", vn);
     if (!mv_tma(mwd_path(p, c, ptrs16)))
       return fail(GIRIH_EINVAL, "%s needs rows of 16-byte multiples and 16-byte aligned buffers", vn);
     if (c->nf != 1) return fail(GIRIH_EINVAL, "%s advances one plane per level and step (nf = 1)", vn);
@@ -138,9 +141,10 @@ int check_config(const Plan* p, const girih_config* c, int64_t* smem_out, int* x
   if (G == 0 && mv == MV_OVL)
     return fail(GIRIH_EINVAL, "dw=%d with a %d-wide slab has %lld tasks on its widened levels: more than the %d "
                 "computing threads of a %d-thread block hold at 1, 2 or 4 per thread (blocks of at most %d, %d, %d "
-                "threads)", c->dw, XW, (long long)mwd_ovl_tasks(R, c->dw, XW, mwd_vx(p->stencil, p->dtype, mv)),
-                c->threads - kOvlMovers, c->threads, async_max_threads(1, ncoef_of(p->stencil) > 0),
-                async_max_threads(2, ncoef_of(p->stencil) > 0), async_max_threads(4, ncoef_of(p->stencil) > 0));
+                "threads)", c->dw, XW, (long long)mwd_ovl_tasks(R, c->dw, XW, mwd_vx(p->stencil, p->dtype, mv), 16 / p->elem),
+                c->threads - kOvlMovers, c->threads, async_max_threads(1, ncoef_of(p->stencil) > 0, R == 4),
+                async_max_threads(2, ncoef_of(p->stencil) > 0, R == 4),
+                async_max_threads(4, ncoef_of(p->stencil) > 0, R == 4));
   if (G == 0 && mv == MV_ASYNC)
     return fail(GIRIH_EINVAL, "dw=%d with a %d-wide slab has %d row pairs x %d vectors: more tasks than the %d "
                 "computing threads of a %d-thread block hold (blocks of at most %d, %d, %d threads for 1, 2, 4 tasks "

@@ -87,10 +87,15 @@ inline bool mv_tma(int mv) { return mv == MV_ASYNC || mv == MV_OVL; }
 // OVERLAP_PERSISTENT: staged columns on each side of a slab, (H - 1) R rounded up to 16 bytes
 // (the bottom level of an unclipped diamond reads (smax + 1) R = (H - 1) R columns beyond it).
 inline int ovl_margin(int H, int R, int a16) { return ((H - 1) * R + a16 - 1) / a16 * a16; }
-// Its tasks (row pair x 16-byte vector over the widened level ranges) for an unclipped diamond on
-// an interior slab of XW columns.
-int64_t mwd_ovl_tasks(int R, int dw, int XW, int vx);
+// Its tasks (row pair x vx columns over the widened level ranges) for an unclipped diamond on an
+// interior slab of XW columns (a16: elements per 16 bytes, the margin's rounding).
+int64_t mwd_ovl_tasks(int R, int dw, int XW, int vx, int a16);
 // stencils the RELAXED_PERSISTENT kernel is built for
+// stencils the OVERLAP_PERSISTENT kernel is built for: those and the radius-4 ones
+inline bool ovl_stencil(int stencil) {
+  return stencil == GIRIH_7PT_CONST || stencil == GIRIH_7PT_VAR || stencil == GIRIH_7PT_RBGS ||
+         stencil == GIRIH_25PT_CONST || stencil == GIRIH_25PT_VAR || stencil == GIRIH_25PT_CGRID;
+}
 inline bool async_stencil(int stencil) {
   return stencil == GIRIH_7PT_CONST || stencil == GIRIH_7PT_VAR || stencil == GIRIH_7PT_RBGS;
 }
@@ -104,9 +109,11 @@ constexpr int kAsyncMovers = 32;    // threads of the RELAXED_PERSISTENT block t
 constexpr int kOvlMovers = 64;      // of the OVERLAP_PERSISTENT block (a staging and a waiting warp)
 constexpr int kAsyncLoadBars = 8;   // its staging mbarriers (the lead is at most 8)
 constexpr int kAsyncLeadMax = GIRIH_ASYNC_LEAD_MAX;
-// Largest block of the RELAXED_PERSISTENT kernel for G tasks per thread (its launch bound); the
-// variable-coefficient stencils hold a prefetched plane of coefficients per task in registers.
-constexpr int async_max_threads(int G, bool coef) {
+// Largest block of the warp-specialised kernels for G tasks per thread (their launch bound); the
+// variable-coefficient stencils hold a prefetched plane of coefficients per task in registers,
+// the radius-4 tasks (OVERLAP_PERSISTENT) windows of 2R+1 planes.
+constexpr int async_max_threads(int G, bool coef, bool r4 = false) {
+  if (r4) return G == 1 ? 512 : (G == 2 ? 320 : 160);  // radius 4: windows of 2R+1 planes
   return coef ? (G == 1 ? 512 : (G == 2 ? 288 : 160)) : (G == 1 ? 640 : (G == 2 ? 512 : 256));
 }
 inline bool mv_shifted(int mv) { return mv != MV_ELEM; }

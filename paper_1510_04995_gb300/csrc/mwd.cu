@@ -113,8 +113,8 @@ int mwd_async_lead(int stencil, int dtype, int dw, int nf, int XW, int threads, 
   return kAsyncLeadMin;
 }
 
-int64_t mwd_ovl_tasks(int R, int dw, int XW, int vx) {
-  const int H = dw / R, hm = ovl_margin(H, R, vx), smax = H - 2;
+int64_t mwd_ovl_tasks(int R, int dw, int XW, int vx, int a16) {
+  const int H = dw / R, hm = ovl_margin(H, R, a16), smax = H - 2;
   int64_t n = 0;
   for (int k = 1; k < H; ++k) {  // level s = k - 1
     const int e = (smax - (k - 1)) * R;
@@ -139,9 +139,10 @@ int mwd_pairs_per_thread(int stencil, int dtype, int dw, int XW, int threads, in
   const int vx = mwd_vx(stencil, dtype, mv), lbf = mwd_lbf(stencil, dtype, mv);
   const int64_t ng = (int64_t)mwd_max_pairs(R, dw) * (XW / vx);
   if (mv == MV_OVL) {  // the block's last two warps move data; the others compute
-    const int64_t nt = mwd_ovl_tasks(R, dw, XW, vx);
+    const int64_t nt = mwd_ovl_tasks(R, dw, XW, vx, 16 / (dtype == GIRIH_F64 ? 8 : 4));
     for (int G : {1, 2, 4})
-      if (threads <= async_max_threads(G, ncoef_of(stencil) > 0) && nt <= (int64_t)G * (threads - kOvlMovers)) return G;
+      if (threads <= async_max_threads(G, ncoef_of(stencil) > 0, R == 4) && nt <= (int64_t)G * (threads - kOvlMovers))
+        return G;
     return 0;
   }
   if (mv == MV_ASYNC) {  // the block's last two warps move data; the others compute

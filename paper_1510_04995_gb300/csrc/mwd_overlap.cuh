@@ -69,10 +69,13 @@ __device__ __forceinline__ void wait_progress(const int* prog, bool left, bool r
 // serve global steps modulo kLoadBars; progress words count global steps).
 template <int S, typename T, int G>
 __device__ __forceinline__ void mwd_ovl_tile(const MwdArgs& A, const int rho, const int a, int& gstep) {
-  static_assert(Traits<S>::R == 1 && !Traits<S>::ORDER2 && !Traits<S>::BOX, "radius-1 first-order stencils");
-  constexpr int R = 1;
+  static_assert((Traits<S>::R == 1 && !Traits<S>::ORDER2 || Traits<S>::R == 4) && !Traits<S>::BOX,
+                "radius-1 first-order or radius-4 stencils");
+  constexpr int R = Traits<S>::R;
   constexpr int NC = Traits<S>::NCOEF;
-  constexpr int VX = 16 / (int)sizeof(T);  // one 16-byte vector per task
+  // columns per task: one 16-byte vector (radius 1), or 8 bytes (radius-4 FP32) and one column
+  // (radius-4 FP64), whose 2R+1 planes per row are read from the ring every step
+  constexpr int VX = R == 1 ? 16 / (int)sizeof(T) : (sizeof(T) == 4 ? 2 : 1);
   extern __shared__ __align__(128) unsigned char smem_raw[];
   T* sm = reinterpret_cast<T*>(smem_raw);
   const int NZ = A.NZ, YW = A.YW, XT = A.XT, XW = A.XW, C = A.C, K = A.K;
@@ -294,101 +297,170 @@ __device__ __forceinline__ void mwd_ovl_tile(const MwdArgs& A, const int rho, co
         T* gp = t_g[g];
         t_g[g] += gplane;
         const bool live = (fl & 1) && z >= 0 && z < nz;
-        if (!__any_sync(0xffffffffu, live)) continue;
-        const T* Vb = sm + t_in[g];
-        const T* P = Vb + po;
-        const bool row1 = fl & 2;
-        // rows y0-1, y0+2 (without a second row, row y0+2 may lie past the tile: row y0+1 is
-        // read instead) and the shared-memory x neighbours of the plane at Q
-        auto load_side = [&](const T* Q) {
-          lds_vec<T, VX>(Q - XT, t_yh[g][0]);
-          lds_vec<T, VX>(Q + (row1 ? 2 * XT : XT), t_yh[g][1]);
-          if (fl & (1 << 16)) {
-            t_xs[g][0] = Q[-1];
-            t_xs[g][1] = Q[XT - 1];
-          }
-          if (fl & (1 << 17)) {
-            t_xs[g][2] = Q[VX];
-            t_xs[g][3] = Q[XT + VX];
-          }
-        };
-        if (live && !(fl & 32)) {  // first plane of the task: load the window (planes z-1, z)
-          const int pm = (po == 0 ? ring : po) - pe;
-          lds_vec<T, VX>(Vb + pm, t_zm[g][0]);
-          lds_vec<T, VX>(Vb + pm + XT, t_zm[g][1]);
-          lds_vec<T, VX>(P, t_zc[g][0]);
-          lds_vec<T, VX>(P + XT, t_zc[g][1]);
-          if (PRE) load_side(P);
-          t_fl[g] |= 32;
-        }
-        const int pp = (po + pe == ring) ? 0 : po + pe;
-        if (!PRE) load_side(P);
-        T yr[4][VX], zp[2][VX], xm[2], xp[2];
-        lds_vec<T, VX>(Vb + pp, zp[0]);
-        lds_vec<T, VX>(Vb + pp + XT, zp[1]);
+        if constexpr (R > 1) {
+          // radius 4: planes z-R .. z+R of both rows, R rows above and below, R columns left and
+          // right, and for the second-order stencils the level t-1 centre (the output buffer
+          // before it is overwritten), all from the ring
+          if (!live) continue;
+          const T* Vb = sm + t_in[g];
+          const T* P = Vb + po;
+          const bool row1 = fl & 2;
+          T* Ub = sm + t_out[g] + po;
+          int od[2 * R + 1];  // ring offsets of planes z-R .. z+R (one add and one wrap each)
+          od[R] = po;
 #pragma unroll
-        for (int i = 0; i < VX; ++i) {
-          yr[0][i] = t_yh[g][0][i];
-          yr[1][i] = t_zc[g][0][i];
-          yr[2][i] = t_zc[g][1][i];
-          yr[3][i] = t_yh[g][1][i];
-        }
+          for (int d = 1; d <= R; ++d) {
+            const int up = od[R + d - 1] + pe;
+            od[R + d] = up >= ring ? up - ring : up;
+            const int dn = od[R - d + 1] - pe;
+            od[R - d] = dn < 0 ? dn + ring : dn;
+          }
+          T w0[(2 * R + 1) * VX], w1[(2 * R + 1) * VX];
 #pragma unroll
-        for (int r = 0; r < 2; ++r) {
-          const T l = __shfl_up_sync(0xffffffffu, yr[1 + r][VX - 1], 1);
-          const T q = __shfl_down_sync(0xffffffffu, yr[1 + r][0], 1);
-          xm[r] = (fl & (1 << 16)) ? t_xs[g][r] : l;
-          xp[r] = (fl & (1 << 17)) ? t_xs[g][2 + r] : q;
-        }
-        if (!live) continue;
-        T r0[VX], r1[VX];
-        if constexpr (NC > 0) {
-          if (!(fl & 32)) load_coef_pair<T, VX, NC>(kp, gstride, ldx, t_kn[g]);  // first plane: not prefetched
-          task_row2<S, T, VX, 0, 0>(yr, t_zm[g], zp, xm, xp, t_kn[g], cst, r0);
-          task_row2<S, T, VX, 1, 0>(yr, t_zm[g], zp, xm, xp, t_kn[g], cst, r1);
-          // prefetch the next plane's coefficients: consumed in the next step
-          if (z + 1 < nz) load_coef_pair<T, VX, NC>(kp + gplane, gstride, ldx, t_kn[g]);
-        } else {
-          T kv[1][VX];
-          task_row<S, T, VX, 0, 0>(yr, t_zm[g], zp, xm, xp, kv, cst, r0);
-          task_row<S, T, VX, 1, 0>(yr, t_zm[g], zp, xm, xp, kv, cst, r1);
-        }
-        if constexpr (Traits<S>::RB) {
-          // red-black: only points with (x + y + z + t) even are updated (row y0+1 has the other
-          // colour); the others keep their value
+          for (int d = 0; d <= 2 * R; ++d) {
+            lds_vec<T, VX>(Vb + od[d], &w0[d * VX]);
+            lds_vec<T, VX>(Vb + od[d] + XT, &w1[d * VX]);
+          }
+          T ylo[R * VX], yhi[R * VX], xl0[VX + 2 * R], xl1[VX + 2 * R];
+#pragma unroll
+          for (int j = 0; j < R; ++j) {
+            lds_vec<T, VX>(P + (j - R) * XT, &ylo[j * VX]);
+            // without a second row, row y0+1+R may lie past the tile: read row y0+R instead
+            const int yo = (j == R - 1 && !row1) ? (1 + j) * XT : (2 + j) * XT;
+            lds_vec<T, VX>(P + yo, &yhi[j * VX]);
+          }
+#pragma unroll
+          for (int d = 1; d <= R; ++d) {
+            xl0[R - d] = P[-d];
+            xl0[R + VX - 1 + d] = P[VX - 1 + d];
+            xl1[R - d] = P[XT - d];
+            xl1[R + VX - 1 + d] = P[XT + VX - 1 + d];
+          }
 #pragma unroll
           for (int i = 0; i < VX; ++i) {
-            const bool odd0 = (t_par[g] + i + z) & 1;
-            if (odd0) r0[i] = yr[1][i];
-            else r1[i] = yr[2][i];
+            xl0[R + i] = w0[R * VX + i];
+            xl1[R + i] = w1[R * VX + i];
           }
-        }
-        T* Ub = sm + t_out[g] + po;
-        if (!(fl & 16)) {
-          sts_vec<T, VX>(Ub, r0);
-          if (row1) sts_vec<T, VX>(Ub + XT, r1);
-          if (fl & 64) sts_vec<T, VX>(gp, r0);  // final values of the own slab go to global memory
-          if (fl & 128) sts_vec<T, VX>(gp + ldx, r1);
-        } else {
+          T u0[VX], u1[VX];
+          if constexpr (Traits<S>::ORDER2) {
+            lds_vec<T, VX>(Ub, u0);
+            lds_vec<T, VX>(Ub + XT, u1);
+          }
           const int lo = (fl >> 8) & 15, hi = (fl >> 12) & 15;
+          T r0[VX], r1[VX];
+          mwd_points<S, T, VX>(w0, w1, ylo, yhi, xl0, xl1, u0, u1, kp, gstride, ldx, hi, true, cst, r0, r1);
+          if (!(fl & 16)) {
+            sts_vec<T, VX>(Ub, r0);
+            if (row1) sts_vec<T, VX>(Ub + XT, r1);
+            if (fl & 64) sts_vec<T, VX>(gp, r0);  // final values of the own slab go to global memory
+            if (fl & 128) sts_vec<T, VX>(gp + ldx, r1);
+          } else {
 #pragma unroll
-          for (int i = 0; i < VX; ++i)
-            if (i >= lo && i < hi) {
-              Ub[i] = r0[i];
-              if (row1) Ub[XT + i] = r1[i];
-              if (fl & 64) gp[i] = r0[i];
-              if (fl & 128) gp[ldx + i] = r1[i];
+            for (int i = 0; i < VX; ++i)
+              if (i >= lo && i < hi) {
+                Ub[i] = r0[i];
+                if (row1) Ub[XT + i] = r1[i];
+                if (fl & 64) gp[i] = r0[i];
+                if (fl & 128) gp[ldx + i] = r1[i];
+              }
+          }
+        } else {
+          if (!__any_sync(0xffffffffu, live)) continue;
+          const T* Vb = sm + t_in[g];
+          const T* P = Vb + po;
+          const bool row1 = fl & 2;
+          // rows y0-1, y0+2 (without a second row, row y0+2 may lie past the tile: row y0+1 is
+          // read instead) and the shared-memory x neighbours of the plane at Q
+          auto load_side = [&](const T* Q) {
+            lds_vec<T, VX>(Q - XT, t_yh[g][0]);
+            lds_vec<T, VX>(Q + (row1 ? 2 * XT : XT), t_yh[g][1]);
+            if (fl & (1 << 16)) {
+              t_xs[g][0] = Q[-1];
+              t_xs[g][1] = Q[XT - 1];
             }
+            if (fl & (1 << 17)) {
+              t_xs[g][2] = Q[VX];
+              t_xs[g][3] = Q[XT + VX];
+            }
+          };
+          if (live && !(fl & 32)) {  // first plane of the task: load the window (planes z-1, z)
+            const int pm = (po == 0 ? ring : po) - pe;
+            lds_vec<T, VX>(Vb + pm, t_zm[g][0]);
+            lds_vec<T, VX>(Vb + pm + XT, t_zm[g][1]);
+            lds_vec<T, VX>(P, t_zc[g][0]);
+            lds_vec<T, VX>(P + XT, t_zc[g][1]);
+            if (PRE) load_side(P);
+            t_fl[g] |= 32;
+          }
+          const int pp = (po + pe == ring) ? 0 : po + pe;
+          if (!PRE) load_side(P);
+          T yr[4][VX], zp[2][VX], xm[2], xp[2];
+          lds_vec<T, VX>(Vb + pp, zp[0]);
+          lds_vec<T, VX>(Vb + pp + XT, zp[1]);
+  #pragma unroll
+          for (int i = 0; i < VX; ++i) {
+            yr[0][i] = t_yh[g][0][i];
+            yr[1][i] = t_zc[g][0][i];
+            yr[2][i] = t_zc[g][1][i];
+            yr[3][i] = t_yh[g][1][i];
+          }
+  #pragma unroll
+          for (int r = 0; r < 2; ++r) {
+            const T l = __shfl_up_sync(0xffffffffu, yr[1 + r][VX - 1], 1);
+            const T q = __shfl_down_sync(0xffffffffu, yr[1 + r][0], 1);
+            xm[r] = (fl & (1 << 16)) ? t_xs[g][r] : l;
+            xp[r] = (fl & (1 << 17)) ? t_xs[g][2 + r] : q;
+          }
+          if (!live) continue;
+          T r0[VX], r1[VX];
+          if constexpr (NC > 0) {
+            if (!(fl & 32)) load_coef_pair<T, VX, NC>(kp, gstride, ldx, t_kn[g]);  // first plane: not prefetched
+            task_row2<S, T, VX, 0, 0>(yr, t_zm[g], zp, xm, xp, t_kn[g], cst, r0);
+            task_row2<S, T, VX, 1, 0>(yr, t_zm[g], zp, xm, xp, t_kn[g], cst, r1);
+            // prefetch the next plane's coefficients: consumed in the next step
+            if (z + 1 < nz) load_coef_pair<T, VX, NC>(kp + gplane, gstride, ldx, t_kn[g]);
+          } else {
+            T kv[1][VX];
+            task_row<S, T, VX, 0, 0>(yr, t_zm[g], zp, xm, xp, kv, cst, r0);
+            task_row<S, T, VX, 1, 0>(yr, t_zm[g], zp, xm, xp, kv, cst, r1);
+          }
+          if constexpr (Traits<S>::RB) {
+            // red-black: only points with (x + y + z + t) even are updated (row y0+1 has the other
+            // colour); the others keep their value
+  #pragma unroll
+            for (int i = 0; i < VX; ++i) {
+              const bool odd0 = (t_par[g] + i + z) & 1;
+              if (odd0) r0[i] = yr[1][i];
+              else r1[i] = yr[2][i];
+            }
+          }
+          T* Ub = sm + t_out[g] + po;
+          if (!(fl & 16)) {
+            sts_vec<T, VX>(Ub, r0);
+            if (row1) sts_vec<T, VX>(Ub + XT, r1);
+            if (fl & 64) sts_vec<T, VX>(gp, r0);  // final values of the own slab go to global memory
+            if (fl & 128) sts_vec<T, VX>(gp + ldx, r1);
+          } else {
+            const int lo = (fl >> 8) & 15, hi = (fl >> 12) & 15;
+  #pragma unroll
+            for (int i = 0; i < VX; ++i)
+              if (i >= lo && i < hi) {
+                Ub[i] = r0[i];
+                if (row1) Ub[XT + i] = r1[i];
+                if (fl & 64) gp[i] = r0[i];
+                if (fl & 128) gp[ldx + i] = r1[i];
+              }
+          }
+          // slide the window one plane up
+  #pragma unroll
+          for (int i = 0; i < VX; ++i) {
+            t_zm[g][0][i] = t_zc[g][0][i];
+            t_zm[g][1][i] = t_zc[g][1][i];
+            t_zc[g][0][i] = zp[0][i];
+            t_zc[g][1][i] = zp[1][i];
+          }
+          if (PRE && z + 1 < nz) load_side(Vb + pp);  // the next plane's rows y0-1, y0+2 and x neighbours
         }
-        // slide the window one plane up
-#pragma unroll
-        for (int i = 0; i < VX; ++i) {
-          t_zm[g][0][i] = t_zc[g][0][i];
-          t_zm[g][1][i] = t_zc[g][1][i];
-          t_zc[g][0][i] = zp[0][i];
-          t_zc[g][1][i] = zp[1][i];
-        }
-        if (PRE && z + 1 < nz) load_side(Vb + pp);  // the next plane's rows y0-1, y0+2 and x neighbours
       }
       fence_proxy_async_shared();  // shared-memory results ordered before later bulk copies into the slots
       __syncwarp();
@@ -427,7 +499,7 @@ __device__ __forceinline__ void mwd_ovl_tile(const MwdArgs& A, const int rho, co
 
 // Persistent kernel: clusters take diamonds from the FIFO as in mwd_async_kernel (Sect. 4.2.3).
 template <int S, typename T, int G>
-__global__ void __launch_bounds__(async_max_threads(G, Traits<S>::NCOEF > 0), 1)
+__global__ void __launch_bounds__(async_max_threads(G, Traits<S>::NCOEF > 0, Traits<S>::R == 4), 1)
     mwd_ovl_kernel(const __grid_constant__ MwdArgs A) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
   const int C = A.C;

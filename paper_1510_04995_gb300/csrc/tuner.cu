@@ -155,14 +155,15 @@ std::vector<girih_config> candidates(Plan* p) {
         }
       }
   // OVERLAP_PERSISTENT: blocks sized to the tasks of the widened levels the same way
-  if (async_stencil(p->stencil) && p->bulk_layout)
+  if (ovl_stencil(p->stencil) && p->bulk_layout)
     for (int dw = 2 * R; dw <= 64 * R; dw += 2 * R)
       for (int C : {1, 2, 4, 8, 16}) {
-        const int64_t tasks = mwd_ovl_tasks(R, dw, slab_width(p, C, MV_OVL), mwd_vx(p->stencil, p->dtype, MV_OVL));
+        const int64_t tasks =
+            mwd_ovl_tasks(R, dw, slab_width(p, C, MV_OVL), mwd_vx(p->stencil, p->dtype, MV_OVL), 16 / p->elem);
         int last = 0;
         for (int G : {1, 2, 4}) {
           const int th = (int)std::max<int64_t>(32, (tasks + 32LL * G - 1) / (32LL * G) * 32) + kOvlMovers;
-          if (th == last || th > async_max_threads(G, ncoef_of(p->stencil) > 0)) continue;
+          if (th == last || th > async_max_threads(G, ncoef_of(p->stencil) > 0, R == 4)) continue;
           last = th;
           girih_config c{GIRIH_ALGO_MWD, dw, 1, C, th, GIRIH_OVERLAP_PERSISTENT};
           if (check_config(p, &c, nullptr, nullptr, nullptr) == GIRIH_OK) out.push_back(c);

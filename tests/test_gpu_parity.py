@@ -468,6 +468,32 @@ def test_overlap_persistent(stencil, dtype):
             assert np.array_equal(pu, nu) and np.array_equal(pup, nup), (dw, cl, T, cfg)
 
 
+# radius 4 on the 70-wide grid: one-level diamonds (Dw = 2R) on a whole-row slab, and three-level
+# diamonds (Dw = 4R, slabs widened by 8 and 4 columns per side) at 1 and 2 tasks per thread
+OVL_R4_CFGS = [(8, 1, 256), (16, 4, 288), (16, 4, 176), (16, 8, 224)]
+
+
+@pytest.mark.parametrize("stencil", [2, 3, 4])
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+def test_overlap_persistent_radius4(stencil, dtype):
+    """The overlapped-slab kernel on the 25-point stencils (second order in time, constant,
+    variable and factor-grid coefficients): bit-identical to the naive sweep.  FP64 rings of
+    Dw = 4R diamonds exceed the shared memory, so FP64 runs Dw = 2R."""
+    nx, ny, nz = SIZES[4]
+    ldx = _aligned_ldx(nx, 4, dtype)
+    for dw, cl, th in OVL_R4_CFGS:
+        if dtype == "f64":
+            dw = 8
+        for T in (1, 3, 2 * (dw // 4) + 3):
+            u, up, co, c = inputs.make_problem(stencil, nx, ny, nz, seed=41 + T + dw, ldx=ldx)
+            nu, nup = gpu_sweep(stencil, dtype, u, up, co, c, T, nx, ny, nz, girih.config(girih.NAIVE), ldx=ldx)
+            kw = dict(dw=dw, nf=1, cluster=cl, threads=th, variant=girih.OVERLAP_PERSISTENT)
+            cfg = feasible_cfg(stencil, dtype, nx, ny, nz, kw, ldx=ldx)
+            assert cfg.variant == girih.OVERLAP_PERSISTENT
+            pu, pup = gpu_sweep(stencil, dtype, u, up, co, c, T, nx, ny, nz, cfg, ldx=ldx)
+            assert np.array_equal(pu, nu) and np.array_equal(pup, nup), (dw, cl, T, cfg)
+
+
 @pytest.mark.parametrize("shape", [(1, 1, 1), (33, 1, 9), (5, 70, 3), (129, 7, 40), (2, 2, 2), (300, 9, 5)])
 def test_overlap_persistent_degenerate_shapes(shape):
     """Slabs narrower than their widening, blocks with no columns, one-row and one-plane grids."""
@@ -487,10 +513,10 @@ def test_overlap_persistent_degenerate_shapes(shape):
 
 
 def test_overlap_persistent_rejections():
-    """Same domain as RELAXED_PERSISTENT: other stencils, unaligned layouts, nf > 1 and blocks too
-    small for the widened tile are rejected."""
+    """The box stencil, unaligned layouts, nf > 1 and blocks too small for the widened tile are
+    rejected."""
     nx, ny, nz = SIZES[1]
-    for stencil in (2, 3, 4, 5):
+    for stencil in (5,):
         R = inputs.RADIUS[stencil]
         p = girih.plan(stencil, *SIZES[R], dtype="f32", T=3, ldx=_aligned_ldx(SIZES[R][0], R, "f32"))
         assert not p.feasible(girih.config(girih.MWD, dw=8 * R, nf=1, cluster=2, threads=256,
