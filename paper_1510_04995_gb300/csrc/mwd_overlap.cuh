@@ -218,6 +218,11 @@ __device__ __forceinline__ void mwd_ovl_tile(const MwdArgs& A, const int rho, co
   // prefetched coefficients already fill the registers, 23 %, so they load after the barrier.
   constexpr bool PRE = S == 0;
   T t_yh[G][2][VX], t_xs[G][4];
+  // radius 4 without coefficient grids (or with the single factor grid): planes z-R .. z+R-1 of
+  // the task's two rows kept in registers and slid one plane per step, so only plane z+R is read
+  // from the ring; the variable-coefficient stencil's 13 grids leave no registers for it
+  constexpr bool WIN = R > 1 && Traits<S>::NCOEF <= 1;
+  T t_w[G][2][WIN ? 2 * R * VX : 1];
   T t_kn[G][NC > 0 ? NC : 1][NC > 0 ? 2 : 1][VX];
   if (!mover) {
     const int ntask = lev_tp[nlev];
@@ -306,20 +311,40 @@ __device__ __forceinline__ void mwd_ovl_tile(const MwdArgs& A, const int rho, co
           const T* P = Vb + po;
           const bool row1 = fl & 2;
           T* Ub = sm + t_out[g] + po;
-          int od[2 * R + 1];  // ring offsets of planes z-R .. z+R (one add and one wrap each)
-          od[R] = po;
-#pragma unroll
-          for (int d = 1; d <= R; ++d) {
-            const int up = od[R + d - 1] + pe;
-            od[R + d] = up >= ring ? up - ring : up;
-            const int dn = od[R - d + 1] - pe;
-            od[R - d] = dn < 0 ? dn + ring : dn;
-          }
           T w0[(2 * R + 1) * VX], w1[(2 * R + 1) * VX];
+          if (!WIN || !(fl & 32)) {
+            int od[2 * R + 1];  // ring offsets of planes z-R .. z+R (one add and one wrap each)
+            od[R] = po;
 #pragma unroll
-          for (int d = 0; d <= 2 * R; ++d) {
-            lds_vec<T, VX>(Vb + od[d], &w0[d * VX]);
-            lds_vec<T, VX>(Vb + od[d] + XT, &w1[d * VX]);
+            for (int d = 1; d <= R; ++d) {
+              const int up = od[R + d - 1] + pe;
+              od[R + d] = up >= ring ? up - ring : up;
+              const int dn = od[R - d + 1] - pe;
+              od[R - d] = dn < 0 ? dn + ring : dn;
+            }
+#pragma unroll
+            for (int d = 0; d <= 2 * R; ++d) {
+              lds_vec<T, VX>(Vb + od[d], &w0[d * VX]);
+              lds_vec<T, VX>(Vb + od[d] + XT, &w1[d * VX]);
+            }
+            if (WIN) t_fl[g] |= 32;
+          } else {
+            int top = po + R * pe;  // plane z+R
+            top = top >= ring ? top - ring : top;
+#pragma unroll
+            for (int j = 0; j < 2 * R * VX; ++j) {
+              w0[j] = t_w[g][0][j];
+              w1[j] = t_w[g][1][j];
+            }
+            lds_vec<T, VX>(Vb + top, &w0[2 * R * VX]);
+            lds_vec<T, VX>(Vb + top + XT, &w1[2 * R * VX]);
+          }
+          if constexpr (WIN) {  // the next step's planes z+1-R .. z+R
+#pragma unroll
+            for (int j = 0; j < 2 * R * VX; ++j) {
+              t_w[g][0][j] = w0[VX + j];
+              t_w[g][1][j] = w1[VX + j];
+            }
           }
           T ylo[R * VX], yhi[R * VX], xl0[VX + 2 * R], xl1[VX + 2 * R];
 #pragma unroll
