@@ -31,7 +31,7 @@ def test_tuned_entries_are_well_formed():
         assert blocked["algo"] == 1 and e["blocked_glups"] > 0
         assert blocked["dw"] % (2 * R) == 0 and 1 <= blocked["nf"] <= 4
         assert blocked["cluster"] in (1, 2, 4, 8, 16) and blocked["threads"] % 32 == 0
-        assert e["best_glups"] >= e["blocked_glups"]
+        assert e["best_glups"] >= e["blocked_glups"] * (1 - 1e-6)  # the database rounds to 6 decimals
 
 
 def test_measured_bytes_cite_existing_profiles():
