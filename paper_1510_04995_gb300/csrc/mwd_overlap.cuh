@@ -209,7 +209,13 @@ __device__ __forceinline__ void mwd_ovl_tile(const MwdArgs& A, const int rho, co
   int t_in[G], t_out[G], t_z[G], t_po[G], t_fl[G], t_par[G];
   const T* t_k[G];
   T* t_g[G];
-  T t_zm[G][2][VX], t_zc[G][2][VX];
+  // planes z-1, z (and z+1 once loaded) of a task's two rows, in three register slots.  With
+  // ROTATE the slots are used in rotation: at step w plane z-1 is in slot w mod 3, plane z in the
+  // next one, and plane z+1 is loaded into the third, so nothing moves between steps (the step
+  // loop is unrolled by 3).  The variable-coefficient stencil, whose prefetched coefficients
+  // fill the registers, slides the window instead (the unrolled loop spilled).
+  constexpr bool ROTATE = R == 1 && NC == 0;
+  T t_b[G][3][2][VX];
   // rows y0-1 and y0+2 of the task's plane and, at the ends of a run, the x neighbours from
   // shared memory.  With PRE they are loaded at the end of the previous step (that plane of
   // level t was completed by level s-1 two steps before it is used), so that after the step's
@@ -288,7 +294,8 @@ __device__ __forceinline__ void mwd_ovl_tile(const MwdArgs& A, const int rho, co
   __syncthreads();
 
   if (!mover) {
-    for (int w = 0; w < W; ++w) {
+    auto step = [&](const int w, auto rot) {
+      constexpr int ROT = decltype(rot)::value;  // w mod 3 (radius 1)
       __syncwarp();  // the named barriers are warp-aligned instructions
       if (w > 0) sync_full(w, NF);
 #pragma unroll
@@ -391,6 +398,9 @@ __device__ __forceinline__ void mwd_ovl_tile(const MwdArgs& A, const int rho, co
           }
         } else {
           if (!__any_sync(0xffffffffu, live)) continue;
+          T(&zm)[2][VX] = t_b[g][ROT];
+          T(&zc)[2][VX] = t_b[g][(ROT + 1) % 3];
+          T(&zp)[2][VX] = t_b[g][(ROT + 2) % 3];
           const T* Vb = sm + t_in[g];
           const T* P = Vb + po;
           const bool row1 = fl & 2;
@@ -410,23 +420,23 @@ __device__ __forceinline__ void mwd_ovl_tile(const MwdArgs& A, const int rho, co
           };
           if (live && !(fl & 32)) {  // first plane of the task: load the window (planes z-1, z)
             const int pm = (po == 0 ? ring : po) - pe;
-            lds_vec<T, VX>(Vb + pm, t_zm[g][0]);
-            lds_vec<T, VX>(Vb + pm + XT, t_zm[g][1]);
-            lds_vec<T, VX>(P, t_zc[g][0]);
-            lds_vec<T, VX>(P + XT, t_zc[g][1]);
+            lds_vec<T, VX>(Vb + pm, zm[0]);
+            lds_vec<T, VX>(Vb + pm + XT, zm[1]);
+            lds_vec<T, VX>(P, zc[0]);
+            lds_vec<T, VX>(P + XT, zc[1]);
             if (PRE) load_side(P);
             t_fl[g] |= 32;
           }
           const int pp = (po + pe == ring) ? 0 : po + pe;
           if (!PRE) load_side(P);
-          T yr[4][VX], zp[2][VX], xm[2], xp[2];
+          T yr[4][VX], xm[2], xp[2];
           lds_vec<T, VX>(Vb + pp, zp[0]);
           lds_vec<T, VX>(Vb + pp + XT, zp[1]);
   #pragma unroll
           for (int i = 0; i < VX; ++i) {
             yr[0][i] = t_yh[g][0][i];
-            yr[1][i] = t_zc[g][0][i];
-            yr[2][i] = t_zc[g][1][i];
+            yr[1][i] = zc[0][i];
+            yr[2][i] = zc[1][i];
             yr[3][i] = t_yh[g][1][i];
           }
   #pragma unroll
@@ -440,14 +450,14 @@ __device__ __forceinline__ void mwd_ovl_tile(const MwdArgs& A, const int rho, co
           T r0[VX], r1[VX];
           if constexpr (NC > 0) {
             if (!(fl & 32)) load_coef_pair<T, VX, NC>(kp, gstride, ldx, t_kn[g]);  // first plane: not prefetched
-            task_row2<S, T, VX, 0, 0>(yr, t_zm[g], zp, xm, xp, t_kn[g], cst, r0);
-            task_row2<S, T, VX, 1, 0>(yr, t_zm[g], zp, xm, xp, t_kn[g], cst, r1);
+            task_row2<S, T, VX, 0, 0>(yr, zm, zp, xm, xp, t_kn[g], cst, r0);
+            task_row2<S, T, VX, 1, 0>(yr, zm, zp, xm, xp, t_kn[g], cst, r1);
             // prefetch the next plane's coefficients: consumed in the next step
             if (z + 1 < nz) load_coef_pair<T, VX, NC>(kp + gplane, gstride, ldx, t_kn[g]);
           } else {
             T kv[1][VX];
-            task_row<S, T, VX, 0, 0>(yr, t_zm[g], zp, xm, xp, kv, cst, r0);
-            task_row<S, T, VX, 1, 0>(yr, t_zm[g], zp, xm, xp, kv, cst, r1);
+            task_row<S, T, VX, 0, 0>(yr, zm, zp, xm, xp, kv, cst, r0);
+            task_row<S, T, VX, 1, 0>(yr, zm, zp, xm, xp, kv, cst, r1);
           }
           if constexpr (Traits<S>::RB) {
             // red-black: only points with (x + y + z + t) even are updated (row y0+1 has the other
@@ -476,13 +486,14 @@ __device__ __forceinline__ void mwd_ovl_tile(const MwdArgs& A, const int rho, co
                 if (fl & 128) gp[ldx + i] = r1[i];
               }
           }
-          // slide the window one plane up
-  #pragma unroll
-          for (int i = 0; i < VX; ++i) {
-            t_zm[g][0][i] = t_zc[g][0][i];
-            t_zm[g][1][i] = t_zc[g][1][i];
-            t_zc[g][0][i] = zp[0][i];
-            t_zc[g][1][i] = zp[1][i];
+          if constexpr (!ROTATE) {  // slide the window one plane up
+#pragma unroll
+            for (int i = 0; i < VX; ++i) {
+              zm[0][i] = zc[0][i];
+              zm[1][i] = zc[1][i];
+              zc[0][i] = zp[0][i];
+              zc[1][i] = zp[1][i];
+            }
           }
           if (PRE && z + 1 < nz) load_side(Vb + pp);  // the next plane's rows y0-1, y0+2 and x neighbours
         }
@@ -490,6 +501,21 @@ __device__ __forceinline__ void mwd_ovl_tile(const MwdArgs& A, const int rho, co
       fence_proxy_async_shared();  // shared-memory results ordered before later bulk copies into the slots
       __syncwarp();
       arrive_done(w, ND);
+    };
+    using R0 = std::integral_constant<int, 0>;
+    using R1 = std::integral_constant<int, 1>;
+    using R2 = std::integral_constant<int, 2>;
+    int w = 0;
+    if constexpr (ROTATE) {
+      for (; w + 2 < W; w += 3) {
+        step(w, R0{});
+        step(w + 1, R1{});
+        step(w + 2, R2{});
+      }
+      if (w < W) step(w, R0{});
+      if (w + 1 < W) step(w + 1, R1{});
+    } else {
+      for (; w < W; ++w) step(w, R0{});
     }
   } else if (stager) {
     // iteration it: step it-1 is done, so the slots of the planes first read at step it+L are
