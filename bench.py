@@ -78,8 +78,8 @@ MEASURED_BYTES_PER_LUP = {
     (("naive",), 6, "f64"): (15.7, "profiles/naive_7pt_rbgs_f64_512x384x256.md"),
     (("naive",), 6, "f32"): (7.29, "profiles/naive_7pt_rbgs_f32_512x384x256.md"),
     (("mwd", 7, 6, 8, 224), 1, "f32"): (15.5, "profiles/mwd_ovl_7pt_var_f32_480x384x192.md"),
-    (("mwd", 7, 8, 4, 640), 0, "f32"): (4.01, "profiles/mwd_ovl_7pt_const_f32_512x384x256.md"),
-    (("mwd", 7, 4, 4, 352), 0, "f64"): (14.62, "profiles/mwd_ovl_7pt_const_f64_512x384x256.md"),
+    (("mwd", 7, 8, 4, 640), 0, "f32"): (4.02, "profiles/mwd_ovl_7pt_const_f32_512x384x256.md"),
+    (("mwd", 7, 4, 4, 352), 0, "f64"): (14.58, "profiles/mwd_ovl_7pt_const_f64_512x384x256.md"),
 }
 # domain-sized streams N_D of the code-balance model and the spatial minimum bytes per LUP (in elements)
 ND = {0: 2, 1: 9, 2: 2, 3: 15, 4: 3, 5: 2, 6: 2}
