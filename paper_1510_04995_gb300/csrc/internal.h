@@ -139,6 +139,7 @@ inline bool vec_only(int stencil) { return stencil == GIRIH_27PT_BOX || stencil 
 inline bool second_order(int stencil) { return stencil >= 2 && stencil <= 4; }
 inline int mwd_vx(int stencil, int dtype, int mv) {
   const bool r1 = radius_of(stencil) == 1;
+  if (mv == MV_OVL && r1 && dtype == GIRIH_F64 && ncoef_of(stencil) == 0) return 1;
   if (mv_shifted(mv)) return r1 ? (dtype == GIRIH_F64 ? 2 : 4) : (dtype == GIRIH_F32 ? 2 : 1);
   return (!r1 && dtype == GIRIH_F64) ? 1 : (dtype == GIRIH_F64 ? 2 : 4);
 }

@@ -73,9 +73,12 @@ __device__ __forceinline__ void mwd_ovl_tile(const MwdArgs& A, const int rho, co
                 "radius-1 first-order or radius-4 stencils");
   constexpr int R = Traits<S>::R;
   constexpr int NC = Traits<S>::NCOEF;
-  // columns per task: one 16-byte vector (radius 1), or 8 bytes (radius-4 FP32) and one column
-  // (radius-4 FP64), whose 2R+1 planes per row are read from the ring every step
-  constexpr int VX = R == 1 ? 16 / (int)sizeof(T) : (sizeof(T) == 4 ? 2 : 1);
+  // columns per task: one 16-byte vector (radius-1 FP32 and the FP64 variable-coefficient
+  // stencil), one column (radius-1 FP64 without coefficient grids: twice the tasks and warps for
+  // a sweep bound by the FP64 pipe, which needs many independent FMAs in flight), 8 bytes
+  // (radius-4 FP32) or one column (radius-4 FP64), whose 2R+1 planes per row are read from the
+  // ring every step
+  constexpr int VX = R == 1 ? ((sizeof(T) == 8 && NC == 0) ? 1 : 16 / (int)sizeof(T)) : (sizeof(T) == 4 ? 2 : 1);
   extern __shared__ __align__(128) unsigned char smem_raw[];
   T* sm = reinterpret_cast<T*>(smem_raw);
   const int NZ = A.NZ, YW = A.YW, XT = A.XT, XW = A.XW, C = A.C, K = A.K;
