@@ -105,8 +105,10 @@ typedef enum { GIRIH_ALGO_NAIVE = 0, GIRIH_ALGO_MWD = 1 } girih_algo;
  *              side, repeating the neighbours' edge columns instead of receiving them (the
  *              results stay bit-identical).  Before storing final values a block checks that
  *              both neighbours have staged the planes concerned (progress words in shared
- *              memory at cluster scope; a bounded wait).  Same stencils,
- *              layout, alignment and EINVAL rules as RELAXED_PERSISTENT.                   */
+ *              memory at cluster scope; a bounded wait).  One staging and one waiting warp
+ *              (blocks of more than 64 threads).  Built for the 7-point, red-black and
+ *              25-point stencils (not the box stencil; EINVAL); layout, alignment and nf = 1
+ *              rules as RELAXED_PERSISTENT.                                               */
 typedef enum {
   GIRIH_FED = 0,
   GIRIH_RELAXED = 1,
