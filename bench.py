@@ -290,7 +290,9 @@ def main():
     ap.add_argument("--nf", type=int, default=1)
     ap.add_argument("--cluster", type=int, default=0)
     ap.add_argument("--threads", type=int, default=256)
-    ap.add_argument("--variant", type=int, default=0, help="0 FED, 1 RELAXED, 2 FED_BULK, 3 FED_ELEM, 4 RELAXED_ELEM, 5 FED_PERSISTENT")
+    ap.add_argument("--variant", type=int, default=0, help="0 FED, 1 RELAXED, 2 FED_BULK, 3 FED_ELEM, 4 RELAXED_ELEM, "
+                    "5 FED_PERSISTENT, 6 RELAXED_PERSISTENT, 7 OVERLAP_PERSISTENT")
+    ap.add_argument("--zseg", type=int, default=0, help="OVERLAP_PERSISTENT: z planes per tile segment (0: whole tiles)")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-naive", action="store_true")
@@ -326,7 +328,7 @@ def main():
         cfg = girih.config(girih.NAIVE)
     elif args.algo == "mwd" and args.dw:
         cfg = girih.config(girih.MWD, dw=args.dw, nf=args.nf, cluster=args.cluster or 1, threads=args.threads,
-                           variant=args.variant)
+                           variant=args.variant, zseg=args.zseg)
     else:
         tuned, _ = _tuned(args.workload)
         cfg = girih.Config(**tuned) if tuned else p.config

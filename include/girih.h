@@ -135,7 +135,18 @@ typedef enum {
  *   nf       wavefront tile width N_F: z planes each time level advances per step (1..4).
  *   cluster  thread blocks sharing one tile along x (1, 2, 4, 8 or 16).
  *   threads  threads per block (multiple of 32, 64..1024).
- *   variant  girih_variant.                                                              */
+ *   variant  girih_variant.
+ *   zseg     OVERLAP_PERSISTENT only (0 elsewhere): the parallelepiped split of an extruded
+ *            diamond along z (Sect. 8).  0 = whole tiles.  zseg >= 1: segment j of a tile runs
+ *            the tile's wavefront steps [j zseg, (j+1) zseg) -- the last segment runs to the
+ *            tile's end -- as its own item of the persistent schedule, so that a diamond of the
+ *            next row starts on its first planes while this one still works on its later ones
+ *            (concurrency for grids with few diamonds per row).  A segment starts once its
+ *            tile's previous segment and, in the two parent diamonds, the segments up to
+ *            j + ceil(((tb - tb_parent - 1) K + R) / zseg) have completed (tb: first level,
+ *            K = R + nf); values cross segments through global memory (each segment but the
+ *            last also stores the values of its last K + R steps, 2K for the second-order
+ *            stencils).  EINVAL: zseg < 0, or zseg > 0 with another variant.              */
 typedef struct girih_config {
   int32_t algo;
   int32_t dw;
@@ -143,6 +154,7 @@ typedef struct girih_config {
   int32_t cluster;
   int32_t threads;
   int32_t variant;
+  int32_t zseg;
 } girih_config;
 
 /* Per-call parameters.  c[] holds the constant coefficients: 7PT_CONST uses c[0]=c0 (centre),

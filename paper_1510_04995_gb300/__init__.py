@@ -39,7 +39,8 @@ class GirihError(RuntimeError):
 
 class Config(ctypes.Structure):
     _fields_ = [("algo", ctypes.c_int32), ("dw", ctypes.c_int32), ("nf", ctypes.c_int32),
-                ("cluster", ctypes.c_int32), ("threads", ctypes.c_int32), ("variant", ctypes.c_int32)]
+                ("cluster", ctypes.c_int32), ("threads", ctypes.c_int32), ("variant", ctypes.c_int32),
+                ("zseg", ctypes.c_int32)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -57,8 +58,8 @@ class TuneRow(ctypes.Structure):
                 ("steps", ctypes.c_int64), ("smem", ctypes.c_int64), ("tune_seconds", ctypes.c_double)]
 
 
-def config(algo=MWD, dw=8, nf=1, cluster=1, threads=256, variant=FED) -> Config:
-    return Config(algo, dw, nf, cluster, threads, variant)
+def config(algo=MWD, dw=8, nf=1, cluster=1, threads=256, variant=FED, zseg=0) -> Config:
+    return Config(algo, dw, nf, cluster, threads, variant, zseg)
 
 
 def config_array(cfgs):
@@ -181,6 +182,14 @@ class Plan:
 
     def feasible(self, cfg: Config) -> bool:
         return lib().girih_config_check(self._h, ctypes.byref(cfg), None) == 0
+
+    def candidates(self) -> list:
+        """The tuner's candidate configurations for this plan (girih_tune_candidates)."""
+        n = _I32()
+        check(lib().girih_tune_candidates(self._h, None, 0, ctypes.byref(n)))
+        arr = (Config * max(n.value, 1))()
+        check(lib().girih_tune_candidates(self._h, arr, n.value, ctypes.byref(n)))
+        return list(arr[:n.value])
 
     def launch_count(self, cfg: Config | None = None) -> int:
         n = _I64()

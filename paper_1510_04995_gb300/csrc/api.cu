@@ -78,7 +78,7 @@ static int mwd_path(const Plan* p, const girih_config* c, bool ptrs16) {
   const int64_t plane = (p->ny + 2 * p->R) * p->ldx;
   const bool vec = p->bulk_layout && ptrs16 && plane < (1LL << 30);
   if (c->variant == GIRIH_RELAXED_PERSISTENT) return vec ? MV_ASYNC : MV_ELEM;
-  if (c->variant == GIRIH_OVERLAP_PERSISTENT) return vec ? MV_OVL : MV_ELEM;
+  if (c->variant == GIRIH_OVERLAP_PERSISTENT) return vec ? (c->zseg > 0 ? MV_OVLZ : MV_OVL) : MV_ELEM;
   return vec ? MV_VEC : MV_ELEM;
 }
 
@@ -101,6 +101,9 @@ int check_config(const Plan* p, const girih_config* c, int64_t* smem_out, int* x
   if (c->algo != GIRIH_ALGO_MWD) return fail(GIRIH_EINVAL, "unknown algo %d", c->algo);
   if (c->variant < GIRIH_FED || c->variant > GIRIH_OVERLAP_PERSISTENT)
     return fail(GIRIH_EINVAL, "unknown variant %d", c->variant);
+  if (c->zseg < 0) return fail(GIRIH_EINVAL, "zseg=%d must be >= 0", c->zseg);
+  if (c->zseg > 0 && c->variant != GIRIH_OVERLAP_PERSISTENT)
+    return fail(GIRIH_EINVAL, "zseg=%d: only OVERLAP_PERSISTENT splits tiles along z", c->zseg);
   if (c->variant == GIRIH_FED_PERSISTENT && mwd_path(p, c, ptrs16) != MV_VEC)
     return fail(GIRIH_EINVAL, "FED_PERSISTENT needs rows of 16-byte multiples and 16-byte aligned buffers");
   if (tma_variant(c->variant)) {
@@ -138,7 +141,7 @@ int check_config(const Plan* p, const girih_config* c, int64_t* smem_out, int* x
   const int XW = slab_width(p, c->cluster, mv);
   const int cthreads = c->threads;
   const int G = mwd_pairs_per_thread(p->stencil, p->dtype, c->dw, XW, c->threads, mv);
-  if (G == 0 && mv == MV_OVL)
+  if (G == 0 && mv_ovl(mv))
     return fail(GIRIH_EINVAL, "dw=%d with a %d-wide slab has %lld tasks on its widened levels: more than the %d "
                 "computing threads of a %d-thread block hold at 1, 2 or 4 per thread (blocks of at most %d, %d, %d "
                 "threads)", c->dw, XW, (long long)mwd_ovl_tasks(R, c->dw, XW, mwd_vx(p->stencil, p->dtype, mv), 16 / p->elem),
@@ -329,25 +332,51 @@ int run_sweep(Plan* p, int64_t T, void* u, void* u_prev, const void* coeffs, con
 // FED_PERSISTENT: build the FIFO of diamonds (row-major) and the per-row table, reset the FIFO
 // counter, bump the epoch (flags of earlier sweeps never equal it) and launch as many clusters
 // as the device holds at once (all resident, so dependency waits cannot deadlock).
+// OVERLAP_PERSISTENT with zseg > 0: the items are (diamond, z segment); item (rho, a, j) waits
+// for (rho, a, j-1) and for segment min(j + delta_rho, nseg - 1) of the two parents, so the FIFO
+// orders them by j + (max delta + 1) rho (every dependency comes earlier), then by row and diamond.
 static int launch_persistent(Plan* p, MwdArgs a, int64_t rows, const girih_config& cfg, int G, int mv,
                              int64_t smem, cudaStream_t st, cudaError_t* e_out) {
-  std::vector<int> items, table;
+  const int zs = cfg.zseg > 0 && cfg.zseg < p->nz ? cfg.zseg : 0;
+  const int nseg = zs ? (int)((p->nz + zs - 1) / zs) : 1;
+  const int Hh = cfg.dw / p->R / 2, K = p->R + cfg.nf;
+  int dmax = 0;
+  for (int64_t rho = 1; rho < rows && zs; ++rho) {
+    const int64_t d = std::max<int64_t>((rho - 1) * Hh + 1, 0) - std::max<int64_t>((rho - 2) * Hh + 1, 0);
+    dmax = std::max(dmax, (int)(((d - 1) * K + p->R + zs - 1) / zs));
+  }
+  struct Item {
+    int64_t key;
+    int rho, a, seg;
+  };
+  std::vector<Item> order;
+  std::vector<int> table;
+  int64_t n_flags = 0;
   for (int64_t rho = 0; rho < rows; ++rho) {
     int64_t a_min = 0, nd = 0;
     mwd_row_span(rho, cfg.dw, p->ny, &a_min, &nd);
-    table.push_back((int)(items.size() / 2));
+    table.push_back((int)n_flags);
     table.push_back((int)a_min);
     table.push_back((int)nd);
-    for (int64_t k = 0; k < nd; ++k) {
-      items.push_back((int)rho);
-      items.push_back((int)(a_min + k));
-    }
+    n_flags += nd * nseg;
+    for (int j = 0; j < nseg; ++j)
+      for (int64_t k = 0; k < nd; ++k) order.push_back({j + (int64_t)(dmax + 1) * rho, (int)rho, (int)(a_min + k), j});
   }
-  const int64_t n_items = (int64_t)items.size() / 2;
+  std::stable_sort(order.begin(), order.end(), [](const Item& x, const Item& y) {
+    return x.key != y.key ? x.key < y.key : (x.rho != y.rho ? x.rho < y.rho : x.a < y.a);
+  });
+  std::vector<int> items, segs;
+  for (const Item& it : order) {
+    items.push_back(it.rho);
+    items.push_back(it.a);
+    segs.push_back(it.seg);
+  }
+  const int64_t n_items = (int64_t)order.size();
   *e_out = cudaSuccess;
   if (n_items == 0) return GIRIH_OK;
   std::vector<int> host(items);
   host.insert(host.end(), table.begin(), table.end());
+  if (nseg > 1) host.insert(host.end(), segs.begin(), segs.end());
   cudaError_t e = cudaSuccess;
   if ((int64_t)host.size() > p->sched_cap) {
     if (p->sched) cudaFree(p->sched);
@@ -358,30 +387,31 @@ static int launch_persistent(Plan* p, MwdArgs a, int64_t rows, const girih_confi
     p->sched_cap = (int64_t)host.size();
     p->sched_T = -1;
   }
-  if (n_items > p->flags_cap) {
+  if (n_flags > p->flags_cap) {
     if (p->flags) cudaFree(p->flags);
     p->flags = nullptr;
     p->flags_cap = 0;
-    e = cudaMalloc(&p->flags, n_items * sizeof(int));
+    e = cudaMalloc(&p->flags, n_flags * sizeof(int));
     if (e != cudaSuccess) return fail(GIRIH_ENOMEM, "flag buffer: %s", cudaGetErrorString(e));
     // cleared on the sweep's own stream, so the clear is ordered before the kernel on any stream
     // (a recycled allocation may still hold an epoch of an earlier plan)
-    e = cudaMemsetAsync(p->flags, 0, n_items * sizeof(int), st);
+    e = cudaMemsetAsync(p->flags, 0, n_flags * sizeof(int), st);
     if (e != cudaSuccess) return cuda_fail(e, "flag reset");
-    p->flags_cap = n_items;
+    p->flags_cap = n_flags;
     p->epoch = 0;
   }
   if (!p->fifo) {
     e = cudaMalloc(&p->fifo, sizeof(int));
     if (e != cudaSuccess) return fail(GIRIH_ENOMEM, "FIFO counter: %s", cudaGetErrorString(e));
   }
-  // the list depends on (T, dw) only: upload it when they change (a pageable copy has taken
-  // the host data when it returns, and is ordered before the launch on the stream)
-  if (p->sched_T != rows || p->sched_dw != cfg.dw) {
+  // the list depends on (T, dw, zseg) only: upload it when they change (a pageable copy has
+  // taken the host data when it returns, and is ordered before the launch on the stream)
+  if (p->sched_T != rows || p->sched_dw != cfg.dw || p->sched_zs != zs) {
     e = cudaMemcpyAsync(p->sched, host.data(), host.size() * sizeof(int), cudaMemcpyHostToDevice, st);
     if (e != cudaSuccess) return cuda_fail(e, "schedule upload");
     p->sched_T = rows;
     p->sched_dw = cfg.dw;
+    p->sched_zs = zs;
   }
   e = cudaMemsetAsync(p->fifo, 0, sizeof(int), st);
   if (e != cudaSuccess) return cuda_fail(e, "schedule upload");
@@ -399,6 +429,9 @@ static int launch_persistent(Plan* p, MwdArgs a, int64_t rows, const girih_confi
   a.epoch = p->epoch;
   a.items = p->sched;
   a.rows = p->sched + 2 * n_items;
+  a.zseg = zs;
+  a.nseg = nseg;
+  a.segs = nseg > 1 ? a.rows + 3 * rows : nullptr;
   a.flags = p->flags;
   a.fifo = p->fifo;
   a.rho = 0;

@@ -60,6 +60,12 @@ struct MwdArgs {
   const int* rows;
   int* flags;
   int* fifo;
+  // OVERLAP_PERSISTENT split along z: items are (rho, a, segment), segs[item] the segment;
+  // segment j runs the tile's wavefront steps [j zseg, (j+1) zseg), the last one to the tile's
+  // end; the flag of (rho, a, j) is rows[3 rho] + (a - a_min(rho)) nseg + j.  nseg = 1: whole
+  // tiles (zseg and segs unused)
+  int32_t zseg, nseg;
+  const int* segs;
   int32_t lead;  // RELAXED_PERSISTENT: steps between a plane's staging and its first use (3..8)
   int32_t PE;    // RELAXED_PERSISTENT: elements per ring slot (YW * XT rounded up to 128 bytes)
   int32_t HMO;   // OVERLAP_PERSISTENT: staged columns on each side of the slab
@@ -82,8 +88,11 @@ struct MwdShape {
 // and the persistent schedule (RELAXED_PERSISTENT, mwd_async.cuh; radius-1 first-order stencils).
 // MV_OVL: the same blocks on x slabs widened by the halo every level needs, with no exchange
 // between blocks inside a step (OVERLAP_PERSISTENT, mwd_overlap.cuh).
-enum { MV_ELEM = 0, MV_VEC = 1, MV_BULK = 2, MV_ASYNC = 3, MV_OVL = 4 };
-inline bool mv_tma(int mv) { return mv == MV_ASYNC || mv == MV_OVL; }
+// MV_OVLZ: MV_OVL with its tiles split along z (separate kernel instances, so that the whole-tile
+// ones carry none of the segment logic).
+enum { MV_ELEM = 0, MV_VEC = 1, MV_BULK = 2, MV_ASYNC = 3, MV_OVL = 4, MV_OVLZ = 5 };
+inline bool mv_ovl(int mv) { return mv == MV_OVL || mv == MV_OVLZ; }
+inline bool mv_tma(int mv) { return mv == MV_ASYNC || mv_ovl(mv); }
 // OVERLAP_PERSISTENT: staged columns on each side of a slab, (H - 1) R rounded up to 16 bytes
 // (the bottom level of an unclipped diamond reads (smax + 1) R = (H - 1) R columns beyond it).
 inline int ovl_margin(int H, int R, int a16) { return ((H - 1) * R + a16 - 1) / a16 * a16; }
@@ -139,7 +148,7 @@ inline bool vec_only(int stencil) { return stencil == GIRIH_27PT_BOX || stencil 
 inline bool second_order(int stencil) { return stencil >= 2 && stencil <= 4; }
 inline int mwd_vx(int stencil, int dtype, int mv) {
   const bool r1 = radius_of(stencil) == 1;
-  if (mv == MV_OVL && r1 && dtype == GIRIH_F64 && ncoef_of(stencil) == 0) return 1;
+  if (mv_ovl(mv) && r1 && dtype == GIRIH_F64 && ncoef_of(stencil) == 0) return 1;
   if (mv_shifted(mv)) return r1 ? (dtype == GIRIH_F64 ? 2 : 4) : (dtype == GIRIH_F32 ? 2 : 1);
   return (!r1 && dtype == GIRIH_F64) ? 1 : (dtype == GIRIH_F64 ? 2 : 4);
 }

@@ -16,11 +16,11 @@ void* mwd_vec_kernel_box(int dtype, int G, bool tma);
 void* mwd_vec_kernel_rb(int dtype, int G, bool tma);
 
 void* mwd_async_kernel_ptr(int stencil, int dtype, int G);
-void* mwd_ovl_kernel_ptr(int stencil, int dtype, int G);
+void* mwd_ovl_kernel_ptr(int stencil, int dtype, int G, bool zseg);
 
 static void* pick(int stencil, int dtype, int G, int mv) {
   if (mv == MV_ASYNC) return mwd_async_kernel_ptr(stencil, dtype, G);
-  if (mv == MV_OVL) return mwd_ovl_kernel_ptr(stencil, dtype, G);
+  if (mv_ovl(mv)) return mwd_ovl_kernel_ptr(stencil, dtype, G, mv == MV_OVLZ);
   if (mv_shifted(mv)) {
     const bool tma = mv == MV_BULK;
     if (stencil == GIRIH_25PT_CGRID) return mwd_vec_kernel_cg(dtype, G, tma);
@@ -39,9 +39,9 @@ MwdShape mwd_shape(int stencil, int dtype, int dw, int nf, int XW, int mv, int l
   const int elem = dtype == GIRIH_F64 ? 8 : 4;
   const int a16 = 16 / elem;
   MwdShape s;
-  if (mv == MV_OVL) {
+  if (mv_ovl(mv)) {
     // the MV_ASYNC ring on widened slabs; load mbarriers, progress words (2) and item slot,
-    // level tables (5H+2)
+    // level tables (5H+3)
     const int L = lead;
     s.HM = ovl_margin(H, R, a16);
     s.NZ = L + 2 * R + 1 + (H - 2) * K;
@@ -50,7 +50,7 @@ MwdShape mwd_shape(int stencil, int dtype, int dw, int nf, int XW, int mv, int l
     const int per128 = 128 / elem;
     s.PE = (s.YW * s.XT + per128 - 1) / per128 * per128;
     const int64_t ring = 2LL * s.NZ * s.PE * elem;
-    s.smem_bytes = (ring + 15) / 16 * 16 + 8LL * kAsyncLoadBars + 16 + (5LL * H + 2) * 4;
+    s.smem_bytes = (ring + 15) / 16 * 16 + 8LL * kAsyncLoadBars + 16 + (5LL * H + 3) * 4;
     return s;
   }
   if (mv == MV_ASYNC) {
@@ -138,7 +138,7 @@ int mwd_pairs_per_thread(int stencil, int dtype, int dw, int XW, int threads, in
   const int R = radius_of(stencil);
   const int vx = mwd_vx(stencil, dtype, mv), lbf = mwd_lbf(stencil, dtype, mv);
   const int64_t ng = (int64_t)mwd_max_pairs(R, dw) * (XW / vx);
-  if (mv == MV_OVL) {  // the block's last two warps move data; the others compute
+  if (mv_ovl(mv)) {  // the block's last two warps move data; the others compute
     const int64_t nt = mwd_ovl_tasks(R, dw, XW, vx, 16 / (dtype == GIRIH_F64 ? 8 : 4));
     for (int G : {1, 2, 4})
       if (threads <= async_max_threads(G, ncoef_of(stencil) > 0, R == 4) && nt <= (int64_t)G * (threads - kOvlMovers))

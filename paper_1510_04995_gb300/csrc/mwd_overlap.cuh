@@ -64,11 +64,21 @@ __device__ __forceinline__ void wait_progress(const int* prog, bool left, bool r
   __syncwarp();
 }
 
-// One tile (diamond (a, a - rho), this block's widened x slab) from staging to write-back.
-// gstep: wavefront steps the block has run in earlier tiles of this launch (the load mbarriers
-// serve global steps modulo kLoadBars; progress words count global steps).
-template <int S, typename T, int G>
-__device__ __forceinline__ void mwd_ovl_tile(const MwdArgs& A, const int rho, const int a, int& gstep) {
+// One tile (diamond (a, a - rho), this block's widened x slab), or its z segment seg, from
+// staging to write-back.  gstep: wavefront steps the block has run in earlier items of this
+// launch (the load mbarriers serve global steps modulo kLoadBars; progress words count global
+// steps).
+//
+// Segments (ZS; Sect. 8's parallelepiped split of the extruded diamond): segment j runs the
+// tile's wavefront steps [j zseg, (j+1) zseg) (the last one to the tile's end), every level
+// advancing through the same steps.  Its first staging brings in every plane the levels read at
+// its first step (those of the earlier segment come from global memory), and a segment other
+// than the last stores, besides the final values, the values of its last B steps, which the next
+// segment reads: level s+1 reads level s R planes below its own, K + R steps back, and the
+// second-order update level s-2 at the centre, 2K steps back (B = K + R or 2K).
+template <int S, typename T, int G, bool ZS>
+__device__ __forceinline__ void mwd_ovl_tile(const MwdArgs& A, const int rho, const int a, const int seg,
+                                             int& gstep) {
   static_assert((Traits<S>::R == 1 && !Traits<S>::ORDER2 || Traits<S>::R == 4) && !Traits<S>::BOX,
                 "radius-1 first-order or radius-4 stencils");
   constexpr int R = Traits<S>::R;
@@ -95,6 +105,7 @@ __device__ __forceinline__ void mwd_ovl_tile(const MwdArgs& A, const int rho, co
   int* lev_nv = lev_f + A.H;  // vectors in that range
   int* lev_tp = lev_nv + A.H;  // tasks of the levels below (H + 1 entries)
   int* tile_sf = lev_tp + A.H + 1;  // first level with final values
+  int* tile_b0 = tile_sf + 1;       // first step of the band (read per step: kept out of registers)
 
   const int nx = (int)A.g.nx, ny = (int)A.g.ny, nz = (int)A.g.nz;
   const int ldx = (int)A.g.ldx;
@@ -121,7 +132,12 @@ __device__ __forceinline__ void mwd_ovl_tile(const MwdArgs& A, const int rho, co
   const int lane = tid & 31;
   const uint32_t lb0 = smem_addr(&lb[0]);
   const int g0 = gstep;
-  const int W = nz + smax * K;
+  // the item's steps [ws, ws + W) of the tile's nz + smax K
+  const bool last_seg = !ZS || seg + 1 >= A.nseg;
+  const int ws = ZS ? seg * A.zseg : 0;
+  const int W = last_seg ? nz + smax * K - ws : A.zseg;
+  // from step band0 on, every value of the block's own slab is stored (all but the last segment)
+  const int band0 = last_seg ? W : max(W - (Traits<S>::ORDER2 ? 2 * K : K + R), 0);
   gstep += W;
 
   // a row's value of level t+1 is final in the tile unless level t+2 also updates the row
@@ -148,18 +164,21 @@ __device__ __forceinline__ void mwd_ovl_tile(const MwdArgs& A, const int rho, co
     }
     lev_tp[nlev] = acc;
     *tile_sf = sf;
+    *tile_b0 = band0;
   }
   __syncthreads();
   const int sf = *tile_sf;
 
-  // ---- mover: staging copies of tile step j (planes -R .. R for step 0, plane j + R for step
-  //      j >= 1), both buffers, completing on load mbarrier (g0 + j) mod kLoadBars ----
+  // ---- mover: staging copies of item step j (for step 0 planes ws - smax K - R .. ws + R,
+  //      from -R at least; plane ws + j + R for step j >= 1), both buffers, completing on load
+  //      mbarrier (g0 + j) mod kLoadBars ----
   const uint32_t box_bytes = (uint32_t)(YW * XT * (int)sizeof(T));
-  // planes are staged in increasing z from -R, so the ring slot of the next one ((z + R) mod NZ)
+  // planes are staged in increasing z, so the ring slot of the next one ((z + R) mod NZ)
   // advances by one per plane (kept by the staging lane)
-  int next_slot = 0;
+  const int zfirst = max(ws - smax * K, 0) - R;
+  int next_slot = (zfirst + R) % NZ;
   auto stage_step = [&](int j) {
-    const int z0 = j == 0 ? -R : j + R, z1 = min(j + R, nz + R - 1);
+    const int z0 = j == 0 ? zfirst : ws + j + R, z1 = min(ws + j + R, nz + R - 1);
     if (lane == 0) {
       uint64_t* m = &lb[(g0 + j) & (kLoadBars - 1)];
       mbar_expect_tx(m, (uint32_t)(z1 >= z0 ? z1 - z0 + 1 : 0) * 2u * box_bytes);
@@ -193,13 +212,15 @@ __device__ __forceinline__ void mwd_ovl_tile(const MwdArgs& A, const int rho, co
     }
     __syncwarp();
   };
-  // step w stores final values to planes up to w - sf K; a neighbour stages plane z in its tile
-  // step max(z - R, 0): wait until both neighbours have landed that step.  The counts last read
-  // are kept, so shared memory is polled only when they do not already suffice.
+  // step w stores values to planes up to ws + w - s0 K (s0 = sf, or 0 in the band); a neighbour
+  // stages plane z in its item step max(z - ws - R, 0): wait until both neighbours have landed
+  // that step.  The counts last read are kept, so shared memory is polled only when they do not
+  // already suffice.
   uint32_t seen_l = 0, seen_r = 0;
   auto check_neighbours = [&](int w) {
-    if (!(has_l || has_r) || sf >= nlev) return;
-    const uint32_t need = (uint32_t)(g0 + max(w - sf * K - R, 0) + 1);
+    const int s0 = w >= band0 ? 0 : sf;
+    if (!(has_l || has_r) || s0 >= nlev) return;
+    const uint32_t need = (uint32_t)(g0 + max(w - s0 * K - R, 0) + 1);
     if ((has_l && seen_l < need) || (has_r && seen_r < need)) {
       wait_progress(prog, has_l, has_r, need, A.err);
       seen_l = ld_relaxed_cluster_u32(&prog[0]);
@@ -255,8 +276,8 @@ __device__ __forceinline__ void mwd_ovl_tile(const MwdArgs& A, const int rho, co
       // whole while any of its lanes has work)
       t_in[g] = valid ? (t & 1) * be + ro : XT + VX;
       t_out[g] = valid ? ((t & 1) ^ 1) * be + ro : XT + VX;
-      t_z[g] = -s * K;
-      t_po[g] = (((-s * K + R) % NZ + NZ) % NZ) * pe;
+      t_z[g] = ws - s * K;
+      t_po[g] = (((ws - s * K + R) % NZ + NZ) % NZ) * pe;
       const int lo = max(0, cl - xl), hi = min(VX, ch - xl);
       const bool row1 = valid && (y0 + 1 < lev_lo[s] + lev_w[s]);
       const bool own = xl >= HM && xl < HM + XW;  // the vector is in the block's own slab
@@ -266,13 +287,14 @@ __device__ __forceinline__ void mwd_ovl_tile(const MwdArgs& A, const int rho, co
       const bool own_r = xr == nv - 1 || lane == 31;
       // bits: 0 valid, 1 second row, 4 partial vector, 5 window loaded, 6 row y0 final, 7 row
       // y0+1 final, 8.. lo, 12.. hi, 16 left neighbour from shared memory, 17 right neighbour
-      // from shared memory
+      // from shared memory, 18 own slab (stored in a segment's band)
       t_fl[g] = (valid ? 1 : 0) | (row1 ? 2 : 0) | ((lo != 0 || hi != VX) ? 16 : 0) | (fin0 ? 64 : 0) |
-                (fin1 ? 128 : 0) | (lo << 8) | (hi << 12) | (own_l ? (1 << 16) : 0) | (own_r ? (1 << 17) : 0);
-      t_g[g] = static_cast<T*>(((t + 1) & 1) ? A.buf1 : A.buf0) + (int64_t)(-s * K + R) * gplane +
+                (fin1 ? 128 : 0) | (lo << 8) | (hi << 12) | (own_l ? (1 << 16) : 0) | (own_r ? (1 << 17) : 0) |
+                ((ZS && valid && own) ? (1 << 18) : 0);
+      t_g[g] = static_cast<T*>(((t + 1) & 1) ? A.buf1 : A.buf0) + (int64_t)(ws - s * K + R) * gplane +
                (int64_t)(y0 + R) * ldx + (sc0 + xl);
       t_par[g] = (sc0 - R + xl + y0 + t) & 1;
-      t_k[g] = NC ? static_cast<const T*>(A.coef) + (int64_t)(-s * K + R) * gplane + (int64_t)(y0 + R) * ldx +
+      t_k[g] = NC ? static_cast<const T*>(A.coef) + (int64_t)(ws - s * K + R) * gplane + (int64_t)(y0 + R) * ldx +
                         (sc0 + xl)
                   : nullptr;
     }
@@ -301,6 +323,13 @@ __device__ __forceinline__ void mwd_ovl_tile(const MwdArgs& A, const int rho, co
       constexpr int ROT = decltype(rot)::value;  // w mod 3 (radius 1)
       __syncwarp();  // the named barriers are warp-aligned instructions
       if (w > 0) sync_full(w, NF);
+      if constexpr (ZS) {
+        if (w == *tile_b0) {  // the band: from here on every value of the own slab goes to global memory
+#pragma unroll
+          for (int g = 0; g < G; ++g)
+            if (t_fl[g] & (1 << 18)) t_fl[g] |= 64 | ((t_fl[g] & 2) ? 128 : 0);
+        }
+      }
 #pragma unroll
       for (int g = 0; g < G; ++g) {
         const int fl = t_fl[g];
@@ -551,8 +580,9 @@ __device__ __forceinline__ void mwd_ovl_tile(const MwdArgs& A, const int rho, co
   }
 }
 
-// Persistent kernel: clusters take diamonds from the FIFO as in mwd_async_kernel (Sect. 4.2.3).
-template <int S, typename T, int G>
+// Persistent kernel: clusters take diamonds, or (ZS) z segments of diamonds, from the FIFO as in
+// mwd_async_kernel (Sect. 4.2.3).
+template <int S, typename T, int G, bool ZS>
 __global__ void __launch_bounds__(async_max_threads(G, Traits<S>::NCOEF > 0, Traits<S>::R == 4), 1)
     mwd_ovl_kernel(const __grid_constant__ MwdArgs A) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
@@ -585,13 +615,16 @@ __global__ void __launch_bounds__(async_max_threads(G, Traits<S>::NCOEF > 0, Tra
     const int it = *reinterpret_cast<volatile int*>(slot);
     if (it >= A.n_items) break;
     const int rho = A.items[2 * it], a = A.items[2 * it + 1];
-    if (rank == 0 && threadIdx.x == 0 && rho > 0) {
-      const int first = A.rows[3 * (rho - 1)], amin = A.rows[3 * (rho - 1) + 1], nd = A.rows[3 * (rho - 1) + 2];
+    const int seg = ZS ? A.segs[it] : 0;
+    // completion flag of (diamond (r, d), segment j)
+    auto flag = [&](int r, int d, int j) { return A.flags + A.rows[3 * r] + (d - A.rows[3 * r + 1]) * A.nseg + j; };
+    if (rank == 0 && threadIdx.x == 0 && (rho > 0 || seg > 0)) {
+      // the tile's previous segment, and the parents' segments up to seg + delta: the parents'
+      // level tb - 1 (this row's first input) lags this row's first level by (tb - tb_parent - 1) K
+      // planes in the wavefront, and this tile reads R planes beyond its own
       const uint64_t t0 = global_ns();
       const bool gave_up = *reinterpret_cast<volatile int*>(A.err) != 0;
-      for (int d = a - 1; d <= a && !gave_up; ++d) {
-        if (d < amin || d >= amin + nd) continue;
-        const int* f = A.flags + first + (d - amin);
+      auto wait_flag = [&](const int* f) {
         int v;
         for (;;) {
           asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(f) : "memory");
@@ -601,16 +634,32 @@ __global__ void __launch_bounds__(async_max_threads(G, Traits<S>::NCOEF > 0, Tra
             break;
           }
         }
+      };
+      if (seg > 0 && !gave_up) wait_flag(flag(rho, a, seg - 1));
+      if (rho > 0) {
+        const int amin = A.rows[3 * (rho - 1) + 1], nd = A.rows[3 * (rho - 1) + 2];
+        int jp = 0;
+        if (ZS) {
+          const int Hh = A.H / 2;
+          const int lag = max((rho - 1) * Hh + 1, 0) - max((rho - 2) * Hh + 1, 0) - 1;
+          jp = min(seg + (lag * A.K + Traits<S>::R + A.zseg - 1) / A.zseg, A.nseg - 1);
+        }
+        for (int d = a - 1; d <= a && !gave_up; ++d)
+          if (d >= amin && d < amin + nd) wait_flag(flag(rho - 1, d, jp));
       }
     }
+    // the item's completion flag (z segments: kept in shared memory over the tile, not in
+    // registers; whole tiles: the FIFO position)
+    if (ZS && rank == 0 && threadIdx.x == 0) slot[1] = (int)(flag(rho, a, seg) - A.flags);
     __syncwarp();
     cluster_barrier();
-    mwd_ovl_tile<S, T, G>(A, rho, a, gstep);
+    mwd_ovl_tile<S, T, G, ZS>(A, rho, a, seg, gstep);
     __syncwarp();
     cluster_barrier();
     if (rank == 0 && threadIdx.x == 0) {
       asm volatile("fence.acq_rel.gpu;" ::: "memory");
-      asm volatile("st.relaxed.gpu.global.u32 [%0], %1;" ::"l"(A.flags + it), "r"(A.epoch) : "memory");
+      asm volatile("st.relaxed.gpu.global.u32 [%0], %1;" ::"l"(A.flags + (ZS ? slot[1] : it)), "r"(A.epoch)
+                   : "memory");
     }
   }
 }

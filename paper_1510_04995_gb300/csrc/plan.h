@@ -22,8 +22,8 @@ struct girih_plan_s {
   // persistent schedule: item list + per-row table, completion flags, FIFO counter, run epoch
   int* sched = nullptr;
   int64_t sched_cap = 0;  // ints
-  int64_t sched_T = -1;   // diamond rows and width of the uploaded list
-  int32_t sched_dw = 0;
+  int64_t sched_T = -1;   // diamond rows, width and z segment of the uploaded list
+  int32_t sched_dw = 0, sched_zs = 0;
   int* flags = nullptr;
   int64_t flags_cap = 0;  // ints
   int* fifo = nullptr;

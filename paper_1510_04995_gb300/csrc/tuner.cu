@@ -166,7 +166,16 @@ std::vector<girih_config> candidates(Plan* p) {
           if (th == last || th > async_max_threads(G, ncoef_of(p->stencil) > 0, R == 4)) continue;
           last = th;
           girih_config c{GIRIH_ALGO_MWD, dw, 1, C, th, GIRIH_OVERLAP_PERSISTENT};
-          if (check_config(p, &c, nullptr, nullptr, nullptr) == GIRIH_OK) out.push_back(c);
+          if (check_config(p, &c, nullptr, nullptr, nullptr) != GIRIH_OK) continue;
+          out.push_back(c);
+          // rows of fewer diamonds than the device has clusters: also split the tiles along z
+          // (Sect. 8), so that the next row's diamonds start before this row's finish
+          if ((p->ny + dw - 1) / dw + 1 < std::max(p->sm_count / C, 1))
+            for (int zs : {32, 64, 128}) {
+              if (zs >= p->nz) break;
+              c.zseg = zs;
+              if (check_config(p, &c, nullptr, nullptr, nullptr) == GIRIH_OK) out.push_back(c);
+            }
         }
       }
   g_err_clear();
@@ -196,9 +205,10 @@ int girih_tune_measure(girih_plan_t plan, const girih_config* cfg, double tol, i
 }
 
 static void append_csv(FILE* f, const Plan* p, const girih_tune_row& r) {
-  fprintf(f, "%d,%d,%lld,%lld,%lld,%d,%d,%d,%d,%d,%d,%.6f,%.6e,%lld,%lld,%.6e\n", p->stencil, p->dtype,
+  fprintf(f, "%d,%d,%lld,%lld,%lld,%d,%d,%d,%d,%d,%d,%.6f,%.6e,%lld,%lld,%.6e,%d\n", p->stencil, p->dtype,
           (long long)p->nx, (long long)p->ny, (long long)p->nz, r.cfg.algo, r.cfg.dw, r.cfg.nf, r.cfg.cluster,
-          r.cfg.threads, r.cfg.variant, r.glups, r.seconds, (long long)r.steps, (long long)r.smem, r.tune_seconds);
+          r.cfg.threads, r.cfg.variant, r.glups, r.seconds, (long long)r.steps, (long long)r.smem, r.tune_seconds,
+          r.cfg.zseg);
 }
 
 static int candidate_list(Plan* p, const girih_config* given, int32_t n, std::vector<girih_config>* out) {

@@ -35,7 +35,7 @@ GRIDS = [(128, 256, 512), (256, 128, 512), (192, 384, 512), (256, 512, 512), (38
          (768, 512, 512), (768, 768, 512)]
 HELD_OUT = (2, 6, 9)
 FIELDS = ["stencil", "dtype", "nx", "ny", "nz", "algo", "dw", "nf", "cluster", "threads", "variant", "glups",
-          "seconds", "steps", "smem", "tune_seconds"]
+          "seconds", "steps", "smem", "tune_seconds", "zseg"]  # zseg: absent in rows written before it existed
 
 
 def _dt(d):
@@ -78,7 +78,7 @@ def space(p) -> list:
         arr = (Config * n.value)()
         check(lib().girih_tune_candidates(p.handle, arr, n.value, ctypes.byref(n)))
         out += [c for c in arr if c.variant in (RELAXED_PERSISTENT, OVERLAP_PERSISTENT)
-                and c.dw in (2 * R, 4 * R, 8 * R, 16 * R) and c.cluster in (4, 8, 16)]
+                and c.dw in (2 * R, 4 * R, 8 * R, 16 * R) and c.cluster in (4, 8, 16) and c.zseg == 0]
     return out
 
 
@@ -120,7 +120,7 @@ def problem_key(r):
 
 def row_config(r) -> Config:
     return Config(int(r["algo"]), int(r["dw"]), int(r["nf"]), int(r["cluster"]), int(r["threads"]),
-                  int(r["variant"]))
+                  int(r["variant"]), int(r.get("zseg", 0)))
 
 
 def features(rows) -> np.ndarray:

@@ -512,6 +512,79 @@ def test_overlap_persistent_degenerate_shapes(shape):
                 assert np.array_equal(pu, nu) and np.array_equal(pup, nup), (shape, dtype, stencil, cfg)
 
 
+# z segments of one plane, shorter than the stored band, ragged (33 = 4 x 7 + 5) and longer than
+# the band
+OVL_ZSEG = [1, 3, 7, 16]
+
+
+@pytest.mark.parametrize("stencil", [0, 1, 6])
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+def test_overlap_persistent_zsegments(stencil, dtype):
+    """OVERLAP_PERSISTENT with its tiles split along z (Sect. 8: each parallelepiped segment is
+    an item of the persistent schedule, started once the tile's previous segment and the parents'
+    segments it reads have completed; values cross segments through global memory): bit-identical
+    to the naive sweep over segment lengths, cluster sizes, diamond widths and truncated rows."""
+    nx, ny, nz = SIZES[1]
+    ldx = _aligned_ldx(nx, 1, dtype)
+    for dw, cl, th in [(4, 1, 256), (8, 4, 96), (6, 16, 96), (12, 8, 224)]:
+        for T in (dw - 1, 2 * dw + 3):
+            u, up, co, c = inputs.make_problem(stencil, nx, ny, nz, seed=53 + T + dw, ldx=ldx)
+            nu, nup = gpu_sweep(stencil, dtype, u, up, co, c, T, nx, ny, nz, girih.config(girih.NAIVE), ldx=ldx)
+            for zs in OVL_ZSEG:
+                kw = dict(dw=dw, nf=1, cluster=cl, threads=th, variant=girih.OVERLAP_PERSISTENT, zseg=zs)
+                cfg = feasible_cfg(stencil, dtype, nx, ny, nz, kw, ldx=ldx)
+                assert cfg.zseg == zs
+                pu, pup = gpu_sweep(stencil, dtype, u, up, co, c, T, nx, ny, nz, cfg, ldx=ldx)
+                assert np.array_equal(pu, nu) and np.array_equal(pup, nup), (dw, cl, T, zs, cfg)
+
+
+@pytest.mark.parametrize("stencil", [2, 3, 4])
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+def test_overlap_persistent_zsegments_radius4(stencil, dtype):
+    """z segments of the 25-point sweeps (second order in time: the stored band also carries level
+    t-2 for the centre of the next segment's updates): bit-identical to the naive sweep."""
+    nx, ny, nz = SIZES[4]
+    ldx = _aligned_ldx(nx, 4, dtype)
+    for dw, cl, th in [(8, 1, 256), (16, 4, 288)]:
+        if dtype == "f64":
+            dw = 8
+        for T in (3, 2 * (dw // 4) + 3):
+            u, up, co, c = inputs.make_problem(stencil, nx, ny, nz, seed=61 + T + dw, ldx=ldx)
+            nu, nup = gpu_sweep(stencil, dtype, u, up, co, c, T, nx, ny, nz, girih.config(girih.NAIVE), ldx=ldx)
+            for zs in (1, 5, 12):
+                kw = dict(dw=dw, nf=1, cluster=cl, threads=th, variant=girih.OVERLAP_PERSISTENT, zseg=zs)
+                cfg = feasible_cfg(stencil, dtype, nx, ny, nz, kw, ldx=ldx)
+                assert cfg.zseg == zs
+                pu, pup = gpu_sweep(stencil, dtype, u, up, co, c, T, nx, ny, nz, cfg, ldx=ldx)
+                assert np.array_equal(pu, nu) and np.array_equal(pup, nup), (dw, cl, T, zs, cfg)
+
+
+def test_zsegments_rejections_and_tuner_candidates():
+    """zseg is OVERLAP_PERSISTENT's alone and not negative; the tuner adds segmented candidates
+    (32, 64, 128 planes) exactly where a diamond row has fewer diamonds than the device has
+    clusters."""
+    import torch
+    nx, ny, nz = SIZES[1]
+    ldx = _aligned_ldx(nx, 1, "f32")
+    p = girih.plan(0, nx, ny, nz, dtype="f32", T=3, ldx=ldx)
+    assert p.feasible(girih.config(girih.MWD, dw=8, nf=1, cluster=2, threads=256,
+                                   variant=girih.OVERLAP_PERSISTENT, zseg=4))
+    assert not p.feasible(girih.config(girih.MWD, dw=8, nf=1, cluster=2, threads=256,
+                                       variant=girih.OVERLAP_PERSISTENT, zseg=-1))
+    for v in (girih.FED, girih.FED_PERSISTENT, girih.RELAXED_PERSISTENT):
+        assert not p.feasible(girih.config(girih.MWD, dw=8, nf=1, cluster=2, threads=320, variant=v, zseg=4)), v
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    for ny in (64, 2048):
+        q = girih.plan(1, 256, ny, 256, dtype="f32", T=8, ldx=_aligned_ldx(256, 1, "f32"))
+        cands = q.candidates()
+        ovl = [c for c in cands if c.variant == girih.OVERLAP_PERSISTENT]
+        for dw, cl, th in {(c.dw, c.cluster, c.threads) for c in ovl}:
+            segs = {c.zseg for c in ovl if (c.dw, c.cluster, c.threads) == (dw, cl, th)}
+            few = (ny + dw - 1) // dw + 1 < max(sms // cl, 1)
+            assert segs == ({0, 32, 64, 128} if few else {0}), (ny, dw, cl, th, segs)
+        assert all(c.zseg == 0 for c in cands if c.variant != girih.OVERLAP_PERSISTENT)
+
+
 def test_overlap_persistent_rejections():
     """The box stencil, unaligned layouts, nf > 1 and blocks too small for the widened tile are
     rejected."""

@@ -52,7 +52,7 @@ def test_db_round_trip(tmp_path):
     with open(p, "w") as f:
         f.write("# comment\n")
         for r in rows:
-            f.write(",".join(str(r[k]) for k in learned.FIELDS) + "\n")
+            f.write(",".join(str(r.get(k, 0)) for k in learned.FIELDS) + "\n")
     back = learned.load_db(str(p))
     assert [learned.problem_key(r) for r in back] == [learned.problem_key(r) for r in rows]
     assert [learned.row_config(r).as_dict() for r in back] == [learned.row_config(r).as_dict() for r in rows]
