@@ -319,9 +319,18 @@ static cudaError_t launch_v(const NaiveArgs& a, cudaStream_t st) {
 
 int naive_tile_y(int stencil, int dtype) {
   const bool f64 = dtype == GIRIH_F64;
+  auto pick = [&](auto s_tag) -> int {
+    constexpr int S = decltype(s_tag)::value;
+    return 2 * (f64 ? naive_ty<S, double>() : naive_ty<S, float>());
+  };
   switch (stencil) {
-    case 3: return 2 * (f64 ? naive_ty<3, double>() : naive_ty<3, float>());
-    default: return 2 * naive_ty<0, float>();
+    case 0: return pick(std::integral_constant<int, 0>());
+    case 1: return pick(std::integral_constant<int, 1>());
+    case 2: return pick(std::integral_constant<int, 2>());
+    case 3: return pick(std::integral_constant<int, 3>());
+    case 4: return pick(std::integral_constant<int, 4>());
+    case 5: return pick(std::integral_constant<int, 5>());
+    default: return pick(std::integral_constant<int, 6>());
   }
 }
 
