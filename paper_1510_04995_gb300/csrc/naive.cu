@@ -36,6 +36,49 @@ struct NaiveAcc {  // one column of the thread's VX columns
   }
 };
 
+// Two columns of the thread as one packed accessor: every value is the pair of the two columns'
+// values (FP32 sweeps with an even number of columns per thread).  D: the second column's offset
+// from the first, 32 (radius 1: the interior starts at an odd shared column, so pairs of
+// neighbours are packed from single loads) or 1 (radius 4: the first column is even, so pairs of
+// y neighbours and of even x offsets are single 8-byte shared loads, and the odd x offsets are
+// assembled from the halves of the even ones).
+template <int S, int TW, int D>
+struct NaiveAcc2 {
+  const float* tc;  // first column's cell in the shared plane tile
+  const float* w0;  // the two columns' register windows
+  const float* w1;
+  const float* kv0;
+  const float* kv1;
+  F2 uc;
+  const float* tcm;
+  const float* tcp;
+  __device__ __forceinline__ F2 c() const { return pack2(w0[Traits<S>::R], w1[Traits<S>::R]); }
+  __device__ __forceinline__ F2 ld2(int o) const {  // the pair at tc + o (D = 1: o even)
+    if constexpr (D == 1) return F2{*reinterpret_cast<const unsigned long long*>(tc + o)};
+    return pack2(tc[o], tc[o + D]);
+  }
+  __device__ __forceinline__ F2 x(int d) const {
+    if constexpr (D == 1) {
+      if (d & 1) {  // (c+d, c+d+1): the high half of the pair at d-1, the low half of the pair at d+1
+        float a0, a1, b0, b1;
+        unpack2(d - 1 == 0 ? c() : ld2(d - 1), a0, a1);
+        unpack2(d + 1 == 0 ? c() : ld2(d + 1), b0, b1);
+        return pack2(a1, b0);
+      }
+    }
+    return ld2(d);
+  }
+  __device__ __forceinline__ F2 y(int d) const { return ld2(d * TW); }
+  __device__ __forceinline__ F2 z(int d) const { return pack2(w0[Traits<S>::R + d], w1[Traits<S>::R + d]); }
+  __device__ __forceinline__ F2 u() const { return uc; }
+  __device__ __forceinline__ F2 k(int g) const { return pack2(kv0[g], kv1[g]); }
+  __device__ __forceinline__ F2 b(int dx, int dy, int dz) const {
+    if (dx == 0 && dy == 0) return z(dz);
+    const float* q = (dz < 0 ? tcm : (dz > 0 ? tcp : tc)) + dy * TW + dx;
+    return pack2(q[0], q[D]);
+  }
+};
+
 // Block = 32 x TY threads over a 32 x 2TY tile of (x, y) columns and a chunk of z planes; each
 // thread owns rows ty and ty + TY.  The tile's planes (with the R-wide halo) stream through a
 // ring of NP = R + PD + 2 (+1 for the box stencil) shared-memory slots filled PD planes ahead of
@@ -52,8 +95,13 @@ struct NaiveAcc {  // one column of the thread's VX columns
 // VX columns per thread, 32 apart (the tile is 32*VX columns wide; a warp's accesses stay on
 // consecutive words, free of bank conflicts): VX > 1 shares each thread's per-plane work
 // (barrier, staging items, loop control) among VX*2 updates.
+// Blocks per SM the register allocation must allow (0: no bound): 2 for the packed FP32 25-point
+// factor-grid sweep, whose two column pairs of 2R+1-plane windows take 122 registers.
+template <int S, typename T, int VX>
+constexpr int naive_min_blocks() { return (S == 4 && sizeof(T) == 4 && VX == 2) ? 2 : 0; }
+
 template <int S, typename T, int TY, int PD, bool V16, int VX>
-__global__ void __launch_bounds__(32 * TY) naive_kernel(const NaiveArgs a) {
+__global__ void __launch_bounds__(32 * TY, (naive_min_blocks<S, T, VX>())) naive_kernel(const NaiveArgs a) {
   constexpr int R = Traits<S>::R;
   constexpr int NC = Traits<S>::NCOEF;
   constexpr int ROWS = 2 * TY;
@@ -73,6 +121,19 @@ __global__ void __launch_bounds__(32 * TY) naive_kernel(const NaiveArgs a) {
   T cst[5];
 #pragma unroll
   for (int i = 0; i < 5; ++i) cst[i] = sizeof(T) == 8 ? static_cast<T>(a.c[i]) : static_cast<T>(a.cf[i]);
+  // FP32 with an even number of columns per thread: two columns per packed update (measured at
+  // full size: 7-point constant 714 -> 739, red-black 707 -> 738, 25-point factor grid with two
+  // columns per thread 284 -> 305 GLUP/s; not the box stencil, 320 -> 314, whose 26 neighbours
+  // packed from single loads cost more moves than the packing saves, nor the 25-point constant
+  // one, 328 -> 325).  Radius 4: the thread's columns are adjacent pairs, 64 apart (2 tx,
+  // 2 tx + 1, 64 + 2 tx, ...), so that a warp's 8-byte loads of a row stay on consecutive words;
+  // otherwise 32 apart.
+  constexpr bool PACK = sizeof(T) == 4 && VX % 2 == 0 && !Traits<S>::BOX && S != 2;
+  constexpr bool PAIRS = PACK && R == 4;
+  constexpr int D2 = PAIRS ? 1 : 32;
+  F2 cst2[5];
+#pragma unroll
+  for (int i = 0; i < 5; ++i) cst2[i] = pack2(a.cf[i], a.cf[i]);
 
   const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * 32 + tx;
   const int nx = (int)a.g.nx, ny = (int)a.g.ny, nz = (int)a.g.nz;
@@ -122,19 +183,22 @@ __global__ void __launch_bounds__(32 * TY) naive_kernel(const NaiveArgs a) {
   for (int q = R - ZB; q <= 2 * R + PD; ++q) stage(q);
 
   bool act[2][VX];
-  int cofs[2];  // shared offset of the thread's first column in each row
+  int cx[VX];  // the thread's columns within the tile
+#pragma unroll
+  for (int v = 0; v < VX; ++v) cx[v] = PAIRS ? 64 * (v >> 1) + 2 * tx + (v & 1) : 32 * v + tx;
+  int cofs[2];  // shared offset of column 0 in each of the thread's rows
   T w[2][VX][2 * R + 1];
 #pragma unroll
   for (int r = 0; r < 2; ++r) {
     const int row = ty + r * TY;
-    cofs[r] = (row + R) * TXW + tx + R;
+    cofs[r] = (row + R) * TXW + R;
 #pragma unroll
     for (int v = 0; v < VX; ++v) {
-      act[r][v] = (bx + v * 32 + tx < nx) && (by + row < ny);
+      act[r][v] = (bx + cx[v] < nx) && (by + row < ny);
       // the R-ZB lowest planes of the window, straight from global memory
 #pragma unroll
       for (int i = 0; i < R - ZB; ++i)
-        w[r][v][i] = act[r][v] ? Vb[(int64_t)i * plane + (row + R) * ldx + tx + R + v * 32] : T(0);
+        w[r][v][i] = act[r][v] ? Vb[(int64_t)i * plane + (row + R) * ldx + R + cx[v]] : T(0);
     }
   }
   cp_async_wait_all();
@@ -144,7 +208,7 @@ __global__ void __launch_bounds__(32 * TY) naive_kernel(const NaiveArgs a) {
 #pragma unroll
     for (int v = 0; v < VX; ++v)
 #pragma unroll
-      for (int i = R - ZB; i <= 2 * R; ++i) w[r][v][i] = ring[(i % NP) * TP + cofs[r] + v * 32];
+      for (int i = R - ZB; i <= 2 * R; ++i) w[r][v][i] = ring[(i % NP) * TP + cofs[r] + cx[v]];
   // every thread has its first window before the first in-loop staging refills a slot
   __syncthreads();
   // per-column pointers, advanced one plane per update: the output point (also the level t-1
@@ -156,7 +220,7 @@ __global__ void __launch_bounds__(32 * TY) naive_kernel(const NaiveArgs a) {
   for (int r = 0; r < 2; ++r)
 #pragma unroll
     for (int v = 0; v < VX; ++v) {
-      const int64_t o = (int64_t)(ty + r * TY) * ldx + v * 32 + tx;
+      const int64_t o = (int64_t)(ty + r * TY) * ldx + cx[v];
       up[r][v] = Ub + o;
       kp[r][v] = coef ? coef + (int64_t)(z0 + R) * plane + (int64_t)(by + R) * ldx + (bx + R) + o : nullptr;
     }
@@ -213,18 +277,47 @@ __global__ void __launch_bounds__(32 * TY) naive_kernel(const NaiveArgs a) {
     const T* tlp = ring + ((zr + R + ZB) % NP) * TP;
 #pragma unroll
     for (int r = 0; r < 2; ++r) {
+      if constexpr (PACK) {
+        // columns v and v+1 in one packed update; a column outside the grid is computed from
+        // in-bounds shared cells and not stored
 #pragma unroll
-      for (int v = 0; v < VX; ++v) {
-        if (act[r][v]) {
-          NaiveAcc<S, T, TXW> acc{tl + cofs[r] + v * 32, w[r][v], kv[r][v], T(0), tlm + cofs[r] + v * 32,
-                                  tlp + cofs[r] + v * 32};
-          if constexpr (Traits<S>::ORDER2) acc.uc = uc[r][v];
-          T res = point_update<S, T>(acc, cst);
-          if constexpr (Traits<S>::RB)  // red-black: only (x + y + z + t) even is updated
-            if ((bx + v * 32 + tx + by + ty + r * TY + z0 + zr + a.t) & 1) res = w[r][v][R];
-          *up[r][v] = res;
+        for (int v = 0; v < VX; v += 2) {
+          if (act[r][v] || act[r][v + 1]) {
+            NaiveAcc2<S, TXW, D2> acc{reinterpret_cast<const float*>(tl) + cofs[r] + cx[v],
+                                  reinterpret_cast<const float*>(w[r][v]),
+                                  reinterpret_cast<const float*>(w[r][v + 1]),
+                                  reinterpret_cast<const float*>(kv[r][v]),
+                                  reinterpret_cast<const float*>(kv[r][v + 1]),
+                                  F2{0},
+                                  reinterpret_cast<const float*>(tlm) + cofs[r] + cx[v],
+                                  reinterpret_cast<const float*>(tlp) + cofs[r] + cx[v]};
+            if constexpr (Traits<S>::ORDER2) acc.uc = pack2((float)uc[r][v], (float)uc[r][v + 1]);
+            float res[2];
+            unpack2(point_update<S, F2>(acc, cst2), res[0], res[1]);
+#pragma unroll
+            for (int e = 0; e < 2; ++e) {
+              if constexpr (Traits<S>::RB)  // red-black: only (x + y + z + t) even is updated
+                if ((bx + cx[v + e] + by + ty + r * TY + z0 + zr + a.t) & 1) res[e] = (float)w[r][v + e][R];
+              if (act[r][v + e]) *up[r][v + e] = (T)res[e];
+            }
+          }
         }
-        up[r][v] += plane;
+#pragma unroll
+        for (int v = 0; v < VX; ++v) up[r][v] += plane;
+      } else {
+#pragma unroll
+        for (int v = 0; v < VX; ++v) {
+          if (act[r][v]) {
+            NaiveAcc<S, T, TXW> acc{tl + cofs[r] + cx[v], w[r][v], kv[r][v], T(0), tlm + cofs[r] + cx[v],
+                                    tlp + cofs[r] + cx[v]};
+            if constexpr (Traits<S>::ORDER2) acc.uc = uc[r][v];
+            T res = point_update<S, T>(acc, cst);
+            if constexpr (Traits<S>::RB)  // red-black: only (x + y + z + t) even is updated
+              if ((bx + cx[v] + by + ty + r * TY + z0 + zr + a.t) & 1) res = w[r][v][R];
+            *up[r][v] = res;
+          }
+          up[r][v] += plane;
+        }
       }
     }
     // advance: stage the plane PD ahead, wait for the next window value, one barrier
@@ -238,7 +331,7 @@ __global__ void __launch_bounds__(32 * TY) naive_kernel(const NaiveArgs a) {
       for (int v = 0; v < VX; ++v) {
 #pragma unroll
         for (int i = 0; i < 2 * R; ++i) w[r][v][i] = w[r][v][i + 1];
-        w[r][v][2 * R] = nw[cofs[r] + v * 32];
+        w[r][v][2 * R] = nw[cofs[r] + cx[v]];
       }
     }
   }
@@ -258,14 +351,14 @@ template <int S, typename T>
 constexpr int naive_pd() { return Traits<S>::R == 1 ? 4 : (S == 2 ? 2 : 3); }
 
 // Columns per thread (16-byte aligned layouts): 4 for the FP32 7-point constant stencil and 2
-// for the FP32 25-point constant and 27-point box ones, whose sweeps were bound by instruction
+// for the FP32 25-point (constant and factor grid) and 27-point box ones, whose sweeps were bound by instruction
 // issue (the thread's per-plane work -- barrier, staging items, loop and address bookkeeping --
 // is then shared by 2*VX updates: 564 -> 715, 291 -> 336 and 304 -> 320 GLUP/s); else 1 (measured: the FP64
 // sweeps are bound by the FP64 pipe, and the stencils with coefficient grids keep a plane of
 // coefficients per column in registers, so more columns cost occupancy).
 template <int S, typename T, bool V16>
 constexpr int naive_vx() {
-  return (V16 && sizeof(T) == 4) ? ((S == 0 || S == 6) ? 4 : ((S == 2 || S == 5) ? 2 : 1)) : 1;
+  return (V16 && sizeof(T) == 4) ? ((S == 0 || S == 6) ? 4 : ((S == 2 || S == 4 || S == 5) ? 2 : 1)) : 1;
 }
 
 template <int S, typename T, bool V16>

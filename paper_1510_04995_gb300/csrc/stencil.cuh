@@ -63,6 +63,45 @@ struct Ops<double> {
   static __device__ __forceinline__ double fma(double a, double b, double c) { return __fma_rn(a, b, c); }
 };
 
+// Two FP32 values in one 64-bit register pair, operated on by the packed FP32 instructions
+// (add/sub/mul/fma .rn.f32x2, sm_100 and later): each lane is rounded exactly as the scalar
+// instruction would round it, so point_update<S, F2> gives, lane by lane, the bits of
+// point_update<S, float> for two points, in half the FP instructions.
+struct F2 {
+  unsigned long long v;
+};
+__device__ __forceinline__ F2 pack2(float lo, float hi) {
+  F2 r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r.v) : "f"(lo), "f"(hi));
+  return r;
+}
+__device__ __forceinline__ void unpack2(F2 a, float& lo, float& hi) {
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(a.v));
+}
+template <>
+struct Ops<F2> {
+  static __device__ __forceinline__ F2 mul(F2 a, F2 b) {
+    F2 r;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r.v) : "l"(a.v), "l"(b.v));
+    return r;
+  }
+  static __device__ __forceinline__ F2 add(F2 a, F2 b) {
+    F2 r;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r.v) : "l"(a.v), "l"(b.v));
+    return r;
+  }
+  static __device__ __forceinline__ F2 sub(F2 a, F2 b) {
+    F2 r;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r.v) : "l"(a.v), "l"(b.v));
+    return r;
+  }
+  static __device__ __forceinline__ F2 fma(F2 a, F2 b, F2 c) {
+    F2 r;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r.v) : "l"(a.v), "l"(b.v), "l"(c.v));
+    return r;
+  }
+};
+
 // An accessor A provides, for the point being updated:
 //   A.c()       centre value of level t                 A.x(d), A.y(d), A.z(d)  neighbours at offset d
 //   A.u()       centre value of level t-1 (ORDER2 only) A.k(g)                  coefficient grid g
