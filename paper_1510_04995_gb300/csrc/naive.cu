@@ -79,6 +79,18 @@ struct NaiveAcc2 {
   }
 };
 
+// The 27-point box stencil's packed 2x2 block (FP32, two columns per thread): q[row][plane][dx]
+// holds, for rows y0-1 .. y0+2 and planes z-1 .. z+1 of the thread's rows y0, y0+1 and columns
+// c, c+1, the pairs of columns (c-1, c), (c, c+1), (c+1, c+2); row ROW of the block reads its
+// 26 neighbours and centre from them.
+template <int ROW>
+struct BoxAcc2 {
+  const F2 (*q)[3][3];
+  __device__ __forceinline__ F2 c() const { return q[ROW + 1][1][1]; }
+  __device__ __forceinline__ F2 z(int d) const { return q[ROW + 1][1 + d][1]; }
+  __device__ __forceinline__ F2 b(int dx, int dy, int dz) const { return q[ROW + 1 + dy][1 + dz][1 + dx]; }
+};
+
 // Block = 32 x TY threads over a 32 x 2TY tile of (x, y) columns and a chunk of z planes; each
 // thread owns rows ty and ty + TY.  The tile's planes (with the R-wide halo) stream through a
 // ring of NP = R + PD + 2 (+1 for the box stencil) shared-memory slots filled PD planes ahead of
@@ -123,14 +135,20 @@ __global__ void __launch_bounds__(32 * TY, (naive_min_blocks<S, T, VX>())) naive
   for (int i = 0; i < 5; ++i) cst[i] = sizeof(T) == 8 ? static_cast<T>(a.c[i]) : static_cast<T>(a.cf[i]);
   // FP32 with an even number of columns per thread: two columns per packed update (measured at
   // full size: 7-point constant 714 -> 739, red-black 707 -> 738, 25-point factor grid with two
-  // columns per thread 284 -> 305 GLUP/s; not the box stencil, 320 -> 314, whose 26 neighbours
-  // packed from single loads cost more moves than the packing saves, nor the 25-point constant
-  // one, 328 -> 325).  Radius 4: the thread's columns are adjacent pairs, 64 apart (2 tx,
+  // columns per thread 284 -> 305 GLUP/s; not the 25-point constant stencil, 328 -> 325; the
+  // box stencil packs differently, below).  Radius 4: the thread's columns are adjacent pairs, 64 apart (2 tx,
   // 2 tx + 1, 64 + 2 tx, ...), so that a warp's 8-byte loads of a row stay on consecutive words;
   // otherwise 32 apart.
   constexpr bool PACK = sizeof(T) == 4 && VX % 2 == 0 && !Traits<S>::BOX && S != 2;
   constexpr bool PAIRS = PACK && R == 4;
   constexpr int D2 = PAIRS ? 1 : 32;
+  // The box stencil (FP32, two columns per thread) instead gives each thread a 2x2 block of
+  // points, rows 2 ty, 2 ty + 1 and columns 2 tx, 2 tx + 1: the block's 4x4x3 neighbourhood is 24
+  // aligned 8-byte shared loads (6 per update instead of 24 single loads), and its pairs of
+  // columns feed packed updates with one repacked pair per row and plane (320 -> 536 GLUP/s at
+  // 512^3).  The same 2x2 block for the 25-point stencils, whose two rows share their y
+  // neighbours, was slower (328 -> 304, factor grid 306 -> 279: 118-126 registers, 2 blocks per SM).
+  constexpr bool BOX2 = Traits<S>::BOX && sizeof(T) == 4 && VX == 2;
   F2 cst2[5];
 #pragma unroll
   for (int i = 0; i < 5; ++i) cst2[i] = pack2(a.cf[i], a.cf[i]);
@@ -183,14 +201,15 @@ __global__ void __launch_bounds__(32 * TY, (naive_min_blocks<S, T, VX>())) naive
   for (int q = R - ZB; q <= 2 * R + PD; ++q) stage(q);
 
   bool act[2][VX];
+  auto row_of = [&](int r) { return BOX2 ? 2 * ty + r : ty + r * TY; };  // the thread's rows
   int cx[VX];  // the thread's columns within the tile
 #pragma unroll
-  for (int v = 0; v < VX; ++v) cx[v] = PAIRS ? 64 * (v >> 1) + 2 * tx + (v & 1) : 32 * v + tx;
+  for (int v = 0; v < VX; ++v) cx[v] = PAIRS ? 64 * (v >> 1) + 2 * tx + (v & 1) : (BOX2 ? 2 * tx + v : 32 * v + tx);
   int cofs[2];  // shared offset of column 0 in each of the thread's rows
   T w[2][VX][2 * R + 1];
 #pragma unroll
   for (int r = 0; r < 2; ++r) {
-    const int row = ty + r * TY;
+    const int row = row_of(r);
     cofs[r] = (row + R) * TXW + R;
 #pragma unroll
     for (int v = 0; v < VX; ++v) {
@@ -220,7 +239,7 @@ __global__ void __launch_bounds__(32 * TY, (naive_min_blocks<S, T, VX>())) naive
   for (int r = 0; r < 2; ++r)
 #pragma unroll
     for (int v = 0; v < VX; ++v) {
-      const int64_t o = (int64_t)(ty + r * TY) * ldx + cx[v];
+      const int64_t o = (int64_t)row_of(r) * ldx + cx[v];
       up[r][v] = Ub + o;
       kp[r][v] = coef ? coef + (int64_t)(z0 + R) * plane + (int64_t)(by + R) * ldx + (bx + R) + o : nullptr;
     }
@@ -275,6 +294,34 @@ __global__ void __launch_bounds__(32 * TY, (naive_min_blocks<S, T, VX>())) naive
     const T* tl = ring + ((zr + R) % NP) * TP;  // padded plane z0 + zr + R = interior plane z0 + zr
     const T* tlm = ring + ((zr + R - ZB) % NP) * TP;  // box: the planes below and above
     const T* tlp = ring + ((zr + R + ZB) % NP) * TP;
+    if constexpr (BOX2) {
+      F2 q[4][3][3];
+      const float* pl[3] = {reinterpret_cast<const float*>(tlm), reinterpret_cast<const float*>(tl),
+                            reinterpret_cast<const float*>(tlp)};
+#pragma unroll
+      for (int rr = 0; rr < 4; ++rr)
+#pragma unroll
+        for (int dz = 0; dz < 3; ++dz) {
+          // shared row 2 ty + rr is tile row 2 ty + rr - 1; shared column 2 tx is column 2 tx - 1
+          const float* p = pl[dz] + (2 * ty + rr) * TXW + 2 * tx;
+          q[rr][dz][0] = F2{*reinterpret_cast<const unsigned long long*>(p)};
+          q[rr][dz][2] = F2{*reinterpret_cast<const unsigned long long*>(p + 2)};
+          float a0, a1, b0, b1;
+          unpack2(q[rr][dz][0], a0, a1);
+          unpack2(q[rr][dz][2], b0, b1);
+          q[rr][dz][1] = pack2(a1, b0);
+        }
+      float res[2][2];
+      unpack2(point_update<S, F2>(BoxAcc2<0>{q}, cst2), res[0][0], res[0][1]);
+      unpack2(point_update<S, F2>(BoxAcc2<1>{q}, cst2), res[1][0], res[1][1]);
+#pragma unroll
+      for (int r = 0; r < 2; ++r)
+#pragma unroll
+        for (int v = 0; v < 2; ++v) {
+          if (act[r][v]) *up[r][v] = (T)res[r][v];
+          up[r][v] += plane;
+        }
+    } else {
 #pragma unroll
     for (int r = 0; r < 2; ++r) {
       if constexpr (PACK) {
@@ -319,6 +366,7 @@ __global__ void __launch_bounds__(32 * TY, (naive_min_blocks<S, T, VX>())) naive
           up[r][v] += plane;
         }
       }
+    }
     }
     // advance: stage the plane PD ahead, wait for the next window value, one barrier
     stage(zr + 2 * R + PD + 1);
