@@ -63,8 +63,8 @@ INSTR_PER_LUP = {0: 7, 1: 7, 2: 28, 3: 28, 4: 28, 5: 27, 6: 7}
 # comes from; the roofline's "traffic" scales it to one launch of the benchmark grid.  Keys:
 # (kernel, stencil, dtype) with kernel ("naive",) or ("mwd", variant, dw, cluster, threads)
 MEASURED_BYTES_PER_LUP = {
-    (("naive",), 0, "f64"): (15.69, "profiles/naive_7pt_const_f64_512x384x256.md"),
-    (("naive",), 0, "f32"): (7.27, "profiles/naive_7pt_const_f32_512x384x256.md"),
+    (("naive",), 0, "f64"): (15.67, "profiles/naive_7pt_const_f64_512x384x256.md"),
+    (("naive",), 0, "f32"): (7.33, "profiles/naive_7pt_const_f32_512x384x256.md"),
     (("naive",), 1, "f64"): (72.81, "profiles/naive_7pt_var_f64_480x384x192.md"),
     (("naive",), 1, "f32"): (36.45, "profiles/naive_7pt_var_f32_480x384x256.md"),
     (("naive",), 2, "f64"): (24.05, "profiles/naive_25pt_const_f64_384x384x192.md"),
@@ -72,14 +72,14 @@ MEASURED_BYTES_PER_LUP = {
     (("naive",), 3, "f64"): (132.06, "profiles/naive_25pt_var_f64_384x384x128.md"),
     (("naive",), 3, "f32"): (65.91, "profiles/naive_25pt_var_f32_384x384x192.md"),
     (("naive",), 4, "f64"): (32.35, "profiles/naive_25pt_cgrid_f64_384x384x192.md"),
-    (("naive",), 4, "f32"): (16.12, "profiles/naive_25pt_cgrid_f32_384x384x256.md"),
+    (("naive",), 4, "f32"): (16.11, "profiles/naive_25pt_cgrid_f32_384x384x256.md"),
     (("naive",), 5, "f64"): (15.33, "profiles/naive_27pt_box_f64_512x384x256.md"),
-    (("naive",), 5, "f32"): (7.26, "profiles/naive_27pt_box_f32_512x384x256.md"),
+    (("naive",), 5, "f32"): (7.38, "profiles/naive_27pt_box_f32_512x384x256.md"),
     (("naive",), 6, "f64"): (15.7, "profiles/naive_7pt_rbgs_f64_512x384x256.md"),
-    (("naive",), 6, "f32"): (7.29, "profiles/naive_7pt_rbgs_f32_512x384x256.md"),
+    (("naive",), 6, "f32"): (7.33, "profiles/naive_7pt_rbgs_f32_512x384x256.md"),
     (("mwd", 7, 6, 8, 224), 1, "f32"): (15.5, "profiles/mwd_ovl_7pt_var_f32_480x384x192.md"),
-    (("mwd", 7, 8, 4, 640), 0, "f32"): (4.02, "profiles/mwd_ovl_7pt_const_f32_512x384x256.md"),
-    (("mwd", 7, 4, 4, 352), 0, "f64"): (14.58, "profiles/mwd_ovl_7pt_const_f64_512x384x256.md"),
+    (("mwd", 7, 8, 4, 640), 0, "f32"): (4.01, "profiles/mwd_ovl_7pt_const_f32_512x384x256.md"),
+    (("mwd", 7, 4, 4, 352), 0, "f64"): (14.57, "profiles/mwd_ovl_7pt_const_f64_512x384x256.md"),
 }
 # domain-sized streams N_D of the code-balance model and the spatial minimum bytes per LUP (in elements)
 ND = {0: 2, 1: 9, 2: 2, 3: 15, 4: 3, 5: 2, 6: 2}
