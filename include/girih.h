@@ -108,7 +108,9 @@ typedef enum { GIRIH_ALGO_NAIVE = 0, GIRIH_ALGO_MWD = 1 } girih_algo;
  *              memory at cluster scope; a bounded wait).  One staging and one waiting warp
  *              (blocks of more than 64 threads).  Built for the 7-point, red-black and
  *              25-point stencils (not the box stencil; EINVAL); layout, alignment and nf = 1
- *              rules as RELAXED_PERSISTENT.                                               */
+ *              rules as RELAXED_PERSISTENT.  With girih_config.zseg > 0 each diamond is split
+ *              along z into segments scheduled as separate items (bounded waits on the
+ *              segments' completion flags, as on the diamonds').                           */
 typedef enum {
   GIRIH_FED = 0,
   GIRIH_RELAXED = 1,
