@@ -130,16 +130,21 @@ def test_blocked_repeatable_under_load(variant):
     ("7pt_const_f64_512", dict(dw=4, nf=1, cluster=8, threads=192, variant=7)),
     ("7pt_var_f32_480", dict(dw=6, nf=1, cluster=8, threads=192, variant=7)),
     ("7pt_rbgs_f32_512", dict(dw=12, nf=1, cluster=16, threads=480, variant=7)),
+    # tiles split along z into segments
+    ("7pt_var_f32_480", dict(dw=6, nf=1, cluster=8, threads=224, variant=7, zseg=64)),
+    ("7pt_const_f64_512", dict(dw=4, nf=1, cluster=4, threads=352, variant=7, zseg=32)),
+    ("7pt_rbgs_f32_512", dict(dw=8, nf=1, cluster=4, threads=640, variant=7, zseg=128)),
+    ("25pt_const_f32_384", dict(dw=16, nf=1, cluster=16, threads=352, variant=7, zseg=48)),
 ])
 def test_persistent_tma_kernels_full_size(workload, cfgkw):
-    """The warp-specialised persistent kernels (RELAXED_PERSISTENT = 6, OVERLAP_PERSISTENT = 7) on
-    the benchmark grids (full T), in cluster and diamond shapes that hold one or two blocks per
-    SM: bit for bit the naive sweep."""
+    """The warp-specialised persistent kernels (RELAXED_PERSISTENT = 6, OVERLAP_PERSISTENT = 7,
+    also with its tiles split along z) on the benchmark grids (full T), in cluster and diamond
+    shapes that hold one or two blocks per SM: bit for bit the naive sweep."""
     import torch
     import bench
     stencil, dtype, nx, ny, nz, T = bench.WORKLOADS[workload]
     a16 = 16 // (8 if dtype == "f64" else 4)
-    ldx = -(-(nx + 2) // a16) * a16
+    ldx = -(-(nx + 2 * inputs.RADIUS[stencil]) // a16) * a16
     p = girih.plan(stencil, nx, ny, nz, dtype=dtype, T=T, ldx=ldx)
     cfg = girih.config(girih.MWD, **cfgkw)
     assert p.feasible(cfg), cfg
