@@ -78,7 +78,10 @@ static int mwd_path(const Plan* p, const girih_config* c, bool ptrs16) {
   const int64_t plane = (p->ny + 2 * p->R) * p->ldx;
   const bool vec = p->bulk_layout && ptrs16 && plane < (1LL << 30);
   if (c->variant == GIRIH_RELAXED_PERSISTENT) return vec ? MV_ASYNC : MV_ELEM;
-  if (c->variant == GIRIH_OVERLAP_PERSISTENT) return vec ? (c->zseg > 0 ? MV_OVLZ : MV_OVL) : MV_ELEM;
+  // segments of nz planes or more leave one segment per tile: the whole-tile kernel (the
+  // segmented one reads the items' segment list, which is uploaded only for two or more)
+  if (c->variant == GIRIH_OVERLAP_PERSISTENT)
+    return vec ? ((c->zseg > 0 && c->zseg < p->nz) ? MV_OVLZ : MV_OVL) : MV_ELEM;
   return vec ? MV_VEC : MV_ELEM;
 }
 

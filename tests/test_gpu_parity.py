@@ -559,6 +559,21 @@ def test_overlap_persistent_zsegments_radius4(stencil, dtype):
                 assert np.array_equal(pu, nu) and np.array_equal(pup, nup), (dw, cl, T, zs, cfg)
 
 
+def test_zsegments_of_nz_planes_or_more_are_whole_tiles():
+    """zseg >= nz leaves one segment per tile: the sweep runs whole tiles, bit for bit naive."""
+    nx, ny, nz = SIZES[1]
+    ldx = _aligned_ldx(nx, 1, "f32")
+    u, up, co, c = inputs.make_problem(1, nx, ny, nz, seed=71, ldx=ldx)
+    T = 9
+    nu, nup = gpu_sweep(1, "f32", u, up, co, c, T, nx, ny, nz, girih.config(girih.NAIVE), ldx=ldx)
+    for zs in (nz, 10 * nz):
+        cfg = feasible_cfg(1, "f32", nx, ny, nz,
+                           dict(dw=8, nf=1, cluster=4, threads=160, variant=girih.OVERLAP_PERSISTENT, zseg=zs), ldx=ldx)
+        assert cfg.zseg == zs
+        pu, pup = gpu_sweep(1, "f32", u, up, co, c, T, nx, ny, nz, cfg, ldx=ldx)
+        assert np.array_equal(pu, nu) and np.array_equal(pup, nup), zs
+
+
 def test_zsegments_rejections_and_tuner_candidates():
     """zseg is OVERLAP_PERSISTENT's alone and not negative; the tuner adds segmented candidates
     (32, 64, 128 planes) exactly where a diamond row has fewer diamonds than the device has
